@@ -1,0 +1,688 @@
+/*
+ * bsk_oracle.c -- plain FP64 CPU oracle for the tensor B-spline heat-equation operator.
+ *
+ * TEST INFRASTRUCTURE. Only the test-suite, the smoke check and the CPU-baseline leg of the
+ * benchmark may load this library. The CUDA product path never links, imports or calls it, and
+ * it shares no code, header, table or helper with that path.
+ *
+ * Everything is double precision, round-to-nearest, with no blocking or fusion beyond what the
+ * paper's definitions state. Passages followed (paper arXiv:1904.03057):
+ *   - B-spline definition and identities: Table tblBsplines (section 2.3): convolution,
+ *     derivative and scalar-product rows.
+ *   - Tensor-product basis: section 2.3, the multivariate B-spline definition.
+ *   - Galerkin system: Eq. RitzGalerkin (section 2.3) and Eq. tensForm (section 2.4) with
+ *     constant coefficients, D = dt and mu_a = 1 (one implicit Euler step of the heat equation).
+ *   - Separable shift-invariant kernels and the filtering algorithm: section 2.4 and
+ *     Fig. FiltAlg (four chains of three 1-D convolutions summed into p).
+ *   - Conjugate gradient: section 2.5 (Fig. figGenTenSolv, stage 3).
+ *   - Indirect B-spline transform (evaluation): section 2.3, Fig. figBspnSignProc.
+ *   - L2 norm: Appendix I.
+ *
+ * Readings where the paper is silent (zero Dirichlet faces by odd reflection, node masks for
+ * curved domains, h = 1/(N+1)) are the ones listed in the design notes of the repository.
+ */
+#include <math.h>
+#include <stdint.h>
+#include <stdlib.h>
+#include <string.h>
+
+typedef struct {
+    int nx, ny, nz;        /* unknowns per axis; array layout [nz][ny][nx], x fastest     */
+    int n;                 /* B-spline degree                                            */
+    double hx, hy, hz;     /* grid steps                                                 */
+    double dt;             /* weight of the stiffness term (implicit Euler time step)    */
+    const uint8_t* mask;   /* [nz][ny][nx] node mask, 1 = active; NULL = whole box       */
+} orc_problem;
+
+/* ------------------------------------------------------------------------------------------ */
+/* 1-D B-splines                                                                               */
+/* ------------------------------------------------------------------------------------------ */
+
+/* Centred B-spline beta^n(x). beta^0 is the unit box on [-1/2, 1/2); beta^n is the (n+1)-fold
+ * self-convolution of beta^0 (Table tblBsplines, convolution row). The two-term recurrence
+ * used here follows from that convolution definition (de Boor's recurrence for uniform knots,
+ * re-centred). */
+double orc_bspline(int n, double x)
+{
+    if (n == 0) return (x >= -0.5 && x < 0.5) ? 1.0 : 0.0;
+    double half = 0.5 * (double)(n + 1);
+    if (x <= -half || x >= half) return 0.0;
+    return ((half + x) * orc_bspline(n - 1, x + 0.5) + (half - x) * orc_bspline(n - 1, x - 0.5)) /
+           (double)n;
+}
+
+/* Derivative: beta^n'(x) = beta^{n-1}(x + 1/2) - beta^{n-1}(x - 1/2) (Table tblBsplines). */
+double orc_bspline_deriv(int n, double x)
+{
+    if (n < 1) return 0.0;
+    return orc_bspline(n - 1, x + 0.5) - orc_bspline(n - 1, x - 0.5);
+}
+
+/* Gauss-Legendre nodes and weights on [-1, 1] (Newton iteration on the Legendre polynomial). */
+static void gauss_legendre(int m, double* t, double* w)
+{
+    for (int i = 0; i < m; i++) {
+        double x = cos(M_PI * (i + 0.75) / (m + 0.5));
+        double dp = 1.0;
+        for (int it = 0; it < 100; it++) {
+            double p0 = 1.0, p1 = x;
+            for (int k = 2; k <= m; k++) {
+                double p2 = ((2.0 * k - 1.0) * x * p1 - (k - 1.0) * p0) / k;
+                p0 = p1;
+                p1 = p2;
+            }
+            if (m == 1) { p1 = x; p0 = 1.0; }
+            dp = m * (x * p1 - p0) / (x * x - 1.0);
+            double dx = p1 / dp;
+            x -= dx;
+            if (fabs(dx) < 1e-16) break;
+        }
+        {
+            double p0 = 1.0, p1 = x;
+            for (int k = 2; k <= m; k++) {
+                double p2 = ((2.0 * k - 1.0) * x * p1 - (k - 1.0) * p0) / k;
+                p0 = p1;
+                p1 = p2;
+            }
+            if (m == 1) { p1 = x; p0 = 1.0; }
+            dp = m * (x * p1 - p0) / (x * x - 1.0);
+        }
+        t[i] = x;
+        w[i] = 2.0 / ((1.0 - x * x) * dp * dp);
+    }
+}
+
+int orc_gauss_legendre(int m, double* t, double* w)
+{
+    if (m < 1 || m > 64) return -1;
+    gauss_legendre(m, t, w);
+    return 0;
+}
+
+/* 1-D Galerkin kernels on a unit grid, by quadrature of the defining integrals:
+ *   mass      m_j = integral beta^n(x) beta^n(x - j) dx
+ *   stiffness k_j = integral beta^n'(x) beta^n'(x - j) dx,     j = -n..n,
+ * stored at index j + n. Both integrands are piecewise polynomials of degree <= 2n whose
+ * breakpoints are the knots of beta^n, so n+1 Gauss points per unit knot interval integrate
+ * them exactly. (The paper states the closed forms through the scalar-product identity of
+ * Table tblBsplines; this routine computes the integrals themselves.) */
+int orc_kernels_1d(int n, double* m, double* k)
+{
+    if (n < 1 || n > 7) return -1;
+    double t[16], w[16];
+    int q = n + 1;
+    gauss_legendre(q, t, w);
+    double half = 0.5 * (double)(n + 1);
+    for (int j = 0; j <= n; j++) {
+        double sm = 0.0, sk = 0.0;
+        for (int iv = 0; iv <= n; iv++) {
+            double a = -half + iv, b = a + 1.0;
+            for (int g = 0; g < q; g++) {
+                double x = 0.5 * (a + b) + 0.5 * (b - a) * t[g];
+                double wt = 0.5 * (b - a) * w[g];
+                sm += wt * orc_bspline(n, x) * orc_bspline(n, x - j);
+                sk += wt * orc_bspline_deriv(n, x) * orc_bspline_deriv(n, x - j);
+            }
+        }
+        m[n + j] = m[n - j] = sm;
+        k[n + j] = k[n - j] = sk;
+    }
+    return 0;
+}
+
+/* Per-axis kernels for grid step h: M = h * m, K = k / h (Galerkin integrals of the
+ * scaled basis beta^n(x/h - i)). */
+int orc_bspline_kernels(int n, double h, double* M, double* K)
+{
+    if (!(h > 0.0)) return -1;
+    if (orc_kernels_1d(n, M, K) != 0) return -1;
+    for (int j = 0; j < 2 * n + 1; j++) {
+        M[j] *= h;
+        K[j] /= h;
+    }
+    return 0;
+}
+
+/* ------------------------------------------------------------------------------------------ */
+/* Ghost extension: zero Dirichlet faces by odd reflection, node mask                          */
+/* ------------------------------------------------------------------------------------------ */
+
+/* Reflected index of array position a (0-based) on an axis of N unknowns. The box faces sit at
+ * positions -1 and N, where the coefficient is zero; beyond them the coefficient is minus its
+ * mirror image. Returns 0 for a zero ghost, else +1/-1 and the source index in *src. */
+static int reflect(int a, int N, int* src)
+{
+    if (a >= 0 && a < N) { *src = a; return 1; }
+    int r = (a < 0) ? (-2 - a) : (2 * N - a);
+    if (r < 0 || r >= N) return 0; /* the face itself (or beyond one reflection: never used) */
+    *src = r;
+    return -1;
+}
+
+/* Deliberate-mistake switch for the test-suite's planted-error checks: 0 = correct odd
+ * reflection (default), 1 = zero ghosts, 2 = even reflection. Tests set it, check that a pin
+ * fails, and reset it. */
+static int g_plant = 0;
+void orc_set_plant(int mode) { g_plant = mode; }
+
+/* E = masked, odd-reflected copy of x on [-n, N+n) per axis; E dims (nz+2n)(ny+2n)(nx+2n).
+ * With absmode set, E holds |x| at interior points and at ghosts (used for error scales). */
+static double* extend_mode(const orc_problem* p, const double* x, int absmode)
+{
+    int n = p->n;
+    int ex = p->nx + 2 * n, ey = p->ny + 2 * n, ez = p->nz + 2 * n;
+    double* E = (double*)malloc(sizeof(double) * (size_t)ex * ey * ez);
+    if (!E) return NULL;
+#pragma omp parallel for schedule(static)
+    for (int kz = 0; kz < ez; kz++) {
+        for (int ky = 0; ky < ey; ky++) {
+            for (int kx = 0; kx < ex; kx++) {
+                int sz, sy, sx;
+                int s = reflect(kz - n, p->nz, &sz);
+                s *= (s ? reflect(ky - n, p->ny, &sy) : 0);
+                s *= (s ? reflect(kx - n, p->nx, &sx) : 0);
+                double v = 0.0;
+                if (s) {
+                    size_t src = ((size_t)sz * p->ny + sy) * p->nx + sx;
+                    if (g_plant == 1 && s < 0) s = 0;
+                    if (g_plant == 2 && s < 0) s = 1;
+                    v = (p->mask && !p->mask[src]) ? 0.0 : s * x[src];
+                    if (absmode) v = fabs(v);
+                }
+                E[((size_t)kz * ey + ky) * ex + kx] = v;
+            }
+        }
+    }
+    return E;
+}
+
+static double* extend(const orc_problem* p, const double* x) { return extend_mode(p, x, 0); }
+
+static int problem_ok(const orc_problem* p)
+{
+    if (!p || p->n < 1 || p->n > 7) return 0;
+    if (p->nx < p->n || p->ny < p->n || p->nz < p->n) return 0;
+    if (!(p->hx > 0 && p->hy > 0 && p->hz > 0)) return 0;
+    return 1;
+}
+
+/* Kernel block layout used by the operator routines: kern = [Mx | Kx | My | Ky | Mz | Kz],
+ * each of length 2n+1. Passing the kernels explicitly lets a test feed deliberately wrong
+ * kernels and check that the independent pins catch them. */
+int orc_problem_kernels(const orc_problem* p, double* kern)
+{
+    if (!problem_ok(p)) return -1;
+    int L = 2 * p->n + 1;
+    if (orc_bspline_kernels(p->n, p->hx, kern + 0 * L, kern + 1 * L)) return -1;
+    if (orc_bspline_kernels(p->n, p->hy, kern + 2 * L, kern + 3 * L)) return -1;
+    if (orc_bspline_kernels(p->n, p->hz, kern + 4 * L, kern + 5 * L)) return -1;
+    return 0;
+}
+
+/* ------------------------------------------------------------------------------------------ */
+/* Operator, definition form: direct (2n+1)^3 stencil                                         */
+/* ------------------------------------------------------------------------------------------ */
+
+/* y = mask o [ (Mz x My x Mx) + dt (Kz x My x Mx + Mz x Ky x Mx + Mz x My x Kx) ] (mask o x),
+ * with odd-reflected ghosts: the constant-coefficient case of Eq. tensForm, written as one
+ * shift-invariant 3-D stencil whose weights are the tensor products of the 1-D kernels
+ * (section 2.4, separability of the kernels). Summation runs over the full 3-D stencil. */
+int orc_op_stencil(const orc_problem* p, const double* kern, const double* x, double* y)
+{
+    if (!problem_ok(p)) return -1;
+    int n = p->n, L = 2 * n + 1;
+    const double *Mx = kern, *Kx = kern + L, *My = kern + 2 * L, *Ky = kern + 3 * L;
+    const double *Mz = kern + 4 * L, *Kz = kern + 5 * L;
+    double* W = (double*)malloc(sizeof(double) * L * L * L);
+    if (!W) return -3;
+    for (int c = 0; c < L; c++)
+        for (int b = 0; b < L; b++)
+            for (int a = 0; a < L; a++)
+                W[(c * L + b) * L + a] = Mz[c] * My[b] * Mx[a] +
+                                         p->dt * (Kz[c] * My[b] * Mx[a] + Mz[c] * Ky[b] * Mx[a] +
+                                                  Mz[c] * My[b] * Kx[a]);
+    double* E = extend(p, x);
+    if (!E) { free(W); return -3; }
+    int ex = p->nx + 2 * n, ey = p->ny + 2 * n;
+#pragma omp parallel for schedule(static)
+    for (int iz = 0; iz < p->nz; iz++) {
+        for (int iy = 0; iy < p->ny; iy++) {
+            for (int ix = 0; ix < p->nx; ix++) {
+                size_t o = ((size_t)iz * p->ny + iy) * p->nx + ix;
+                if (p->mask && !p->mask[o]) { y[o] = 0.0; continue; }
+                double s = 0.0;
+                for (int c = 0; c < L; c++)
+                    for (int b = 0; b < L; b++)
+                        for (int a = 0; a < L; a++)
+                            s += W[(c * L + b) * L + a] *
+                                 E[((size_t)(iz + c) * ey + (iy + b)) * ex + (ix + a)];
+                y[o] = s;
+            }
+        }
+    }
+    free(E);
+    free(W);
+    return 0;
+}
+
+/* ------------------------------------------------------------------------------------------ */
+/* Operator, the paper's filtering algorithm: separable 1-D convolution chains                 */
+/* ------------------------------------------------------------------------------------------ */
+
+/* "Valid" correlation of in (dims d[0]=x, d[1]=y, d[2]=z) with a symmetric (2n+1)-tap kernel
+ * along one axis; the output is 2n shorter along that axis. */
+static void conv_axis(const double* in, const int* d, int axis, const double* t, int n, double* out)
+{
+    int o[3] = {d[0], d[1], d[2]};
+    o[axis] -= 2 * n;
+    size_t stride = axis == 0 ? 1 : axis == 1 ? (size_t)d[0] : (size_t)d[0] * d[1];
+#pragma omp parallel for schedule(static)
+    for (int kz = 0; kz < o[2]; kz++)
+        for (int ky = 0; ky < o[1]; ky++)
+            for (int kx = 0; kx < o[0]; kx++) {
+                size_t base = ((size_t)kz * d[1] + ky) * d[0] + kx;
+                double s = 0.0;
+                for (int j = 0; j < 2 * n + 1; j++) s += t[j] * in[base + j * stride];
+                out[((size_t)kz * o[1] + ky) * o[0] + kx] = s;
+            }
+}
+
+/* p = dt (d * w_x f_y f_z) + dt (d * f_x w_y f_z) + dt (d * f_x f_y w_z) + (m * f_x f_y f_z)
+ * with d == 1, m == 1 (constant coefficients), w = stiffness and f = mass kernels: the four
+ * chains of Fig. FiltAlg, each a sequence of three 1-D convolutions along axes 1, 2, 3
+ * (x, y, z here), applied to the ghost-extended coefficients and summed. With mass_only set,
+ * only the last chain runs (the mass operator used for right-hand sides). */
+static int op_separable(const orc_problem* p, const double* kern, const double* x, double* y,
+                        int mass_only, int absmode)
+{
+    if (!problem_ok(p)) return -1;
+    int n = p->n, L = 2 * n + 1;
+    const double* Mk[3] = {kern, kern + 2 * L, kern + 4 * L};
+    const double* Kk[3] = {kern + L, kern + 3 * L, kern + 5 * L};
+    double* E = extend_mode(p, x, absmode);
+    if (!E) return -3;
+    int d0[3] = {p->nx + 2 * n, p->ny + 2 * n, p->nz + 2 * n};
+    size_t nout = (size_t)p->nx * p->ny * p->nz;
+    int d1[3] = {p->nx, d0[1], d0[2]};
+    int d2[3] = {p->nx, p->ny, d0[2]};
+    double* t1 = (double*)malloc(sizeof(double) * (size_t)d1[0] * d1[1] * d1[2]);
+    double* t2 = (double*)malloc(sizeof(double) * (size_t)d2[0] * d2[1] * d2[2]);
+    double* t3 = (double*)malloc(sizeof(double) * nout);
+    if (!t1 || !t2 || !t3) { free(E); free(t1); free(t2); free(t3); return -3; }
+    memset(y, 0, sizeof(double) * nout);
+    for (int chain = 0; chain < 4; chain++) {
+        if (mass_only && chain < 3) continue;
+        /* chain c < 3 puts the stiffness kernel on axis c; chain 3 is mass on every axis */
+        const double* tx = chain == 0 ? Kk[0] : Mk[0];
+        const double* ty = chain == 1 ? Kk[1] : Mk[1];
+        const double* tz = chain == 2 ? Kk[2] : Mk[2];
+        double wgt = chain < 3 ? p->dt : 1.0;
+        conv_axis(E, d0, 0, tx, n, t1);
+        conv_axis(t1, d1, 1, ty, n, t2);
+        conv_axis(t2, d2, 2, tz, n, t3);
+#pragma omp parallel for schedule(static)
+        for (long long i = 0; i < (long long)nout; i++) y[i] += wgt * t3[i];
+    }
+    if (p->mask) {
+#pragma omp parallel for schedule(static)
+        for (long long i = 0; i < (long long)nout; i++)
+            if (!p->mask[i]) y[i] = 0.0;
+    }
+    free(E);
+    free(t1);
+    free(t2);
+    free(t3);
+    return 0;
+}
+
+int orc_op_separable(const orc_problem* p, const double* kern, const double* x, double* y)
+{
+    return op_separable(p, kern, x, y, 0, 0);
+}
+
+int orc_mass(const orc_problem* p, const double* kern, const double* x, double* y)
+{
+    return op_separable(p, kern, x, y, 1, 0);
+}
+
+/* (|A| |x|)_i: every kernel tap and every (ghost-extended) coefficient replaced by its absolute
+ * value. This bounds the magnitude of the terms summed into (A x)_i and is the scale against
+ * which operator rounding errors are measured (the stiffness kernel sums to zero, so (A x)_i
+ * itself can be far smaller than its terms). */
+int orc_abs_op(const orc_problem* p, const double* kern, const double* x, double* y)
+{
+    if (!problem_ok(p)) return -1;
+    int L = 2 * p->n + 1;
+    double* ak = (double*)malloc(sizeof(double) * 6 * L);
+    if (!ak) return -3;
+    for (int i = 0; i < 6 * L; i++) ak[i] = fabs(kern[i]);
+    orc_problem q = *p;
+    q.dt = fabs(p->dt);
+    int rc = op_separable(&q, ak, x, y, 0, 1);
+    free(ak);
+    return rc;
+}
+
+/* ------------------------------------------------------------------------------------------ */
+/* Brute-force Galerkin matrix on tiny grids                                                   */
+/* ------------------------------------------------------------------------------------------ */
+
+/* 1-D basis with zero Dirichlet faces at 0 and (N+1)h: the tensor B-spline centred at i h,
+ * minus its mirror images in both faces (odd, 2(N+1)h-periodic extension), i = 1..N. */
+static double psi_1d(int n, int N, double h, int i, double x, int deriv)
+{
+    double s = 0.0, u = x / h;
+    for (int k = -1; k <= 1; k++) {
+        double shift = 2.0 * k * (N + 1);
+        if (deriv) {
+            s += orc_bspline_deriv(n, u - i - shift) - orc_bspline_deriv(n, u + i - shift);
+        } else {
+            s += orc_bspline(n, u - i - shift) - orc_bspline(n, u + i - shift);
+        }
+    }
+    return deriv ? s / h : s;
+}
+
+/* Quadrature rule on [0, (N+1)h]: sub-intervals of length h/2 (they contain every knot of
+ * both even and odd degree), n+1 Gauss points each. Returns the number of points. */
+static int axis_rule(int n, int N, double h, double* xs, double* ws)
+{
+    double t[16], w[16];
+    int q = n + 1, cnt = 0;
+    gauss_legendre(q, t, w);
+    for (int c = 0; c < 2 * (N + 1); c++) {
+        double a = 0.5 * h * c, b = a + 0.5 * h;
+        for (int g = 0; g < q; g++) {
+            xs[cnt] = 0.5 * (a + b) + 0.5 * (b - a) * t[g];
+            ws[cnt] = 0.5 * (b - a) * w[g];
+            cnt++;
+        }
+    }
+    return cnt;
+}
+
+/* A_ij = integral over [0,1]^3 of ( psi_i psi_j + dt grad psi_i . grad psi_j ) for active i, j
+ * (Eq. RitzGalerkin with D = dt, mu_a = 1, no boundary term: the basis vanishes on the faces),
+ * assembled by Gauss quadrature from point values of the basis. The active nodes are
+ * numbered in array order; A is na x na, row-major. With full3d set the integral is summed
+ * over the 3-D tensor quadrature grid point by point; otherwise it is factorised by Fubini
+ * into 1-D Gram matrices (same integral, fewer operations). */
+int orc_bruteforce_matrix(const orc_problem* p, int full3d, double* A, int* na_out)
+{
+    if (!problem_ok(p)) return -1;
+    int n = p->n, N[3] = {p->nx, p->ny, p->nz};
+    double h[3] = {p->hx, p->hy, p->hz};
+    size_t ntot = (size_t)N[0] * N[1] * N[2];
+    int* act = (int*)malloc(sizeof(int) * ntot);
+    int na = 0;
+    for (size_t i = 0; i < ntot; i++) act[i] = (!p->mask || p->mask[i]) ? na++ : -1;
+    *na_out = na;
+    if (!A) { free(act); return 0; }
+    /* 1-D tables: value and derivative of each basis function at each quadrature point */
+    double* xs[3]; double* ws[3]; double* B[3]; double* D[3]; int nq[3];
+    for (int d = 0; d < 3; d++) {
+        int maxq = 2 * (N[d] + 1) * (n + 1);
+        xs[d] = (double*)malloc(sizeof(double) * maxq);
+        ws[d] = (double*)malloc(sizeof(double) * maxq);
+        nq[d] = axis_rule(n, N[d], h[d], xs[d], ws[d]);
+        B[d] = (double*)malloc(sizeof(double) * (size_t)N[d] * nq[d]);
+        D[d] = (double*)malloc(sizeof(double) * (size_t)N[d] * nq[d]);
+        for (int i = 0; i < N[d]; i++)
+            for (int q = 0; q < nq[d]; q++) {
+                B[d][(size_t)i * nq[d] + q] = psi_1d(n, N[d], h[d], i + 1, xs[d][q], 0);
+                D[d][(size_t)i * nq[d] + q] = psi_1d(n, N[d], h[d], i + 1, xs[d][q], 1);
+            }
+    }
+    memset(A, 0, sizeof(double) * (size_t)na * na);
+    double* GM[3]; double* GK[3];
+    for (int d = 0; d < 3; d++) {
+        GM[d] = (double*)calloc((size_t)N[d] * N[d], sizeof(double));
+        GK[d] = (double*)calloc((size_t)N[d] * N[d], sizeof(double));
+        for (int i = 0; i < N[d]; i++)
+            for (int j = 0; j < N[d]; j++) {
+                double sm = 0, sk = 0;
+                for (int q = 0; q < nq[d]; q++) {
+                    sm += ws[d][q] * B[d][(size_t)i * nq[d] + q] * B[d][(size_t)j * nq[d] + q];
+                    sk += ws[d][q] * D[d][(size_t)i * nq[d] + q] * D[d][(size_t)j * nq[d] + q];
+                }
+                GM[d][i * N[d] + j] = sm;
+                GK[d][i * N[d] + j] = sk;
+            }
+    }
+#pragma omp parallel for schedule(dynamic)
+    for (long long I = 0; I < (long long)ntot; I++) {
+        if (act[I] < 0) continue;
+        int ix = (int)(I % N[0]), iy = (int)((I / N[0]) % N[1]), iz = (int)(I / ((size_t)N[0] * N[1]));
+        for (size_t J = 0; J < ntot; J++) {
+            if (act[J] < 0) continue;
+            int jx = (int)(J % N[0]), jy = (int)((J / N[0]) % N[1]), jz = (int)(J / ((size_t)N[0] * N[1]));
+            double v;
+            if (full3d) {
+                v = 0.0;
+                for (int qz = 0; qz < nq[2]; qz++) {
+                    double bz_i = B[2][(size_t)iz * nq[2] + qz], bz_j = B[2][(size_t)jz * nq[2] + qz];
+                    double dz_i = D[2][(size_t)iz * nq[2] + qz], dz_j = D[2][(size_t)jz * nq[2] + qz];
+                    if (bz_i == 0 && bz_j == 0 && dz_i == 0 && dz_j == 0) continue;
+                    for (int qy = 0; qy < nq[1]; qy++) {
+                        double by_i = B[1][(size_t)iy * nq[1] + qy], by_j = B[1][(size_t)jy * nq[1] + qy];
+                        double dy_i = D[1][(size_t)iy * nq[1] + qy], dy_j = D[1][(size_t)jy * nq[1] + qy];
+                        for (int qx = 0; qx < nq[0]; qx++) {
+                            double bx_i = B[0][(size_t)ix * nq[0] + qx], bx_j = B[0][(size_t)jx * nq[0] + qx];
+                            double dx_i = D[0][(size_t)ix * nq[0] + qx], dx_j = D[0][(size_t)jx * nq[0] + qx];
+                            double w = ws[2][qz] * ws[1][qy] * ws[0][qx];
+                            double pi = bz_i * by_i * bx_i, pj = bz_j * by_j * bx_j;
+                            double g = (dz_i * by_i * bx_i) * (dz_j * by_j * bx_j) +
+                                       (bz_i * dy_i * bx_i) * (bz_j * dy_j * bx_j) +
+                                       (bz_i * by_i * dx_i) * (bz_j * by_j * dx_j);
+                            v += w * (pi * pj + p->dt * g);
+                        }
+                    }
+                }
+            } else {
+                double mx = GM[0][ix * N[0] + jx], my = GM[1][iy * N[1] + jy], mz = GM[2][iz * N[2] + jz];
+                double kx = GK[0][ix * N[0] + jx], ky = GK[1][iy * N[1] + jy], kz = GK[2][iz * N[2] + jz];
+                v = mz * my * mx + p->dt * (kz * my * mx + mz * ky * mx + mz * my * kx);
+            }
+            A[(size_t)act[I] * na + act[J]] = v;
+        }
+    }
+    for (int d = 0; d < 3; d++) { free(xs[d]); free(ws[d]); free(B[d]); free(D[d]); free(GM[d]); free(GK[d]); }
+    free(act);
+    return 0;
+}
+
+/* ------------------------------------------------------------------------------------------ */
+/* Vectors and conjugate gradient                                                              */
+/* ------------------------------------------------------------------------------------------ */
+
+/* Deterministic dot product: fixed chunks of 4096 summed in a fixed order, whatever the
+ * number of threads. */
+static double dot(const double* a, const double* b, size_t len)
+{
+    size_t nchunk = (len + 4095) / 4096;
+    double* part = (double*)malloc(sizeof(double) * (nchunk ? nchunk : 1));
+#pragma omp parallel for schedule(static)
+    for (long long c = 0; c < (long long)nchunk; c++) {
+        size_t lo = (size_t)c * 4096, hi = lo + 4096 < len ? lo + 4096 : len;
+        double s = 0.0;
+        for (size_t i = lo; i < hi; i++) s += a[i] * b[i];
+        part[c] = s;
+    }
+    double s = 0.0;
+    for (size_t c = 0; c < nchunk; c++) s += part[c];
+    free(part);
+    return s;
+}
+
+double orc_dot(const double* a, const double* b, long long len) { return dot(a, b, (size_t)len); }
+
+/* Textbook conjugate gradient (Hestenes-Stiefel) for A x = b, A from orc_op_separable
+ * (section 2.5: the iterative solver of F(c) = t). Stops when the recursively updated residual
+ * satisfies ||r|| <= tol ||b||. On return *iters holds the iteration count and *relres the
+ * true relative residual ||b - A x|| / ||b|| recomputed from x. Returns 0 if converged, 1 if
+ * max_iter was reached, -5 on breakdown (p.Ap <= 0 or NaN). */
+int orc_cg(const orc_problem* p, const double* kern, const double* b, double* x, double tol,
+           int max_iter, int* iters, double* relres)
+{
+    if (!problem_ok(p)) return -1;
+    size_t len = (size_t)p->nx * p->ny * p->nz;
+    double* r = (double*)malloc(sizeof(double) * len);
+    double* pv = (double*)malloc(sizeof(double) * len);
+    double* q = (double*)malloc(sizeof(double) * len);
+    if (!r || !pv || !q) { free(r); free(pv); free(q); return -3; }
+    int status = 1, it = 0;
+    double bb = dot(b, b, len);
+    orc_op_separable(p, kern, x, q);
+#pragma omp parallel for schedule(static)
+    for (long long i = 0; i < (long long)len; i++) { r[i] = b[i] - q[i]; pv[i] = r[i]; }
+    double rr = dot(r, r, len);
+    if (bb == 0.0) {
+        memset(x, 0, sizeof(double) * len);
+        status = 0;
+    } else if (sqrt(rr) <= tol * sqrt(bb)) {
+        status = 0;
+    } else {
+        for (it = 1; it <= max_iter; it++) {
+            orc_op_separable(p, kern, pv, q);
+            double pq = dot(pv, q, len);
+            if (!(pq > 0.0)) { status = -5; break; }
+            double alpha = rr / pq;
+#pragma omp parallel for schedule(static)
+            for (long long i = 0; i < (long long)len; i++) {
+                x[i] += alpha * pv[i];
+                r[i] -= alpha * q[i];
+            }
+            double rr_new = dot(r, r, len);
+            if (sqrt(rr_new) <= tol * sqrt(bb)) { status = 0; break; }
+            double beta = rr_new / rr;
+#pragma omp parallel for schedule(static)
+            for (long long i = 0; i < (long long)len; i++) pv[i] = r[i] + beta * pv[i];
+            rr = rr_new;
+        }
+        if (it > max_iter) it = max_iter;
+    }
+    *iters = it;
+    orc_op_separable(p, kern, x, q);
+#pragma omp parallel for schedule(static)
+    for (long long i = 0; i < (long long)len; i++) r[i] = b[i] - q[i];
+    *relres = bb > 0 ? sqrt(dot(r, r, len) / bb) : 0.0;
+    free(r);
+    free(pv);
+    free(q);
+    return status;
+}
+
+/* Implicit Euler steps of u_t = Laplace(u) + g: (M + dt K) u^{k+1} = M (u^k + dt q), where q
+ * holds the B-spline coefficients of the source (Eq. RitzGalerkin right-hand side with the
+ * source expanded in the same basis) and M, K are the 3-D mass and stiffness operators. q may be
+ * NULL (no source). Each solve starts from u^k. iters_out (length nsteps, may be NULL) receives
+ * the CG iteration counts. Returns the first non-zero CG status, else 0. */
+int orc_heat(const orc_problem* p, const double* kern, double* u, const double* q, int nsteps,
+             double tol, int max_iter, int* iters_out, double* relres_out)
+{
+    if (!problem_ok(p)) return -1;
+    size_t len = (size_t)p->nx * p->ny * p->nz;
+    double* t = (double*)malloc(sizeof(double) * len);
+    double* b = (double*)malloc(sizeof(double) * len);
+    if (!t || !b) { free(t); free(b); return -3; }
+    int status = 0;
+    for (int s = 0; s < nsteps; s++) {
+#pragma omp parallel for schedule(static)
+        for (long long i = 0; i < (long long)len; i++) t[i] = u[i] + (q ? p->dt * q[i] : 0.0);
+        orc_mass(p, kern, t, b);
+        int it = 0;
+        double rel = 0.0;
+        int st = orc_cg(p, kern, b, u, tol, max_iter, &it, &rel);
+        if (iters_out) iters_out[s] = it;
+        if (relres_out) relres_out[s] = rel;
+        if (st != 0 && status == 0) status = st;
+    }
+    free(t);
+    free(b);
+    return status;
+}
+
+/* ------------------------------------------------------------------------------------------ */
+/* Indirect B-spline transform on tensor grids                                                 */
+/* ------------------------------------------------------------------------------------------ */
+
+/* out[kz][ky][kx] = sum_i c_i psi_i(xs[kx], ys[ky], zs[kz]) (indirect B-spline transform,
+ * section 2.3), evaluated axis by axis. The mask is applied to c first. With transpose set,
+ * computes instead c_i = sum_k wts_k f_k psi_i(x_k) (load vector of a function f given on the
+ * grid with weights wx, wy, wz), the adjoint map used for L2 projections. */
+int orc_eval_tensor(const orc_problem* p, int transpose, const double* in, int qx, const double* xs,
+                    const double* wx, int qy, const double* ys, const double* wy, int qz,
+                    const double* zs, const double* wz, double* out)
+{
+    if (!problem_ok(p)) return -1;
+    int n = p->n, N[3] = {p->nx, p->ny, p->nz}, Q[3] = {qx, qy, qz};
+    double h[3] = {p->hx, p->hy, p->hz};
+    const double* pts[3] = {xs, ys, zs};
+    const double* wts[3] = {wx, wy, wz};
+    double* Bt[3];
+    for (int d = 0; d < 3; d++) {
+        Bt[d] = (double*)malloc(sizeof(double) * (size_t)N[d] * Q[d]);
+        for (int q = 0; q < Q[d]; q++)
+            for (int i = 0; i < N[d]; i++) {
+                double v = psi_1d(n, N[d], h[d], i + 1, pts[d][q], 0);
+                if (transpose && wts[d]) v *= wts[d][q];
+                Bt[d][(size_t)q * N[d] + i] = v; /* [q][i] */
+            }
+    }
+    /* forward: in dims N, out dims Q; transpose: in dims Q, out dims N */
+    int din[3], dout[3];
+    for (int d = 0; d < 3; d++) {
+        din[d] = transpose ? Q[d] : N[d];
+        dout[d] = transpose ? N[d] : Q[d];
+    }
+    size_t lin = (size_t)din[0] * din[1] * din[2];
+    double* cur = (double*)malloc(sizeof(double) * lin);
+    memcpy(cur, in, sizeof(double) * lin);
+    if (!transpose && p->mask)
+        for (size_t i = 0; i < lin; i++)
+            if (!p->mask[i]) cur[i] = 0.0;
+    int cd[3] = {din[0], din[1], din[2]};
+    for (int axis = 0; axis < 3; axis++) {
+        int nd[3] = {cd[0], cd[1], cd[2]};
+        nd[axis] = dout[axis];
+        double* nxt = (double*)malloc(sizeof(double) * (size_t)nd[0] * nd[1] * nd[2]);
+        size_t sc = axis == 0 ? 1 : axis == 1 ? (size_t)cd[0] : (size_t)cd[0] * cd[1];
+        size_t sn = axis == 0 ? 1 : axis == 1 ? (size_t)nd[0] : (size_t)nd[0] * nd[1];
+#pragma omp parallel for schedule(static)
+        for (int kz = 0; kz < nd[2]; kz++)
+            for (int ky = 0; ky < nd[1]; ky++)
+                for (int kx = 0; kx < nd[0]; kx++) {
+                    int k[3] = {kx, ky, kz};
+                    int o = k[axis];
+                    k[axis] = 0;
+                    size_t basec = ((size_t)k[2] * cd[1] + k[1]) * cd[0] + k[0];
+                    double s = 0.0;
+                    for (int j = 0; j < cd[axis]; j++) {
+                        double bv = transpose ? Bt[axis][(size_t)j * N[axis] + o]
+                                              : Bt[axis][(size_t)o * N[axis] + j];
+                        s += bv * cur[basec + j * sc];
+                    }
+                    nxt[((size_t)kz * nd[1] + ky) * nd[0] + kx] = s;
+                    (void)sn;
+                }
+        free(cur);
+        cur = nxt;
+        cd[0] = nd[0]; cd[1] = nd[1]; cd[2] = nd[2];
+    }
+    size_t lout = (size_t)dout[0] * dout[1] * dout[2];
+    if (transpose && p->mask)
+        for (size_t i = 0; i < lout; i++)
+            if (!p->mask[i]) cur[i] = 0.0;
+    memcpy(out, cur, sizeof(double) * lout);
+    free(cur);
+    for (int d = 0; d < 3; d++) free(Bt[d]);
+    return 0;
+}
+
+/* 1-D quadrature rule on [0, 1] for a grid of N unknowns (the rule of the brute-force
+ * assembly): returns the number of points written to xs, ws (capacity 2(N+1)(n+1)). */
+int orc_axis_rule(int n, int N, double h, double* xs, double* ws)
+{
+    if (n < 1 || n > 7 || N < 1 || !(h > 0)) return -1;
+    return axis_rule(n, N, h, xs, ws);
+}
