@@ -1,0 +1,293 @@
+#!/usr/bin/env python
+"""Benchmark: implicit Euler heat steps of the tensor B-spline operator at 928^3.
+
+Workload (the paper's ~0.8 G-node scale, synthetic): 928^3 = 799,178,752 unknowns on the unit
+cube, cubic B-splines, zero Dirichlet faces, dt = 5e-4, initial coefficients = 64 seeded sine
+modes (k in {1..16}^3, amplitudes N(0,1)/|k|^2), one implicit Euler step per benchmark step,
+solved to a 1e-8 true relative residual by CG with FP32 operator sweeps and FP64 iterative
+refinement (FP64 residual, FP64 CG scalars).
+
+value = operator throughput inside the solve: unknowns x operator applications / time, summed
+over ranks, where every application of the full operator counts (inner FP32 CG iterations and
+FP64 true residuals; the mass-only right-hand side is not counted). Each rank solves its own
+problem (weak scaling, no collective on the data path).
+
+--impl reference runs the FP64 CPU oracle (the test-suite's reference implementation) on a
+bounded slab of the same workload, in the same unit.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "operator GDoF/s (% HBM peak) at 928³; time-to-1e-8 residual, FCG-net vs CG"
+N_GRID, DEGREE, DT, TOL, SEED, NMODES, KMAX = 928, 3, 5e-4, 1e-8, 3, 64, 16
+WORKLOAD = "heat3d_928cube_cubic_f32sweeps_f64refinement"
+
+
+def peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            d = json.load(f)
+        return float(d["hbm_gbs"]), "measured"
+    except Exception:
+        return 6800.0, "fallback"
+
+
+class ClockSampler:
+    """nvidia-smi clock / throttle samples (200 ms) during the timed region."""
+
+    FIELDS = ("clocks.sm,clocks.max.sm,clocks_event_reasons.hw_slowdown,"
+              "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+              "clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, dev: int):
+        self.dev, self.lines, self.proc = dev, [], None
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                 "-lms", "200", "-i", str(self.dev)], stdout=subprocess.PIPE,
+                stderr=subprocess.DEVNULL, text=True)
+            threading.Thread(target=self._read, daemon=True).start()
+        except Exception:
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        time.sleep(0.25)
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            parts = [p.strip() for p in ln.split(",")]
+            if len(parts) < 6:
+                continue
+            try:
+                sm.append(float(parts[0]))
+                mx.append(float(parts[1]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, parts[2:6]):
+                if v.lower().startswith("active"):
+                    reasons.add(nm)
+        sm.sort()
+        return {"sm_mhz": sm[len(sm) // 2] if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "samples": len(sm), "reasons": sorted(reasons)}
+
+
+def cpu_oracle_sample(reps: int = 3, planes: int = 16):
+    """FP64 oracle operator (Fig. FiltAlg separable chains, OpenMP) on a 928 x 928 x planes slab
+    of the workload's field; returns (GDoF/s, cores, seconds, description)."""
+    import numpy as np
+    import torch
+
+    import oracle
+    from paper_1904_03057_gb300 import inputs
+    h = 1.0 / (N_GRID + 1)
+    modes = inputs.random_sine_modes(SEED, NMODES, KMAX)
+    full = inputs.sine_mode_field(N_GRID, N_GRID, planes, modes, h=h, dtype=torch.float64)
+    x = full.numpy()
+    p = oracle.Problem(N_GRID, N_GRID, planes, DEGREE, h, dt=DT)
+    oracle.op_separable(p, x)  # warm-up (page faults, thread start)
+    t0 = time.perf_counter()
+    for _ in range(reps):
+        oracle.op_separable(p, x)
+    dt_s = time.perf_counter() - t0
+    dofs = N_GRID * N_GRID * planes * reps
+    cores = int(os.environ.get("OMP_NUM_THREADS", os.cpu_count() or 1))
+    desc = (f"{reps} FP64 oracle operator applications on a 928x928x{planes} slab "
+            f"({N_GRID * N_GRID * planes} unknowns) of the 928^3 workload")
+    return dofs / dt_s / 1e9, cores, dt_s, desc
+
+
+def run_reference(args, rank, world):
+    if rank != 0:
+        return
+    for _ in range(args.warmup):
+        cpu_oracle_sample(reps=1)
+    vals, total = [], 0.0
+    for _ in range(args.steps):
+        v, cores, secs, desc = cpu_oracle_sample(reps=1)
+        vals.append(v)
+        total += secs
+    value = len(vals) / sum(1.0 / v for v in vals)
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": "GDoF/s", "n_gpus": 0,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * total / args.steps,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+        "data": "synthetic", "config": {"workload": WORKLOAD, "sample": desc},
+        "cpu_baseline": {"value": value, "unit": "GDoF/s", "cores": cores, "kind": "oracle",
+                         "sample": desc},
+        "e2e": {"value": value, "unit": "GDoF/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+
+
+def run_ours(args, rank, world, dist):
+    import torch
+
+    from paper_1904_03057_gb300 import api, inputs
+    dev = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(dev)
+    N = N_GRID
+    h = 1.0 / (N + 1)
+    dofs = N ** 3
+    modes = inputs.random_sine_modes(SEED + rank, NMODES, KMAX)
+    u = inputs.sine_mode_field(N, N, N, modes, device="cuda", dtype=torch.float64)
+    stream = torch.cuda.current_stream()
+    H = api.Handle(N, N, N, DEGREE, h, DT, precision="f32_ir", stream=stream)
+    opts = dict(tol=TOL, check_every=16)
+
+    def barrier():
+        torch.cuda.synchronize()
+        if dist is not None:
+            dist.barrier()
+        torch.cuda.synchronize()
+
+    for _ in range(args.warmup):
+        H.heat_step(u, None, 1, **opts)
+    barrier()
+    sampler = ClockSampler(dev)
+    sampler.start()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    reps = []
+    e0.record(stream)
+    for _ in range(args.steps):
+        reps.append(H.heat_step(u, None, 1, **opts))
+    e1.record(stream)
+    barrier()
+    clocks = sampler.stop()
+    elapsed_ms = e0.elapsed_time(e1)
+    if dist is not None:
+        t = torch.tensor([elapsed_ms], device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        elapsed_ms = float(t.item())
+    inner = sum(r["iterations"] for r in reps)
+    outer = sum(r["outer_iterations"] for r in reps)
+    op_apps = inner + outer + len(reps)          # inner CG + FP64 residuals (one per outer + final)
+    launches = sum(r["kernel_launches"] for r in reps)
+    value = world * dofs * op_apps / (elapsed_ms * 1e-3) / 1e9
+    ms_step = elapsed_ms / args.steps
+    worst_res = max(r["rel_residual"] for r in reps)
+
+    # end to end through the public API with host buffers: H2D of u, heat_step, D2H of u
+    e2e = None
+    if not args.no_e2e:
+        uh = torch.empty((N, N, N), dtype=torch.float64, pin_memory=True)
+        uh.copy_(u)
+        barrier()
+        e2e_steps = max(1, min(args.steps, 2))
+        t0 = time.perf_counter()
+        e2e_apps = 0
+        for _ in range(e2e_steps):
+            u.copy_(uh, non_blocking=True)
+            r = H.heat_step(u, None, 1, **opts)
+            uh.copy_(u, non_blocking=True)
+            torch.cuda.current_stream().synchronize()
+            e2e_apps += r["iterations"] + r["outer_iterations"] + 1
+        t_e2e = time.perf_counter() - t0
+        if dist is not None:
+            t = torch.tensor([t_e2e], device="cuda")
+            dist.all_reduce(t, op=dist.ReduceOp.MAX)
+            t_e2e = float(t.item())
+        e2e = {"value": world * dofs * e2e_apps / t_e2e / 1e9, "unit": "GDoF/s",
+               "h2d_bytes_per_step": dofs * 8, "d2h_bytes_per_step": dofs * 8}
+        del uh
+
+    # dominant kernel timing (CUDA events on the handle's stream): the fused CG pass, FP32
+    hbm, peak_kind = peaks()
+    ms_fused = H.time_kernel(api.KERNEL_CG_FUSED, reps=10)
+    bytes_fused = 24.0 * dofs   # read r, p_old, x; write p, q, x (FP32)
+    ms_op = H.time_kernel(api.KERNEL_OP, reps=10)
+    bytes_op = 8.0 * dofs       # read x, write y (FP32)
+    ms_res64 = H.time_kernel(api.KERNEL_RES64, reps=3)
+    ms_upd = H.time_kernel(api.KERNEL_CG_UPDATE, reps=10)
+    ach = bytes_fused / (ms_fused * 1e-3) / 1e9
+
+    line = {
+        "metric": METRIC, "value": value, "unit": "GDoF/s", "n_gpus": world,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_step,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32/f64",
+        "data": "synthetic",
+        "config": {
+            "workload": WORKLOAD, "grid": f"{N}^3", "unknowns": dofs, "degree": DEGREE, "dt": DT,
+            "tol": TOL, "precision": "FP32 operator sweeps, FP64 true residual + CG scalars",
+            "l2": "inputs larger than L2 (3.2 GB FP32 / 6.4 GB FP64 vectors)",
+            "op_applications_per_step": op_apps / len(reps),
+            "cg_iterations_per_step": inner / len(reps),
+            "refinement_steps_per_step": outer / len(reps),
+            "max_true_rel_residual": worst_res,
+            "kernel_ms": {"cg_fused_f32": ms_fused, "cg_update_f32": ms_upd, "op_f32": ms_op,
+                          "residual_f64": ms_res64},
+            "op_apply_gdofs": dofs / (ms_op * 1e-3) / 1e9,
+            "op_apply_hbm_frac": bytes_op / (ms_op * 1e-3) / 1e9 / hbm,
+            "parallelism": f"{world} independent problems (one per GPU)",
+        },
+        "roofline": {"kernel": "cg_fused_f32 (p update + operator + p.Ap + deferred x update)",
+                     "bound": "hbm", "achieved": ach, "peak": hbm, "unit": "GB/s",
+                     "frac": ach / hbm, "traffic": None,
+                     "note": f"peak = {peak_kind} HBM copy bandwidth; algorithmic 24 B/unknown"},
+        "clocks": clocks,
+        "gpu_launches": launches,
+    }
+    if e2e is not None:
+        line["e2e"] = e2e
+    if rank == 0 and not args.no_cpu_baseline:
+        v, cores, secs, desc = cpu_oracle_sample()
+        line["cpu_baseline"] = {"value": v, "unit": "GDoF/s", "cores": cores, "kind": "oracle",
+                                "sample": desc}
+    H.close()
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=4)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    dist = None
+    if args.impl == "reference":
+        run_reference(args, rank, world)
+        return
+    if world > 1:
+        import torch
+        import torch.distributed as tdist
+        torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", "0")))
+        tdist.init_process_group("nccl")
+        dist = tdist
+    try:
+        run_ours(args, rank, world, dist)
+    finally:
+        if dist is not None:
+            dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,167 @@
+/*
+ * bsk.h -- C ABI of the GB300 tensor B-spline heat-equation library.
+ *
+ * The library applies, matrix-free, the Galerkin operator of one implicit Euler step of the heat
+ * equation discretised with degree-n tensor B-splines on a uniform grid,
+ *
+ *     A = Mz (x) My (x) Mx  +  dt ( Kz (x) My (x) Mx + Mz (x) Ky (x) Mx + Mz (x) My (x) Kx ),
+ *
+ * and solves A x = b with conjugate gradients (paper arXiv:1904.03057: Eq. RitzGalerkin and
+ * Eq. tensForm with constant coefficients D = dt, mu_a = 1; the separable shift-invariant
+ * kernels of section 2.4 and the filtering algorithm of Fig. FiltAlg; the CG stage of
+ * section 2.5). Md and Kd are the (2n+1)-tap mass and stiffness kernels of axis d,
+ * Md = hd * beta^{2n+1}(j) and Kd = -(1/hd) * (beta^{2n-1}(j+1) - 2 beta^{2n-1}(j) +
+ * beta^{2n-1}(j-1)), j = -n..n (scalar-product and derivative identities, Table tblBsplines).
+ *
+ * Conventions shared by every entry point:
+ *   - Arrays are dense, x fastest: element (k, j, i) of an nx*ny*nz grid sits at
+ *     ((k * ny) + j) * nx + i. Unknown i of an axis is the B-spline centred at (i + 1) h.
+ *   - Zero Dirichlet data on the box faces: coefficients are odd-reflected about the faces,
+ *     which sit one grid step beyond the first and the last unknown (positions 0 and
+ *     (N + 1) h), where the coefficient is zero. This needs N >= n unknowns per axis.
+ *   - An optional node mask selects the active unknowns (1 = active). Inactive unknowns are
+ *     removed from the system: they read as zero and are written as zero.
+ *   - Every vector argument is a DEVICE pointer owned by the caller, with the element type of
+ *     the handle's precision (see bsk_create). Input and output vectors must not overlap.
+ *   - All work is enqueued on the handle's CUDA stream. Entry points that report results
+ *     (cg_solve, heat_step) synchronise that stream before returning; op_apply and mass_apply
+ *     return as soon as the work is enqueued.
+ *   - Functions return a status code: 0 on success, > 0 for soft outcomes, < 0 for errors.
+ *     Errors never abort the process and never trap the GPU; bsk_last_error() describes the
+ *     most recent error of the calling thread.
+ */
+#ifndef BSK_H
+#define BSK_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* ---- status codes ------------------------------------------------------------------------ */
+#define BSK_OK 0
+#define BSK_NOT_CONVERGED 1   /* max_iter reached before the tolerance                       */
+#define BSK_STALLED 2         /* residual stopped decreasing (stall window exceeded)          */
+#define BSK_EINVAL (-1)       /* invalid argument (null pointer, size, degree, overlap, ...)  */
+#define BSK_ECUDA (-2)        /* a CUDA runtime call failed                                   */
+#define BSK_ENOMEM (-3)       /* device or host allocation failed                             */
+#define BSK_ETIMEOUT (-4)     /* the solve exceeded its wall-clock limit                      */
+#define BSK_EBREAKDOWN (-5)   /* CG breakdown: p.Ap <= 0, or a NaN/Inf in a reduction         */
+
+/* ---- precision modes --------------------------------------------------------------------- */
+#define BSK_F64 0     /* vectors double; operator and reductions in FP64                         */
+#define BSK_F32 1     /* vectors float; operator in FP32; CG scalars and reductions in FP64       */
+#define BSK_F32_IR 2  /* vectors double; FP64 true residual b - A x and FP64 update of x around an
+                         inner FP32 CG (iterative refinement); CG scalars in FP64                 */
+
+/* Galerkin kernels of degree-n B-splines on a grid of step h (Table tblBsplines, scalar-product
+ * and derivative rows):
+ *   mass[j + n]  = h * beta^{2n+1}(j),
+ *   stiff[j + n] = -(1/h) * (beta^{2n-1}(j+1) - 2 beta^{2n-1}(j) + beta^{2n-1}(j-1)),
+ * j = -n..n. mass and stiff are HOST arrays of 2n+1 doubles owned by the caller. The values are
+ * exact rationals (integer numerators over (2n+1)! and (2n-1)!) rounded once to double, then
+ * scaled by h or 1/h. Returns BSK_EINVAL for n < 1, n > 5, h <= 0 (or NaN) or a null pointer. */
+int bspline_kernels(int n, double h, double* mass, double* stiff);
+
+/* A heat problem on a box grid. */
+typedef struct bsk_problem {
+    int nx, ny, nz;        /* unknowns per axis, each >= degree                                 */
+    int degree;            /* B-spline degree n, 1..5                                           */
+    double hx, hy, hz;     /* grid steps (> 0); the library does not assume hd = 1/(Nd + 1)     */
+    double dt;             /* implicit Euler time step, the weight of the stiffness term (>= 0) */
+    const uint8_t* mask;   /* DEVICE pointer to nz*ny*nx bytes (non-zero = active), or NULL for
+                              the whole box. Copied at bsk_create; the caller keeps ownership.  */
+} bsk_problem;
+
+typedef struct bsk_handle bsk_handle;
+
+/* Creates a solver handle: validates the problem, uploads the kernels and the mask, allocates
+ * every work vector the handle needs for op_apply, mass_apply, cg_solve and heat_step (the hot
+ * loop never allocates), and binds the handle to `stream` (a cudaStream_t; NULL = the legacy
+ * default stream). precision is BSK_F64, BSK_F32 or BSK_F32_IR. On success *out receives the
+ * handle, to be released with bsk_destroy. */
+int bsk_create(const bsk_problem* prob, int precision, void* stream, bsk_handle** out);
+
+/* Releases the handle and its device memory (after synchronising its stream). NULL is a no-op. */
+void bsk_destroy(bsk_handle* h);
+
+/* Changes dt (the stiffness weight) of an existing handle. */
+int bsk_set_dt(bsk_handle* h, double dt);
+
+/* y = A x: the full operator, three axis sweeps fused in one pass (Fig. FiltAlg). x and y are
+ * device vectors of nx*ny*nz elements of the handle's element type. */
+int op_apply(bsk_handle* h, const void* x, void* y);
+
+/* y = (Mz (x) My (x) Mx) x: the mass operator alone (the mass chain of Fig. FiltAlg). */
+int mass_apply(bsk_handle* h, const void* x, void* y);
+
+/* Options of the iterative solvers. Zero-initialise and set what is needed; zero fields take
+ * the defaults given in brackets. */
+typedef struct bsk_cg_opts {
+    double tol;            /* stop when ||r|| <= tol ||b|| [1e-8]                                */
+    int max_iter;          /* CG iterations (inner iterations summed, in BSK_F32_IR) [10000]     */
+    int check_every;       /* iterations per device-side chunk between host polls [16]          */
+    int stall_window;      /* stop with BSK_STALLED when ||r|| has not reached a new minimum for
+                              this many iterations [0 = off]                                     */
+    double inner_tol;      /* BSK_F32_IR: relative tolerance of each inner FP32 solve [1e-4]    */
+    int max_outer;         /* BSK_F32_IR: refinement steps [30]                                 */
+    double time_limit_s;   /* wall-clock limit of one call [0 = none]                            */
+} bsk_cg_opts;
+
+/* What a solve did. */
+typedef struct bsk_cg_report {
+    int status;            /* the returned status                                               */
+    int iterations;        /* CG iterations (all inner iterations in BSK_F32_IR)                */
+    int outer_iterations;  /* refinement steps (BSK_F32_IR), else 0                              */
+    double rel_residual;   /* true ||b - A x|| / ||b||, recomputed from x after the solve, in the
+                              handle's operator precision (FP64 for BSK_F64 and BSK_F32_IR)      */
+    double elapsed_ms;     /* wall-clock time of the call                                        */
+    long long kernel_launches; /* kernels this call launched on the GPU (graph nodes included) */
+} bsk_cg_report;
+
+/* Solves A x = b by conjugate gradients (section 2.5), starting from the x passed in, which
+ * receives the solution. The operator application, the p.Ap and r.r reductions and the vector
+ * updates run on the device; the host only polls a status word every check_every iterations.
+ * opts and report may be NULL. Returns BSK_OK, BSK_NOT_CONVERGED, BSK_STALLED or an error. */
+int cg_solve(bsk_handle* h, const void* b, void* x, const bsk_cg_opts* opts, bsk_cg_report* report);
+
+/* nsteps implicit Euler steps of u_t = Laplace(u) + g with zero Dirichlet faces:
+ * (M + dt K) u^{k+1} = M (u^k + dt q), each solved by cg_solve from u^k. u (in/out) holds the
+ * B-spline coefficients; q (may be NULL) the coefficients of the time-constant source g
+ * (Eq. RitzGalerkin right-hand side with the source in the same basis). report (may be NULL)
+ * sums the iterations over the steps and gives the last step's residual. */
+int heat_step(bsk_handle* h, void* u, const void* q, int nsteps, const bsk_cg_opts* opts,
+              bsk_cg_report* report);
+
+/* Device-side sum of squares of a handle vector (FP64 accumulation); *out is written on the
+ * host after synchronising the stream. Used to check results without a host copy. */
+int bsk_norm2(bsk_handle* h, const void* x, double* out);
+
+/* Kernel timing for roofline measurements. Launches one of the library's kernels `reps` times
+ * back to back on the handle's stream, on the handle's own work vectors (which it first zeroes,
+ * so any state of a previous solve is lost), and writes the mean device time of one launch in
+ * milliseconds (CUDA events on the handle's stream) to *ms. kernel selects:
+ *   BSK_KERNEL_OP        y = A x in the CG precision (FP32 for BSK_F32 and BSK_F32_IR)
+ *   BSK_KERNEL_CG_FUSED  the fused CG pass: p = r + beta p, x += alpha p_old, q = A p, p.q
+ *   BSK_KERNEL_CG_UPDATE the CG residual pass: r -= alpha q, r.r
+ *   BSK_KERNEL_RES64     the FP64 true residual b - A x of iterative refinement (BSK_F32_IR)
+ * Returns BSK_EINVAL for an unknown kernel or reps < 1. */
+#define BSK_KERNEL_OP 0
+#define BSK_KERNEL_CG_FUSED 1
+#define BSK_KERNEL_CG_UPDATE 2
+#define BSK_KERNEL_RES64 3
+int bsk_time_kernel(bsk_handle* h, int kernel, int reps, double* ms);
+
+/* Text of the last error raised on the calling thread ("" if none). */
+const char* bsk_last_error(void);
+
+/* Human-readable name of a status code. */
+const char* bsk_status_string(int status);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* BSK_H */

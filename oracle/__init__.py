@@ -69,6 +69,8 @@ def lib():
             L.orc_set_plant.argtypes = [ctypes.c_int]
             for name in ("orc_op_stencil", "orc_op_separable", "orc_mass", "orc_abs_op"):
                 getattr(L, name).argtypes = [P, _D, _D, _D]
+            L.orc_op_points.argtypes = [P, _D, ctypes.c_void_p, ctypes.c_int, ctypes.c_longlong,
+                                        ctypes.POINTER(ctypes.c_longlong), _D]
             L.orc_bruteforce_matrix.argtypes = [P, ctypes.c_int, _D, _I]
             L.orc_dot.restype = ctypes.c_double
             L.orc_dot.argtypes = [_D, _D, ctypes.c_longlong]
@@ -181,6 +183,20 @@ def op_stencil(prob: Problem, x, kern=None):
 def op_separable(prob: Problem, x, kern=None):
     """y = A x by the four separable 1-D convolution chains of Fig. FiltAlg."""
     return _op("orc_op_separable", prob, x, kern)
+
+
+def op_points(prob: Problem, x, points, kern=None):
+    """(A x) at the given flat indices only (direct stencil definition). x may be float32 or
+    float64 (read as is, accumulated in double)."""
+    x = np.ascontiguousarray(x)
+    assert x.dtype in (np.float32, np.float64) and x.size == prob.nx * prob.ny * prob.nz
+    pts = np.ascontiguousarray(points, dtype=np.int64)
+    out = np.zeros(pts.size)
+    kern = prob.kernels() if kern is None else _f64(kern)
+    _check(lib().orc_op_points(ctypes.byref(prob._c()), _dp(kern), x.ctypes.data,
+                               int(x.dtype == np.float32), pts.size,
+                               pts.ctypes.data_as(ctypes.POINTER(ctypes.c_longlong)), _dp(out)))
+    return out
 
 
 def mass(prob: Problem, x, kern=None):

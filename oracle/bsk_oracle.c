@@ -265,6 +265,55 @@ int orc_op_stencil(const orc_problem* p, const double* kern, const double* x, do
     return 0;
 }
 
+/* The same definition evaluated at selected points only, for parity checks at sizes where a
+ * full oracle pass is too slow: y at each flat index pts[i] (array order), with x read as float
+ * (x_is_f32 != 0) or double. Ghost values follow the same odd-reflection and mask rules. */
+int orc_op_points(const orc_problem* p, const double* kern, const void* x, int x_is_f32,
+                  long long npts, const long long* pts, double* out)
+{
+    if (!problem_ok(p)) return -1;
+    int n = p->n, L = 2 * n + 1;
+    const double *Mx = kern, *Kx = kern + L, *My = kern + 2 * L, *Ky = kern + 3 * L;
+    const double *Mz = kern + 4 * L, *Kz = kern + 5 * L;
+    double* W = (double*)malloc(sizeof(double) * L * L * L);
+    if (!W) return -3;
+    for (int c = 0; c < L; c++)
+        for (int b = 0; b < L; b++)
+            for (int a = 0; a < L; a++)
+                W[(c * L + b) * L + a] = Mz[c] * My[b] * Mx[a] +
+                                         p->dt * (Kz[c] * My[b] * Mx[a] + Mz[c] * Ky[b] * Mx[a] +
+                                                  Mz[c] * My[b] * Kx[a]);
+    const float* xf = (const float*)x;
+    const double* xd = (const double*)x;
+#pragma omp parallel for schedule(dynamic, 16)
+    for (long long t = 0; t < npts; t++) {
+        long long I = pts[t];
+        int ix = (int)(I % p->nx), iy = (int)((I / p->nx) % p->ny);
+        int iz = (int)(I / ((long long)p->nx * p->ny));
+        if (p->mask && !p->mask[I]) { out[t] = 0.0; continue; }
+        double s = 0.0;
+        for (int c = 0; c < L; c++) {
+            int sz, sgn_z = reflect(iz + c - n, p->nz, &sz);
+            if (!sgn_z) continue;
+            for (int b = 0; b < L; b++) {
+                int sy, sgn_y = reflect(iy + b - n, p->ny, &sy);
+                if (!sgn_y) continue;
+                for (int a = 0; a < L; a++) {
+                    int sx, sgn_x = reflect(ix + a - n, p->nx, &sx);
+                    if (!sgn_x) continue;
+                    size_t src = ((size_t)sz * p->ny + sy) * p->nx + sx;
+                    if (p->mask && !p->mask[src]) continue;
+                    double v = x_is_f32 ? (double)xf[src] : xd[src];
+                    s += W[(c * L + b) * L + a] * (sgn_z * sgn_y * sgn_x) * v;
+                }
+            }
+        }
+        out[t] = s;
+    }
+    free(W);
+    return 0;
+}
+
 /* ------------------------------------------------------------------------------------------ */
 /* Operator, the paper's filtering algorithm: separable 1-D convolution chains                 */
 /* ------------------------------------------------------------------------------------------ */
@@ -519,8 +568,9 @@ double orc_dot(const double* a, const double* b, long long len) { return dot(a, 
 /* Textbook conjugate gradient (Hestenes-Stiefel) for A x = b, A from orc_op_separable
  * (section 2.5: the iterative solver of F(c) = t). Stops when the recursively updated residual
  * satisfies ||r|| <= tol ||b||. On return *iters holds the iteration count and *relres the
- * true relative residual ||b - A x|| / ||b|| recomputed from x. Returns 0 if converged, 1 if
- * max_iter was reached, -5 on breakdown (p.Ap <= 0 or NaN). */
+ * true relative residual ||b - A x|| / ||b|| recomputed from x. Entries of b and x at inactive
+ * nodes are treated as zero (x is zeroed there). Returns 0 if converged, 1 if max_iter was
+ * reached, -5 on breakdown (p.Ap <= 0 or NaN). */
 int orc_cg(const orc_problem* p, const double* kern, const double* b, double* x, double tol,
            int max_iter, int* iters, double* relres)
 {
@@ -531,6 +581,15 @@ int orc_cg(const orc_problem* p, const double* kern, const double* b, double* x,
     double* q = (double*)malloc(sizeof(double) * len);
     if (!r || !pv || !q) { free(r); free(pv); free(q); return -3; }
     int status = 1, it = 0;
+    /* the system lives on the active nodes: inactive entries of b and x are treated as zero */
+    double* bm = (double*)malloc(sizeof(double) * len);
+    if (!bm) { free(r); free(pv); free(q); return -3; }
+    for (size_t i = 0; i < len; i++) {
+        int act = !p->mask || p->mask[i];
+        bm[i] = act ? b[i] : 0.0;
+        if (!act) x[i] = 0.0;
+    }
+    b = bm;
     double bb = dot(b, b, len);
     orc_op_separable(p, kern, x, q);
 #pragma omp parallel for schedule(static)
@@ -569,6 +628,7 @@ int orc_cg(const orc_problem* p, const double* kern, const double* b, double* x,
     free(r);
     free(pv);
     free(q);
+    free(bm);
     return status;
 }
 

@@ -1,0 +1,96 @@
+"""ctypes binding of libbsk.so (include/bsk.h). Argument marshalling only: every step of the
+path runs in the library's CUDA kernels. Importing this module loads the library and raises if
+it is missing or fails to load: there is no fallback."""
+from __future__ import annotations
+
+import ctypes
+import os
+
+from . import build as _build
+
+_lib = None
+
+
+class Problem(ctypes.Structure):
+    _fields_ = [
+        ("nx", ctypes.c_int), ("ny", ctypes.c_int), ("nz", ctypes.c_int),
+        ("degree", ctypes.c_int),
+        ("hx", ctypes.c_double), ("hy", ctypes.c_double), ("hz", ctypes.c_double),
+        ("dt", ctypes.c_double),
+        ("mask", ctypes.c_void_p),
+    ]
+
+
+class CgOpts(ctypes.Structure):
+    _fields_ = [
+        ("tol", ctypes.c_double), ("max_iter", ctypes.c_int), ("check_every", ctypes.c_int),
+        ("stall_window", ctypes.c_int), ("inner_tol", ctypes.c_double),
+        ("max_outer", ctypes.c_int), ("time_limit_s", ctypes.c_double),
+    ]
+
+
+class CgReport(ctypes.Structure):
+    _fields_ = [
+        ("status", ctypes.c_int), ("iterations", ctypes.c_int),
+        ("outer_iterations", ctypes.c_int), ("rel_residual", ctypes.c_double),
+        ("elapsed_ms", ctypes.c_double), ("kernel_launches", ctypes.c_longlong),
+    ]
+
+
+# exported symbols and their signatures: (restype, argtypes)
+SIGNATURES = {
+    "bspline_kernels": (ctypes.c_int, [ctypes.c_int, ctypes.c_double, ctypes.c_void_p,
+                                       ctypes.c_void_p]),
+    "bsk_create": (ctypes.c_int, [ctypes.POINTER(Problem), ctypes.c_int, ctypes.c_void_p,
+                                  ctypes.POINTER(ctypes.c_void_p)]),
+    "bsk_destroy": (None, [ctypes.c_void_p]),
+    "bsk_set_dt": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_double]),
+    "op_apply": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p]),
+    "mass_apply": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p]),
+    "cg_solve": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p,
+                                ctypes.POINTER(CgOpts), ctypes.POINTER(CgReport)]),
+    "heat_step": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int,
+                                 ctypes.POINTER(CgOpts), ctypes.POINTER(CgReport)]),
+    "bsk_norm2": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p,
+                                 ctypes.POINTER(ctypes.c_double)]),
+    "bsk_time_kernel": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int, ctypes.c_int,
+                                       ctypes.POINTER(ctypes.c_double)]),
+    "bsk_last_error": (ctypes.c_char_p, []),
+    "bsk_status_string": (ctypes.c_char_p, [ctypes.c_int]),
+}
+
+
+def library_path() -> str:
+    return _build.LIB
+
+
+def load(build_if_missing: bool = True):
+    """Loads libbsk.so (building it first if needed and allowed). Raises on any failure."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    path = _build.LIB
+    if build_if_missing and not _build.up_to_date():
+        _build.build()
+    if not os.path.exists(path):
+        raise RuntimeError(f"CUDA library not built: {path} (run __graft_entry__.build())")
+    L = ctypes.CDLL(path)
+    for name, (res, args) in SIGNATURES.items():
+        fn = getattr(L, name)
+        fn.restype = res
+        fn.argtypes = args
+    _lib = L
+    return L
+
+
+class BskError(RuntimeError):
+    def __init__(self, code, msg):
+        super().__init__(f"bsk status {code}: {msg}")
+        self.code = code
+
+
+def check(rc: int) -> int:
+    if rc < 0:
+        L = load()
+        raise BskError(rc, L.bsk_last_error().decode())
+    return rc

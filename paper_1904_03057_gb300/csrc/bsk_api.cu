@@ -1,0 +1,749 @@
+// bsk_api.cu -- the C ABI declared in include/bsk.h: kernel tables, solver handles, the CG
+// driver (device-resident iteration in CUDA graphs, host polling), iterative refinement and
+// implicit Euler stepping. Every arithmetic step of the path runs in the kernels of
+// kernels_f32.cu / kernels_f64.cu; this file only validates, allocates and sequences.
+#include <algorithm>
+#include <chrono>
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <new>
+#include <string>
+
+#include "bsk.h"
+#include "bsk_launch.h"
+
+using bsk::Scalars;
+
+namespace {
+
+thread_local std::string g_err;
+
+int fail(int code, const char* fmt, ...)
+{
+    char buf[512];
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(buf, sizeof buf, fmt, ap);
+    va_end(ap);
+    g_err = buf;
+    return code;
+}
+
+int cuda_fail(cudaError_t e, const char* what)
+{
+    return fail(BSK_ECUDA, "%s: %s", what, cudaGetErrorString(e));
+}
+
+#define BSK_CUDA(call)                                              \
+    do {                                                            \
+        cudaError_t e_ = (call);                                    \
+        if (e_ != cudaSuccess) return cuda_fail(e_, #call);         \
+    } while (0)
+
+// m! * beta^m(j) for odd m: with (m+1)/2 an integer every term of the truncated-power sum
+// (beta^m = (m+1)-fold convolution of the unit box, Table tblBsplines) is an integer, so the
+// value is exact in 64-bit arithmetic for m <= 11.
+long long bspline_odd_scaled(int m, int j)
+{
+    const int half = (m + 1) / 2;
+    long long s = 0, binom = 1;
+    for (int k = 0; k <= m + 1; k++) {
+        long long t = (long long)j + half - k;
+        if (t > 0) {
+            long long p = 1;
+            for (int e = 0; e < m; e++) p *= t;
+            s += (k & 1) ? -binom * p : binom * p;
+        }
+        binom = binom * (m + 1 - k) / (k + 1);
+    }
+    return s;
+}
+
+double factorial(int m)
+{
+    double f = 1.0;
+    for (int i = 2; i <= m; i++) f *= i;
+    return f;
+}
+
+}  // namespace
+
+extern "C" int bspline_kernels(int n, double h, double* mass, double* stiff)
+{
+    if (n < 1 || n > 5) return fail(BSK_EINVAL, "degree %d outside 1..5", n);
+    if (!(h > 0.0) || !std::isfinite(h)) return fail(BSK_EINVAL, "grid step must be > 0");
+    if (!mass || !stiff) return fail(BSK_EINVAL, "null output array");
+    // scalar-product row of Table tblBsplines: integral beta^n(x-k) beta^n(x-l) = beta^{2n+1}(k-l);
+    // with the derivative row, integral beta^n'(x-k) beta^n'(x-l) = -(second difference of
+    // beta^{2n-1}) at k-l.
+    const int mm = 2 * n + 1, mk = 2 * n - 1;
+    const double fm = factorial(mm), fk = factorial(mk);
+    for (int j = -n; j <= n; j++) {
+        const double m1 = (double)bspline_odd_scaled(mm, j) / fm;
+        const long long d2 = bspline_odd_scaled(mk, j + 1) - 2 * bspline_odd_scaled(mk, j) +
+                             bspline_odd_scaled(mk, j - 1);
+        const double k1 = -(double)d2 / fk;
+        mass[j + n] = h * m1;
+        stiff[j + n] = k1 / h;
+    }
+    return BSK_OK;
+}
+
+struct bsk_handle {
+    int nx, ny, nz, n, prec;
+    double h[3];
+    double dt;
+    size_t len;
+    cudaStream_t stream;       // the caller's stream: every launch goes here
+    cudaStream_t cap_stream;   // private stream used only to capture the CG graph (the legacy
+                               // default stream cannot be captured; the graph runs on `stream`)
+    uint8_t* mask;
+    double M[3][bsk::kMaxTaps];   // per-axis mass kernels
+    double K[3][bsk::kMaxTaps];   // per-axis stiffness kernels (not yet multiplied by dt)
+    // CG vectors in the CG element type (double for BSK_F64, float otherwise)
+    void *x, *r, *p0, *p1, *q, *bvec;
+    // iterative refinement (FP64 outer vectors)
+    double *r64, *b64;
+    Scalars *sc, *sc64, *sc_aux;
+    Scalars* h_sc;   // pinned host mirror
+    double* partials;
+    cudaGraphExec_t graph;
+    int graph_chunk;
+    long long launches;   // kernels launched since the counter was last read
+};
+
+namespace {
+
+size_t user_es(const bsk_handle* h) { return h->prec == BSK_F32 ? sizeof(float) : sizeof(double); }
+size_t cg_es(const bsk_handle* h) { return h->prec == BSK_F64 ? sizeof(double) : sizeof(float); }
+
+void fill_launch(const bsk_handle* h, bsk::OpLaunch& L, int mode)
+{
+    memset(&L, 0, sizeof L);
+    L.mode = mode;
+    L.degree = h->n;
+    L.nx = h->nx;
+    L.ny = h->ny;
+    L.nz = h->nz;
+    L.mask = h->mask;
+    for (int d = 0; d < 3; d++)
+        for (int j = 0; j < bsk::kMaxTaps; j++) {
+            L.M[d][j] = h->M[d][j];
+            L.Kdt[d][j] = h->dt * h->K[d][j];
+        }
+}
+
+template <typename T>
+cudaError_t op_launch(const bsk::OpLaunch& L, cudaStream_t s)
+{
+    return bsk::launch_op<T>(L, s);
+}
+
+cudaError_t op_launch_es(size_t es, const bsk::OpLaunch& L, cudaStream_t s)
+{
+    return es == sizeof(double) ? bsk::launch_op<double>(L, s) : bsk::launch_op<float>(L, s);
+}
+
+// Counts one kernel launch of the handle (for the launch totals of bsk_cg_report).
+#define BSK_LAUNCH(h, call)          \
+    do {                             \
+        BSK_CUDA(call);              \
+        (h)->launches += 1;          \
+    } while (0)
+
+int sync_scalars(bsk_handle* h, Scalars* dev)
+{
+    BSK_CUDA(cudaMemcpyAsync(h->h_sc, dev, sizeof(Scalars), cudaMemcpyDeviceToHost, h->stream));
+    BSK_CUDA(cudaStreamSynchronize(h->stream));
+    return BSK_OK;
+}
+
+int init_scalars(bsk_handle* h, Scalars* dev, double tol, int max_iter, int stall_window)
+{
+    Scalars s;
+    memset(&s, 0, sizeof s);
+    s.tol2 = tol * tol;
+    s.max_iter = max_iter;
+    s.stall_window = stall_window;
+    // the pinned mirror is reused as the staging buffer: wait for earlier copies out of it
+    BSK_CUDA(cudaStreamSynchronize(h->stream));
+    *h->h_sc = s;
+    BSK_CUDA(cudaMemcpyAsync(dev, h->h_sc, sizeof(Scalars), cudaMemcpyHostToDevice, h->stream));
+    BSK_CUDA(cudaStreamSynchronize(h->stream));
+    return BSK_OK;
+}
+
+struct Opts {
+    double tol, inner_tol, time_limit;
+    int max_iter, check_every, stall_window, max_outer;
+};
+
+Opts resolve(const bsk_cg_opts* o)
+{
+    Opts r;
+    r.tol = (o && o->tol > 0) ? o->tol : 1e-8;
+    r.max_iter = (o && o->max_iter > 0) ? o->max_iter : 10000;
+    r.check_every = (o && o->check_every > 0) ? o->check_every : 16;
+    r.check_every += r.check_every & 1;   // even: ping-pong parity repeats across graph launches
+    r.stall_window = (o && o->stall_window > 0) ? o->stall_window : 0;
+    r.inner_tol = (o && o->inner_tol > 0) ? o->inner_tol : 1e-5;
+    r.max_outer = (o && o->max_outer > 0) ? o->max_outer : 30;
+    r.time_limit = (o && o->time_limit_s > 0) ? o->time_limit_s : 0.0;
+    return r;
+}
+
+// The device-resident CG chunk: `chunk` iterations of (fused p-update + operator + p.Ap, then
+// r update + r.r), captured once per handle into a CUDA graph and replayed.
+template <typename T>
+int enqueue_chunk(bsk_handle* h, int chunk)
+{
+    cudaStream_t s = h->cap_stream;
+    T* p[2] = {static_cast<T*>(h->p0), static_cast<T*>(h->p1)};
+    for (int it = 0; it < chunk; it++) {
+        bsk::OpLaunch L;
+        fill_launch(h, L, bsk::MODE_CGP);
+        L.in0 = h->r;
+        L.in1 = p[it & 1];
+        L.out0 = h->q;
+        L.out1 = p[(it + 1) & 1];
+        L.xvec = h->x;
+        L.sc = h->sc;
+        L.partials = h->partials;
+        L.fin = bsk::FIN_CGP;
+        L.p_parity = (it + 1) & 1;
+        BSK_CUDA(op_launch<T>(L, s));
+        BSK_CUDA(bsk::launch_cg_update<T>(static_cast<T*>(h->r), static_cast<const T*>(h->q),
+                                          h->len, h->sc, h->partials, s));
+    }
+    return BSK_OK;
+}
+
+template <typename T>
+int ensure_graph(bsk_handle* h, int chunk)
+{
+    if (h->graph && h->graph_chunk == chunk) return BSK_OK;
+    if (h->graph) {
+        cudaGraphExecDestroy(h->graph);
+        h->graph = nullptr;
+    }
+    cudaGraph_t g = nullptr;
+    BSK_CUDA(cudaStreamBeginCapture(h->cap_stream, cudaStreamCaptureModeThreadLocal));
+    int rc = enqueue_chunk<T>(h, chunk);
+    cudaError_t e = cudaStreamEndCapture(h->cap_stream, &g);
+    if (rc != BSK_OK) {
+        if (g) cudaGraphDestroy(g);
+        return rc;
+    }
+    if (e != cudaSuccess) return cuda_fail(e, "cudaStreamEndCapture");
+    e = cudaGraphInstantiate(&h->graph, g, 0);
+    cudaGraphDestroy(g);
+    if (e != cudaSuccess) return cuda_fail(e, "cudaGraphInstantiate");
+    h->graph_chunk = chunk;
+    return BSK_OK;
+}
+
+double seconds_since(std::chrono::steady_clock::time_point t0)
+{
+    return std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
+}
+
+// Runs the CG iteration on the handle's CG vectors from the state set up by an init kernel
+// (r, rr, bb in h->sc; p0 zeroed), until the device reports done. Returns the CG status.
+template <typename T>
+int run_iterations(bsk_handle* h, const Opts& o, std::chrono::steady_clock::time_point t0,
+                   int* iters_out)
+{
+    int rc = ensure_graph<T>(h, o.check_every);
+    if (rc) return rc;
+    if ((rc = sync_scalars(h, h->sc))) return rc;
+    while (!h->h_sc->done) {
+        BSK_CUDA(cudaGraphLaunch(h->graph, h->stream));
+        h->launches += 2LL * h->graph_chunk;
+        if ((rc = sync_scalars(h, h->sc))) return rc;
+        if (o.time_limit > 0 && !h->h_sc->done && seconds_since(t0) > o.time_limit) {
+            *iters_out = h->h_sc->iter;
+            return fail(BSK_ETIMEOUT, "solve exceeded its time limit of %.3f s", o.time_limit);
+        }
+    }
+    BSK_LAUNCH(h, bsk::launch_cg_flush<T>(static_cast<T*>(h->x), static_cast<const T*>(h->p0),
+                                     static_cast<const T*>(h->p1), h->len, h->sc, h->stream));
+    *iters_out = h->h_sc->iter;
+    switch (h->h_sc->status) {
+    case 0: return BSK_OK;
+    case 1: return BSK_NOT_CONVERGED;
+    case 2: return BSK_STALLED;
+    default: return fail(BSK_EBREAKDOWN, "CG breakdown (p.Ap <= 0 or non-finite reduction)");
+    }
+}
+
+// Plain CG (BSK_F64 / BSK_F32): x (user) is copied into the handle's x, solved, copied back.
+template <typename T>
+int cg_plain(bsk_handle* h, const T* b, T* x, const Opts& o, bsk_cg_report* rep,
+             std::chrono::steady_clock::time_point t0)
+{
+    int rc;
+    BSK_LAUNCH(h, bsk::launch_copy_masked<T>(x, static_cast<T*>(h->x), h->len, h->mask, h->stream));
+    if ((rc = init_scalars(h, h->sc, o.tol, o.max_iter, o.stall_window))) return rc;
+    bsk::OpLaunch L;
+    fill_launch(h, L, bsk::MODE_RES);
+    L.in0 = h->x;
+    L.b = b;
+    L.out0 = h->r;
+    L.sc = h->sc;
+    L.partials = h->partials;
+    L.fin = bsk::FIN_RES_INIT;
+    BSK_LAUNCH(h, op_launch<T>(L, h->stream));
+    BSK_CUDA(cudaMemsetAsync(h->p0, 0, h->len * sizeof(T), h->stream));
+    int iters = 0;
+    int st = run_iterations<T>(h, o, t0, &iters);
+    if (st < 0 && st != BSK_EBREAKDOWN) return st;
+    if (h->h_sc->zero_b) BSK_CUDA(cudaMemsetAsync(h->x, 0, h->len * sizeof(T), h->stream));
+    BSK_LAUNCH(h, bsk::launch_copy_masked<T>(static_cast<const T*>(h->x), x, h->len, h->mask, h->stream));
+    // true residual of the returned x
+    fill_launch(h, L, bsk::MODE_RES);
+    L.in0 = x;
+    L.b = b;
+    L.out0 = h->r;
+    L.sc = h->sc_aux;
+    L.partials = h->partials;
+    L.fin = bsk::FIN_RES_TRUE;
+    BSK_LAUNCH(h, op_launch<T>(L, h->stream));
+    if ((rc = sync_scalars(h, h->sc_aux))) return rc;
+    if (rep) {
+        rep->iterations += iters;
+        rep->rel_residual = h->h_sc->bb_true > 0 ? std::sqrt(h->h_sc->rr_true / h->h_sc->bb_true) : 0.0;
+    }
+    return st;
+}
+
+// Mixed precision: FP64 true residual and update around inner FP32 CG solves.
+int cg_ir(bsk_handle* h, const double* b, double* x, const Opts& o, bsk_cg_report* rep,
+          std::chrono::steady_clock::time_point t0)
+{
+    int rc;
+    int total_iters = 0, outer = 0, st = BSK_NOT_CONVERGED;
+    double rel = 0.0;
+    BSK_LAUNCH(h, bsk::launch_copy_masked<double>(x, x, h->len, h->mask, h->stream));
+    for (;; outer++) {
+        bsk::OpLaunch L;
+        fill_launch(h, L, bsk::MODE_RES);
+        L.in0 = x;
+        L.b = b;
+        L.out0 = h->r64;
+        L.sc = h->sc64;
+        L.partials = h->partials;
+        L.fin = bsk::FIN_RES_TRUE;
+        BSK_LAUNCH(h, op_launch<double>(L, h->stream));
+        if ((rc = sync_scalars(h, h->sc64))) return rc;
+        const double rr = h->h_sc->rr_true, bb = h->h_sc->bb_true;
+        if (!std::isfinite(rr) || !std::isfinite(bb))
+            return fail(BSK_EBREAKDOWN, "non-finite residual in iterative refinement");
+        if (bb == 0.0) {
+            BSK_CUDA(cudaMemsetAsync(x, 0, h->len * sizeof(double), h->stream));
+            rel = 0.0;
+            st = BSK_OK;
+            break;
+        }
+        rel = std::sqrt(rr / bb);
+        if (rel <= o.tol) { st = BSK_OK; break; }
+        if (outer >= o.max_outer || total_iters >= o.max_iter) { st = BSK_NOT_CONVERGED; break; }
+        if (o.time_limit > 0 && seconds_since(t0) > o.time_limit) {
+            if (rep) { rep->iterations += total_iters; rep->outer_iterations += outer; rep->rel_residual = rel; }
+            return fail(BSK_ETIMEOUT, "solve exceeded its time limit of %.3f s", o.time_limit);
+        }
+        // inner FP32 solve of A d = r / ||r|| from d = 0, only as accurately as this step needs
+        double inner = std::max(o.inner_tol, 0.3 * o.tol / rel);
+        if (inner > 0.5) inner = 0.5;
+        BSK_LAUNCH(h, bsk::launch_ir_scale_down(h->r64, static_cast<float*>(h->r), h->len, h->sc64,
+                                           h->stream));
+        if ((rc = init_scalars(h, h->sc, inner, o.max_iter - total_iters, o.stall_window))) return rc;
+        BSK_LAUNCH(h, bsk::launch_cg_init_zero<float>(static_cast<const float*>(h->r),
+                                                 static_cast<float*>(h->r), static_cast<float*>(h->x),
+                                                 h->len, h->mask, h->sc, h->partials, h->stream));
+        BSK_CUDA(cudaMemsetAsync(h->p0, 0, h->len * sizeof(float), h->stream));
+        int it = 0;
+        int ist = run_iterations<float>(h, o, t0, &it);
+        total_iters += it;
+        if (ist == BSK_ETIMEOUT) {
+            if (rep) { rep->iterations += total_iters; rep->outer_iterations += outer + 1; rep->rel_residual = rel; }
+            return ist;
+        }
+        if (ist < 0 && ist != BSK_EBREAKDOWN) return ist;
+        if (ist == BSK_EBREAKDOWN && it == 0) return ist;
+        BSK_LAUNCH(h, bsk::launch_ir_update(x, static_cast<const float*>(h->x), h->len, h->sc64, h->stream));
+    }
+    if (rep) {
+        rep->iterations += total_iters;
+        rep->outer_iterations += outer;
+        rep->rel_residual = rel;
+    }
+    return st;
+}
+
+int check_handle(const bsk_handle* h)
+{
+    if (!h) return fail(BSK_EINVAL, "null handle");
+    return BSK_OK;
+}
+
+int solve_dispatch(bsk_handle* h, const void* b, void* x, const Opts& o, bsk_cg_report* rep,
+                   std::chrono::steady_clock::time_point t0)
+{
+    switch (h->prec) {
+    case BSK_F64: return cg_plain<double>(h, (const double*)b, (double*)x, o, rep, t0);
+    case BSK_F32: return cg_plain<float>(h, (const float*)b, (float*)x, o, rep, t0);
+    default: return cg_ir(h, (const double*)b, (double*)x, o, rep, t0);
+    }
+}
+
+bool overlaps(const void* a, const void* b, size_t bytes)
+{
+    const char *pa = (const char*)a, *pb = (const char*)b;
+    return pa < pb + bytes && pb < pa + bytes;
+}
+
+}  // namespace
+
+extern "C" int bsk_create(const bsk_problem* prob, int precision, void* stream, bsk_handle** out)
+{
+    if (!prob || !out) return fail(BSK_EINVAL, "null argument");
+    *out = nullptr;
+    const int n = prob->degree;
+    if (n < 1 || n > 5) return fail(BSK_EINVAL, "degree %d outside 1..5", n);
+    if (prob->nx < n || prob->ny < n || prob->nz < n)
+        return fail(BSK_EINVAL, "each axis needs at least degree (%d) unknowns, got %d x %d x %d", n,
+                    prob->nx, prob->ny, prob->nz);
+    if (!(prob->hx > 0) || !(prob->hy > 0) || !(prob->hz > 0) || !std::isfinite(prob->hx) ||
+        !std::isfinite(prob->hy) || !std::isfinite(prob->hz))
+        return fail(BSK_EINVAL, "grid steps must be finite and > 0");
+    if (!(prob->dt >= 0) || !std::isfinite(prob->dt)) return fail(BSK_EINVAL, "dt must be finite and >= 0");
+    if (precision != BSK_F64 && precision != BSK_F32 && precision != BSK_F32_IR)
+        return fail(BSK_EINVAL, "unknown precision %d", precision);
+    const size_t len = (size_t)prob->nx * prob->ny * prob->nz;
+    if ((size_t)prob->nx * prob->ny > (size_t)1 << 31 || len > ((size_t)1 << 40))
+        return fail(BSK_EINVAL, "grid too large");
+
+    bsk_handle* h = new (std::nothrow) bsk_handle;
+    if (!h) return fail(BSK_ENOMEM, "host allocation failed");
+    memset(h, 0, sizeof *h);
+    h->nx = prob->nx;
+    h->ny = prob->ny;
+    h->nz = prob->nz;
+    h->n = n;
+    h->prec = precision;
+    h->h[0] = prob->hx;
+    h->h[1] = prob->hy;
+    h->h[2] = prob->hz;
+    h->dt = prob->dt;
+    h->len = len;
+    h->stream = (cudaStream_t)stream;
+    for (int d = 0; d < 3; d++) {
+        double m[bsk::kMaxTaps] = {0}, k[bsk::kMaxTaps] = {0};
+        bspline_kernels(n, h->h[d], m, k);
+        for (int j = 0; j < 2 * n + 1; j++) {
+            h->M[d][j] = m[j];
+            h->K[d][j] = k[j];
+        }
+    }
+    auto cleanup = [&](int code) {
+        bsk_destroy(h);
+        return code;
+    };
+    cudaError_t e;
+#define BSK_ALLOC(ptr, bytes)                                                                  \
+    do {                                                                                       \
+        e = cudaMalloc((void**)&(ptr), (bytes));                                               \
+        if (e != cudaSuccess) {                                                                \
+            cudaGetLastError();                                                                \
+            int c_ = fail(e == cudaErrorMemoryAllocation ? BSK_ENOMEM : BSK_ECUDA,             \
+                          "cudaMalloc(%zu) failed: %s", (size_t)(bytes), cudaGetErrorString(e)); \
+            bsk_destroy(h);                                                                    \
+            return c_;                                                                         \
+        }                                                                                      \
+    } while (0)
+
+    e = bsk::prepare_op<float>(n);
+    if (e == cudaSuccess) e = bsk::prepare_op<double>(n);
+    if (e != cudaSuccess) return cleanup(cuda_fail(e, "kernel set-up"));
+    e = cudaStreamCreateWithFlags(&h->cap_stream, cudaStreamNonBlocking);
+    if (e != cudaSuccess) return cleanup(cuda_fail(e, "cudaStreamCreate"));
+    if (prob->mask) {
+        BSK_ALLOC(h->mask, len);
+        e = cudaMemcpyAsync(h->mask, prob->mask, len, cudaMemcpyDeviceToDevice, h->stream);
+        if (e != cudaSuccess) return cleanup(cuda_fail(e, "mask copy"));
+    }
+    const size_t ces = cg_es(h);
+    BSK_ALLOC(h->x, len * ces);
+    BSK_ALLOC(h->r, len * ces);
+    BSK_ALLOC(h->p0, len * ces);
+    BSK_ALLOC(h->p1, len * ces);
+    BSK_ALLOC(h->q, len * ces);
+    if (precision == BSK_F32_IR) {
+        BSK_ALLOC(h->r64, len * sizeof(double));
+        BSK_ALLOC(h->b64, len * sizeof(double));
+    } else {
+        BSK_ALLOC(h->bvec, len * ces);
+    }
+    BSK_ALLOC(h->sc, sizeof(Scalars));
+    BSK_ALLOC(h->sc64, sizeof(Scalars));
+    BSK_ALLOC(h->sc_aux, sizeof(Scalars));
+    const size_t nb = std::max(bsk::op_grid_blocks(h->nx, h->ny, h->nz, n), (size_t)bsk::vec_grid(len));
+    BSK_ALLOC(h->partials, 2 * nb * sizeof(double));
+    e = cudaMallocHost((void**)&h->h_sc, sizeof(Scalars));
+    if (e != cudaSuccess) return cleanup(fail(BSK_ENOMEM, "pinned allocation failed"));
+    memset(h->h_sc, 0, sizeof(Scalars));
+    for (Scalars* s : {h->sc, h->sc64, h->sc_aux}) {
+        e = cudaMemsetAsync(s, 0, sizeof(Scalars), h->stream);
+        if (e != cudaSuccess) return cleanup(cuda_fail(e, "memset"));
+    }
+    e = cudaStreamSynchronize(h->stream);
+    if (e != cudaSuccess) return cleanup(cuda_fail(e, "bsk_create"));
+#undef BSK_ALLOC
+    *out = h;
+    return BSK_OK;
+}
+
+extern "C" void bsk_destroy(bsk_handle* h)
+{
+    if (!h) return;
+    cudaStreamSynchronize(h->stream);
+    if (h->graph) cudaGraphExecDestroy(h->graph);
+    void* ptrs[] = {h->mask, h->x, h->r, h->p0, h->p1, h->q, h->bvec, h->r64, h->b64,
+                    h->sc, h->sc64, h->sc_aux, h->partials};
+    for (void* p : ptrs)
+        if (p) cudaFree(p);
+    if (h->h_sc) cudaFreeHost(h->h_sc);
+    if (h->cap_stream) cudaStreamDestroy(h->cap_stream);
+    delete h;
+}
+
+extern "C" int bsk_set_dt(bsk_handle* h, double dt)
+{
+    if (int rc = check_handle(h)) return rc;
+    if (!(dt >= 0) || !std::isfinite(dt)) return fail(BSK_EINVAL, "dt must be finite and >= 0");
+    if (dt != h->dt && h->graph) {   // the kernels of the captured graph carry dt * K by value
+        cudaStreamSynchronize(h->stream);
+        cudaGraphExecDestroy(h->graph);
+        h->graph = nullptr;
+    }
+    h->dt = dt;
+    return BSK_OK;
+}
+
+static int apply_common(bsk_handle* h, const void* x, void* y, int mode)
+{
+    if (int rc = check_handle(h)) return rc;
+    if (!x || !y) return fail(BSK_EINVAL, "null vector");
+    const size_t es = user_es(h);
+    if (overlaps(x, y, h->len * es)) return fail(BSK_EINVAL, "x and y overlap");
+    bsk::OpLaunch L;
+    fill_launch(h, L, mode);
+    L.in0 = x;
+    L.out0 = y;
+    L.fin = bsk::FIN_NONE;
+    cudaError_t e = op_launch_es(es, L, h->stream);
+    if (e != cudaSuccess) return cuda_fail(e, "operator launch");
+    h->launches += 1;
+    return BSK_OK;
+}
+
+extern "C" int op_apply(bsk_handle* h, const void* x, void* y)
+{
+    return apply_common(h, x, y, bsk::MODE_OP);
+}
+
+extern "C" int mass_apply(bsk_handle* h, const void* x, void* y)
+{
+    return apply_common(h, x, y, bsk::MODE_MASS);
+}
+
+extern "C" int cg_solve(bsk_handle* h, const void* b, void* x, const bsk_cg_opts* opts,
+                        bsk_cg_report* report)
+{
+    auto t0 = std::chrono::steady_clock::now();
+    if (int rc = check_handle(h)) return rc;
+    if (!b || !x) return fail(BSK_EINVAL, "null vector");
+    if (overlaps(b, x, h->len * user_es(h))) return fail(BSK_EINVAL, "b and x overlap");
+    const Opts o = resolve(opts);
+    if (report) memset(report, 0, sizeof *report);
+    h->launches = 0;
+    int st = solve_dispatch(h, b, x, o, report, t0);
+    if (report) {
+        report->status = st;
+        report->elapsed_ms = 1e3 * seconds_since(t0);
+        report->kernel_launches = h->launches;
+    }
+    return st;
+}
+
+extern "C" int heat_step(bsk_handle* h, void* u, const void* q, int nsteps, const bsk_cg_opts* opts,
+                         bsk_cg_report* report)
+{
+    auto t0 = std::chrono::steady_clock::now();
+    if (int rc = check_handle(h)) return rc;
+    if (!u) return fail(BSK_EINVAL, "null vector");
+    if (nsteps < 0) return fail(BSK_EINVAL, "nsteps < 0");
+    const size_t es = user_es(h);
+    if (q && overlaps(u, q, h->len * es)) return fail(BSK_EINVAL, "u and q overlap");
+    const Opts o = resolve(opts);
+    if (report) memset(report, 0, sizeof *report);
+    void* b = h->prec == BSK_F32_IR ? (void*)h->b64 : h->bvec;
+    int st = BSK_OK;
+    h->launches = 0;
+    for (int s = 0; s < nsteps; s++) {
+        bsk::OpLaunch L;
+        fill_launch(h, L, bsk::MODE_MASS);
+        L.in0 = u;
+        L.in1 = q;
+        L.s = h->dt;
+        L.out0 = b;
+        L.fin = bsk::FIN_NONE;
+        cudaError_t e = op_launch_es(es, L, h->stream);
+        if (e != cudaSuccess) return cuda_fail(e, "right-hand side launch");
+        h->launches += 1;
+        int rs = solve_dispatch(h, b, u, o, report, t0);
+        if (rs < 0) { st = rs; break; }
+        if (rs > 0 && st == BSK_OK) st = rs;
+    }
+    if (report) {
+        report->status = st;
+        report->elapsed_ms = 1e3 * seconds_since(t0);
+        report->kernel_launches = h->launches;
+    }
+    return st;
+}
+
+extern "C" int bsk_time_kernel(bsk_handle* h, int kernel, int reps, double* ms)
+{
+    if (int rc = check_handle(h)) return rc;
+    if (!ms || reps < 1) return fail(BSK_EINVAL, "bad arguments");
+    if (kernel < BSK_KERNEL_OP || kernel > BSK_KERNEL_RES64) return fail(BSK_EINVAL, "unknown kernel %d", kernel);
+    if (kernel == BSK_KERNEL_RES64 && h->prec != BSK_F32_IR)
+        return fail(BSK_EINVAL, "the FP64 residual kernel exists only for BSK_F32_IR handles");
+    const size_t ces = cg_es(h);
+    for (void* p : {h->x, h->r, h->p0, h->p1, h->q})
+        BSK_CUDA(cudaMemsetAsync(p, 0, h->len * ces, h->stream));
+    if (h->r64) BSK_CUDA(cudaMemsetAsync(h->r64, 0, h->len * sizeof(double), h->stream));
+    if (h->b64) BSK_CUDA(cudaMemsetAsync(h->b64, 0, h->len * sizeof(double), h->stream));
+    if (int rc = init_scalars(h, h->sc_aux, 0.0, 1 << 30, 0)) return rc;
+    auto one = [&](int i) -> cudaError_t {
+        bsk::OpLaunch L;
+        switch (kernel) {
+        case BSK_KERNEL_OP:
+            fill_launch(h, L, bsk::MODE_OP);
+            L.in0 = h->x;
+            L.out0 = h->q;
+            L.fin = bsk::FIN_NONE;
+            return op_launch_es(ces, L, h->stream);
+        case BSK_KERNEL_CG_FUSED:
+            fill_launch(h, L, bsk::MODE_CGP);
+            L.in0 = h->r;
+            L.in1 = (i & 1) ? h->p1 : h->p0;
+            L.out1 = (i & 1) ? h->p0 : h->p1;
+            L.out0 = h->q;
+            L.xvec = h->x;
+            L.sc = h->sc_aux;
+            L.partials = h->partials;
+            L.fin = bsk::FIN_NORM;   // reduces p.q without touching the CG state of sc
+            return op_launch_es(ces, L, h->stream);
+        case BSK_KERNEL_CG_UPDATE:
+            return ces == sizeof(double)
+                       ? bsk::launch_cg_update<double>((double*)h->r, (const double*)h->q, h->len,
+                                                       h->sc_aux, h->partials, h->stream)
+                       : bsk::launch_cg_update<float>((float*)h->r, (const float*)h->q, h->len,
+                                                      h->sc_aux, h->partials, h->stream);
+        default:  // BSK_KERNEL_RES64
+            fill_launch(h, L, bsk::MODE_RES);
+            L.in0 = h->b64;
+            L.b = h->b64;
+            L.out0 = h->r64;
+            L.sc = h->sc_aux;
+            L.partials = h->partials;
+            L.fin = bsk::FIN_RES_TRUE;
+            return op_launch_es(sizeof(double), L, h->stream);
+        }
+    };
+    // one untimed launch (first-launch set-up), then the timed batch
+    BSK_CUDA(one(0));
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    BSK_CUDA(cudaEventCreate(&e0));
+    cudaError_t err = cudaEventCreate(&e1);
+    if (err == cudaSuccess) err = cudaEventRecord(e0, h->stream);
+    for (int i = 0; i < reps && err == cudaSuccess; i++) err = one(i + 1);
+    if (err == cudaSuccess) err = cudaEventRecord(e1, h->stream);
+    if (err == cudaSuccess) err = cudaEventSynchronize(e1);
+    float total = 0.f;
+    if (err == cudaSuccess) err = cudaEventElapsedTime(&total, e0, e1);
+    cudaEventDestroy(e0);
+    if (e1) cudaEventDestroy(e1);
+    if (err != cudaSuccess) return cuda_fail(err, "bsk_time_kernel");
+    *ms = (double)total / reps;
+    return BSK_OK;
+}
+
+extern "C" int bsk_norm2(bsk_handle* h, const void* x, double* out)
+{
+    if (int rc = check_handle(h)) return rc;
+    if (!x || !out) return fail(BSK_EINVAL, "null argument");
+    cudaError_t e = user_es(h) == sizeof(double)
+                        ? bsk::launch_norm2<double>((const double*)x, h->len, h->sc_aux, h->partials, h->stream)
+                        : bsk::launch_norm2<float>((const float*)x, h->len, h->sc_aux, h->partials, h->stream);
+    if (e != cudaSuccess) return cuda_fail(e, "norm launch");
+    if (int rc = sync_scalars(h, h->sc_aux)) return rc;
+    *out = h->h_sc->rr_true;
+    return BSK_OK;
+}
+
+extern "C" const char* bsk_last_error(void) { return g_err.c_str(); }
+
+extern "C" const char* bsk_status_string(int s)
+{
+    switch (s) {
+    case BSK_OK: return "ok";
+    case BSK_NOT_CONVERGED: return "not converged (max_iter)";
+    case BSK_STALLED: return "stalled";
+    case BSK_EINVAL: return "invalid argument";
+    case BSK_ECUDA: return "CUDA error";
+    case BSK_ENOMEM: return "out of memory";
+    case BSK_ETIMEOUT: return "time limit exceeded";
+    case BSK_EBREAKDOWN: return "breakdown";
+    default: return "unknown status";
+    }
+}
+
+// ---- grid helpers shared with the kernel translation units --------------------------------
+namespace bsk {
+
+dim3 op_grid(int nx, int ny, int nz, int degree, int* tz)
+{
+    (void)degree;
+    const int bx = (nx + kGenTX - 1) / kGenTX, by = (ny + kGenTY - 1) / kGenTY;
+    const long long bxy = (long long)bx * by;
+    // enough blocks for several waves on 152 SMs, but at least 16 planes per block so that the
+    // 2n halo planes re-staged per block stay a small overhead
+    long long nzc = (1216 + bxy - 1) / bxy;
+    int t = (int)((nz + nzc - 1) / nzc);
+    if (t < 16) t = 16;
+    if (t > nz) t = nz;
+    *tz = t;
+    return dim3(bx, by, (nz + t - 1) / t);
+}
+
+size_t op_grid_blocks(int nx, int ny, int nz, int degree)
+{
+    int tz;
+    dim3 g = op_grid(nx, ny, nz, degree, &tz);
+    return (size_t)g.x * g.y * g.z;
+}
+
+int vec_grid(size_t len)
+{
+    size_t b = (len + 4 * 256 - 1) / (4 * 256);
+    if (b > 152 * 8) b = 152 * 8;
+    if (b < 1) b = 1;
+    return (int)b;
+}
+
+}  // namespace bsk

@@ -1,0 +1,66 @@
+// bsk_launch.h -- host-side launch interface between the C ABI (bsk_api.cu) and the kernel
+// translation units (one per element type).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stddef.h>
+#include <stdint.h>
+
+#include "bsk_device.cuh"
+
+namespace bsk {
+
+struct OpLaunch {
+    int mode;                    // OpMode
+    int degree;                  // 1..5
+    int nx, ny, nz;
+    const uint8_t* mask;         // device node mask or nullptr
+    double M[3][kMaxTaps];       // per-axis mass kernels (axis 0 = x)
+    double Kdt[3][kMaxTaps];     // per-axis stiffness kernels, multiplied by dt
+    const void* in0;
+    const void* in1;
+    void* out0;
+    void* out1;
+    void* xvec;
+    const void* b;
+    double s;
+    Scalars* sc;
+    double* partials;
+    int fin;
+    int p_parity;
+};
+
+// Grid of the operator kernel for a problem; partial-sum buffers hold 2 doubles per block.
+dim3 op_grid(int nx, int ny, int nz, int degree, int* tz);
+size_t op_grid_blocks(int nx, int ny, int nz, int degree);
+int vec_grid(size_t len);
+
+// One-time per-process set-up of the operator kernels of one degree (shared-memory limits);
+// called by bsk_create, never inside a stream capture.
+template <typename T>
+cudaError_t prepare_op(int degree);
+
+template <typename T>
+cudaError_t launch_op(const OpLaunch& L, cudaStream_t s);
+
+template <typename T>
+cudaError_t launch_cg_update(T* r, const T* q, size_t len, Scalars* sc, double* partials,
+                             cudaStream_t s);
+template <typename T>
+cudaError_t launch_cg_flush(T* x, const T* p0, const T* p1, size_t len, const Scalars* sc,
+                            cudaStream_t s);
+template <typename T>
+cudaError_t launch_cg_init_zero(const T* b, T* r, T* x, size_t len, const uint8_t* mask,
+                                Scalars* sc, double* partials, cudaStream_t s);
+template <typename T>
+cudaError_t launch_copy_masked(const T* src, T* dst, size_t len, const uint8_t* mask,
+                               cudaStream_t s);
+template <typename T>
+cudaError_t launch_norm2(const T* x, size_t len, Scalars* sc, double* partials, cudaStream_t s);
+
+cudaError_t launch_ir_scale_down(const double* r64, float* r32, size_t len, const Scalars* outer,
+                                 cudaStream_t s);
+cudaError_t launch_ir_update(double* x64, const float* d32, size_t len, const Scalars* outer,
+                             cudaStream_t s);
+
+}  // namespace bsk
