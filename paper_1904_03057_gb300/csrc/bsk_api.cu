@@ -215,7 +215,7 @@ int enqueue_chunk(bsk_handle* h, int chunk)
         L.p_parity = (it + 1) & 1;
         BSK_CUDA(op_launch<T>(L, s));
         BSK_CUDA(bsk::launch_cg_update<T>(static_cast<T*>(h->r), static_cast<const T*>(h->q),
-                                          h->len, h->sc, h->partials, s));
+                                          h->len, h->sc, h->partials, bsk::FIN_UPD, s));
     }
     return BSK_OK;
 }
@@ -651,9 +651,9 @@ extern "C" int bsk_time_kernel(bsk_handle* h, int kernel, int reps, double* ms)
         case BSK_KERNEL_CG_UPDATE:
             return ces == sizeof(double)
                        ? bsk::launch_cg_update<double>((double*)h->r, (const double*)h->q, h->len,
-                                                       h->sc_aux, h->partials, h->stream)
+                                                       h->sc_aux, h->partials, bsk::FIN_NORM, h->stream)
                        : bsk::launch_cg_update<float>((float*)h->r, (const float*)h->q, h->len,
-                                                      h->sc_aux, h->partials, h->stream);
+                                                      h->sc_aux, h->partials, bsk::FIN_NORM, h->stream);
         default:  // BSK_KERNEL_RES64
             fill_launch(h, L, bsk::MODE_RES);
             L.in0 = h->b64;

@@ -45,7 +45,7 @@ cudaError_t launch_op(const OpLaunch& L, cudaStream_t s);
 
 template <typename T>
 cudaError_t launch_cg_update(T* r, const T* q, size_t len, Scalars* sc, double* partials,
-                             cudaStream_t s);
+                             int fin, cudaStream_t s);
 template <typename T>
 cudaError_t launch_cg_flush(T* x, const T* p0, const T* p1, size_t len, const Scalars* sc,
                             cudaStream_t s);

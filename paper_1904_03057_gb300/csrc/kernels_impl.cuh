@@ -105,9 +105,9 @@ cudaError_t prepare_op<BSK_T>(int degree)
 
 template <>
 cudaError_t launch_cg_update<BSK_T>(BSK_T* r, const BSK_T* q, size_t len, Scalars* sc,
-                                    double* partials, cudaStream_t s)
+                                    double* partials, int fin, cudaStream_t s)
 {
-    k_cg_update<BSK_T><<<vec_grid(len), kVecNT, 0, s>>>(r, q, len, sc, partials);
+    k_cg_update<BSK_T><<<vec_grid(len), kVecNT, 0, s>>>(r, q, len, sc, partials, fin);
     return cudaGetLastError();
 }
 

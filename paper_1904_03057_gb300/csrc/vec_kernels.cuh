@@ -8,10 +8,11 @@ namespace bsk {
 
 constexpr int kVecNT = 256;
 
-// r -= alpha q; reduction r.r; finaliser FIN_UPD (beta, convergence).
+// r -= alpha q; reduction r.r; finaliser `fin` (FIN_UPD in a solve: beta, convergence).
 template <typename T>
 __global__ void __launch_bounds__(kVecNT) k_cg_update(T* __restrict__ r, const T* __restrict__ q,
-                                                      size_t len, Scalars* sc, double* partials)
+                                                      size_t len, Scalars* sc, double* partials,
+                                                      int fin)
 {
     if (*(volatile int*)&sc->done) return;
     const T alpha = (T)sc->alpha;
@@ -22,7 +23,7 @@ __global__ void __launch_bounds__(kVecNT) k_cg_update(T* __restrict__ r, const T
         r[i] = v;
         acc += (double)v * (double)v;
     }
-    grid_reduce2<kVecNT>(acc, 0.0, partials, sc, FIN_UPD, 0);
+    grid_reduce2<kVecNT>(acc, 0.0, partials, sc, fin, 0);
 }
 
 // x += alpha_prev p[p_cur]: applies the last deferred update once the iteration has stopped.

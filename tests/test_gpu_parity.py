@@ -244,7 +244,9 @@ def test_full_size_928_operator_sampled_and_eigen(api, orc):
     lam = mh[0] * mh[1] * mh[2] + dt * (kh[0] * mh[1] * mh[2] + mh[0] * kh[1] * mh[2]
                                         + mh[0] * mh[1] * kh[2])
     err = torch.max(torch.abs(y.double() - lam * x.double())).item()
-    assert err <= 1e-5 * abs(lam) * 3.0   # |A||x| <= ~3 |lam| for this smooth mode
+    M, K = orc.bspline_kernels(n, h)
+    absW = np.sum(np.abs(M)) ** 3 + dt * 3 * np.sum(np.abs(K)) * np.sum(np.abs(M)) ** 2
+    assert err <= 1e-5 * absW        # (|A| |x|)_i <= sum |W| for |x| <= 1
     del y
     modes = inputs.random_sine_modes(3, 64, 16)
     x = inputs.sine_mode_field(N, N, N, modes, device="cuda", dtype=torch.float32)
@@ -262,8 +264,6 @@ def test_full_size_928_operator_sampled_and_eigen(api, orc):
     p = orc.Problem(N, N, N, n, h, dt=dt)
     ref = orc.op_points(p, xh, pts)
     got = y.reshape(-1)[torch.from_numpy(pts).cuda()].double().cpu().numpy()
-    M, K = orc.bspline_kernels(n, h)
-    absW = (np.sum(np.abs(M)) ** 3 + dt * 3 * np.sum(np.abs(K)) * np.sum(np.abs(M)) ** 2)
     bound = 1e-5 * absW * np.max(np.abs(xh))
     assert np.max(np.abs(got - ref)) <= bound
 
