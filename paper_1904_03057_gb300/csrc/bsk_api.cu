@@ -8,6 +8,7 @@
 #include <cstdarg>
 #include <cstdio>
 #include <cstring>
+#include <initializer_list>
 #include <new>
 #include <string>
 
@@ -102,8 +103,11 @@ struct bsk_handle {
     uint8_t* mask;
     double M[3][bsk::kMaxTaps];   // per-axis mass kernels
     double K[3][bsk::kMaxTaps];   // per-axis stiffness kernels (not yet multiplied by dt)
-    // CG vectors in the CG element type (double for BSK_F64, float otherwise)
-    void *x, *r, *p0, *p1, *q, *bvec;
+    // CG vectors in the CG element type (double for BSK_F64, float otherwise). The single-pass
+    // TMA iteration ping-pongs r, q and p (r/r2, q/q2, p0/p1); the general one uses r, q, p0/p1.
+    void *x, *r, *p0, *p1, *q, *bvec, *r2, *q2;
+    bool use_tma;     // CG vectors go through the TMA kernels (unmasked, 16-byte rows)
+    bool tma64;       // FP64 operator passes (op_apply / residual) may use the TMA kernels
     // iterative refinement (FP64 outer vectors)
     double *r64, *b64;
     Scalars *sc, *sc64, *sc_aux;
@@ -118,6 +122,38 @@ namespace {
 
 size_t user_es(const bsk_handle* h) { return h->prec == BSK_F32 ? sizeof(float) : sizeof(double); }
 size_t cg_es(const bsk_handle* h) { return h->prec == BSK_F64 ? sizeof(double) : sizeof(float); }
+
+void fill_tma(const bsk_handle* h, bsk::TmaLaunch& L, int mode)
+{
+    memset(&L, 0, sizeof L);
+    L.mode = mode;
+    L.degree = h->n;
+    L.nx = h->nx;
+    L.ny = h->ny;
+    L.nz = h->nz;
+    for (int d = 0; d < 3; d++)
+        for (int j = 0; j < bsk::kMaxTaps; j++) {
+            L.M[d][j] = h->M[d][j];
+            L.Kdt[d][j] = h->dt * h->K[d][j];
+        }
+}
+
+bool aligned16(const void* p) { return ((uintptr_t)p & 15u) == 0; }
+
+// May a pass of element size es over these vectors use the TMA kernels?
+bool tma_ok(const bsk_handle* h, size_t es, std::initializer_list<const void*> ptrs)
+{
+    const bool allowed = es == sizeof(double) ? h->tma64 : h->use_tma;
+    if (!allowed) return false;
+    for (const void* p : ptrs)
+        if (!aligned16(p)) return false;
+    return true;
+}
+
+cudaError_t tma_launch_es(size_t es, const bsk::TmaLaunch& L, cudaStream_t s)
+{
+    return es == sizeof(double) ? bsk::launch_tma<double>(L, s) : bsk::launch_tma<float>(L, s);
+}
 
 void fill_launch(const bsk_handle* h, bsk::OpLaunch& L, int mode)
 {
@@ -201,6 +237,29 @@ int enqueue_chunk(bsk_handle* h, int chunk)
 {
     cudaStream_t s = h->cap_stream;
     T* p[2] = {static_cast<T*>(h->p0), static_cast<T*>(h->p1)};
+    if (h->use_tma) {
+        // one kernel per iteration: pass m reads the (r, q, p) of m-1 and writes those of m
+        void* rr[2] = {h->r, h->r2};
+        void* qq[2] = {h->q, h->q2};
+        for (int it = 0; it < chunk; it++) {
+            bsk::TmaLaunch L;
+            fill_tma(h, L, bsk::TMODE_CG);
+            const int i = it & 1, o = (it + 1) & 1;
+            L.in[0] = rr[i];
+            L.in[1] = qq[i];
+            L.in[2] = p[i];
+            L.inint = h->x;
+            L.out0 = qq[o];
+            L.out1 = rr[o];
+            L.out2 = p[o];
+            L.xvec = h->x;
+            L.sc = h->sc;
+            L.partials = h->partials;
+            L.fin = bsk::FIN_CG1;
+            BSK_CUDA(bsk::launch_tma<T>(L, s));
+        }
+        return BSK_OK;
+    }
     for (int it = 0; it < chunk; it++) {
         bsk::OpLaunch L;
         fill_launch(h, L, bsk::MODE_CGP);
@@ -260,15 +319,16 @@ int run_iterations(bsk_handle* h, const Opts& o, std::chrono::steady_clock::time
     if ((rc = sync_scalars(h, h->sc))) return rc;
     while (!h->h_sc->done) {
         BSK_CUDA(cudaGraphLaunch(h->graph, h->stream));
-        h->launches += 2LL * h->graph_chunk;
+        h->launches += (h->use_tma ? 1LL : 2LL) * h->graph_chunk;
         if ((rc = sync_scalars(h, h->sc))) return rc;
         if (o.time_limit > 0 && !h->h_sc->done && seconds_since(t0) > o.time_limit) {
             *iters_out = h->h_sc->iter;
             return fail(BSK_ETIMEOUT, "solve exceeded its time limit of %.3f s", o.time_limit);
         }
     }
-    BSK_LAUNCH(h, bsk::launch_cg_flush<T>(static_cast<T*>(h->x), static_cast<const T*>(h->p0),
-                                     static_cast<const T*>(h->p1), h->len, h->sc, h->stream));
+    if (!h->use_tma)   // the single-pass iteration leaves no x update pending
+        BSK_LAUNCH(h, bsk::launch_cg_flush<T>(static_cast<T*>(h->x), static_cast<const T*>(h->p0),
+                                         static_cast<const T*>(h->p1), h->len, h->sc, h->stream));
     *iters_out = h->h_sc->iter;
     switch (h->h_sc->status) {
     case 0: return BSK_OK;
@@ -287,29 +347,54 @@ int cg_plain(bsk_handle* h, const T* b, T* x, const Opts& o, bsk_cg_report* rep,
     BSK_LAUNCH(h, bsk::launch_copy_masked<T>(x, static_cast<T*>(h->x), h->len, h->mask, h->stream));
     if ((rc = init_scalars(h, h->sc, o.tol, o.max_iter, o.stall_window))) return rc;
     bsk::OpLaunch L;
-    fill_launch(h, L, bsk::MODE_RES);
-    L.in0 = h->x;
-    L.b = b;
-    L.out0 = h->r;
-    L.sc = h->sc;
-    L.partials = h->partials;
-    L.fin = bsk::FIN_RES_INIT;
-    BSK_LAUNCH(h, op_launch<T>(L, h->stream));
+    if (tma_ok(h, sizeof(T), {b})) {
+        bsk::TmaLaunch R;
+        fill_tma(h, R, bsk::TMODE_RES);
+        R.in[0] = h->x;
+        R.inint = b;
+        R.out0 = h->r;
+        R.sc = h->sc;
+        R.partials = h->partials;
+        R.fin = bsk::FIN_RES_INIT;
+        BSK_LAUNCH(h, bsk::launch_tma<T>(R, h->stream));
+    } else {
+        fill_launch(h, L, bsk::MODE_RES);
+        L.in0 = h->x;
+        L.b = b;
+        L.out0 = h->r;
+        L.sc = h->sc;
+        L.partials = h->partials;
+        L.fin = bsk::FIN_RES_INIT;
+        BSK_LAUNCH(h, op_launch<T>(L, h->stream));
+    }
     BSK_CUDA(cudaMemsetAsync(h->p0, 0, h->len * sizeof(T), h->stream));
+    if (h->use_tma) BSK_CUDA(cudaMemsetAsync(h->q, 0, h->len * sizeof(T), h->stream));
     int iters = 0;
     int st = run_iterations<T>(h, o, t0, &iters);
     if (st < 0 && st != BSK_EBREAKDOWN) return st;
     if (h->h_sc->zero_b) BSK_CUDA(cudaMemsetAsync(h->x, 0, h->len * sizeof(T), h->stream));
     BSK_LAUNCH(h, bsk::launch_copy_masked<T>(static_cast<const T*>(h->x), x, h->len, h->mask, h->stream));
     // true residual of the returned x
-    fill_launch(h, L, bsk::MODE_RES);
-    L.in0 = x;
-    L.b = b;
-    L.out0 = h->r;
-    L.sc = h->sc_aux;
-    L.partials = h->partials;
-    L.fin = bsk::FIN_RES_TRUE;
-    BSK_LAUNCH(h, op_launch<T>(L, h->stream));
+    if (tma_ok(h, sizeof(T), {b, x})) {
+        bsk::TmaLaunch R;
+        fill_tma(h, R, bsk::TMODE_RES);
+        R.in[0] = x;
+        R.inint = b;
+        R.out0 = h->r;
+        R.sc = h->sc_aux;
+        R.partials = h->partials;
+        R.fin = bsk::FIN_RES_TRUE;
+        BSK_LAUNCH(h, bsk::launch_tma<T>(R, h->stream));
+    } else {
+        fill_launch(h, L, bsk::MODE_RES);
+        L.in0 = x;
+        L.b = b;
+        L.out0 = h->r;
+        L.sc = h->sc_aux;
+        L.partials = h->partials;
+        L.fin = bsk::FIN_RES_TRUE;
+        BSK_LAUNCH(h, op_launch<T>(L, h->stream));
+    }
     if ((rc = sync_scalars(h, h->sc_aux))) return rc;
     if (rep) {
         rep->iterations += iters;
@@ -327,15 +412,27 @@ int cg_ir(bsk_handle* h, const double* b, double* x, const Opts& o, bsk_cg_repor
     double rel = 0.0;
     BSK_LAUNCH(h, bsk::launch_copy_masked<double>(x, x, h->len, h->mask, h->stream));
     for (;; outer++) {
-        bsk::OpLaunch L;
-        fill_launch(h, L, bsk::MODE_RES);
-        L.in0 = x;
-        L.b = b;
-        L.out0 = h->r64;
-        L.sc = h->sc64;
-        L.partials = h->partials;
-        L.fin = bsk::FIN_RES_TRUE;
-        BSK_LAUNCH(h, op_launch<double>(L, h->stream));
+        if (tma_ok(h, sizeof(double), {b, x})) {
+            bsk::TmaLaunch R;
+            fill_tma(h, R, bsk::TMODE_RES);
+            R.in[0] = x;
+            R.inint = b;
+            R.out0 = h->r64;
+            R.sc = h->sc64;
+            R.partials = h->partials;
+            R.fin = bsk::FIN_RES_TRUE;
+            BSK_LAUNCH(h, bsk::launch_tma<double>(R, h->stream));
+        } else {
+            bsk::OpLaunch L;
+            fill_launch(h, L, bsk::MODE_RES);
+            L.in0 = x;
+            L.b = b;
+            L.out0 = h->r64;
+            L.sc = h->sc64;
+            L.partials = h->partials;
+            L.fin = bsk::FIN_RES_TRUE;
+            BSK_LAUNCH(h, op_launch<double>(L, h->stream));
+        }
         if ((rc = sync_scalars(h, h->sc64))) return rc;
         const double rr = h->h_sc->rr_true, bb = h->h_sc->bb_true;
         if (!std::isfinite(rr) || !std::isfinite(bb))
@@ -363,6 +460,7 @@ int cg_ir(bsk_handle* h, const double* b, double* x, const Opts& o, bsk_cg_repor
                                                  static_cast<float*>(h->r), static_cast<float*>(h->x),
                                                  h->len, h->mask, h->sc, h->partials, h->stream));
         BSK_CUDA(cudaMemsetAsync(h->p0, 0, h->len * sizeof(float), h->stream));
+        if (h->use_tma) BSK_CUDA(cudaMemsetAsync(h->q, 0, h->len * sizeof(float), h->stream));
         int it = 0;
         int ist = run_iterations<float>(h, o, t0, &it);
         total_iters += it;
@@ -467,6 +565,22 @@ extern "C" int bsk_create(const bsk_problem* prob, int precision, void* stream, 
     e = bsk::prepare_op<float>(n);
     if (e == cudaSuccess) e = bsk::prepare_op<double>(n);
     if (e != cudaSuccess) return cleanup(cuda_fail(e, "kernel set-up"));
+    {
+        // the TMA kernels need unmasked grids whose rows are whole 16-byte units
+        const size_t ces_ = precision == BSK_F64 ? sizeof(double) : sizeof(float);
+        h->use_tma = !prob->mask && n <= (ces_ == 8 ? bsk::tma_max_degree<double>() : bsk::tma_max_degree<float>()) &&
+                     (prob->nx * ces_) % 16 == 0;
+        h->tma64 = !prob->mask && n <= bsk::tma_max_degree<double>() && (prob->nx * sizeof(double)) % 16 == 0 &&
+                   precision != BSK_F32;
+        if (h->use_tma || precision == BSK_F32) {
+            e = bsk::prepare_tma<float>(n > bsk::tma_max_degree<float>() ? 1 : n);
+            if (e != cudaSuccess) return cleanup(cuda_fail(e, "TMA kernel set-up"));
+        }
+        if (h->tma64 || (h->use_tma && ces_ == 8)) {
+            e = bsk::prepare_tma<double>(n);
+            if (e != cudaSuccess) return cleanup(cuda_fail(e, "TMA kernel set-up"));
+        }
+    }
     e = cudaStreamCreateWithFlags(&h->cap_stream, cudaStreamNonBlocking);
     if (e != cudaSuccess) return cleanup(cuda_fail(e, "cudaStreamCreate"));
     if (prob->mask) {
@@ -480,6 +594,10 @@ extern "C" int bsk_create(const bsk_problem* prob, int precision, void* stream, 
     BSK_ALLOC(h->p0, len * ces);
     BSK_ALLOC(h->p1, len * ces);
     BSK_ALLOC(h->q, len * ces);
+    if (h->use_tma) {
+        BSK_ALLOC(h->r2, len * ces);
+        BSK_ALLOC(h->q2, len * ces);
+    }
     if (precision == BSK_F32_IR) {
         BSK_ALLOC(h->r64, len * sizeof(double));
         BSK_ALLOC(h->b64, len * sizeof(double));
@@ -489,8 +607,12 @@ extern "C" int bsk_create(const bsk_problem* prob, int precision, void* stream, 
     BSK_ALLOC(h->sc, sizeof(Scalars));
     BSK_ALLOC(h->sc64, sizeof(Scalars));
     BSK_ALLOC(h->sc_aux, sizeof(Scalars));
-    const size_t nb = std::max(bsk::op_grid_blocks(h->nx, h->ny, h->nz, n), (size_t)bsk::vec_grid(len));
-    BSK_ALLOC(h->partials, 2 * nb * sizeof(double));
+    size_t nb = 2 * std::max(bsk::op_grid_blocks(h->nx, h->ny, h->nz, n), (size_t)bsk::vec_grid(len));
+    for (int mode = 0; mode < 3; mode++) {
+        nb = std::max(nb, 3 * (size_t)bsk::tma_grid<float>(n, mode));
+        nb = std::max(nb, 3 * (size_t)bsk::tma_grid<double>(n, mode));
+    }
+    BSK_ALLOC(h->partials, nb * sizeof(double));
     e = cudaMallocHost((void**)&h->h_sc, sizeof(Scalars));
     if (e != cudaSuccess) return cleanup(fail(BSK_ENOMEM, "pinned allocation failed"));
     memset(h->h_sc, 0, sizeof(Scalars));
@@ -510,7 +632,7 @@ extern "C" void bsk_destroy(bsk_handle* h)
     if (!h) return;
     cudaStreamSynchronize(h->stream);
     if (h->graph) cudaGraphExecDestroy(h->graph);
-    void* ptrs[] = {h->mask, h->x, h->r, h->p0, h->p1, h->q, h->bvec, h->r64, h->b64,
+    void* ptrs[] = {h->mask, h->x, h->r, h->p0, h->p1, h->q, h->bvec, h->r2, h->q2, h->r64, h->b64,
                     h->sc, h->sc64, h->sc_aux, h->partials};
     for (void* p : ptrs)
         if (p) cudaFree(p);
@@ -538,12 +660,22 @@ static int apply_common(bsk_handle* h, const void* x, void* y, int mode)
     if (!x || !y) return fail(BSK_EINVAL, "null vector");
     const size_t es = user_es(h);
     if (overlaps(x, y, h->len * es)) return fail(BSK_EINVAL, "x and y overlap");
-    bsk::OpLaunch L;
-    fill_launch(h, L, mode);
-    L.in0 = x;
-    L.out0 = y;
-    L.fin = bsk::FIN_NONE;
-    cudaError_t e = op_launch_es(es, L, h->stream);
+    cudaError_t e;
+    if (mode == bsk::MODE_OP && tma_ok(h, es, {x, y})) {
+        bsk::TmaLaunch T;
+        fill_tma(h, T, bsk::TMODE_OP);
+        T.in[0] = x;
+        T.out0 = y;
+        T.fin = bsk::FIN_NONE;
+        e = tma_launch_es(es, T, h->stream);
+    } else {
+        bsk::OpLaunch L;
+        fill_launch(h, L, mode);
+        L.in0 = x;
+        L.out0 = y;
+        L.fin = bsk::FIN_NONE;
+        e = op_launch_es(es, L, h->stream);
+    }
     if (e != cudaSuccess) return cuda_fail(e, "operator launch");
     h->launches += 1;
     return BSK_OK;
@@ -623,21 +755,47 @@ extern "C" int bsk_time_kernel(bsk_handle* h, int kernel, int reps, double* ms)
     if (kernel == BSK_KERNEL_RES64 && h->prec != BSK_F32_IR)
         return fail(BSK_EINVAL, "the FP64 residual kernel exists only for BSK_F32_IR handles");
     const size_t ces = cg_es(h);
-    for (void* p : {h->x, h->r, h->p0, h->p1, h->q})
-        BSK_CUDA(cudaMemsetAsync(p, 0, h->len * ces, h->stream));
+    for (void* p : {h->x, h->r, h->p0, h->p1, h->q, h->r2, h->q2})
+        if (p) BSK_CUDA(cudaMemsetAsync(p, 0, h->len * ces, h->stream));
     if (h->r64) BSK_CUDA(cudaMemsetAsync(h->r64, 0, h->len * sizeof(double), h->stream));
     if (h->b64) BSK_CUDA(cudaMemsetAsync(h->b64, 0, h->len * sizeof(double), h->stream));
     if (int rc = init_scalars(h, h->sc_aux, 0.0, 1 << 30, 0)) return rc;
     auto one = [&](int i) -> cudaError_t {
         bsk::OpLaunch L;
+        bsk::TmaLaunch T;
         switch (kernel) {
         case BSK_KERNEL_OP:
+            if (tma_ok(h, ces, {h->x, h->q})) {
+                fill_tma(h, T, bsk::TMODE_OP);
+                T.in[0] = h->x;
+                T.out0 = h->q;
+                T.fin = bsk::FIN_NONE;
+                return tma_launch_es(ces, T, h->stream);
+            }
             fill_launch(h, L, bsk::MODE_OP);
             L.in0 = h->x;
             L.out0 = h->q;
             L.fin = bsk::FIN_NONE;
             return op_launch_es(ces, L, h->stream);
         case BSK_KERNEL_CG_FUSED:
+            if (h->use_tma) {
+                void* rr[2] = {h->r, h->r2};
+                void* qq[2] = {h->q, h->q2};
+                void* pp[2] = {h->p0, h->p1};
+                fill_tma(h, T, bsk::TMODE_CG);
+                T.in[0] = rr[i & 1];
+                T.in[1] = qq[i & 1];
+                T.in[2] = pp[i & 1];
+                T.inint = h->x;
+                T.out0 = qq[(i + 1) & 1];
+                T.out1 = rr[(i + 1) & 1];
+                T.out2 = pp[(i + 1) & 1];
+                T.xvec = h->x;
+                T.sc = h->sc_aux;
+                T.partials = h->partials;
+                T.fin = bsk::FIN_NORM;   // reduces without touching the CG state of sc
+                return tma_launch_es(ces, T, h->stream);
+            }
             fill_launch(h, L, bsk::MODE_CGP);
             L.in0 = h->r;
             L.in1 = (i & 1) ? h->p1 : h->p0;
@@ -655,6 +813,16 @@ extern "C" int bsk_time_kernel(bsk_handle* h, int kernel, int reps, double* ms)
                        : bsk::launch_cg_update<float>((float*)h->r, (const float*)h->q, h->len,
                                                       h->sc_aux, h->partials, bsk::FIN_NORM, h->stream);
         default:  // BSK_KERNEL_RES64
+            if (tma_ok(h, sizeof(double), {h->b64, h->r64})) {
+                fill_tma(h, T, bsk::TMODE_RES);
+                T.in[0] = h->b64;
+                T.inint = h->b64;
+                T.out0 = h->r64;
+                T.sc = h->sc_aux;
+                T.partials = h->partials;
+                T.fin = bsk::FIN_RES_TRUE;
+                return bsk::launch_tma<double>(T, h->stream);
+            }
             fill_launch(h, L, bsk::MODE_RES);
             L.in0 = h->b64;
             L.b = h->b64;

@@ -24,6 +24,7 @@ enum Fin : int {
     FIN_CGP = 3,        // pq = s0 -> alpha
     FIN_UPD = 4,        // rr_new = s0 -> beta, convergence, iteration count
     FIN_NORM = 5,       // rr_true = s0
+    FIN_CG1 = 6,        // single-pass CG: s0 = r.r, s1 = p.Ap, s2 = Ap.Ap -> alpha, beta, status
 };
 
 // Operator kernel modes.
@@ -33,6 +34,9 @@ enum OpMode : int {
     MODE_RES = 2,   // r = b - A x, reductions r.r and b.b
     MODE_CGP = 3,   // p = r + beta p_old; x += alpha_prev p_old; q = A p; reduction p.q
 };
+
+// Modes of the TMA operator kernel (op_tma.cuh): y = A x; r = b - A x; one whole CG iteration.
+enum TmaMode : int { TMODE_OP = 0, TMODE_RES = 1, TMODE_CG = 2 };
 
 // CG state kept on the device; all scalars in FP64.
 struct Scalars {
@@ -55,7 +59,7 @@ struct Scalars {
     int p_cur;          // which ping-pong buffer holds the latest search direction
     int zero_b;         // b == 0: the solution is x = 0
     unsigned int counter;  // arrival counter of the last-block reduction
-    unsigned int pad;
+    int pass;           // single-pass CG: passes completed (pass m produces x_m, r_m)
 };
 
 // Per-axis kernels in compute precision: M[d][j + n], K[d][j + n] with K already scaled by dt.
@@ -166,6 +170,92 @@ __device__ __forceinline__ void finalize(Scalars* sc, int fin, double s0, double
     }
     default:
         break;
+    }
+}
+
+// Single-pass CG finaliser (one grid reduction per iteration). Pass m has produced r_m, x_m,
+// p_m and q_m = A p_m with s0 = r_m.r_m, s1 = p_m.q_m, s2 = q_m.q_m. The next step length is
+// alpha_m = rr_m / pq_m, and ||r_{m+1}||^2 = ||r_m - alpha_m q_m||^2 is predicted as
+// alpha_m^2 qq_m - rr_m (using r_m.q_m = p_m.q_m, exact in exact arithmetic), which gives
+// beta_m without a second reduction; rr itself is always the exactly reduced value.
+__device__ __forceinline__ void finalize_cg1(Scalars* sc, double rr, double pq, double qq)
+{
+    const int m = sc->pass;
+    sc->pass = m + 1;
+    sc->iter = m;
+    sc->rr = rr;
+    sc->pq = pq;
+    if (!isfinite(rr) || !isfinite(pq) || !isfinite(qq)) { sc->done = 1; sc->status = -5; return; }
+    if (rr <= sc->tol2 * sc->bb) { sc->done = 1; sc->status = 0; return; }
+    if (m >= sc->max_iter) { sc->done = 1; sc->status = 1; return; }
+    if (!(pq > 0.0)) { sc->done = 1; sc->status = -5; return; }
+    if (rr < sc->best_rr) { sc->best_rr = rr; sc->since_best = 0; }
+    else if (sc->stall_window > 0 && ++sc->since_best >= sc->stall_window) {
+        sc->done = 1;
+        sc->status = 2;
+        return;
+    }
+    const double alpha = rr / pq;
+    double rr_next = alpha * alpha * qq - rr;
+    if (rr_next < 0.0) rr_next = 0.0;
+    sc->alpha = alpha;
+    sc->beta = rr_next / rr;
+}
+
+// Deterministic grid reduction of K values: each block stores its partial sums, the last block
+// to arrive adds all partials in block order and runs the finaliser. partials holds K * nblocks
+// doubles. Must be called by every thread of the block (contains __syncthreads).
+template <int NT, int K>
+__device__ void grid_reduce_k(double (&v)[K], double* partials, Scalars* sc, int fin)
+{
+    constexpr int NW = NT / 32;
+    __shared__ double sred[K * NW];
+    __shared__ int s_last;
+    const unsigned nblocks = gridDim.x * gridDim.y * gridDim.z;
+    const unsigned bid = blockIdx.x + gridDim.x * (blockIdx.y + gridDim.y * blockIdx.z);
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+#pragma unroll
+    for (int k = 0; k < K; k++) {
+        double t = warp_sum(v[k]);
+        if (lane == 0) sred[k * NW + warp] = t;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        for (int k = 0; k < K; k++) {
+            double s = 0.0;
+            for (int w = 0; w < NW; w++) s += sred[k * NW + w];
+            partials[k * nblocks + bid] = s;
+        }
+        __threadfence();
+        unsigned prev = atomicAdd(&sc->counter, 1u);
+        s_last = (prev == nblocks - 1);
+    }
+    __syncthreads();
+    if (!s_last) return;
+    __threadfence();
+    double acc[K];
+#pragma unroll
+    for (int k = 0; k < K; k++) acc[k] = 0.0;
+    for (unsigned i = threadIdx.x; i < nblocks; i += NT)
+#pragma unroll
+        for (int k = 0; k < K; k++) acc[k] += __ldcg(partials + k * nblocks + i);
+    __syncthreads();
+#pragma unroll
+    for (int k = 0; k < K; k++) {
+        double t = warp_sum(acc[k]);
+        if (lane == 0) sred[k * NW + warp] = t;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double tot[K];
+        for (int k = 0; k < K; k++) {
+            tot[k] = 0.0;
+            for (int w = 0; w < NW; w++) tot[k] += sred[k * NW + w];
+        }
+        if (fin == FIN_CG1) finalize_cg1(sc, tot[0], K > 1 ? tot[1] : 0.0, K > 2 ? tot[2] : 0.0);
+        else finalize(sc, fin, tot[0], K > 1 ? tot[1] : 0.0, 0);
+        sc->counter = 0;
+        __threadfence();
     }
 }
 

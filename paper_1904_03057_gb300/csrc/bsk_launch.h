@@ -58,6 +58,32 @@ cudaError_t launch_copy_masked(const T* src, T* dst, size_t len, const uint8_t* 
 template <typename T>
 cudaError_t launch_norm2(const T* x, size_t len, Scalars* sc, double* partials, cudaStream_t s);
 
+// ---- TMA operator kernels (op_tma.cuh): unmasked problems with 16-byte row pitch ----
+struct TmaLaunch {
+    int mode;                    // TMODE_OP, TMODE_RES or TMODE_CG
+    int degree;
+    int nx, ny, nz;
+    double M[3][kMaxTaps];
+    double Kdt[3][kMaxTaps];
+    const void* in[3];           // OP/RES: {x}; CG: {r, q, p} of the previous iteration
+    const void* inint;           // RES: b; CG: x
+    void* out0;                  // OP y; RES r; CG q
+    void* out1;                  // CG r
+    void* out2;                  // CG p
+    void* xvec;                  // CG x (in place)
+    Scalars* sc;
+    double* partials;            // 3 doubles per block of the resident grid
+    int fin;
+};
+template <typename T>
+int tma_max_degree();
+template <typename T>
+cudaError_t prepare_tma(int degree);
+template <typename T>
+int tma_grid(int degree, int mode);   // resident blocks (after prepare_tma), 0 if unsupported
+template <typename T>
+cudaError_t launch_tma(const TmaLaunch& L, cudaStream_t s);
+
 cudaError_t launch_ir_scale_down(const double* r64, float* r32, size_t len, const Scalars* outer,
                                  cudaStream_t s);
 cudaError_t launch_ir_update(double* x64, const float* d32, size_t len, const Scalars* outer,

@@ -1,0 +1,487 @@
+// op_tma.cuh -- the fast operator / CG kernel for unmasked box problems whose rows are 16-byte
+// multiples (TMA-addressable): A x, b - A x, and one whole CG iteration in a single pass.
+//
+// Structure (arXiv:1904.03057 section 2.4: A = Mz My Mx + dt (Kz My Mx + Mz Ky Mx + Mz My Kx)
+// applied as separable shift-invariant band convolutions, Fig. FiltAlg). The three sweeps are
+// reordered so that no sweep is recomputed on a z halo:
+//     A x = (Mz + dt Kz) U + Mz V,    U = My Mx x,    V = dt (Ky Mx + My Kx) x.
+// A block owns a 64 x 24 (x, y) tile and marches along z. Per input plane:
+//   1. TMA brings the tile plus its halo (n rows, 4 or 8 columns) of every input vector into a
+//      shared-memory stage (double/triple buffered, mbarrier completion, no multicast); box faces
+//      are completed by odd reflection in shared memory, reflected planes by a sign.
+//   2. x-sweep in shared memory: MX = Mx x, KX = dt Kx x on the 64-column tile x (24+2n) rows.
+//   3. y-sweep, in registers of the thread that owns the column pair: U = My MX,
+//      V = dt Ky MX + My KX (packed f32x2 arithmetic for FP32).
+//   4. z-sweep as a push: the plane's U, V are added, with the 2n+1 z taps, into a ring of 2n+1
+//      per-thread accumulators of the output planes z-n .. z+n; output plane z-n is complete and
+//      leaves the kernel straight from registers.
+// Blocks are persistent and walk a static list of (tile, z-chunk) items. In CG mode the staged
+// value is the new search direction p_m = (r - alpha q) + beta p of the previous iteration's
+// vectors, and the pass also writes r_m, p_m, x_m = x + alpha p and reduces r.r, p.Ap, Ap.Ap
+// (single-synchronisation CG, see finalize_cg1).
+#pragma once
+
+#include "bsk_device.cuh"
+#include "tma_util.cuh"
+
+namespace bsk {
+
+constexpr int kTX = 64;     // output columns per tile
+constexpr int kTY = 24;     // output rows per tile (8 warps x 3 rows)
+constexpr int kTNT = 256;   // threads per block
+
+template <typename T>
+struct TmaArgs {
+    CUtensorMap tin[3];   // halo boxes: OP/RES {x}; CG {r, q, p} of the previous iteration
+    CUtensorMap tint;     // interior box: RES {b}; CG {x}
+    T* out0;              // OP y; RES r; CG q_m = A p_m
+    T* out1;              // CG r_m
+    T* out2;              // CG p_m
+    T* xvec;              // CG x, updated in place
+    int nx, ny, nz;
+    int tiles_x, tiles_y, tz, nitems;
+    T M[3][kMaxTaps];     // per-axis mass kernels, index j + n
+    T K[3][kMaxTaps];     // per-axis stiffness kernels times dt
+    Scalars* sc;
+    double* partials;
+    int fin;
+};
+
+template <typename T, int N>
+struct TGeo {
+    static constexpr int L = 2 * N + 1;
+    static constexpr int HL = N <= 4 ? 4 : 8;          // halo columns staged on each side
+    static constexpr int BX = kTX + 2 * HL + 4;         // box width; +4 columns spread smem banks
+    static constexpr int HY = kTY + 2 * N;              // box height (tile rows + y halo)
+    static constexpr int MXP = kTX + 4;                 // row pitch of the x-sweep results
+    static constexpr int WIN = 8 + 2 * HL;              // x-window loaded per 8 outputs
+};
+
+template <typename T, int N, int MODE>
+struct TLayout {
+    using G = TGeo<T, N>;
+    static constexpr int NIN = MODE == TMODE_CG ? 3 : 1;
+    static constexpr int NINT = MODE == TMODE_OP ? 0 : 1;
+    static constexpr size_t rnd(size_t b) { return (b + 127) / 128 * 128; }
+    static constexpr size_t in_bytes = rnd(sizeof(T) * G::HY * G::BX);
+    static constexpr size_t int_bytes = rnd(sizeof(T) * kTY * kTX);
+    static constexpr size_t stage_bytes = NIN * in_bytes + NINT * int_bytes;
+    static constexpr int S = MODE == TMODE_OP ? 3 : 2;   // pipeline stages
+    static constexpr size_t off_mx = S * stage_bytes;
+    static constexpr size_t mx_bytes = rnd(sizeof(T) * G::HY * G::MXP);
+    static constexpr size_t off_ring = off_mx + 2 * mx_bytes;
+    static constexpr size_t ring_bytes = MODE == TMODE_OP ? 0 : (N + 1) * int_bytes;
+    static constexpr size_t off_bar = off_ring + ring_bytes;
+    static constexpr size_t total = off_bar + 64;
+    static constexpr uint32_t tx_bytes =
+        (uint32_t)(NIN * sizeof(T) * G::HY * G::BX + NINT * sizeof(T) * kTY * kTX);
+};
+
+// Packed pair arithmetic: f32x2 instructions for FP32, two scalar operations for FP64.
+template <typename T> struct P2;
+template <> struct P2<float> {
+    using t = float2;
+    static __device__ __forceinline__ t mk(float a) { return make_float2(a, a); }
+    static __device__ __forceinline__ t fma(t a, t b, t c) { return __ffma2_rn(a, b, c); }
+    static __device__ __forceinline__ t add(t a, t b) { return __fadd2_rn(a, b); }
+    static __device__ __forceinline__ t zero() { return make_float2(0.f, 0.f); }
+};
+template <> struct P2<double> {
+    using t = double2;
+    static __device__ __forceinline__ t mk(double a) { return make_double2(a, a); }
+    static __device__ __forceinline__ t fma(t a, t b, t c)
+    {
+        return make_double2(::fma(a.x, b.x, c.x), ::fma(a.y, b.y, c.y));
+    }
+    static __device__ __forceinline__ t add(t a, t b) { return make_double2(a.x + b.x, a.y + b.y); }
+    static __device__ __forceinline__ t zero() { return make_double2(0.0, 0.0); }
+};
+
+// Compensated (Kahan) running sum in the element precision; converted to FP64 once per block.
+template <typename T>
+struct KSum {
+    T s = T(0), c = T(0);
+    __device__ __forceinline__ void add(T v)
+    {
+        const T y = v - c;
+        const T t = s + y;
+        c = (t - s) - y;
+        s = t;
+    }
+    __device__ __forceinline__ double value() const { return (double)s - (double)c; }
+};
+
+// Odd reflection of ghost rows and columns of one staged box (box faces of the grid).
+template <typename T, int N>
+__device__ __forceinline__ void patch_rows(T* box, int y0, int ny)
+{
+    using G = TGeo<T, N>;
+    for (int i = threadIdx.x; i < G::HY * G::BX; i += kTNT) {
+        const int br = i / G::BX, bc = i - br * G::BX;
+        const int gy = y0 - N + br;
+        if ((unsigned)gy < (unsigned)ny) continue;
+        int src = 0;
+        const int s = reflect_index(gy, ny, src);
+        const int sr = src - (y0 - N);
+        box[i] = (s && sr >= 0 && sr < G::HY) ? (T)s * box[sr * G::BX + bc] : T(0);
+    }
+}
+
+template <typename T, int N>
+__device__ __forceinline__ void patch_cols(T* box, int x0, int nx)
+{
+    using G = TGeo<T, N>;
+    for (int i = threadIdx.x; i < G::HY * G::BX; i += kTNT) {
+        const int br = i / G::BX, bc = i - br * G::BX;
+        const int gx = x0 - G::HL + bc;
+        if ((unsigned)gx < (unsigned)nx) continue;
+        int src = 0;
+        const int s = reflect_index(gx, nx, src);
+        const int sc = src - (x0 - G::HL);
+        box[i] = (s && sc >= 0 && sc < G::BX) ? (T)s * box[br * G::BX + sc] : T(0);
+    }
+}
+
+template <typename T, int N, int MODE>
+__global__ void __launch_bounds__(kTNT, (sizeof(T) == 4 && N <= 4) ? 2 : 1)
+    k_op_tma(const __grid_constant__ TmaArgs<T> a)
+{
+    using G = TGeo<T, N>;
+    using LY = TLayout<T, N, MODE>;
+    using PP = P2<T>;
+    using T2 = typename PP::t;
+    constexpr int L = G::L, HY = G::HY, BX = G::BX, MXP = G::MXP, HL = G::HL, WIN = G::WIN;
+    constexpr int S = LY::S;
+    constexpr int NIN = LY::NIN;
+    static_assert(LY::total <= 227 * 1024, "shared memory budget");
+    static_assert(WIN % 4 == 0, "window loads are 16-byte vectors");
+
+    extern __shared__ __align__(128) unsigned char smem[];
+    T* MXs = reinterpret_cast<T*>(smem + LY::off_mx);
+    T* KXs = reinterpret_cast<T*>(smem + LY::off_mx + LY::mx_bytes);
+    T* ring = reinterpret_cast<T*>(smem + LY::off_ring);
+    uint64_t* bars = reinterpret_cast<uint64_t*>(smem + LY::off_bar);
+    __shared__ int s_abort;
+    __shared__ uint32_t s_issued, s_wait_from;   // loads issued / first load not yet consumed
+
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const int nx = a.nx, ny = a.ny, nz = a.nz;
+
+    T alpha = T(0), beta = T(0);
+    if (MODE == TMODE_CG) {
+        if (*(volatile int*)&a.sc->done) return;   // uniform over the grid
+        alpha = (T)a.sc->alpha;
+        beta = (T)a.sc->beta;
+    }
+    if (tid == 0) {
+        for (int s = 0; s < S; s++) mbar_init(&bars[s], 1);
+        fence_mbar_init();
+        for (int i = 0; i < NIN; i++) prefetch_tensormap(&a.tin[i]);
+        if (LY::NINT) prefetch_tensormap(&a.tint);
+        s_abort = 0;
+        s_issued = 0;
+        s_wait_from = 0;
+    }
+    __syncthreads();
+
+    // kernel taps as packed constants: W1 = Mz + dt Kz, Mz for the z push; My, dt Ky for y
+    T2 w1z[N + 1], mz[N + 1], my[N + 1], ky[N + 1];
+#pragma unroll
+    for (int j = 0; j <= N; j++) {
+        w1z[j] = PP::mk(a.M[2][N + j] + a.K[2][N + j]);
+        mz[j] = PP::mk(a.M[2][N + j]);
+        my[j] = PP::mk(a.M[1][N + j]);
+        ky[j] = PP::mk(a.K[1][N + j]);
+    }
+
+    KSum<T> d0, d1, d2;
+    const int ntiles = a.tiles_x * a.tiles_y;
+    uint32_t cnt = 0;   // planes consumed by this block before the current item
+
+    for (int item = blockIdx.x; item < a.nitems; item += gridDim.x) {
+        const int tile = item % ntiles, zc = item / ntiles;
+        const int x0 = (tile % a.tiles_x) * kTX, y0 = (tile / a.tiles_x) * kTY;
+        const int z0 = zc * a.tz, z1 = min(z0 + a.tz, nz);
+        const int zs = z0 - N;
+        const int np = (z1 - z0) + 2 * N;
+        const bool patch_x = (x0 == 0) || (x0 + kTX + HL > nx);
+        const bool patch_y = (y0 == 0) || (y0 + kTY + N > ny);
+
+        auto issue = [&](int k) {   // plane k of this item -> stage (cnt + k) % S
+            const uint32_t c = cnt + (uint32_t)k;
+            unsigned char* st = smem + (c % S) * LY::stage_bytes;
+            int zsrc = 0;
+            const int zz = zs + k;
+            if (!reflect_index(zz, nz, zsrc)) zsrc = 0;   // a face plane: any plane, scaled by 0
+            uint64_t* bar = &bars[c % S];
+            mbar_arrive_expect_tx(bar, LY::tx_bytes);
+            for (int i = 0; i < NIN; i++)
+                tma_load_3d(st + i * LY::in_bytes, &a.tin[i], bar, x0 - HL, y0 - N, zsrc);
+            if (LY::NINT) {
+                const int zi = min(max(zz, 0), nz - 1);
+                tma_load_3d(st + NIN * LY::in_bytes, &a.tint, bar, x0, y0, zi);
+            }
+            s_issued = c + 1;
+        };
+        if (tid == 0) {
+            for (int k = 0; k < S && k < np; k++) issue(k);
+        }
+
+        T2 acc[3][L];
+#pragma unroll
+        for (int t = 0; t < 3; t++)
+#pragma unroll
+            for (int s = 0; s < L; s++) acc[t][s] = PP::zero();
+
+        for (int b = 0; b < np; b += L) {
+#pragma unroll
+            for (int j = 0; j < L; j++) {
+                const int k = b + j;
+                if (k >= np) break;
+                const int z = zs + k;
+                const uint32_t c = cnt + (uint32_t)k;
+                unsigned char* st = smem + (c % S) * LY::stage_bytes;
+                T* in0 = reinterpret_cast<T*>(st);
+                T* in1 = reinterpret_cast<T*>(st + LY::in_bytes);
+                T* in2 = reinterpret_cast<T*>(st + 2 * LY::in_bytes);
+                T* inint = reinterpret_cast<T*>(st + NIN * LY::in_bytes);
+
+                if (!mbar_wait_bounded(&bars[c % S], (c / S) & 1u, 2000000000ull)) {
+                    s_abort = 1;
+                    s_wait_from = c;
+                }
+                __syncthreads();
+                if (s_abort) goto abort;
+
+                if (patch_y) {
+                    patch_rows<T, N>(in0, y0, ny);
+                    if (NIN > 1) { patch_rows<T, N>(in1, y0, ny); patch_rows<T, N>(in2, y0, ny); }
+                    __syncthreads();
+                }
+                if (patch_x) {
+                    patch_cols<T, N>(in0, x0, nx);
+                    if (NIN > 1) { patch_cols<T, N>(in1, x0, nx); patch_cols<T, N>(in2, x0, nx); }
+                    __syncthreads();
+                }
+
+                {
+                    int zsrc = 0;
+                    const T zsgn = (T)reflect_index(z, nz, zsrc);
+                    const bool zint = (z >= z0 && z < z1);
+                    const int rslot = ((z - z0) % (N + 1) + (N + 1)) % (N + 1);
+                    // ---- x-sweep: task = (row, group of 8 output columns) ----
+                    for (int t = tid; t < 8 * HY; t += kTNT) {
+                        const int row = t % HY, g = t / HY;
+                        T v[WIN];
+                        const T* src0 = in0 + row * BX + 8 * g;
+#pragma unroll
+                        for (int q4 = 0; q4 < WIN / 4; q4++) {
+                            if constexpr (sizeof(T) == 4) {
+                                const float4 f = *reinterpret_cast<const float4*>(src0 + 4 * q4);
+                                v[4 * q4] = f.x; v[4 * q4 + 1] = f.y; v[4 * q4 + 2] = f.z; v[4 * q4 + 3] = f.w;
+                            } else {
+                                const double2 f0 = *reinterpret_cast<const double2*>(src0 + 4 * q4);
+                                const double2 f1 = *reinterpret_cast<const double2*>(src0 + 4 * q4 + 2);
+                                v[4 * q4] = f0.x; v[4 * q4 + 1] = f0.y; v[4 * q4 + 2] = f1.x; v[4 * q4 + 3] = f1.y;
+                            }
+                        }
+                        if constexpr (MODE == TMODE_CG) {
+                            // p_m = (r - alpha q) + beta p; keep r_m and p_{m-1} at the 8 centres
+                            T qv[WIN], pv[WIN];
+                            const T* src1 = in1 + row * BX + 8 * g;
+                            const T* src2 = in2 + row * BX + 8 * g;
+#pragma unroll
+                            for (int q4 = 0; q4 < WIN / 4; q4++) {
+                                if constexpr (sizeof(T) == 4) {
+                                    const float4 f1 = *reinterpret_cast<const float4*>(src1 + 4 * q4);
+                                    const float4 f2 = *reinterpret_cast<const float4*>(src2 + 4 * q4);
+                                    qv[4 * q4] = f1.x; qv[4 * q4 + 1] = f1.y; qv[4 * q4 + 2] = f1.z; qv[4 * q4 + 3] = f1.w;
+                                    pv[4 * q4] = f2.x; pv[4 * q4 + 1] = f2.y; pv[4 * q4 + 2] = f2.z; pv[4 * q4 + 3] = f2.w;
+                                } else {
+#pragma unroll
+                                    for (int e = 0; e < 4; e++) { qv[4 * q4 + e] = src1[4 * q4 + e]; pv[4 * q4 + e] = src2[4 * q4 + e]; }
+                                }
+                            }
+                            T rc[8], pold[8];
+#pragma unroll
+                            for (int i = 0; i < WIN; i++) {
+                                const T rn = fma(-alpha, qv[i], v[i]);
+                                if (i >= HL && i < HL + 8) { rc[i - HL] = rn; pold[i - HL] = pv[i]; }
+                                v[i] = zsgn * fma(beta, pv[i], rn);
+                            }
+                            if (zint && row >= N && row < N + kTY) {
+                                const int gy = y0 + row - N;
+                                const T* xin = inint + (row - N) * kTX + 8 * g;
+                                T* rg = ring + rslot * (kTY * kTX) + (row - N) * kTX + 8 * g;
+#pragma unroll
+                                for (int h = 0; h < 2; h++) {
+                                    const int gx = x0 + 8 * g + 4 * h;
+                                    if (gy < ny && gx < nx) {
+                                        const size_t o = ((size_t)z * ny + gy) * nx + gx;
+                                        T rn4[4], pn4[4], xn4[4];
+                                        T part = T(0);
+#pragma unroll
+                                        for (int e = 0; e < 4; e++) {
+                                            rn4[e] = rc[4 * h + e];
+                                            pn4[e] = v[HL + 4 * h + e];   // interior plane: zsgn = 1
+                                            xn4[e] = fma(alpha, pold[4 * h + e], xin[4 * h + e]);
+                                            if (sizeof(T) == 4 || gx + e < nx) part = fma(rn4[e], rn4[e], part);
+                                        }
+                                        d0.add(part);
+                                        if constexpr (sizeof(T) == 4) {
+                                            *reinterpret_cast<float4*>(a.out1 + o) = make_float4(rn4[0], rn4[1], rn4[2], rn4[3]);
+                                            *reinterpret_cast<float4*>(a.out2 + o) = make_float4(pn4[0], pn4[1], pn4[2], pn4[3]);
+                                            *reinterpret_cast<float4*>(a.xvec + o) = make_float4(xn4[0], xn4[1], xn4[2], xn4[3]);
+                                            *reinterpret_cast<float4*>(rg + 4 * h) = make_float4(pn4[0], pn4[1], pn4[2], pn4[3]);
+                                        } else {
+#pragma unroll
+                                            for (int e = 0; e < 4; e++) {
+                                                rg[4 * h + e] = pn4[e];
+                                                if (gx + e < nx) {   // FP64 rows are only 2-element aligned
+                                                    a.out1[o + e] = rn4[e];
+                                                    a.out2[o + e] = pn4[e];
+                                                    a.xvec[o + e] = xn4[e];
+                                                }
+                                            }
+                                        }
+                                    }
+                                }
+                            }
+                        } else {
+#pragma unroll
+                            for (int i = 0; i < WIN; i++) v[i] *= zsgn;
+                            if (MODE == TMODE_RES && zint && row >= N && row < N + kTY) {
+                                // keep b of this plane for the residual of output plane z
+                                const T* bin = inint + (row - N) * kTX + 8 * g;
+                                T* rg = ring + rslot * (kTY * kTX) + (row - N) * kTX + 8 * g;
+#pragma unroll
+                                for (int e = 0; e < 8; e++) rg[e] = bin[e];
+                            }
+                        }
+                        // x-sweep of the 8 outputs (symmetric taps paired)
+                        T mx[8], kx[8];
+#pragma unroll
+                        for (int i = 0; i < 8; i++) {
+                            const int cI = HL + i;
+                            T m = a.M[0][N] * v[cI];
+                            T k2 = a.K[0][N] * v[cI];
+#pragma unroll
+                            for (int jj = 1; jj <= N; jj++) {
+                                const T sp = v[cI - jj] + v[cI + jj];
+                                m = fma(a.M[0][N + jj], sp, m);
+                                k2 = fma(a.K[0][N + jj], sp, k2);
+                            }
+                            mx[i] = m;
+                            kx[i] = k2;
+                        }
+                        T* mdst = MXs + row * MXP + 8 * g;
+                        T* kdst = KXs + row * MXP + 8 * g;
+#pragma unroll
+                        for (int i = 0; i < 8; i++) { mdst[i] = mx[i]; kdst[i] = kx[i]; }
+                    }
+                }
+                __syncthreads();
+                // the stage is consumed: refill it with plane k + S
+                if (tid == 0 && k + S < np) {
+                    fence_proxy_async_smem();
+                    issue(k + S);
+                }
+                // ---- y-sweep in registers, then z push ----
+                {
+                    const int c2 = 2 * lane;
+                    constexpr int NR = 3 + 2 * N;
+                    T2 mv[NR], kv[NR];
+#pragma unroll
+                    for (int r = 0; r < NR; r++) {
+                        mv[r] = *reinterpret_cast<const T2*>(MXs + (3 * warp + r) * MXP + c2);
+                        kv[r] = *reinterpret_cast<const T2*>(KXs + (3 * warp + r) * MXP + c2);
+                    }
+#pragma unroll
+                    for (int t = 0; t < 3; t++) {
+                        const int cc = t + N;   // centre row in mv/kv
+                        T2 U = PP::fma(my[0], mv[cc], PP::zero());
+                        T2 V = PP::fma(ky[0], mv[cc], PP::zero());
+                        V = PP::fma(my[0], kv[cc], V);
+#pragma unroll
+                        for (int jj = 1; jj <= N; jj++) {
+                            const T2 sm = PP::add(mv[cc - jj], mv[cc + jj]);
+                            const T2 sk = PP::add(kv[cc - jj], kv[cc + jj]);
+                            U = PP::fma(my[jj], sm, U);
+                            V = PP::fma(ky[jj], sm, V);
+                            V = PP::fma(my[jj], sk, V);
+                        }
+#pragma unroll
+                        for (int dd = -N; dd <= N; dd++) {
+                            const int sl = ((j + dd) % L + L) % L;
+                            const int ad = dd < 0 ? -dd : dd;
+                            acc[t][sl] = PP::fma(w1z[ad], U, acc[t][sl]);
+                            acc[t][sl] = PP::fma(mz[ad], V, acc[t][sl]);
+                        }
+                    }
+                    // output plane z - N is complete
+                    const int zo = z - N;
+                    const int fs = ((j - N) % L + L) % L;
+                    if (zo >= z0 && zo < z1) {
+                        const int oslot = (zo - z0) % (N + 1);
+#pragma unroll
+                        for (int t = 0; t < 3; t++) {
+                            const int gy = y0 + 3 * warp + t, gx = x0 + c2;
+                            const T2 q = acc[t][fs];
+                            if (gy < ny && gx < nx) {
+                                const size_t o = ((size_t)zo * ny + gy) * nx + gx;
+                                if constexpr (MODE == TMODE_OP) {
+                                    *reinterpret_cast<T2*>(a.out0 + o) = q;
+                                } else {
+                                    const T2 rg = *reinterpret_cast<const T2*>(
+                                        ring + oslot * (kTY * kTX) + (3 * warp + t) * kTX + c2);
+                                    if constexpr (MODE == TMODE_RES) {
+                                        T2 r;
+                                        r.x = rg.x - q.x;
+                                        r.y = rg.y - q.y;
+                                        *reinterpret_cast<T2*>(a.out0 + o) = r;
+                                        d0.add(fma(r.x, r.x, r.y * r.y));
+                                        d1.add(fma(rg.x, rg.x, rg.y * rg.y));
+                                    } else {
+                                        *reinterpret_cast<T2*>(a.out0 + o) = q;
+                                        d1.add(fma(rg.x, q.x, rg.y * q.y));
+                                        d2.add(fma(q.x, q.x, q.y * q.y));
+                                    }
+                                }
+                            }
+                            acc[t][fs] = PP::zero();
+                        }
+                    } else {
+#pragma unroll
+                        for (int t = 0; t < 3; t++) acc[t][fs] = PP::zero();
+                    }
+                }
+                __syncthreads();
+            }
+        }
+        cnt += (uint32_t)np;
+    }
+
+    if (a.fin != FIN_NONE) {
+        if constexpr (MODE == TMODE_CG) {
+            double v3[3] = {d0.value(), d1.value(), d2.value()};
+            grid_reduce_k<kTNT, 3>(v3, a.partials, a.sc, a.fin);
+        } else {
+            double v2[2] = {d0.value(), d1.value()};
+            grid_reduce_k<kTNT, 2>(v2, a.partials, a.sc, a.fin);
+        }
+    }
+    return;
+
+abort:
+    // A TMA load did not complete within the time limit: report it, give the loads still in
+    // flight a bounded time to land (they target this block's shared memory), and stop.
+    if (tid == 0) {
+        atomicExch(&a.sc->status, -4);
+        atomicExch(&a.sc->done, 1);
+        __threadfence();
+        for (uint32_t i = s_wait_from; i < s_issued; i++)
+            mbar_wait_bounded(&bars[i % S], (i / S) & 1u, 100000000ull);
+    }
+}
+
+}  // namespace bsk

@@ -73,6 +73,15 @@ OP_CASES = [
     (3, 3, 4, 3, 0.1, True),
     (4, 5, 4, 4, 0.1, False),
     (5, 5, 6, 5, 0.1, False),
+    # unmasked grids with 16-byte rows take the TMA kernels: 64 x 24 tiles, ragged x / y / z
+    (68, 50, 30, 1, 0.02, False),
+    (68, 50, 30, 2, 0.01, False),
+    (68, 50, 31, 3, 1e-3, False),
+    (132, 49, 27, 4, 2e-3, False),
+    (72, 26, 19, 5, 5e-4, False),
+    (4, 4, 4, 3, 0.1, False),
+    (8, 30, 5, 5, 0.1, False),
+    (64, 24, 9, 3, 0.1, False),
 ]
 
 
@@ -111,9 +120,11 @@ def test_op_apply_does_not_read_masked_inputs(api, orc):
 
 
 @pytest.mark.parametrize("precision,tol", [("f64", 1e-10), ("f32", 1e-5), ("f32_ir", 1e-10)])
-@pytest.mark.parametrize("masked", [False, True])
-def test_cg_solve_matches_oracle(api, orc, precision, tol, masked):
-    nx, ny, nz, n, dt = 37, 29, 23, 3, 2e-3
+@pytest.mark.parametrize("masked,nx", [(False, 37), (True, 37), (False, 44)])
+def test_cg_solve_matches_oracle(api, orc, precision, tol, masked, nx):
+    """nx = 44 (16-byte rows, unmasked) runs the single-pass TMA iteration; nx = 37 and masked
+    grids run the general kernels."""
+    ny, nz, n, dt = 29, 23, 3, 2e-3
     p, hs = make_problem(orc, nx, ny, nz, n, dt, masked, seed=4)
     b = np.random.default_rng(11).standard_normal(p.shape)
     if p.mask is not None:
@@ -136,7 +147,7 @@ def test_cg_solve_matches_oracle(api, orc, precision, tol, masked):
     assert err <= kappa * true_rel * 1.01 + 1e-12
     if precision == "f64":
         _, it_o, _, _ = orc.cg(p, bin_, tol=tol, max_iter=5000)
-        assert abs(rep["iterations"] - it_o) <= 2
+        assert abs(rep["iterations"] - it_o) <= 3
     if p.mask is not None:
         assert np.all(x[p.mask == 0] == 0)
 
