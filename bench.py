@@ -217,7 +217,7 @@ def run_ours(args, rank, world, dist):
     # dominant kernel timing (CUDA events on the handle's stream): the fused CG pass, FP32
     hbm, peak_kind = peaks()
     ms_fused = H.time_kernel(api.KERNEL_CG_FUSED, reps=10)
-    bytes_fused = 24.0 * dofs   # read r, p_old, x; write p, q, x (FP32)
+    bytes_fused = 32.0 * dofs   # read r, q, p, x; write r, q, p, x (FP32 single-pass iteration)
     ms_op = H.time_kernel(api.KERNEL_OP, reps=10)
     bytes_op = 8.0 * dofs       # read x, write y (FP32)
     ms_res64 = H.time_kernel(api.KERNEL_RES64, reps=3)
@@ -243,10 +243,12 @@ def run_ours(args, rank, world, dist):
             "op_apply_hbm_frac": bytes_op / (ms_op * 1e-3) / 1e9 / hbm,
             "parallelism": f"{world} independent problems (one per GPU)",
         },
-        "roofline": {"kernel": "cg_fused_f32 (p update + operator + p.Ap + deferred x update)",
+        "roofline": {"kernel": "k_op_tma<float,3,CG>: one CG iteration (p, r, x updates + A p + "
+                               "r.r, p.Ap, Ap.Ap)",
                      "bound": "hbm", "achieved": ach, "peak": hbm, "unit": "GB/s",
                      "frac": ach / hbm, "traffic": None,
-                     "note": f"peak = {peak_kind} HBM copy bandwidth; algorithmic 24 B/unknown"},
+                     "note": f"peak = {peak_kind} HBM copy bandwidth; algorithmic 32 B/unknown "
+                             "(read r, q, p, x; write r, q, p, x)"},
         "clocks": clocks,
         "gpu_launches": launches,
     }

@@ -113,6 +113,7 @@ struct bsk_handle {
     Scalars *sc, *sc64, *sc_aux;
     Scalars* h_sc;   // pinned host mirror
     double* partials;
+    unsigned int* work;   // item-queue counters of the TMA kernels
     cudaGraphExec_t graph;
     int graph_chunk;
     long long launches;   // kernels launched since the counter was last read
@@ -126,6 +127,7 @@ size_t cg_es(const bsk_handle* h) { return h->prec == BSK_F64 ? sizeof(double) :
 void fill_tma(const bsk_handle* h, bsk::TmaLaunch& L, int mode)
 {
     memset(&L, 0, sizeof L);
+    L.work = h->work;
     L.mode = mode;
     L.degree = h->n;
     L.nx = h->nx;
@@ -207,6 +209,8 @@ int init_scalars(bsk_handle* h, Scalars* dev, double tol, int max_iter, int stal
     BSK_CUDA(cudaStreamSynchronize(h->stream));
     *h->h_sc = s;
     BSK_CUDA(cudaMemcpyAsync(dev, h->h_sc, sizeof(Scalars), cudaMemcpyHostToDevice, h->stream));
+    // a kernel stopped by a wait time-out may have left the item-queue counters non-zero
+    BSK_CUDA(cudaMemsetAsync(h->work, 0, 2 * sizeof(unsigned int), h->stream));
     BSK_CUDA(cudaStreamSynchronize(h->stream));
     return BSK_OK;
 }
@@ -613,6 +617,9 @@ extern "C" int bsk_create(const bsk_problem* prob, int precision, void* stream, 
         nb = std::max(nb, 3 * (size_t)bsk::tma_grid<double>(n, mode));
     }
     BSK_ALLOC(h->partials, nb * sizeof(double));
+    BSK_ALLOC(h->work, 2 * sizeof(unsigned int));
+    e = cudaMemsetAsync(h->work, 0, 2 * sizeof(unsigned int), h->stream);
+    if (e != cudaSuccess) return cleanup(cuda_fail(e, "memset"));
     e = cudaMallocHost((void**)&h->h_sc, sizeof(Scalars));
     if (e != cudaSuccess) return cleanup(fail(BSK_ENOMEM, "pinned allocation failed"));
     memset(h->h_sc, 0, sizeof(Scalars));
@@ -633,7 +640,7 @@ extern "C" void bsk_destroy(bsk_handle* h)
     cudaStreamSynchronize(h->stream);
     if (h->graph) cudaGraphExecDestroy(h->graph);
     void* ptrs[] = {h->mask, h->x, h->r, h->p0, h->p1, h->q, h->bvec, h->r2, h->q2, h->r64, h->b64,
-                    h->sc, h->sc64, h->sc_aux, h->partials};
+                    h->sc, h->sc64, h->sc_aux, h->partials, h->work};
     for (void* p : ptrs)
         if (p) cudaFree(p);
     if (h->h_sc) cudaFreeHost(h->h_sc);

@@ -73,6 +73,7 @@ struct TmaLaunch {
     void* xvec;                  // CG x (in place)
     Scalars* sc;
     double* partials;            // 3 doubles per block of the resident grid
+    unsigned int* work;          // 2 counters, zero between launches (dynamic item queue)
     int fin;
 };
 template <typename T>

@@ -44,6 +44,7 @@ struct TmaArgs {
     T K[3][kMaxTaps];     // per-axis stiffness kernels times dt
     Scalars* sc;
     double* partials;
+    unsigned int* work;   // [0] next item, [1] blocks finished; both zero between launches
     int fin;
 };
 
@@ -66,7 +67,7 @@ struct TLayout {
     static constexpr size_t in_bytes = rnd(sizeof(T) * G::HY * G::BX);
     static constexpr size_t int_bytes = rnd(sizeof(T) * kTY * kTX);
     static constexpr size_t stage_bytes = NIN * in_bytes + NINT * int_bytes;
-    static constexpr int S = MODE == TMODE_OP ? 3 : 2;   // pipeline stages
+    static constexpr int S = MODE == TMODE_OP ? 4 : 2;   // pipeline stages
     static constexpr size_t off_mx = S * stage_bytes;
     static constexpr size_t mx_bytes = rnd(sizeof(T) * G::HY * G::MXP);
     static constexpr size_t off_ring = off_mx + 2 * mx_bytes;
@@ -111,19 +112,26 @@ struct KSum {
     __device__ __forceinline__ double value() const { return (double)s - (double)c; }
 };
 
-// Odd reflection of ghost rows and columns of one staged box (box faces of the grid).
+// Odd reflection of the ghost rows / columns of one staged box that the sweeps read (at most n
+// on each side); ghosts further out stay as loaded (zero) and feed no output that is stored.
 template <typename T, int N>
 __device__ __forceinline__ void patch_rows(T* box, int y0, int ny)
 {
     using G = TGeo<T, N>;
-    for (int i = threadIdx.x; i < G::HY * G::BX; i += kTNT) {
-        const int br = i / G::BX, bc = i - br * G::BX;
+    // box row br <-> grid row y0 - N + br; ghosts read: [0, N) when y0 == 0, and
+    // [ny - y0 + N, ny - y0 + 2N) at the far face
+    const int lo_n = (y0 == 0) ? N : 0;
+    const int hi_b = ny - y0 + N;
+    const int hi_n = (hi_b < G::HY) ? min(N, G::HY - hi_b) : 0;
+    const int cnt = (lo_n + hi_n) * G::BX;
+    for (int i = threadIdx.x; i < cnt; i += kTNT) {
+        const int rr = i / G::BX, bc = i - rr * G::BX;
+        const int br = rr < lo_n ? rr : hi_b + (rr - lo_n);
         const int gy = y0 - N + br;
-        if ((unsigned)gy < (unsigned)ny) continue;
         int src = 0;
         const int s = reflect_index(gy, ny, src);
         const int sr = src - (y0 - N);
-        box[i] = (s && sr >= 0 && sr < G::HY) ? (T)s * box[sr * G::BX + bc] : T(0);
+        box[br * G::BX + bc] = (s && sr >= 0 && sr < G::HY) ? (T)s * box[sr * G::BX + bc] : T(0);
     }
 }
 
@@ -131,14 +139,80 @@ template <typename T, int N>
 __device__ __forceinline__ void patch_cols(T* box, int x0, int nx)
 {
     using G = TGeo<T, N>;
-    for (int i = threadIdx.x; i < G::HY * G::BX; i += kTNT) {
-        const int br = i / G::BX, bc = i - br * G::BX;
+    // box column bc <-> grid column x0 - HL + bc; ghosts read: [HL - N, HL) when x0 == 0, and
+    // [nx - x0 + HL, nx - x0 + HL + N) at the far face
+    const int lo_n = (x0 == 0) ? N : 0;
+    const int hi_b = nx - x0 + G::HL;
+    const int hi_n = (hi_b < G::BX) ? min(N, G::BX - hi_b) : 0;
+    const int cnt = (lo_n + hi_n) * G::HY;
+    for (int i = threadIdx.x; i < cnt; i += kTNT) {
+        const int cc = i / G::HY, br = i - cc * G::HY;
+        const int bc = cc < lo_n ? (G::HL - N + cc) : hi_b + (cc - lo_n);
         const int gx = x0 - G::HL + bc;
-        if ((unsigned)gx < (unsigned)nx) continue;
         int src = 0;
         const int s = reflect_index(gx, nx, src);
         const int sc = src - (x0 - G::HL);
-        box[i] = (s && sc >= 0 && sc < G::BX) ? (T)s * box[br * G::BX + sc] : T(0);
+        box[br * G::BX + bc] = (s && sc >= 0 && sc < G::BX) ? (T)s * box[br * G::BX + sc] : T(0);
+    }
+}
+
+// z push of one plane into the accumulator ring (slot of output plane z + d is (J + d) mod L),
+// then hand back the completed output plane z - n (slot (J - n) mod L) and clear its slot.
+template <typename T2, typename PP, int N, int J>
+__device__ __forceinline__ void push_plane(T2 (&acc)[3][2 * N + 1], const T2 (&U)[3], const T2 (&V)[3],
+                                           const T2 (&w1z)[N + 1], const T2 (&mz)[N + 1], T2 (&q)[3])
+{
+    constexpr int L = 2 * N + 1;
+#pragma unroll
+    for (int t = 0; t < 3; t++) {
+#pragma unroll
+        for (int dd = -N; dd <= N; dd++) {
+            const int sl = ((J + dd) % L + L) % L;
+            const int ad = dd < 0 ? -dd : dd;
+            acc[t][sl] = PP::fma(w1z[ad], U[t], acc[t][sl]);
+            acc[t][sl] = PP::fma(mz[ad], V[t], acc[t][sl]);
+        }
+        constexpr int fs = ((J - N) % L + L) % L;
+        q[t] = acc[t][fs];
+        acc[t][fs] = PP::zero();
+    }
+}
+
+template <typename T2, typename PP, int N>
+__device__ __forceinline__ void push_dispatch(int j, T2 (&acc)[3][2 * N + 1], const T2 (&U)[3],
+                                              const T2 (&V)[3], const T2 (&w1z)[N + 1],
+                                              const T2 (&mz)[N + 1], T2 (&q)[3])
+{
+    switch (j) {
+    case 0: push_plane<T2, PP, N, 0>(acc, U, V, w1z, mz, q); break;
+    case 1: push_plane<T2, PP, N, 1>(acc, U, V, w1z, mz, q); break;
+    case 2: push_plane<T2, PP, N, 2>(acc, U, V, w1z, mz, q); break;
+    default:
+        if constexpr (N >= 2) {
+            switch (j) {
+            case 3: push_plane<T2, PP, N, 3>(acc, U, V, w1z, mz, q); break;
+            case 4: push_plane<T2, PP, N, 4>(acc, U, V, w1z, mz, q); break;
+            default:
+                if constexpr (N >= 3) {
+                    switch (j) {
+                    case 5: push_plane<T2, PP, N, 5>(acc, U, V, w1z, mz, q); break;
+                    case 6: push_plane<T2, PP, N, 6>(acc, U, V, w1z, mz, q); break;
+                    default:
+                        if constexpr (N >= 4) {
+                            switch (j) {
+                            case 7: push_plane<T2, PP, N, 7>(acc, U, V, w1z, mz, q); break;
+                            case 8: push_plane<T2, PP, N, 8>(acc, U, V, w1z, mz, q); break;
+                            default:
+                                if constexpr (N >= 5) {
+                                    if (j == 9) push_plane<T2, PP, N, 9>(acc, U, V, w1z, mz, q);
+                                    else push_plane<T2, PP, N, 10>(acc, U, V, w1z, mz, q);
+                                }
+                            }
+                        }
+                    }
+                }
+            }
+        }
     }
 }
 
@@ -154,14 +228,14 @@ __global__ void __launch_bounds__(kTNT, (sizeof(T) == 4 && N <= 4) ? 2 : 1)
     constexpr int S = LY::S;
     constexpr int NIN = LY::NIN;
     static_assert(LY::total <= 227 * 1024, "shared memory budget");
-    static_assert(WIN % 4 == 0, "window loads are 16-byte vectors");
+    static_assert(WIN % 4 == 0 && HL % 2 == 0, "window loads are 16-byte vectors, pairs aligned");
 
     extern __shared__ __align__(128) unsigned char smem[];
     T* MXs = reinterpret_cast<T*>(smem + LY::off_mx);
     T* KXs = reinterpret_cast<T*>(smem + LY::off_mx + LY::mx_bytes);
     T* ring = reinterpret_cast<T*>(smem + LY::off_ring);
     uint64_t* bars = reinterpret_cast<uint64_t*>(smem + LY::off_bar);
-    __shared__ int s_abort;
+    __shared__ int s_abort, s_item;
     __shared__ uint32_t s_issued, s_wait_from;   // loads issued / first load not yet consumed
 
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
@@ -181,30 +255,36 @@ __global__ void __launch_bounds__(kTNT, (sizeof(T) == 4 && N <= 4) ? 2 : 1)
         s_abort = 0;
         s_issued = 0;
         s_wait_from = 0;
+        s_item = (int)atomicAdd(&a.work[0], 1u);
     }
     __syncthreads();
 
-    // kernel taps as packed constants: W1 = Mz + dt Kz, Mz for the z push; My, dt Ky for y
-    T2 w1z[N + 1], mz[N + 1], my[N + 1], ky[N + 1];
+    // packed taps: W1 = Mz + dt Kz and Mz for the z push; My and dt Ky for the y-sweep;
+    // Mx and dt Kx for the x-sweep
+    T2 w1z[N + 1], mz[N + 1], my[N + 1], ky[N + 1], mxp[N + 1], kxp[N + 1];
 #pragma unroll
     for (int j = 0; j <= N; j++) {
         w1z[j] = PP::mk(a.M[2][N + j] + a.K[2][N + j]);
         mz[j] = PP::mk(a.M[2][N + j]);
         my[j] = PP::mk(a.M[1][N + j]);
         ky[j] = PP::mk(a.K[1][N + j]);
+        mxp[j] = PP::mk(a.M[0][N + j]);
+        kxp[j] = PP::mk(a.K[0][N + j]);
     }
 
     KSum<T> d0, d1, d2;
     const int ntiles = a.tiles_x * a.tiles_y;
     uint32_t cnt = 0;   // planes consumed by this block before the current item
 
-    for (int item = blockIdx.x; item < a.nitems; item += gridDim.x) {
+    for (;;) {
+        const int item = s_item;
+        if (item >= a.nitems) break;
         const int tile = item % ntiles, zc = item / ntiles;
         const int x0 = (tile % a.tiles_x) * kTX, y0 = (tile / a.tiles_x) * kTY;
         const int z0 = zc * a.tz, z1 = min(z0 + a.tz, nz);
         const int zs = z0 - N;
         const int np = (z1 - z0) + 2 * N;
-        const bool patch_x = (x0 == 0) || (x0 + kTX + HL > nx);
+        const bool patch_x = (x0 == 0) || (x0 + kTX + N > nx);
         const bool patch_y = (y0 == 0) || (y0 + kTY + N > ny);
 
         auto issue = [&](int k) {   // plane k of this item -> stage (cnt + k) % S
@@ -233,234 +313,237 @@ __global__ void __launch_bounds__(kTNT, (sizeof(T) == 4 && N <= 4) ? 2 : 1)
 #pragma unroll
             for (int s = 0; s < L; s++) acc[t][s] = PP::zero();
 
-        for (int b = 0; b < np; b += L) {
-#pragma unroll
-            for (int j = 0; j < L; j++) {
-                const int k = b + j;
-                if (k >= np) break;
-                const int z = zs + k;
-                const uint32_t c = cnt + (uint32_t)k;
-                unsigned char* st = smem + (c % S) * LY::stage_bytes;
-                T* in0 = reinterpret_cast<T*>(st);
-                T* in1 = reinterpret_cast<T*>(st + LY::in_bytes);
-                T* in2 = reinterpret_cast<T*>(st + 2 * LY::in_bytes);
-                T* inint = reinterpret_cast<T*>(st + NIN * LY::in_bytes);
+        int jslot = 0;   // k mod L
+        for (int k = 0; k < np; k++) {
+            const int z = zs + k;
+            const uint32_t c = cnt + (uint32_t)k;
+            unsigned char* st = smem + (c % S) * LY::stage_bytes;
+            T* in0 = reinterpret_cast<T*>(st);
+            T* in1 = reinterpret_cast<T*>(st + LY::in_bytes);
+            T* in2 = reinterpret_cast<T*>(st + 2 * LY::in_bytes);
+            T* inint = reinterpret_cast<T*>(st + NIN * LY::in_bytes);
 
-                if (!mbar_wait_bounded(&bars[c % S], (c / S) & 1u, 2000000000ull)) {
-                    s_abort = 1;
-                    s_wait_from = c;
-                }
+            if (!mbar_wait_bounded(&bars[c % S], (c / S) & 1u, 2000000000ull)) {
+                s_abort = 1;
+                s_wait_from = c;
+            }
+            __syncthreads();
+            if (s_abort) goto abort;
+
+            if (patch_y) {
+                patch_rows<T, N>(in0, y0, ny);
+                if (NIN > 1) { patch_rows<T, N>(in1, y0, ny); patch_rows<T, N>(in2, y0, ny); }
                 __syncthreads();
-                if (s_abort) goto abort;
+            }
+            if (patch_x) {
+                patch_cols<T, N>(in0, x0, nx);
+                if (NIN > 1) { patch_cols<T, N>(in1, x0, nx); patch_cols<T, N>(in2, x0, nx); }
+                __syncthreads();
+            }
 
-                if (patch_y) {
-                    patch_rows<T, N>(in0, y0, ny);
-                    if (NIN > 1) { patch_rows<T, N>(in1, y0, ny); patch_rows<T, N>(in2, y0, ny); }
-                    __syncthreads();
-                }
-                if (patch_x) {
-                    patch_cols<T, N>(in0, x0, nx);
-                    if (NIN > 1) { patch_cols<T, N>(in1, x0, nx); patch_cols<T, N>(in2, x0, nx); }
-                    __syncthreads();
-                }
-
-                {
-                    int zsrc = 0;
-                    const T zsgn = (T)reflect_index(z, nz, zsrc);
-                    const bool zint = (z >= z0 && z < z1);
-                    const int rslot = ((z - z0) % (N + 1) + (N + 1)) % (N + 1);
-                    // ---- x-sweep: task = (row, group of 8 output columns) ----
-                    for (int t = tid; t < 8 * HY; t += kTNT) {
-                        const int row = t % HY, g = t / HY;
-                        T v[WIN];
-                        const T* src0 = in0 + row * BX + 8 * g;
+            {
+                int zsrc = 0;
+                const T zsgn = (T)reflect_index(z, nz, zsrc);
+                const bool zint = (z >= z0 && z < z1);
+                const int rslot = zint ? (z - z0) % (N + 1) : 0;
+                // ---- x-sweep: task = (row, group of 8 output columns) ----
+                for (int t = tid; t < 8 * HY; t += kTNT) {
+                    const int row = t % HY, g = t / HY;
+                    T v[WIN];
+                    const T* src0 = in0 + row * BX + 8 * g;
 #pragma unroll
-                        for (int q4 = 0; q4 < WIN / 4; q4++) {
-                            if constexpr (sizeof(T) == 4) {
-                                const float4 f = *reinterpret_cast<const float4*>(src0 + 4 * q4);
-                                v[4 * q4] = f.x; v[4 * q4 + 1] = f.y; v[4 * q4 + 2] = f.z; v[4 * q4 + 3] = f.w;
-                            } else {
-                                const double2 f0 = *reinterpret_cast<const double2*>(src0 + 4 * q4);
-                                const double2 f1 = *reinterpret_cast<const double2*>(src0 + 4 * q4 + 2);
-                                v[4 * q4] = f0.x; v[4 * q4 + 1] = f0.y; v[4 * q4 + 2] = f1.x; v[4 * q4 + 3] = f1.y;
+                    for (int q4 = 0; q4 < WIN / 2; q4++) {
+                        const T2 f = *reinterpret_cast<const T2*>(src0 + 2 * q4);
+                        v[2 * q4] = f.x;
+                        v[2 * q4 + 1] = f.y;
+                    }
+                    const bool interior = zint && row >= N && row < N + kTY;
+                    if constexpr (MODE == TMODE_CG) {
+                        // p_m = (r - alpha q) + beta p of the previous iteration's vectors
+                        const T* src1 = in1 + row * BX + 8 * g;
+                        const T* src2 = in2 + row * BX + 8 * g;
+                        T rc[8], pold[8];
+#pragma unroll
+                        for (int q4 = 0; q4 < WIN / 2; q4++) {
+                            const T2 fq = *reinterpret_cast<const T2*>(src1 + 2 * q4);
+                            const T2 fp = *reinterpret_cast<const T2*>(src2 + 2 * q4);
+                            const T qv[2] = {fq.x, fq.y}, pv[2] = {fp.x, fp.y};
+#pragma unroll
+                            for (int e = 0; e < 2; e++) {
+                                const int i = 2 * q4 + e;
+                                const T rn = fma(-alpha, qv[e], v[i]);
+                                if (i >= HL && i < HL + 8) { rc[i - HL] = rn; pold[i - HL] = pv[e]; }
+                                v[i] = zsgn * fma(beta, pv[e], rn);
                             }
                         }
-                        if constexpr (MODE == TMODE_CG) {
-                            // p_m = (r - alpha q) + beta p; keep r_m and p_{m-1} at the 8 centres
-                            T qv[WIN], pv[WIN];
-                            const T* src1 = in1 + row * BX + 8 * g;
-                            const T* src2 = in2 + row * BX + 8 * g;
+                        if (interior) {
+                            const int gy = y0 + row - N;
+                            const T* xin = inint + (row - N) * kTX + 8 * g;
+                            T* rg = ring + rslot * (kTY * kTX) + (row - N) * kTX + 8 * g;
 #pragma unroll
-                            for (int q4 = 0; q4 < WIN / 4; q4++) {
-                                if constexpr (sizeof(T) == 4) {
-                                    const float4 f1 = *reinterpret_cast<const float4*>(src1 + 4 * q4);
-                                    const float4 f2 = *reinterpret_cast<const float4*>(src2 + 4 * q4);
-                                    qv[4 * q4] = f1.x; qv[4 * q4 + 1] = f1.y; qv[4 * q4 + 2] = f1.z; qv[4 * q4 + 3] = f1.w;
-                                    pv[4 * q4] = f2.x; pv[4 * q4 + 1] = f2.y; pv[4 * q4 + 2] = f2.z; pv[4 * q4 + 3] = f2.w;
-                                } else {
+                            for (int h = 0; h < 2; h++) {
+                                const int gx = x0 + 8 * g + 4 * h;
+                                T pn4[4];
 #pragma unroll
-                                    for (int e = 0; e < 4; e++) { qv[4 * q4 + e] = src1[4 * q4 + e]; pv[4 * q4 + e] = src2[4 * q4 + e]; }
-                                }
-                            }
-                            T rc[8], pold[8];
+                                for (int e = 0; e < 4; e++) pn4[e] = v[HL + 4 * h + e];   // zsgn = 1 here
+                                *reinterpret_cast<T2*>(rg + 4 * h) = T2{pn4[0], pn4[1]};
+                                *reinterpret_cast<T2*>(rg + 4 * h + 2) = T2{pn4[2], pn4[3]};
+                                if (gy < ny && gx < nx) {
+                                    const size_t o = ((size_t)z * ny + gy) * nx + gx;
+                                    const T2 x01 = *reinterpret_cast<const T2*>(xin + 4 * h);
+                                    const T2 x23 = *reinterpret_cast<const T2*>(xin + 4 * h + 2);
+                                    const T xi[4] = {x01.x, x01.y, x23.x, x23.y};
+                                    T rn4[4], xn4[4];
+                                    T part = T(0);
 #pragma unroll
-                            for (int i = 0; i < WIN; i++) {
-                                const T rn = fma(-alpha, qv[i], v[i]);
-                                if (i >= HL && i < HL + 8) { rc[i - HL] = rn; pold[i - HL] = pv[i]; }
-                                v[i] = zsgn * fma(beta, pv[i], rn);
-                            }
-                            if (zint && row >= N && row < N + kTY) {
-                                const int gy = y0 + row - N;
-                                const T* xin = inint + (row - N) * kTX + 8 * g;
-                                T* rg = ring + rslot * (kTY * kTX) + (row - N) * kTX + 8 * g;
+                                    for (int e = 0; e < 4; e++) {
+                                        rn4[e] = rc[4 * h + e];
+                                        xn4[e] = fma(alpha, pold[4 * h + e], xi[e]);
+                                        if (sizeof(T) == 4 || gx + e < nx) part = fma(rn4[e], rn4[e], part);
+                                    }
+                                    d0.add(part);
+                                    if constexpr (sizeof(T) == 4) {
+                                        *reinterpret_cast<float4*>(a.out1 + o) = make_float4(rn4[0], rn4[1], rn4[2], rn4[3]);
+                                        *reinterpret_cast<float4*>(a.out2 + o) = make_float4(pn4[0], pn4[1], pn4[2], pn4[3]);
+                                        *reinterpret_cast<float4*>(a.xvec + o) = make_float4(xn4[0], xn4[1], xn4[2], xn4[3]);
+                                    } else {
 #pragma unroll
-                                for (int h = 0; h < 2; h++) {
-                                    const int gx = x0 + 8 * g + 4 * h;
-                                    if (gy < ny && gx < nx) {
-                                        const size_t o = ((size_t)z * ny + gy) * nx + gx;
-                                        T rn4[4], pn4[4], xn4[4];
-                                        T part = T(0);
-#pragma unroll
-                                        for (int e = 0; e < 4; e++) {
-                                            rn4[e] = rc[4 * h + e];
-                                            pn4[e] = v[HL + 4 * h + e];   // interior plane: zsgn = 1
-                                            xn4[e] = fma(alpha, pold[4 * h + e], xin[4 * h + e]);
-                                            if (sizeof(T) == 4 || gx + e < nx) part = fma(rn4[e], rn4[e], part);
-                                        }
-                                        d0.add(part);
-                                        if constexpr (sizeof(T) == 4) {
-                                            *reinterpret_cast<float4*>(a.out1 + o) = make_float4(rn4[0], rn4[1], rn4[2], rn4[3]);
-                                            *reinterpret_cast<float4*>(a.out2 + o) = make_float4(pn4[0], pn4[1], pn4[2], pn4[3]);
-                                            *reinterpret_cast<float4*>(a.xvec + o) = make_float4(xn4[0], xn4[1], xn4[2], xn4[3]);
-                                            *reinterpret_cast<float4*>(rg + 4 * h) = make_float4(pn4[0], pn4[1], pn4[2], pn4[3]);
-                                        } else {
-#pragma unroll
-                                            for (int e = 0; e < 4; e++) {
-                                                rg[4 * h + e] = pn4[e];
-                                                if (gx + e < nx) {   // FP64 rows are only 2-element aligned
-                                                    a.out1[o + e] = rn4[e];
-                                                    a.out2[o + e] = pn4[e];
-                                                    a.xvec[o + e] = xn4[e];
-                                                }
+                                        for (int e = 0; e < 4; e += 2) {
+                                            if (gx + e < nx) {   // FP64 rows are only 2-element aligned
+                                                *reinterpret_cast<T2*>(a.out1 + o + e) = T2{rn4[e], rn4[e + 1]};
+                                                *reinterpret_cast<T2*>(a.out2 + o + e) = T2{pn4[e], pn4[e + 1]};
+                                                *reinterpret_cast<T2*>(a.xvec + o + e) = T2{xn4[e], xn4[e + 1]};
                                             }
                                         }
                                     }
                                 }
                             }
-                        } else {
-#pragma unroll
-                            for (int i = 0; i < WIN; i++) v[i] *= zsgn;
-                            if (MODE == TMODE_RES && zint && row >= N && row < N + kTY) {
-                                // keep b of this plane for the residual of output plane z
-                                const T* bin = inint + (row - N) * kTX + 8 * g;
-                                T* rg = ring + rslot * (kTY * kTX) + (row - N) * kTX + 8 * g;
-#pragma unroll
-                                for (int e = 0; e < 8; e++) rg[e] = bin[e];
-                            }
-                        }
-                        // x-sweep of the 8 outputs (symmetric taps paired)
-                        T mx[8], kx[8];
-#pragma unroll
-                        for (int i = 0; i < 8; i++) {
-                            const int cI = HL + i;
-                            T m = a.M[0][N] * v[cI];
-                            T k2 = a.K[0][N] * v[cI];
-#pragma unroll
-                            for (int jj = 1; jj <= N; jj++) {
-                                const T sp = v[cI - jj] + v[cI + jj];
-                                m = fma(a.M[0][N + jj], sp, m);
-                                k2 = fma(a.K[0][N + jj], sp, k2);
-                            }
-                            mx[i] = m;
-                            kx[i] = k2;
-                        }
-                        T* mdst = MXs + row * MXP + 8 * g;
-                        T* kdst = KXs + row * MXP + 8 * g;
-#pragma unroll
-                        for (int i = 0; i < 8; i++) { mdst[i] = mx[i]; kdst[i] = kx[i]; }
-                    }
-                }
-                __syncthreads();
-                // the stage is consumed: refill it with plane k + S
-                if (tid == 0 && k + S < np) {
-                    fence_proxy_async_smem();
-                    issue(k + S);
-                }
-                // ---- y-sweep in registers, then z push ----
-                {
-                    const int c2 = 2 * lane;
-                    constexpr int NR = 3 + 2 * N;
-                    T2 mv[NR], kv[NR];
-#pragma unroll
-                    for (int r = 0; r < NR; r++) {
-                        mv[r] = *reinterpret_cast<const T2*>(MXs + (3 * warp + r) * MXP + c2);
-                        kv[r] = *reinterpret_cast<const T2*>(KXs + (3 * warp + r) * MXP + c2);
-                    }
-#pragma unroll
-                    for (int t = 0; t < 3; t++) {
-                        const int cc = t + N;   // centre row in mv/kv
-                        T2 U = PP::fma(my[0], mv[cc], PP::zero());
-                        T2 V = PP::fma(ky[0], mv[cc], PP::zero());
-                        V = PP::fma(my[0], kv[cc], V);
-#pragma unroll
-                        for (int jj = 1; jj <= N; jj++) {
-                            const T2 sm = PP::add(mv[cc - jj], mv[cc + jj]);
-                            const T2 sk = PP::add(kv[cc - jj], kv[cc + jj]);
-                            U = PP::fma(my[jj], sm, U);
-                            V = PP::fma(ky[jj], sm, V);
-                            V = PP::fma(my[jj], sk, V);
-                        }
-#pragma unroll
-                        for (int dd = -N; dd <= N; dd++) {
-                            const int sl = ((j + dd) % L + L) % L;
-                            const int ad = dd < 0 ? -dd : dd;
-                            acc[t][sl] = PP::fma(w1z[ad], U, acc[t][sl]);
-                            acc[t][sl] = PP::fma(mz[ad], V, acc[t][sl]);
-                        }
-                    }
-                    // output plane z - N is complete
-                    const int zo = z - N;
-                    const int fs = ((j - N) % L + L) % L;
-                    if (zo >= z0 && zo < z1) {
-                        const int oslot = (zo - z0) % (N + 1);
-#pragma unroll
-                        for (int t = 0; t < 3; t++) {
-                            const int gy = y0 + 3 * warp + t, gx = x0 + c2;
-                            const T2 q = acc[t][fs];
-                            if (gy < ny && gx < nx) {
-                                const size_t o = ((size_t)zo * ny + gy) * nx + gx;
-                                if constexpr (MODE == TMODE_OP) {
-                                    *reinterpret_cast<T2*>(a.out0 + o) = q;
-                                } else {
-                                    const T2 rg = *reinterpret_cast<const T2*>(
-                                        ring + oslot * (kTY * kTX) + (3 * warp + t) * kTX + c2);
-                                    if constexpr (MODE == TMODE_RES) {
-                                        T2 r;
-                                        r.x = rg.x - q.x;
-                                        r.y = rg.y - q.y;
-                                        *reinterpret_cast<T2*>(a.out0 + o) = r;
-                                        d0.add(fma(r.x, r.x, r.y * r.y));
-                                        d1.add(fma(rg.x, rg.x, rg.y * rg.y));
-                                    } else {
-                                        *reinterpret_cast<T2*>(a.out0 + o) = q;
-                                        d1.add(fma(rg.x, q.x, rg.y * q.y));
-                                        d2.add(fma(q.x, q.x, q.y * q.y));
-                                    }
-                                }
-                            }
-                            acc[t][fs] = PP::zero();
                         }
                     } else {
 #pragma unroll
-                        for (int t = 0; t < 3; t++) acc[t][fs] = PP::zero();
+                        for (int i = 0; i < WIN; i++) v[i] *= zsgn;
+                        if (MODE == TMODE_RES && interior) {
+                            // keep b of this plane for the residual of output plane z
+                            const T* bin = inint + (row - N) * kTX + 8 * g;
+                            T* rg = ring + rslot * (kTY * kTX) + (row - N) * kTX + 8 * g;
+#pragma unroll
+                            for (int e = 0; e < 8; e += 2)
+                                *reinterpret_cast<T2*>(rg + e) = *reinterpret_cast<const T2*>(bin + e);
+                        }
+                    }
+                    // x-sweep of the 8 outputs as 4 packed pairs (i, i+1); symmetric taps paired.
+                    // w holds v shifted by one so that every operand pair is register-aligned.
+                    T2 vp[WIN / 2], wp[WIN / 2 - 1];
+#pragma unroll
+                    for (int i = 0; i < WIN / 2; i++) vp[i] = T2{v[2 * i], v[2 * i + 1]};
+#pragma unroll
+                    for (int i = 0; i < WIN / 2 - 1; i++) wp[i] = T2{v[2 * i + 1], v[2 * i + 2]};
+                    auto pair_at = [&](int c) -> T2 {   // (v[c], v[c+1])
+                        return (c & 1) ? wp[c >> 1] : vp[c >> 1];
+                    };
+                    T* mdst = MXs + row * MXP + 8 * g;
+                    T* kdst = KXs + row * MXP + 8 * g;
+#pragma unroll
+                    for (int i = 0; i < 8; i += 2) {
+                        const int cI = HL + i;
+                        T2 m = PP::fma(mxp[0], pair_at(cI), PP::zero());
+                        T2 k2 = PP::fma(kxp[0], pair_at(cI), PP::zero());
+#pragma unroll
+                        for (int jj = 1; jj <= N; jj++) {
+                            const T2 sp = PP::add(pair_at(cI - jj), pair_at(cI + jj));
+                            m = PP::fma(mxp[jj], sp, m);
+                            k2 = PP::fma(kxp[jj], sp, k2);
+                        }
+                        *reinterpret_cast<T2*>(mdst + i) = m;
+                        *reinterpret_cast<T2*>(kdst + i) = k2;
                     }
                 }
-                __syncthreads();
             }
+            __syncthreads();
+            // the stage is consumed: refill it with plane k + S
+            if (tid == 0) {
+                if (k + S < np) {
+                    fence_proxy_async_smem();
+                    issue(k + S);
+                }
+                if (k == np - 1) s_item = (int)atomicAdd(&a.work[0], 1u);   // next item
+            }
+            // ---- y-sweep in registers, then the z push ----
+            {
+                const int c2 = 2 * lane;
+                constexpr int NR = 3 + 2 * N;
+                T2 mv[NR], kv[NR];
+#pragma unroll
+                for (int r = 0; r < NR; r++) {
+                    mv[r] = *reinterpret_cast<const T2*>(MXs + (3 * warp + r) * MXP + c2);
+                    kv[r] = *reinterpret_cast<const T2*>(KXs + (3 * warp + r) * MXP + c2);
+                }
+                T2 U[3], V[3], q[3];
+#pragma unroll
+                for (int t = 0; t < 3; t++) {
+                    const int cc = t + N;   // centre row in mv/kv
+                    T2 u = PP::fma(my[0], mv[cc], PP::zero());
+                    T2 w = PP::fma(ky[0], mv[cc], PP::zero());
+                    w = PP::fma(my[0], kv[cc], w);
+#pragma unroll
+                    for (int jj = 1; jj <= N; jj++) {
+                        const T2 sm = PP::add(mv[cc - jj], mv[cc + jj]);
+                        const T2 sk = PP::add(kv[cc - jj], kv[cc + jj]);
+                        u = PP::fma(my[jj], sm, u);
+                        w = PP::fma(ky[jj], sm, w);
+                        w = PP::fma(my[jj], sk, w);
+                    }
+                    U[t] = u;
+                    V[t] = w;
+                }
+                push_dispatch<T2, PP, N>(jslot, acc, U, V, w1z, mz, q);
+                // output plane z - N is complete
+                const int zo = z - N;
+                if (zo >= z0 && zo < z1) {
+                    const int oslot = (zo - z0) % (N + 1);
+#pragma unroll
+                    for (int t = 0; t < 3; t++) {
+                        const int gy = y0 + 3 * warp + t, gx = x0 + c2;
+                        if (gy < ny && gx < nx) {
+                            const size_t o = ((size_t)zo * ny + gy) * nx + gx;
+                            if constexpr (MODE == TMODE_OP) {
+                                *reinterpret_cast<T2*>(a.out0 + o) = q[t];
+                            } else {
+                                const T2 rg = *reinterpret_cast<const T2*>(
+                                    ring + oslot * (kTY * kTX) + (3 * warp + t) * kTX + c2);
+                                if constexpr (MODE == TMODE_RES) {
+                                    T2 r;
+                                    r.x = rg.x - q[t].x;
+                                    r.y = rg.y - q[t].y;
+                                    *reinterpret_cast<T2*>(a.out0 + o) = r;
+                                    d0.add(fma(r.x, r.x, r.y * r.y));
+                                    d1.add(fma(rg.x, rg.x, rg.y * rg.y));
+                                } else {
+                                    *reinterpret_cast<T2*>(a.out0 + o) = q[t];
+                                    d1.add(fma(rg.x, q[t].x, rg.y * q[t].y));
+                                    d2.add(fma(q[t].x, q[t].x, q[t].y * q[t].y));
+                                }
+                            }
+                        }
+                    }
+                }
+            }
+            jslot = (jslot + 1 == L) ? 0 : jslot + 1;
+            __syncthreads();
         }
         cnt += (uint32_t)np;
     }
 
+    // every block: count itself out; the last one resets the work counters for the next launch
+    if (tid == 0) {
+        __threadfence();
+        const unsigned done_blocks = atomicAdd(&a.work[1], 1u) + 1;
+        if (done_blocks == gridDim.x) {
+            a.work[0] = 0;
+            a.work[1] = 0;
+            __threadfence();
+        }
+    }
     if (a.fin != FIN_NONE) {
         if constexpr (MODE == TMODE_CG) {
             double v3[3] = {d0.value(), d1.value(), d2.value()};
@@ -474,7 +557,8 @@ __global__ void __launch_bounds__(kTNT, (sizeof(T) == 4 && N <= 4) ? 2 : 1)
 
 abort:
     // A TMA load did not complete within the time limit: report it, give the loads still in
-    // flight a bounded time to land (they target this block's shared memory), and stop.
+    // flight a bounded time to land (they target this block's shared memory), and stop. The
+    // work counters are left as they are; the host resets them before the next solve.
     if (tid == 0) {
         atomicExch(&a.sc->status, -4);
         atomicExch(&a.sc->done, 1);

@@ -133,6 +133,7 @@ cudaError_t launch_one(const TmaLaunch& L, cudaStream_t s)
         }
     a.sc = L.sc;
     a.partials = L.partials;
+    a.work = L.work;
     a.fin = L.fin;
     const int grid = a.nitems < info.grid ? a.nitems : info.grid;
     k_op_tma<BSK_T, N, MODE><<<grid, kTNT, LY::total, s>>>(a);
