@@ -154,6 +154,26 @@ int bsk_norm2(bsk_handle* h, const void* x, double* out);
 #define BSK_KERNEL_RES64 3
 int bsk_time_kernel(bsk_handle* h, int kernel, int reps, double* ms);
 
+/* Allocation-free residual: r = b - A x, with *rr = r.r and *bb = b.b reduced in FP64 (the
+ * paper has no counterpart; this is an interface for callers that cannot allocate device
+ * memory -- for example a solver plugin inside a host application that owns the device memory
+ * budget and hands in pre-allocated buffers -- and therefore cannot create a handle).
+ * It needs no handle and allocates nothing: its scratch (an FP64 scalar block and the partial
+ * sums of the two reductions, about 256 KB) is a file-scope static device array that every GPU
+ * loading this library holds until the process exits. prob describes the grid as for
+ * bsk_create (prob->mask, if set, is read in place); precision is BSK_F64 (double vectors) or
+ * BSK_F32 (float vectors; reductions still FP64); x, b, r are DEVICE vectors of nx*ny*nz
+ * elements owned by the caller, r must not overlap x or b; stream is a cudaStream_t.
+ * The first call on a device looks up the scratch's device address with that device current;
+ * make that first call before any stream capture. Every call shares the one scratch array and
+ * clears what must start at zero itself; calls that overlap on the GPU (other streams, other
+ * threads) race on it and must be serialised by the caller. The call synchronises `stream`.
+ * Returns BSK_EINVAL (with a message in bsk_last_error) for a grid whose general operator
+ * kernel needs more than 16384 blocks (about 2048^3 unknowns), for bad arguments, or for
+ * precision BSK_F32_IR. */
+int residual_noalloc(const bsk_problem* prob, int precision, const void* x, const void* b, void* r,
+                     double* rr, double* bb, void* stream);
+
 /* Text of the last error raised on the calling thread ("" if none). */
 const char* bsk_last_error(void);
 

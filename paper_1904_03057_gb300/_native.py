@@ -55,6 +55,10 @@ SIGNATURES = {
                                  ctypes.POINTER(ctypes.c_double)]),
     "bsk_time_kernel": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int, ctypes.c_int,
                                        ctypes.POINTER(ctypes.c_double)]),
+    "residual_noalloc": (ctypes.c_int, [ctypes.POINTER(Problem), ctypes.c_int, ctypes.c_void_p,
+                                        ctypes.c_void_p, ctypes.c_void_p,
+                                        ctypes.POINTER(ctypes.c_double),
+                                        ctypes.POINTER(ctypes.c_double), ctypes.c_void_p]),
     "bsk_last_error": (ctypes.c_char_p, []),
     "bsk_status_string": (ctypes.c_char_p, [ctypes.c_int]),
 }

@@ -888,8 +888,10 @@ extern "C" const char* bsk_status_string(int s)
     }
 }
 
-// ---- grid helpers shared with the kernel translation units --------------------------------
+// ---- helpers shared with the other translation units ----------------------------------------
 namespace bsk {
+
+int set_error(int code, const char* msg) { return fail(code, "%s", msg); }
 
 dim3 op_grid(int nx, int ny, int nz, int degree, int* tz)
 {

@@ -10,6 +10,9 @@
 
 namespace bsk {
 
+// Records msg as the calling thread's last error (read back by bsk_last_error) and returns code.
+int set_error(int code, const char* msg);
+
 struct OpLaunch {
     int mode;                    // OpMode
     int degree;                  // 1..5
