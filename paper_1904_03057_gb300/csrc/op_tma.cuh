@@ -112,6 +112,26 @@ struct KSum {
     __device__ __forceinline__ double value() const { return (double)s - (double)c; }
 };
 
+// W consecutive elements from 16-byte aligned shared memory, in 16-byte vector loads.
+template <typename T, int W>
+__device__ __forceinline__ void load_window(T (&v)[W], const T* src)
+{
+    static_assert(W % 4 == 0, "whole vectors");
+    if constexpr (sizeof(T) == 4) {
+#pragma unroll
+        for (int q = 0; q < W / 4; q++) {
+            const float4 f = reinterpret_cast<const float4*>(src)[q];
+            v[4 * q] = f.x; v[4 * q + 1] = f.y; v[4 * q + 2] = f.z; v[4 * q + 3] = f.w;
+        }
+    } else {
+#pragma unroll
+        for (int q = 0; q < W / 2; q++) {
+            const double2 f = reinterpret_cast<const double2*>(src)[q];
+            v[2 * q] = f.x; v[2 * q + 1] = f.y;
+        }
+    }
+}
+
 // Odd reflection of the ghost rows / columns of one staged box that the sweeps read (at most n
 // on each side); ghosts further out stay as loaded (zero) and feed no output that is stored.
 template <typename T, int N>
@@ -272,6 +292,14 @@ __global__ void __launch_bounds__(kTNT, (sizeof(T) == 4 && N <= 4) ? 2 : 1)
         kxp[j] = PP::mk(a.K[0][N + j]);
     }
 
+    // x-sweep task of this thread (one task per thread when 8 * HY <= block size)
+    constexpr int NTASK = 8 * HY;
+    constexpr bool ONE_TASK = NTASK <= kTNT;
+    const int xrow = tid % HY, xg = tid / HY;
+    // y-sweep / z push: this thread's column pair and first row in the x-sweep results
+    const T* mxb = MXs + 3 * warp * MXP + 2 * lane;
+    const T* kxb = KXs + 3 * warp * MXP + 2 * lane;
+
     KSum<T> d0, d1, d2;
     const int ntiles = a.tiles_x * a.tiles_y;
     uint32_t cnt = 0;   // planes consumed by this block before the current item
@@ -343,64 +371,56 @@ __global__ void __launch_bounds__(kTNT, (sizeof(T) == 4 && N <= 4) ? 2 : 1)
 
             {
                 int zsrc = 0;
-                const T zsgn = (T)reflect_index(z, nz, zsrc);
+                const T zsgn = (T)reflect_index(z, nz, zsrc);   // 1, -1 (mirror plane) or 0 (face)
                 const bool zint = (z >= z0 && z < z1);
                 const int rslot = zint ? (z - z0) % (N + 1) : 0;
                 // ---- x-sweep: task = (row, group of 8 output columns) ----
-                for (int t = tid; t < 8 * HY; t += kTNT) {
-                    const int row = t % HY, g = t / HY;
+#pragma unroll 1
+                for (int t = tid; t < NTASK; t += kTNT) {
+                    int row, g;
+                    if constexpr (ONE_TASK) { row = xrow; g = xg; }
+                    else { row = t % HY; g = t / HY; }
                     T v[WIN];
-                    const T* src0 = in0 + row * BX + 8 * g;
-#pragma unroll
-                    for (int q4 = 0; q4 < WIN / 2; q4++) {
-                        const T2 f = *reinterpret_cast<const T2*>(src0 + 2 * q4);
-                        v[2 * q4] = f.x;
-                        v[2 * q4 + 1] = f.y;
-                    }
+                    load_window<T, WIN>(v, in0 + row * BX + 8 * g);
                     const bool interior = zint && row >= N && row < N + kTY;
                     if constexpr (MODE == TMODE_CG) {
                         // p_m = (r - alpha q) + beta p of the previous iteration's vectors
-                        const T* src1 = in1 + row * BX + 8 * g;
-                        const T* src2 = in2 + row * BX + 8 * g;
+                        T qv[WIN], pv[WIN];
+                        load_window<T, WIN>(qv, in1 + row * BX + 8 * g);
+                        load_window<T, WIN>(pv, in2 + row * BX + 8 * g);
                         T rc[8], pold[8];
 #pragma unroll
-                        for (int q4 = 0; q4 < WIN / 2; q4++) {
-                            const T2 fq = *reinterpret_cast<const T2*>(src1 + 2 * q4);
-                            const T2 fp = *reinterpret_cast<const T2*>(src2 + 2 * q4);
-                            const T qv[2] = {fq.x, fq.y}, pv[2] = {fp.x, fp.y};
-#pragma unroll
-                            for (int e = 0; e < 2; e++) {
-                                const int i = 2 * q4 + e;
-                                const T rn = fma(-alpha, qv[e], v[i]);
-                                if (i >= HL && i < HL + 8) { rc[i - HL] = rn; pold[i - HL] = pv[e]; }
-                                v[i] = zsgn * fma(beta, pv[e], rn);
-                            }
+                        for (int i = 0; i < WIN; i++) {
+                            const T rn = fma(-alpha, qv[i], v[i]);
+                            if (i >= HL && i < HL + 8) { rc[i - HL] = rn; pold[i - HL] = pv[i]; }
+                            v[i] = fma(beta, pv[i], rn);
                         }
                         if (interior) {
                             const int gy = y0 + row - N;
                             const T* xin = inint + (row - N) * kTX + 8 * g;
                             T* rg = ring + rslot * (kTY * kTX) + (row - N) * kTX + 8 * g;
+                            T xi8[8];
+                            load_window<T, 8>(xi8, xin);
 #pragma unroll
                             for (int h = 0; h < 2; h++) {
                                 const int gx = x0 + 8 * g + 4 * h;
-                                T pn4[4];
+                                T pn4[4], rn4[4], xn4[4];
+                                T part = T(0);
 #pragma unroll
-                                for (int e = 0; e < 4; e++) pn4[e] = v[HL + 4 * h + e];   // zsgn = 1 here
-                                *reinterpret_cast<T2*>(rg + 4 * h) = T2{pn4[0], pn4[1]};
-                                *reinterpret_cast<T2*>(rg + 4 * h + 2) = T2{pn4[2], pn4[3]};
+                                for (int e = 0; e < 4; e++) {
+                                    pn4[e] = v[HL + 4 * h + e];   // interior plane: no sign
+                                    rn4[e] = rc[4 * h + e];
+                                    xn4[e] = fma(alpha, pold[4 * h + e], xi8[4 * h + e]);
+                                    if (sizeof(T) == 4 || gx + e < nx) part = fma(rn4[e], rn4[e], part);
+                                }
+                                if constexpr (sizeof(T) == 4) {
+                                    *reinterpret_cast<float4*>(rg + 4 * h) = make_float4(pn4[0], pn4[1], pn4[2], pn4[3]);
+                                } else {
+                                    *reinterpret_cast<T2*>(rg + 4 * h) = T2{pn4[0], pn4[1]};
+                                    *reinterpret_cast<T2*>(rg + 4 * h + 2) = T2{pn4[2], pn4[3]};
+                                }
                                 if (gy < ny && gx < nx) {
                                     const size_t o = ((size_t)z * ny + gy) * nx + gx;
-                                    const T2 x01 = *reinterpret_cast<const T2*>(xin + 4 * h);
-                                    const T2 x23 = *reinterpret_cast<const T2*>(xin + 4 * h + 2);
-                                    const T xi[4] = {x01.x, x01.y, x23.x, x23.y};
-                                    T rn4[4], xn4[4];
-                                    T part = T(0);
-#pragma unroll
-                                    for (int e = 0; e < 4; e++) {
-                                        rn4[e] = rc[4 * h + e];
-                                        xn4[e] = fma(alpha, pold[4 * h + e], xi[e]);
-                                        if (sizeof(T) == 4 || gx + e < nx) part = fma(rn4[e], rn4[e], part);
-                                    }
                                     d0.add(part);
                                     if constexpr (sizeof(T) == 4) {
                                         *reinterpret_cast<float4*>(a.out1 + o) = make_float4(rn4[0], rn4[1], rn4[2], rn4[3]);
@@ -419,20 +439,21 @@ __global__ void __launch_bounds__(kTNT, (sizeof(T) == 4 && N <= 4) ? 2 : 1)
                                 }
                             }
                         }
-                    } else {
+                    } else if (MODE == TMODE_RES && interior) {
+                        // keep b of this plane for the residual of output plane z
+                        T b8[8];
+                        load_window<T, 8>(b8, inint + (row - N) * kTX + 8 * g);
+                        T* rg = ring + rslot * (kTY * kTX) + (row - N) * kTX + 8 * g;
+                        if constexpr (sizeof(T) == 4) {
+                            reinterpret_cast<float4*>(rg)[0] = make_float4(b8[0], b8[1], b8[2], b8[3]);
+                            reinterpret_cast<float4*>(rg)[1] = make_float4(b8[4], b8[5], b8[6], b8[7]);
+                        } else {
 #pragma unroll
-                        for (int i = 0; i < WIN; i++) v[i] *= zsgn;
-                        if (MODE == TMODE_RES && interior) {
-                            // keep b of this plane for the residual of output plane z
-                            const T* bin = inint + (row - N) * kTX + 8 * g;
-                            T* rg = ring + rslot * (kTY * kTX) + (row - N) * kTX + 8 * g;
-#pragma unroll
-                            for (int e = 0; e < 8; e += 2)
-                                *reinterpret_cast<T2*>(rg + e) = *reinterpret_cast<const T2*>(bin + e);
+                            for (int e = 0; e < 8; e += 2) *reinterpret_cast<T2*>(rg + e) = T2{b8[e], b8[e + 1]};
                         }
                     }
                     // x-sweep of the 8 outputs as 4 packed pairs (i, i+1); symmetric taps paired.
-                    // w holds v shifted by one so that every operand pair is register-aligned.
+                    // wp holds v shifted by one so that every operand pair is register-aligned.
                     T2 vp[WIN / 2], wp[WIN / 2 - 1];
 #pragma unroll
                     for (int i = 0; i < WIN / 2; i++) vp[i] = T2{v[2 * i], v[2 * i + 1]};
@@ -441,8 +462,7 @@ __global__ void __launch_bounds__(kTNT, (sizeof(T) == 4 && N <= 4) ? 2 : 1)
                     auto pair_at = [&](int c) -> T2 {   // (v[c], v[c+1])
                         return (c & 1) ? wp[c >> 1] : vp[c >> 1];
                     };
-                    T* mdst = MXs + row * MXP + 8 * g;
-                    T* kdst = KXs + row * MXP + 8 * g;
+                    T2 mo[4], ko[4];
 #pragma unroll
                     for (int i = 0; i < 8; i += 2) {
                         const int cI = HL + i;
@@ -454,8 +474,30 @@ __global__ void __launch_bounds__(kTNT, (sizeof(T) == 4 && N <= 4) ? 2 : 1)
                             m = PP::fma(mxp[jj], sp, m);
                             k2 = PP::fma(kxp[jj], sp, k2);
                         }
-                        *reinterpret_cast<T2*>(mdst + i) = m;
-                        *reinterpret_cast<T2*>(kdst + i) = k2;
+                        mo[i / 2] = m;
+                        ko[i / 2] = k2;
+                    }
+                    if (zsgn != T(1)) {   // mirrored plane (-1) or a face plane (0)
+                        const T2 sg = PP::mk(zsgn);
+#pragma unroll
+                        for (int i = 0; i < 4; i++) {
+                            mo[i] = PP::fma(sg, mo[i], PP::zero());
+                            ko[i] = PP::fma(sg, ko[i], PP::zero());
+                        }
+                    }
+                    T* mdst = MXs + row * MXP + 8 * g;
+                    T* kdst = KXs + row * MXP + 8 * g;
+                    if constexpr (sizeof(T) == 4) {
+                        reinterpret_cast<float4*>(mdst)[0] = make_float4(mo[0].x, mo[0].y, mo[1].x, mo[1].y);
+                        reinterpret_cast<float4*>(mdst)[1] = make_float4(mo[2].x, mo[2].y, mo[3].x, mo[3].y);
+                        reinterpret_cast<float4*>(kdst)[0] = make_float4(ko[0].x, ko[0].y, ko[1].x, ko[1].y);
+                        reinterpret_cast<float4*>(kdst)[1] = make_float4(ko[2].x, ko[2].y, ko[3].x, ko[3].y);
+                    } else {
+#pragma unroll
+                        for (int i = 0; i < 4; i++) {
+                            *reinterpret_cast<T2*>(mdst + 2 * i) = mo[i];
+                            *reinterpret_cast<T2*>(kdst + 2 * i) = ko[i];
+                        }
                     }
                 }
             }
@@ -475,8 +517,8 @@ __global__ void __launch_bounds__(kTNT, (sizeof(T) == 4 && N <= 4) ? 2 : 1)
                 T2 mv[NR], kv[NR];
 #pragma unroll
                 for (int r = 0; r < NR; r++) {
-                    mv[r] = *reinterpret_cast<const T2*>(MXs + (3 * warp + r) * MXP + c2);
-                    kv[r] = *reinterpret_cast<const T2*>(KXs + (3 * warp + r) * MXP + c2);
+                    mv[r] = *reinterpret_cast<const T2*>(mxb + r * MXP);
+                    kv[r] = *reinterpret_cast<const T2*>(kxb + r * MXP);
                 }
                 T2 U[3], V[3], q[3];
 #pragma unroll
