@@ -139,6 +139,39 @@ int heat_step(bsk_handle* h, void* u, const void* q, int nsteps, const bsk_cg_op
  * host after synchronising the stream. Used to check results without a host copy. */
 int bsk_norm2(bsk_handle* h, const void* x, double* out);
 
+/* ---- batches of independent problems ------------------------------------------------------
+ * Many unmasked box problems (any sizes, degrees 1..5, one shared dt) solved together: each CG
+ * iteration of the whole batch is one persistent launch per degree present, whose blocks take
+ * (problem, tile, z-chunk) work items from a device queue; every problem keeps its own CG
+ * scalars and convergence test and leaves the queue once converged. Inner iterations run in
+ * FP32 inside CUDA graphs; each problem's true residual and update are FP64 (iterative
+ * refinement, precision must be BSK_F32_IR). The batch owns its work vectors (row-padded FP32
+ * copies plus FP64 residuals), allocated at creation. */
+typedef struct bsk_batch bsk_batch;
+
+/* probs: HOST array of `count` problems (mask must be NULL; all dt equal). */
+int bsk_batch_create(const bsk_problem* probs, int count, int precision, void* stream, bsk_batch** out);
+void bsk_batch_destroy(bsk_batch* b);
+
+/* b, x: HOST arrays of `count` DEVICE pointers to dense double vectors (x in: start, out:
+ * solution). reports (may be NULL): HOST array of `count` reports. The returned status is the
+ * worst of the problems' statuses. opts as for cg_solve (applied to every problem). */
+int bsk_batch_cg_solve(bsk_batch* b, const void* const* bvec, void* const* x, const bsk_cg_opts* opts,
+                       bsk_cg_report* reports);
+
+/* nsteps implicit Euler steps of every problem (as heat_step); q may be NULL or hold NULLs. */
+int bsk_batch_heat_step(bsk_batch* b, void* const* u, const void* const* q, int nsteps,
+                        const bsk_cg_opts* opts, bsk_cg_report* reports);
+
+/* Autotuner: times whole-batch CG iterations (`reps` each, CUDA events) for several work
+ * decompositions (z-chunks per problem 1, 2, 3, 4, 6, 8), keeps the fastest and derives the
+ * graph length from its iteration time. Overwrites the batch's work vectors. Outputs (may be
+ * NULL): chosen z-chunks, graph length, mean ms per batched iteration. */
+int bsk_batch_autotune(bsk_batch* b, int reps, int* nzc, int* check_every, double* ms);
+
+/* Sets the decomposition and graph length directly (e.g. from a cached autotuning result). */
+int bsk_batch_configure(bsk_batch* b, int nzc, int check_every);
+
 /* Kernel timing for roofline measurements. Launches one of the library's kernels `reps` times
  * back to back on the handle's stream, on the handle's own work vectors (which it first zeroes,
  * so any state of a previous solve is lost), and writes the mean device time of one launch in

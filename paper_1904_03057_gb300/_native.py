@@ -59,6 +59,19 @@ SIGNATURES = {
                                         ctypes.c_void_p, ctypes.c_void_p,
                                         ctypes.POINTER(ctypes.c_double),
                                         ctypes.POINTER(ctypes.c_double), ctypes.c_void_p]),
+    "bsk_batch_create": (ctypes.c_int, [ctypes.POINTER(Problem), ctypes.c_int, ctypes.c_int,
+                                        ctypes.c_void_p, ctypes.POINTER(ctypes.c_void_p)]),
+    "bsk_batch_destroy": (None, [ctypes.c_void_p]),
+    "bsk_batch_cg_solve": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p,
+                                          ctypes.POINTER(CgOpts), ctypes.POINTER(CgReport)]),
+    "bsk_batch_heat_step": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p,
+                                           ctypes.c_int, ctypes.POINTER(CgOpts),
+                                           ctypes.POINTER(CgReport)]),
+    "bsk_batch_autotune": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int,
+                                          ctypes.POINTER(ctypes.c_int),
+                                          ctypes.POINTER(ctypes.c_int),
+                                          ctypes.POINTER(ctypes.c_double)]),
+    "bsk_batch_configure": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int, ctypes.c_int]),
     "bsk_last_error": (ctypes.c_char_p, []),
     "bsk_status_string": (ctypes.c_char_p, [ctypes.c_int]),
 }

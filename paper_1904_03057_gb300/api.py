@@ -142,6 +142,108 @@ class Handle:
         return out.value
 
 
+class BatchHandle:
+    """Many independent unmasked box problems solved together (bsk_batch_*). problems: a list of
+    objects with nx, ny, nz, degree, h (scalar or 3-tuple); all share dt. Vectors are float64."""
+
+    def __init__(self, problems, dt: float, stream: Optional[torch.cuda.Stream] = None):
+        self._lib = _native.load()
+        self._ptr = ctypes.c_void_p(None)
+        self.count = len(problems)
+        self.shapes = []
+        arr = (_native.Problem * self.count)()
+        for i, p in enumerate(problems):
+            hs = (float(p.h),) * 3 if np.isscalar(p.h) else tuple(float(v) for v in p.h)
+            arr[i] = _native.Problem(int(p.nx), int(p.ny), int(p.nz), int(p.degree), hs[0], hs[1],
+                                     hs[2], float(dt), None)
+            self.shapes.append((int(p.nz), int(p.ny), int(p.nx)))
+        self.stream = stream if stream is not None else torch.cuda.current_stream()
+        _native.check(self._lib.bsk_batch_create(arr, self.count, F32_IR,
+                                                 ctypes.c_void_p(self.stream.cuda_stream),
+                                                 ctypes.byref(self._ptr)))
+
+    def _ptrs(self, vecs, name, allow_none=False):
+        if vecs is None:
+            return None
+        if len(vecs) != self.count:
+            raise ValueError(f"{name}: expected {self.count} vectors")
+        out = (ctypes.c_void_p * self.count)()
+        for i, (v, shp) in enumerate(zip(vecs, self.shapes)):
+            if v is None and allow_none:
+                out[i] = None
+                continue
+            if not (isinstance(v, torch.Tensor) and v.is_cuda and v.dtype == torch.float64
+                    and v.is_contiguous() and v.numel() == shp[0] * shp[1] * shp[2]):
+                raise ValueError(f"{name}[{i}] must be a contiguous CUDA float64 tensor of {shp}")
+            out[i] = v.data_ptr()
+        return out
+
+    def _reports(self, reps):
+        return [_report(r) for r in reps]
+
+    def cg_solve(self, bs, xs, **opts):
+        o = _opts(**opts)
+        reps = (_native.CgReport * self.count)()
+        _native.check(self._lib.bsk_batch_cg_solve(self._ptr, self._ptrs(bs, "b"),
+                                                   self._ptrs(xs, "x"), ctypes.byref(o), reps))
+        return self._reports(reps)
+
+    def heat_step(self, us, qs=None, nsteps: int = 1, **opts):
+        o = _opts(**opts)
+        reps = (_native.CgReport * self.count)()
+        _native.check(self._lib.bsk_batch_heat_step(self._ptr, self._ptrs(us, "u"),
+                                                    self._ptrs(qs, "q", allow_none=True),
+                                                    int(nsteps), ctypes.byref(o), reps))
+        return self._reports(reps)
+
+    def autotune(self, reps: int = 3) -> dict:
+        nzc, ce, ms = ctypes.c_int(0), ctypes.c_int(0), ctypes.c_double(0.0)
+        _native.check(self._lib.bsk_batch_autotune(self._ptr, int(reps), ctypes.byref(nzc),
+                                                   ctypes.byref(ce), ctypes.byref(ms)))
+        return {"nzc": nzc.value, "check_every": ce.value, "ms_per_iteration": ms.value}
+
+    def configure(self, nzc: int, check_every: int):
+        _native.check(self._lib.bsk_batch_configure(self._ptr, int(nzc), int(check_every)))
+
+    def close(self):
+        if self._ptr:
+            self._lib.bsk_batch_destroy(self._ptr)
+            self._ptr = ctypes.c_void_p(None)
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def autotune_cached(batch: BatchHandle, key_problems, cache_path: str, reps: int = 3) -> dict:
+    """Autotunes a batch once per (GPU, problem list) and keeps the result in a JSON cache file."""
+    import hashlib
+    import json
+    import os
+    gpu = torch.cuda.get_device_name()
+    desc = ";".join(f"{p.nx}x{p.ny}x{p.nz}n{p.degree}" for p in key_problems)
+    key = f"{gpu}|f32|{hashlib.sha1(desc.encode()).hexdigest()}"
+    cache = {}
+    if os.path.exists(cache_path):
+        try:
+            with open(cache_path) as f:
+                cache = json.load(f)
+        except (OSError, ValueError):
+            cache = {}
+    if key in cache:
+        batch.configure(cache[key]["nzc"], cache[key]["check_every"])
+        return dict(cache[key], cached=True)
+    res = batch.autotune(reps)
+    cache[key] = res
+    tmp = cache_path + ".tmp"
+    with open(tmp, "w") as f:
+        json.dump(cache, f, indent=1)
+    os.replace(tmp, cache_path)
+    return dict(res, cached=False)
+
+
 # Module-level forms with the C ABI's names.
 def bsk_create(nx, ny, nz, degree, h, dt=0.0, mask=None, precision="f64", stream=None) -> Handle:
     return Handle(nx, ny, nz, degree, h, dt, mask, precision, stream)

@@ -88,6 +88,27 @@ int tma_grid(int degree, int mode);   // resident blocks (after prepare_tma), 0 
 template <typename T>
 cudaError_t launch_tma(const TmaLaunch& L, cudaStream_t s);
 
+// Batched single-pass CG iteration (FP32): one persistent launch over the items of all the
+// problems of one degree; desc points to BatchProblem<float>[nprobs] in device memory.
+struct TmaBatchLaunch {
+    int degree;
+    const void* desc;
+    int nprobs;
+    int nitems;
+    int parity;
+    unsigned int* work;          // 2 counters, zero between launches
+    Scalars* status;             // receives a wait time-out
+};
+size_t batch_problem_bytes();
+int batch_grid(int degree);     // resident blocks (after prepare_tma<float>(degree))
+// Fills one BatchProblem<float> (host memory, batch_problem_bytes() bytes) for a padded problem.
+cudaError_t fill_batch_problem(void* host_desc, int degree, int nx, int ny, int nz, int pitch,
+                               int nzc, int item0, const double (*M)[kMaxTaps],
+                               const double (*Kdt)[kMaxTaps], float* const r[2], float* const q[2],
+                               float* const p[2], float* x, Scalars* sc, double* partials,
+                               unsigned int* items_done, int timing, int* nitems_out);
+cudaError_t launch_tma_batch(const TmaBatchLaunch& L, cudaStream_t s);
+
 cudaError_t launch_ir_scale_down(const double* r64, float* r32, size_t len, const Scalars* outer,
                                  cudaStream_t s);
 cudaError_t launch_ir_update(double* x64, const float* d32, size_t len, const Scalars* outer,

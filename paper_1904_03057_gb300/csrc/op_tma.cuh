@@ -39,6 +39,7 @@ struct TmaArgs {
     T* out2;              // CG p_m
     T* xvec;              // CG x, updated in place
     int nx, ny, nz;
+    int pitch;            // elements per row in memory (>= nx; rows of 16-byte multiples)
     int tiles_x, tiles_y, tz, nitems;
     T M[3][kMaxTaps];     // per-axis mass kernels, index j + n
     T K[3][kMaxTaps];     // per-axis stiffness kernels times dt
@@ -46,6 +47,31 @@ struct TmaArgs {
     double* partials;
     unsigned int* work;   // [0] next item, [1] blocks finished; both zero between launches
     int fin;
+    // batched CG (BATCH kernels): the problems, their first items, and the ping-pong parity
+    const void* batch;    // BatchProblem<T>[nprobs] in device memory
+    int nprobs;
+    int parity;
+};
+
+// One problem of a batched CG pass, in device memory. The pass with parity P reads the halo
+// boxes tin[P] = (r, q, p) and writes (q, r, p) to out*[P]; x is updated in place.
+template <typename T>
+struct BatchProblem {
+    CUtensorMap tin[2][3];
+    CUtensorMap tint;            // interior box of x
+    T* out0[2];                  // q
+    T* out1[2];                  // r
+    T* out2[2];                  // p
+    T* xvec;
+    int nx, ny, nz, pitch;
+    int tiles_x, tiles_y, tz, nitems, item0;   // item0: first item of this problem in the pass
+    T M[3][kMaxTaps];
+    T K[3][kMaxTaps];
+    Scalars* sc;
+    double* partials;            // 3 doubles per item of this problem
+    unsigned int* items_done;    // items of this problem finished in the current pass
+    int timing;                  // non-zero: skip the finaliser (kernel timing passes)
+    int pad[5];
 };
 
 template <typename T, int N>
@@ -236,8 +262,8 @@ __device__ __forceinline__ void push_dispatch(int j, T2 (&acc)[3][2 * N + 1], co
     }
 }
 
-template <typename T, int N, int MODE>
-__global__ void __launch_bounds__(kTNT, (sizeof(T) == 4 && N <= 4) ? 2 : 1)
+template <typename T, int N, int MODE, bool BATCH>
+__global__ void __launch_bounds__(kTNT, (sizeof(T) == 4 && N <= 4 && !BATCH) ? 2 : 1)
     k_op_tma(const __grid_constant__ TmaArgs<T> a)
 {
     using G = TGeo<T, N>;
@@ -249,48 +275,78 @@ __global__ void __launch_bounds__(kTNT, (sizeof(T) == 4 && N <= 4) ? 2 : 1)
     constexpr int NIN = LY::NIN;
     static_assert(LY::total <= 227 * 1024, "shared memory budget");
     static_assert(WIN % 4 == 0 && HL % 2 == 0, "window loads are 16-byte vectors, pairs aligned");
+    static_assert(!BATCH || MODE == TMODE_CG, "batched passes are CG iterations");
 
     extern __shared__ __align__(128) unsigned char smem[];
     T* MXs = reinterpret_cast<T*>(smem + LY::off_mx);
     T* KXs = reinterpret_cast<T*>(smem + LY::off_mx + LY::mx_bytes);
     T* ring = reinterpret_cast<T*>(smem + LY::off_ring);
     uint64_t* bars = reinterpret_cast<uint64_t*>(smem + LY::off_bar);
-    __shared__ int s_abort, s_item;
+    __shared__ int s_abort, s_item, s_prob, s_last;
     __shared__ uint32_t s_issued, s_wait_from;   // loads issued / first load not yet consumed
+    __shared__ double s_red[3 * (kTNT / 32)];
+    const BatchProblem<T>* probs = static_cast<const BatchProblem<T>*>(a.batch);
 
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-    const int nx = a.nx, ny = a.ny, nz = a.nz;
 
-    T alpha = T(0), beta = T(0);
-    if (MODE == TMODE_CG) {
+    if (!BATCH && MODE == TMODE_CG) {
         if (*(volatile int*)&a.sc->done) return;   // uniform over the grid
-        alpha = (T)a.sc->alpha;
-        beta = (T)a.sc->beta;
     }
+    // item fetch (thread 0): next item of the queue and, for a batch, its problem
+    auto fetch = [&]() {
+        const int it = (int)atomicAdd(&a.work[0], 1u);
+        s_item = it;
+        if (BATCH && it < a.nitems) {
+            int lo = 0, hi = a.nprobs - 1;   // last problem with item0 <= it
+            while (lo < hi) {
+                const int mid = (lo + hi + 1) >> 1;
+                if (probs[mid].item0 <= it) lo = mid; else hi = mid - 1;
+            }
+            s_prob = lo;
+        }
+    };
     if (tid == 0) {
         for (int s = 0; s < S; s++) mbar_init(&bars[s], 1);
         fence_mbar_init();
-        for (int i = 0; i < NIN; i++) prefetch_tensormap(&a.tin[i]);
-        if (LY::NINT) prefetch_tensormap(&a.tint);
+        if (!BATCH) {
+            for (int i = 0; i < NIN; i++) prefetch_tensormap(&a.tin[i]);
+            if (LY::NINT) prefetch_tensormap(&a.tint);
+        }
         s_abort = 0;
         s_issued = 0;
         s_wait_from = 0;
-        s_item = (int)atomicAdd(&a.work[0], 1u);
+        s_prob = 0;
+        fetch();
     }
     __syncthreads();
 
+    // ---- the current problem (fixed for a single problem, per item for a batch) ----
+    const CUtensorMap *tin0 = &a.tin[0], *tin1 = &a.tin[1], *tin2 = &a.tin[2], *tint = &a.tint;
+    T *out0 = a.out0, *out1 = a.out1, *out2 = a.out2, *xvec = a.xvec;
+    int nx = a.nx, ny = a.ny, nz = a.nz, pitch = a.pitch;
+    int tiles_x = a.tiles_x, tiles_y = a.tiles_y, tz = a.tz, item0 = 0;
+    Scalars* sc = a.sc;
+    T alpha = T(0), beta = T(0);
+    if (!BATCH && MODE == TMODE_CG) {
+        alpha = (T)a.sc->alpha;
+        beta = (T)a.sc->beta;
+    }
     // packed taps: W1 = Mz + dt Kz and Mz for the z push; My and dt Ky for the y-sweep;
     // Mx and dt Kx for the x-sweep
     T2 w1z[N + 1], mz[N + 1], my[N + 1], ky[N + 1], mxp[N + 1], kxp[N + 1];
+    auto load_taps = [&](const T (&M)[3][kMaxTaps], const T (&K)[3][kMaxTaps]) {
 #pragma unroll
-    for (int j = 0; j <= N; j++) {
-        w1z[j] = PP::mk(a.M[2][N + j] + a.K[2][N + j]);
-        mz[j] = PP::mk(a.M[2][N + j]);
-        my[j] = PP::mk(a.M[1][N + j]);
-        ky[j] = PP::mk(a.K[1][N + j]);
-        mxp[j] = PP::mk(a.M[0][N + j]);
-        kxp[j] = PP::mk(a.K[0][N + j]);
-    }
+        for (int j = 0; j <= N; j++) {
+            w1z[j] = PP::mk(M[2][N + j] + K[2][N + j]);
+            mz[j] = PP::mk(M[2][N + j]);
+            my[j] = PP::mk(M[1][N + j]);
+            ky[j] = PP::mk(K[1][N + j]);
+            mxp[j] = PP::mk(M[0][N + j]);
+            kxp[j] = PP::mk(K[0][N + j]);
+        }
+    };
+    if (!BATCH) load_taps(a.M, a.K);
+    int cur_prob = -1;
 
     // x-sweep task of this thread (one task per thread when 8 * HY <= block size)
     constexpr int NTASK = 8 * HY;
@@ -301,15 +357,43 @@ __global__ void __launch_bounds__(kTNT, (sizeof(T) == 4 && N <= 4) ? 2 : 1)
     const T* kxb = KXs + 3 * warp * MXP + 2 * lane;
 
     KSum<T> d0, d1, d2;
-    const int ntiles = a.tiles_x * a.tiles_y;
     uint32_t cnt = 0;   // planes consumed by this block before the current item
 
     for (;;) {
-        const int item = s_item;
-        if (item >= a.nitems) break;
+        const int item_g = s_item;
+        if (item_g >= a.nitems) break;
+        if (BATCH) {
+            const int pi = s_prob;
+            const BatchProblem<T>& P = probs[pi];
+            if (*(volatile int*)&P.sc->done) {   // converged earlier: its items are skipped
+                __syncthreads();
+                if (tid == 0) fetch();
+                __syncthreads();
+                continue;
+            }
+            if (pi != cur_prob) {
+                cur_prob = pi;
+                tin0 = &P.tin[a.parity][0];
+                tin1 = &P.tin[a.parity][1];
+                tin2 = &P.tin[a.parity][2];
+                tint = &P.tint;
+                out0 = P.out0[a.parity];
+                out1 = P.out1[a.parity];
+                out2 = P.out2[a.parity];
+                xvec = P.xvec;
+                nx = P.nx; ny = P.ny; nz = P.nz; pitch = P.pitch;
+                tiles_x = P.tiles_x; tiles_y = P.tiles_y; tz = P.tz; item0 = P.item0;
+                sc = P.sc;
+                alpha = (T)P.sc->alpha;
+                beta = (T)P.sc->beta;
+                load_taps(P.M, P.K);
+            }
+        }
+        const int item = item_g - item0;
+        const int ntiles = tiles_x * tiles_y;
         const int tile = item % ntiles, zc = item / ntiles;
-        const int x0 = (tile % a.tiles_x) * kTX, y0 = (tile / a.tiles_x) * kTY;
-        const int z0 = zc * a.tz, z1 = min(z0 + a.tz, nz);
+        const int x0 = (tile % tiles_x) * kTX, y0 = (tile / tiles_x) * kTY;
+        const int z0 = zc * tz, z1 = min(z0 + tz, nz);
         const int zs = z0 - N;
         const int np = (z1 - z0) + 2 * N;
         const bool patch_x = (x0 == 0) || (x0 + kTX + N > nx);
@@ -323,11 +407,12 @@ __global__ void __launch_bounds__(kTNT, (sizeof(T) == 4 && N <= 4) ? 2 : 1)
             if (!reflect_index(zz, nz, zsrc)) zsrc = 0;   // a face plane: any plane, scaled by 0
             uint64_t* bar = &bars[c % S];
             mbar_arrive_expect_tx(bar, LY::tx_bytes);
+            const CUtensorMap* maps[3] = {tin0, tin1, tin2};
             for (int i = 0; i < NIN; i++)
-                tma_load_3d(st + i * LY::in_bytes, &a.tin[i], bar, x0 - HL, y0 - N, zsrc);
+                tma_load_3d(st + i * LY::in_bytes, maps[i], bar, x0 - HL, y0 - N, zsrc);
             if (LY::NINT) {
                 const int zi = min(max(zz, 0), nz - 1);
-                tma_load_3d(st + NIN * LY::in_bytes, &a.tint, bar, x0, y0, zi);
+                tma_load_3d(st + NIN * LY::in_bytes, tint, bar, x0, y0, zi);
             }
             s_issued = c + 1;
         };
@@ -411,7 +496,7 @@ __global__ void __launch_bounds__(kTNT, (sizeof(T) == 4 && N <= 4) ? 2 : 1)
                                     pn4[e] = v[HL + 4 * h + e];   // interior plane: no sign
                                     rn4[e] = rc[4 * h + e];
                                     xn4[e] = fma(alpha, pold[4 * h + e], xi8[4 * h + e]);
-                                    if (sizeof(T) == 4 || gx + e < nx) part = fma(rn4[e], rn4[e], part);
+                                    if (gx + e < nx) part = fma(rn4[e], rn4[e], part);
                                 }
                                 if constexpr (sizeof(T) == 4) {
                                     *reinterpret_cast<float4*>(rg + 4 * h) = make_float4(pn4[0], pn4[1], pn4[2], pn4[3]);
@@ -420,19 +505,21 @@ __global__ void __launch_bounds__(kTNT, (sizeof(T) == 4 && N <= 4) ? 2 : 1)
                                     *reinterpret_cast<T2*>(rg + 4 * h + 2) = T2{pn4[2], pn4[3]};
                                 }
                                 if (gy < ny && gx < nx) {
-                                    const size_t o = ((size_t)z * ny + gy) * nx + gx;
+                                    // rows are padded to 16-byte multiples: a partial group of
+                                    // four writes into the padding, which no kernel reads
+                                    const size_t o = ((size_t)z * ny + gy) * pitch + gx;
                                     d0.add(part);
                                     if constexpr (sizeof(T) == 4) {
-                                        *reinterpret_cast<float4*>(a.out1 + o) = make_float4(rn4[0], rn4[1], rn4[2], rn4[3]);
-                                        *reinterpret_cast<float4*>(a.out2 + o) = make_float4(pn4[0], pn4[1], pn4[2], pn4[3]);
-                                        *reinterpret_cast<float4*>(a.xvec + o) = make_float4(xn4[0], xn4[1], xn4[2], xn4[3]);
+                                        *reinterpret_cast<float4*>(out1 + o) = make_float4(rn4[0], rn4[1], rn4[2], rn4[3]);
+                                        *reinterpret_cast<float4*>(out2 + o) = make_float4(pn4[0], pn4[1], pn4[2], pn4[3]);
+                                        *reinterpret_cast<float4*>(xvec + o) = make_float4(xn4[0], xn4[1], xn4[2], xn4[3]);
                                     } else {
 #pragma unroll
                                         for (int e = 0; e < 4; e += 2) {
                                             if (gx + e < nx) {   // FP64 rows are only 2-element aligned
-                                                *reinterpret_cast<T2*>(a.out1 + o + e) = T2{rn4[e], rn4[e + 1]};
-                                                *reinterpret_cast<T2*>(a.out2 + o + e) = T2{pn4[e], pn4[e + 1]};
-                                                *reinterpret_cast<T2*>(a.xvec + o + e) = T2{xn4[e], xn4[e + 1]};
+                                                *reinterpret_cast<T2*>(out1 + o + e) = T2{rn4[e], rn4[e + 1]};
+                                                *reinterpret_cast<T2*>(out2 + o + e) = T2{pn4[e], pn4[e + 1]};
+                                                *reinterpret_cast<T2*>(xvec + o + e) = T2{xn4[e], xn4[e + 1]};
                                             }
                                         }
                                     }
@@ -508,7 +595,7 @@ __global__ void __launch_bounds__(kTNT, (sizeof(T) == 4 && N <= 4) ? 2 : 1)
                     fence_proxy_async_smem();
                     issue(k + S);
                 }
-                if (k == np - 1) s_item = (int)atomicAdd(&a.work[0], 1u);   // next item
+                if (!BATCH && k == np - 1) fetch();   // next item (a batch fetches after its reduction)
             }
             // ---- y-sweep in registers, then the z push ----
             {
@@ -547,9 +634,10 @@ __global__ void __launch_bounds__(kTNT, (sizeof(T) == 4 && N <= 4) ? 2 : 1)
                     for (int t = 0; t < 3; t++) {
                         const int gy = y0 + 3 * warp + t, gx = x0 + c2;
                         if (gy < ny && gx < nx) {
-                            const size_t o = ((size_t)zo * ny + gy) * nx + gx;
+                            const size_t o = ((size_t)zo * ny + gy) * pitch + gx;
+                            const T wy = (gx + 1 < nx) ? T(1) : T(0);   // second of the pair in range?
                             if constexpr (MODE == TMODE_OP) {
-                                *reinterpret_cast<T2*>(a.out0 + o) = q[t];
+                                *reinterpret_cast<T2*>(out0 + o) = q[t];
                             } else {
                                 const T2 rg = *reinterpret_cast<const T2*>(
                                     ring + oslot * (kTY * kTX) + (3 * warp + t) * kTX + c2);
@@ -557,13 +645,13 @@ __global__ void __launch_bounds__(kTNT, (sizeof(T) == 4 && N <= 4) ? 2 : 1)
                                     T2 r;
                                     r.x = rg.x - q[t].x;
                                     r.y = rg.y - q[t].y;
-                                    *reinterpret_cast<T2*>(a.out0 + o) = r;
-                                    d0.add(fma(r.x, r.x, r.y * r.y));
-                                    d1.add(fma(rg.x, rg.x, rg.y * rg.y));
+                                    *reinterpret_cast<T2*>(out0 + o) = r;
+                                    d0.add(fma(r.x, r.x, wy * r.y * r.y));
+                                    d1.add(fma(rg.x, rg.x, wy * rg.y * rg.y));
                                 } else {
-                                    *reinterpret_cast<T2*>(a.out0 + o) = q[t];
-                                    d1.add(fma(rg.x, q[t].x, rg.y * q[t].y));
-                                    d2.add(fma(q[t].x, q[t].x, q[t].y * q[t].y));
+                                    *reinterpret_cast<T2*>(out0 + o) = q[t];
+                                    d1.add(fma(rg.x, q[t].x, wy * rg.y * q[t].y));
+                                    d2.add(fma(q[t].x, q[t].x, wy * q[t].y * q[t].y));
                                 }
                             }
                         }
@@ -574,6 +662,58 @@ __global__ void __launch_bounds__(kTNT, (sizeof(T) == 4 && N <= 4) ? 2 : 1)
             __syncthreads();
         }
         cnt += (uint32_t)np;
+
+        if constexpr (BATCH) {
+            // this item's dot products -> its problem's partials; the block finishing the
+            // problem's last item adds them in item order and runs the CG finaliser
+            double v3[3] = {d0.value(), d1.value(), d2.value()};
+            d0 = KSum<T>();
+            d1 = KSum<T>();
+            d2 = KSum<T>();
+#pragma unroll
+            for (int kk = 0; kk < 3; kk++) {
+                const double t = warp_sum(v3[kk]);
+                if (lane == 0) s_red[kk * (kTNT / 32) + warp] = t;
+            }
+            __syncthreads();
+            const BatchProblem<T>& P = probs[cur_prob];
+            if (tid == 0) {
+                for (int kk = 0; kk < 3; kk++) {
+                    double t = 0.0;
+                    for (int w = 0; w < kTNT / 32; w++) t += s_red[kk * (kTNT / 32) + w];
+                    P.partials[3 * item + kk] = t;
+                }
+                __threadfence();
+                const unsigned prev = atomicAdd(P.items_done, 1u);
+                s_last = (prev + 1 == (unsigned)P.nitems);
+            }
+            __syncthreads();
+            if (s_last) {
+                __threadfence();
+                double acc3[3] = {0.0, 0.0, 0.0};
+                for (int i = tid; i < P.nitems; i += kTNT)
+#pragma unroll
+                    for (int kk = 0; kk < 3; kk++) acc3[kk] += __ldcg(P.partials + 3 * i + kk);
+#pragma unroll
+                for (int kk = 0; kk < 3; kk++) {
+                    const double t = warp_sum(acc3[kk]);
+                    if (lane == 0) s_red[kk * (kTNT / 32) + warp] = t;
+                }
+                __syncthreads();
+                if (tid == 0) {
+                    double tot[3];
+                    for (int kk = 0; kk < 3; kk++) {
+                        tot[kk] = 0.0;
+                        for (int w = 0; w < kTNT / 32; w++) tot[kk] += s_red[kk * (kTNT / 32) + w];
+                    }
+                    if (!P.timing) finalize_cg1(P.sc, tot[0], tot[1], tot[2]);
+                    *P.items_done = 0;
+                    __threadfence();
+                }
+            }
+            if (tid == 0) fetch();
+            __syncthreads();
+        }
     }
 
     // every block: count itself out; the last one resets the work counters for the next launch
@@ -586,7 +726,7 @@ __global__ void __launch_bounds__(kTNT, (sizeof(T) == 4 && N <= 4) ? 2 : 1)
             __threadfence();
         }
     }
-    if (a.fin != FIN_NONE) {
+    if (!BATCH && a.fin != FIN_NONE) {
         if constexpr (MODE == TMODE_CG) {
             double v3[3] = {d0.value(), d1.value(), d2.value()};
             grid_reduce_k<kTNT, 3>(v3, a.partials, a.sc, a.fin);

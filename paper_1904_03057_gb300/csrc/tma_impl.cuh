@@ -59,11 +59,11 @@ cudaError_t prepare_one()
     TmaInfo& info = tma_info<N, MODE>();
     if (info.ready) return cudaSuccess;
     using LY = TLayout<BSK_T, N, MODE>;
-    cudaError_t e = cudaFuncSetAttribute(k_op_tma<BSK_T, N, MODE>,
+    cudaError_t e = cudaFuncSetAttribute(k_op_tma<BSK_T, N, MODE, false>,
                                          cudaFuncAttributeMaxDynamicSharedMemorySize, (int)LY::total);
     if (e != cudaSuccess) return e;
     int per_sm = 0, dev = 0, sms = 0;
-    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_op_tma<BSK_T, N, MODE>, kTNT, LY::total);
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_op_tma<BSK_T, N, MODE, false>, kTNT, LY::total);
     if (e != cudaSuccess) return e;
     if ((e = cudaGetDevice(&dev)) != cudaSuccess) return e;
     if ((e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev)) != cudaSuccess) return e;
@@ -125,6 +125,7 @@ cudaError_t launch_one(const TmaLaunch& L, cudaStream_t s)
     a.nx = L.nx;
     a.ny = L.ny;
     a.nz = L.nz;
+    a.pitch = L.nx;
     plan(L.nx, L.ny, L.nz, N, info.grid, a.tiles_x, a.tiles_y, a.tz, a.nitems);
     for (int d = 0; d < 3; d++)
         for (int j = 0; j < kMaxTaps; j++) {
@@ -136,7 +137,7 @@ cudaError_t launch_one(const TmaLaunch& L, cudaStream_t s)
     a.work = L.work;
     a.fin = L.fin;
     const int grid = a.nitems < info.grid ? a.nitems : info.grid;
-    k_op_tma<BSK_T, N, MODE><<<grid, kTNT, LY::total, s>>>(a);
+    k_op_tma<BSK_T, N, MODE, false><<<grid, kTNT, LY::total, s>>>(a);
     return cudaGetLastError();
 }
 

@@ -83,3 +83,20 @@ def test_invalid_arguments_rejected_before_any_gpu_work(native):
     assert L.op_apply(None, None, None) == -1
     assert L.cg_solve(None, None, None, None, None) == -1
     assert L.bsk_status_string(-5) == b"breakdown"
+
+
+def test_batch_create_rejects_bad_problems(native):
+    L = native.load()
+    h = ctypes.c_void_p()
+    arr = (native.Problem * 2)()
+    arr[0] = native.Problem(20, 20, 20, 3, 0.05, 0.05, 0.05, 1e-3, None)
+    arr[1] = native.Problem(20, 20, 20, 3, 0.05, 0.05, 0.05, 2e-3, None)   # dt differs
+    assert L.bsk_batch_create(arr, 2, 2, None, ctypes.byref(h)) == -1
+    arr[1] = native.Problem(20, 20, 20, 6, 0.05, 0.05, 0.05, 1e-3, None)   # degree 6
+    assert L.bsk_batch_create(arr, 2, 2, None, ctypes.byref(h)) == -1
+    arr[1] = native.Problem(20, 20, 20, 3, 0.05, 0.05, 0.05, 1e-3, 1234)   # masked
+    assert L.bsk_batch_create(arr, 2, 2, None, ctypes.byref(h)) == -1
+    arr[1] = native.Problem(20, 20, 20, 3, 0.05, 0.05, 0.05, 1e-3, None)
+    assert L.bsk_batch_create(arr, 2, 0, None, ctypes.byref(h)) == -1      # not F32_IR
+    assert L.bsk_batch_create(arr, 0, 2, None, ctypes.byref(h)) == -1      # empty
+    assert not h.value
