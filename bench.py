@@ -34,6 +34,23 @@ N_GRID, DEGREE, DT, TOL, SEED, NMODES, KMAX = 928, 3, 5e-4, 1e-8, 3, 64, 16
 WORKLOAD = "heat3d_928cube_cubic_f32sweeps_f64refinement"
 
 
+# DRAM bytes per unknown of one fused CG-iteration launch (dram__bytes_read.sum +
+# dram__bytes_write.sum over the unknowns of the launch), from the ncu capture summarised in
+# profiles/; valid only while the kernel's sources hash to CG_TRAFFIC_SOURCES_SHA256.
+CG_TRAFFIC_BYTES_PER_UNKNOWN = None
+CG_TRAFFIC_SOURCES_SHA256 = None
+CG_KERNEL_SOURCES = ("op_tma.cuh", "tma_impl.cuh", "tma_util.cuh", "bsk_device.cuh", "tma_f32.cu")
+
+
+def cg_kernel_sources_sha256() -> str:
+    import hashlib
+    d = hashlib.sha256()
+    for name in CG_KERNEL_SOURCES:
+        with open(os.path.join(ROOT, "paper_1904_03057_gb300", "csrc", name), "rb") as f:
+            d.update(f.read())
+    return d.hexdigest()
+
+
 def peaks():
     try:
         with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
@@ -149,7 +166,7 @@ def run_ours(args, rank, world, dist):
     from paper_1904_03057_gb300 import api, inputs
     dev = int(os.environ.get("LOCAL_RANK", "0"))
     torch.cuda.set_device(dev)
-    N = N_GRID
+    N = args.grid
     h = 1.0 / (N + 1)
     dofs = N ** 3
     modes = inputs.random_sine_modes(SEED + rank, NMODES, KMAX)
@@ -214,15 +231,23 @@ def run_ours(args, rank, world, dist):
                "h2d_bytes_per_step": dofs * 8, "d2h_bytes_per_step": dofs * 8}
         del uh
 
-    # dominant kernel timing (CUDA events on the handle's stream): the fused CG pass, FP32
+    # dominant kernel: the fused CG iteration (one launch per inner iteration). Its average
+    # duration inside the timed region comes from the CUDA events the library records on the
+    # handle's stream around the CG-graph launches (iter_ms / iterations: an upper bound, it
+    # includes the graph's inter-kernel gaps); time_kernel gives the same kernel timed alone.
     hbm, peak_kind = peaks()
+    iter_ms = sum(r["iter_ms"] for r in reps)
+    ms_fused_live = iter_ms / max(inner, 1)
     ms_fused = H.time_kernel(api.KERNEL_CG_FUSED, reps=10)
     bytes_fused = 32.0 * dofs   # read r, q, p, x; write r, q, p, x (FP32 single-pass iteration)
     ms_op = H.time_kernel(api.KERNEL_OP, reps=10)
     bytes_op = 8.0 * dofs       # read x, write y (FP32)
     ms_res64 = H.time_kernel(api.KERNEL_RES64, reps=3)
     ms_upd = H.time_kernel(api.KERNEL_CG_UPDATE, reps=10)
-    ach = bytes_fused / (ms_fused * 1e-3) / 1e9
+    ach = bytes_fused / (ms_fused_live * 1e-3) / 1e9
+    traffic = None
+    if CG_TRAFFIC_BYTES_PER_UNKNOWN is not None and cg_kernel_sources_sha256() == CG_TRAFFIC_SOURCES_SHA256:
+        traffic = CG_TRAFFIC_BYTES_PER_UNKNOWN * dofs
 
     line = {
         "metric": METRIC, "value": value, "unit": "GDoF/s", "n_gpus": world,
@@ -230,15 +255,18 @@ def run_ours(args, rank, world, dist):
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32/f64",
         "data": "synthetic",
         "config": {
-            "workload": WORKLOAD, "grid": f"{N}^3", "unknowns": dofs, "degree": DEGREE, "dt": DT,
+            "workload": WORKLOAD if N == N_GRID else WORKLOAD.replace(str(N_GRID), str(N)),
+            "grid": f"{N}^3", "unknowns": dofs, "degree": DEGREE, "dt": DT,
             "tol": TOL, "precision": "FP32 operator sweeps, FP64 true residual + CG scalars",
-            "l2": "inputs larger than L2 (3.2 GB FP32 / 6.4 GB FP64 vectors)",
+            "l2": f"inputs larger than L2 ({4 * dofs / 1e9:.2f} GB FP32 / {8 * dofs / 1e9:.2f} GB FP64 vectors)",
             "op_applications_per_step": op_apps / len(reps),
             "cg_iterations_per_step": inner / len(reps),
             "refinement_steps_per_step": outer / len(reps),
             "max_true_rel_residual": worst_res,
-            "kernel_ms": {"cg_fused_f32": ms_fused, "cg_update_f32": ms_upd, "op_f32": ms_op,
+            "kernel_ms": {"cg_fused_f32_in_timed_region": ms_fused_live,
+                          "cg_fused_f32_alone": ms_fused, "cg_update_f32": ms_upd, "op_f32": ms_op,
                           "residual_f64": ms_res64},
+            "cg_iteration_share_of_timed_region": iter_ms / elapsed_ms if world == 1 else None,
             "op_apply_gdofs": dofs / (ms_op * 1e-3) / 1e9,
             "op_apply_hbm_frac": bytes_op / (ms_op * 1e-3) / 1e9 / hbm,
             "parallelism": f"{world} independent problems (one per GPU)",
@@ -246,9 +274,10 @@ def run_ours(args, rank, world, dist):
         "roofline": {"kernel": "k_op_tma<float,3,CG>: one CG iteration (p, r, x updates + A p + "
                                "r.r, p.Ap, Ap.Ap)",
                      "bound": "hbm", "achieved": ach, "peak": hbm, "unit": "GB/s",
-                     "frac": ach / hbm, "traffic": None,
+                     "frac": ach / hbm, "traffic": traffic,
                      "note": f"peak = {peak_kind} HBM copy bandwidth; algorithmic 32 B/unknown "
-                             "(read r, q, p, x; write r, q, p, x)"},
+                             "(read r, q, p, x; write r, q, p, x); duration = mean per iteration "
+                             "over the timed region (CUDA events on the launching stream)"},
         "clocks": clocks,
         "gpu_launches": launches,
     }
@@ -271,7 +300,12 @@ def main():
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--grid", type=int, default=N_GRID,
+                    help="grid edge (default: the benchmark workload; smaller grids are the "
+                         "profiler's small case)")
     args = ap.parse_args()
+    if args.grid < 16 or args.grid % 4:
+        ap.error("--grid must be a multiple of 4 (16-byte FP32 rows for the TMA kernels), >= 16")
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
     dist = None

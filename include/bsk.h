@@ -119,6 +119,14 @@ typedef struct bsk_cg_report {
                               handle's operator precision (FP64 for BSK_F64 and BSK_F32_IR)      */
     double elapsed_ms;     /* wall-clock time of the call                                        */
     long long kernel_launches; /* kernels this call launched on the GPU (graph nodes included) */
+    int fallback_iter;     /* fcg_solve: inner iteration at which the last inner solve fell back
+                              to plain CG, -1 if it never did; 0 for the other solvers            */
+    double iter_ms;        /* cg_solve / heat_step: device time (CUDA events on the handle's
+                              stream) from the first to the end of the last CUDA-graph launch of
+                              the CG iterations, summed over the inner solves; iter_ms divided by
+                              the iterations bounds the time of one iteration's kernel from above
+                              (the few launches that find the solve done add to it). 0 for
+                              fcg_solve and the batch solvers.                                    */
 } bsk_cg_report;
 
 /* Solves A x = b by conjugate gradients (section 2.5), starting from the x passed in, which
@@ -171,6 +179,60 @@ int bsk_batch_autotune(bsk_batch* b, int reps, int* nzc, int* check_every, doubl
 
 /* Sets the decomposition and graph length directly (e.g. from a cached autotuning result). */
 int bsk_batch_configure(bsk_batch* b, int nzc, int check_every);
+
+/* ---- the learned preconditioner and flexible CG ---------------------------------------------
+ * A 3-level convolutional network N maps a normalised residual to an error estimate
+ * (16 channels, 3^3 kernels, BF16 weights and activations, FP32 accumulation; the 16 -> 16
+ * convolutions run on the tensor cores):
+ *   a1 = relu(conv_s2(r) + b1); a2 = relu(conv_s2(a1) + b2); a3 = relu(conv_s1(a2) + b3);
+ *   a4 = relu(convT_s2(a3) + b4 + a1); z = mask * (convT_s2(a4) + b5 + conv_s1(r; Wf))
+ * with stride-2 convolutions halving each axis (ceil) and their transposes restoring it. The
+ * paper has no learned component; the network is an addition of this library to the CG stage.
+ * Parameters are bsk_net_param_count() FP32 values (layout in net.cu); training runs on the
+ * GPU through bsk_net_backward (loss = mean over active voxels of (N(r) - e)^2) and Adam. */
+typedef struct bsk_net bsk_net;
+
+int bsk_net_param_count(void);
+/* Network for an nx*ny*nz grid (each >= 2); allocates its activations and gradients. */
+int bsk_net_create(int nx, int ny, int nz, void* stream, bsk_net** out);
+void bsk_net_destroy(bsk_net* net);
+/* params: host or device pointer to bsk_net_param_count() floats; resets the Adam state. */
+int bsk_net_set_params(bsk_net* net, const float* params);
+int bsk_net_get_params(bsk_net* net, float* params);
+/* z = N(r); r, z: DEVICE float vectors of the grid; mask: DEVICE uint8 or NULL. */
+int bsk_net_forward(bsk_net* net, const float* r, const uint8_t* mask, float* z);
+/* Activation of the hidden layers: BSK_ACT_RELU (default) or BSK_ACT_LINEAR (identity, and the
+ * biases are ignored and receive no gradient, so the network is a linear map of r: a fixed
+ * linear multilevel preconditioner, which flexible CG handles far better than a nonlinear one). */
+#define BSK_ACT_RELU 0
+#define BSK_ACT_LINEAR 1
+int bsk_net_set_activation(bsk_net* net, int act);
+/* Zero the accumulated gradients and loss. */
+int bsk_net_zero_grad(bsk_net* net);
+/* Forward and backward of one sample (r, e): accumulates loss_weight/2 * sum (N(r) - e)^2
+ * over active voxels and its parameter gradients (loss_weight = 2 / active voxels gives the
+ * mean squared error). */
+int bsk_net_backward(bsk_net* net, const float* r, const float* e, const uint8_t* mask, float loss_weight);
+/* Forward and backward of one sample for a loss the caller evaluates: dz (DEVICE floats of the
+ * grid) is dL/dz, used times scale on active voxels; accumulates the parameter gradients only
+ * (the accumulated loss is unchanged). Used for the energy-norm loss
+ * (z - e)^T A (z - e), whose gradient 2 A (z - e) needs the operator. */
+int bsk_net_backward_grad(bsk_net* net, const float* r, const float* dz, const uint8_t* mask, float scale);
+/* Adam step (beta1 0.9, beta2 0.999) with learning rate lr on the gradients times grad_scale. */
+int bsk_net_adam(bsk_net* net, float lr, float grad_scale);
+/* Accumulated loss (host float) and, if grads is not NULL, the gradients (host floats). */
+int bsk_net_read_loss(bsk_net* net, float* loss, float* grads);
+
+/* Flexible CG (FCG(1)) preconditioned by the network, z = ||r|| N(r / ||r||) / (hx hy hz) (the
+ * coarse path is a correction on top of the full-resolution 3^3 filter Wf), as the inner FP32
+ * solver of iterative
+ * refinement (handle precision BSK_F32_IR; b, x double). The network must have been created for
+ * the handle's grid. Falls back to plain CG for the rest of an inner solve when the network's
+ * direction is not a descent direction or the residual stops improving (stall_window,
+ * default 8); the FP64 true residual decides convergence. net == NULL runs the same iteration
+ * without preconditioner (plain CG). The first call allocates the handle's FCG work vectors. */
+int fcg_solve(bsk_handle* h, bsk_net* net, const void* b, void* x, const bsk_cg_opts* opts,
+              bsk_cg_report* report);
 
 /* Kernel timing for roofline measurements. Launches one of the library's kernels `reps` times
  * back to back on the handle's stream, on the handle's own work vectors (which it first zeroes,

@@ -34,6 +34,7 @@ class CgReport(ctypes.Structure):
         ("status", ctypes.c_int), ("iterations", ctypes.c_int),
         ("outer_iterations", ctypes.c_int), ("rel_residual", ctypes.c_double),
         ("elapsed_ms", ctypes.c_double), ("kernel_launches", ctypes.c_longlong),
+        ("fallback_iter", ctypes.c_int), ("iter_ms", ctypes.c_double),
     ]
 
 
@@ -72,6 +73,26 @@ SIGNATURES = {
                                           ctypes.POINTER(ctypes.c_int),
                                           ctypes.POINTER(ctypes.c_double)]),
     "bsk_batch_configure": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int, ctypes.c_int]),
+    "bsk_net_param_count": (ctypes.c_int, []),
+    "bsk_net_create": (ctypes.c_int, [ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_void_p,
+                                      ctypes.POINTER(ctypes.c_void_p)]),
+    "bsk_net_destroy": (None, [ctypes.c_void_p]),
+    "bsk_net_set_params": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p]),
+    "bsk_net_get_params": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p]),
+    "bsk_net_forward": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p,
+                                       ctypes.c_void_p]),
+    "bsk_net_set_activation": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int]),
+    "bsk_net_zero_grad": (ctypes.c_int, [ctypes.c_void_p]),
+    "bsk_net_backward": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p,
+                                        ctypes.c_void_p, ctypes.c_float]),
+    "bsk_net_backward_grad": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p,
+                                              ctypes.c_void_p, ctypes.c_float]),
+    "bsk_net_adam": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_float, ctypes.c_float]),
+    "bsk_net_read_loss": (ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(ctypes.c_float),
+                                         ctypes.c_void_p]),
+    "fcg_solve": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p,
+                                 ctypes.c_void_p, ctypes.POINTER(CgOpts),
+                                 ctypes.POINTER(CgReport)]),
     "bsk_last_error": (ctypes.c_char_p, []),
     "bsk_status_string": (ctypes.c_char_p, [ctypes.c_int]),
 }

@@ -46,7 +46,8 @@ def _opts(tol=None, max_iter=None, check_every=None, stall_window=None, inner_to
 def _report(rep: _native.CgReport) -> dict:
     return {"status": rep.status, "iterations": rep.iterations,
             "outer_iterations": rep.outer_iterations, "rel_residual": rep.rel_residual,
-            "elapsed_ms": rep.elapsed_ms, "kernel_launches": rep.kernel_launches}
+            "elapsed_ms": rep.elapsed_ms, "kernel_launches": rep.kernel_launches,
+            "fallback_iter": rep.fallback_iter, "iter_ms": rep.iter_ms}
 
 
 class Handle:
@@ -129,6 +130,17 @@ class Handle:
                                           ctypes.byref(o), ctypes.byref(rep)))
         return _report(rep)
 
+    def fcg_solve(self, b: torch.Tensor, x: torch.Tensor, net: Optional["Net"] = None,
+                  **opts) -> dict:
+        """Flexible CG with the learned preconditioner (net=None: no preconditioner) inside
+        iterative refinement (BSK_F32_IR handles)."""
+        o = _opts(**opts)
+        rep = _native.CgReport()
+        _native.check(self._lib.fcg_solve(self._ptr, net._ptr if net is not None else None,
+                                          self._vec(b, "b"), self._vec(x, "x"), ctypes.byref(o),
+                                          ctypes.byref(rep)))
+        return _report(rep)
+
     def time_kernel(self, kernel: int, reps: int = 10) -> float:
         """Mean device time (ms) of one launch of a library kernel (bsk_time_kernel)."""
         out = ctypes.c_double(0.0)
@@ -208,6 +220,91 @@ class BatchHandle:
     def close(self):
         if self._ptr:
             self._lib.bsk_batch_destroy(self._ptr)
+            self._ptr = ctypes.c_void_p(None)
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+class Net:
+    """The learned preconditioner network for one grid (bsk_net_*)."""
+
+    def __init__(self, nx: int, ny: int, nz: int, stream: Optional[torch.cuda.Stream] = None,
+                 activation: str = "relu"):
+        self._lib = _native.load()
+        self._ptr = ctypes.c_void_p(None)
+        self.shape = (int(nz), int(ny), int(nx))
+        self.stream = stream if stream is not None else torch.cuda.current_stream()
+        self.nparam = self._lib.bsk_net_param_count()
+        _native.check(self._lib.bsk_net_create(int(nx), int(ny), int(nz),
+                                               ctypes.c_void_p(self.stream.cuda_stream),
+                                               ctypes.byref(self._ptr)))
+        self.set_activation(activation)
+
+    def set_activation(self, activation: str):
+        """"relu" or "linear" (bsk_net_set_activation)."""
+        act = {"relu": 0, "linear": 1}[activation]
+        _native.check(self._lib.bsk_net_set_activation(self._ptr, act))
+        self.activation = activation
+
+    def _f32(self, t, name):
+        if not (isinstance(t, torch.Tensor) and t.is_cuda and t.dtype == torch.float32
+                and t.is_contiguous() and tuple(t.shape) == self.shape):
+            raise ValueError(f"{name} must be a contiguous CUDA float32 tensor of {self.shape}")
+        return t.data_ptr()
+
+    @staticmethod
+    def _mask(m):
+        return None if m is None else m.data_ptr()
+
+    def set_params(self, params: torch.Tensor):
+        p = params.detach().to(torch.float32).contiguous()
+        assert p.numel() == self.nparam
+        _native.check(self._lib.bsk_net_set_params(self._ptr, p.data_ptr()))
+        torch.cuda.current_stream().synchronize()
+
+    def get_params(self) -> torch.Tensor:
+        out = torch.empty(self.nparam, dtype=torch.float32)
+        _native.check(self._lib.bsk_net_get_params(self._ptr, out.data_ptr()))
+        return out
+
+    def forward(self, r: torch.Tensor, mask=None, z: Optional[torch.Tensor] = None):
+        z = torch.empty_like(r) if z is None else z
+        _native.check(self._lib.bsk_net_forward(self._ptr, self._f32(r, "r"), self._mask(mask),
+                                                self._f32(z, "z")))
+        return z
+
+    def zero_grad(self):
+        _native.check(self._lib.bsk_net_zero_grad(self._ptr))
+
+    def backward(self, r, e, mask=None, loss_weight=None):
+        if loss_weight is None:
+            active = r.numel() if mask is None else int(mask.sum().item())
+            loss_weight = 2.0 / max(active, 1)
+        _native.check(self._lib.bsk_net_backward(self._ptr, self._f32(r, "r"), self._f32(e, "e"),
+                                                 self._mask(mask), float(loss_weight)))
+
+    def backward_grad(self, r, dz, mask=None, scale: float = 1.0):
+        """Parameter gradients for a caller-evaluated loss with output gradient dz."""
+        _native.check(self._lib.bsk_net_backward_grad(self._ptr, self._f32(r, "r"), self._f32(dz, "dz"),
+                                                      self._mask(mask), float(scale)))
+
+    def adam(self, lr: float, grad_scale: float = 1.0):
+        _native.check(self._lib.bsk_net_adam(self._ptr, float(lr), float(grad_scale)))
+
+    def read(self, grads: bool = False):
+        loss = ctypes.c_float(0.0)
+        g = np.zeros(self.nparam, dtype=np.float32) if grads else None
+        _native.check(self._lib.bsk_net_read_loss(self._ptr, ctypes.byref(loss),
+                                                  g.ctypes.data if grads else None))
+        return (loss.value, g) if grads else loss.value
+
+    def close(self):
+        if self._ptr:
+            self._lib.bsk_net_destroy(self._ptr)
             self._ptr = ctypes.c_void_p(None)
 
     def __del__(self):

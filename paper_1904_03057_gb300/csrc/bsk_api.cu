@@ -117,6 +117,11 @@ struct bsk_handle {
     cudaGraphExec_t graph;
     int graph_chunk;
     long long launches;   // kernels launched since the counter was last read
+    cudaEvent_t it_ev[2]; // bracket the inner iterations on `stream` (bsk_cg_report.iter_ms)
+    double iter_ms;       // device time of the inner iterations since the counter was last read
+    float* fcg_ws;        // FCG work vectors z, rn, zn (allocated by the first fcg_solve)
+    double* fcg_partials;
+    void* fcg_state;
 };
 
 namespace {
@@ -321,6 +326,7 @@ int run_iterations(bsk_handle* h, const Opts& o, std::chrono::steady_clock::time
     int rc = ensure_graph<T>(h, o.check_every);
     if (rc) return rc;
     if ((rc = sync_scalars(h, h->sc))) return rc;
+    BSK_CUDA(cudaEventRecord(h->it_ev[0], h->stream));
     while (!h->h_sc->done) {
         BSK_CUDA(cudaGraphLaunch(h->graph, h->stream));
         h->launches += (h->use_tma ? 1LL : 2LL) * h->graph_chunk;
@@ -330,6 +336,11 @@ int run_iterations(bsk_handle* h, const Opts& o, std::chrono::steady_clock::time
             return fail(BSK_ETIMEOUT, "solve exceeded its time limit of %.3f s", o.time_limit);
         }
     }
+    BSK_CUDA(cudaEventRecord(h->it_ev[1], h->stream));
+    BSK_CUDA(cudaEventSynchronize(h->it_ev[1]));
+    float ms = 0.f;
+    BSK_CUDA(cudaEventElapsedTime(&ms, h->it_ev[0], h->it_ev[1]));
+    h->iter_ms += ms;
     if (!h->use_tma)   // the single-pass iteration leaves no x update pending
         BSK_LAUNCH(h, bsk::launch_cg_flush<T>(static_cast<T*>(h->x), static_cast<const T*>(h->p0),
                                          static_cast<const T*>(h->p1), h->len, h->sc, h->stream));
@@ -587,6 +598,10 @@ extern "C" int bsk_create(const bsk_problem* prob, int precision, void* stream, 
     }
     e = cudaStreamCreateWithFlags(&h->cap_stream, cudaStreamNonBlocking);
     if (e != cudaSuccess) return cleanup(cuda_fail(e, "cudaStreamCreate"));
+    for (int i = 0; i < 2; i++) {
+        e = cudaEventCreate(&h->it_ev[i]);
+        if (e != cudaSuccess) return cleanup(cuda_fail(e, "cudaEventCreate"));
+    }
     if (prob->mask) {
         BSK_ALLOC(h->mask, len);
         e = cudaMemcpyAsync(h->mask, prob->mask, len, cudaMemcpyDeviceToDevice, h->stream);
@@ -644,7 +659,12 @@ extern "C" void bsk_destroy(bsk_handle* h)
     for (void* p : ptrs)
         if (p) cudaFree(p);
     if (h->h_sc) cudaFreeHost(h->h_sc);
+    if (h->fcg_ws) cudaFree(h->fcg_ws);
+    if (h->fcg_partials) cudaFree(h->fcg_partials);
+    if (h->fcg_state) cudaFree(h->fcg_state);
     if (h->cap_stream) cudaStreamDestroy(h->cap_stream);
+    for (int i = 0; i < 2; i++)
+        if (h->it_ev[i]) cudaEventDestroy(h->it_ev[i]);
     delete h;
 }
 
@@ -708,11 +728,13 @@ extern "C" int cg_solve(bsk_handle* h, const void* b, void* x, const bsk_cg_opts
     const Opts o = resolve(opts);
     if (report) memset(report, 0, sizeof *report);
     h->launches = 0;
+    h->iter_ms = 0.0;
     int st = solve_dispatch(h, b, x, o, report, t0);
     if (report) {
         report->status = st;
         report->elapsed_ms = 1e3 * seconds_since(t0);
         report->kernel_launches = h->launches;
+        report->iter_ms = h->iter_ms;
     }
     return st;
 }
@@ -731,6 +753,7 @@ extern "C" int heat_step(bsk_handle* h, void* u, const void* q, int nsteps, cons
     void* b = h->prec == BSK_F32_IR ? (void*)h->b64 : h->bvec;
     int st = BSK_OK;
     h->launches = 0;
+    h->iter_ms = 0.0;
     for (int s = 0; s < nsteps; s++) {
         bsk::OpLaunch L;
         fill_launch(h, L, bsk::MODE_MASS);
@@ -750,6 +773,122 @@ extern "C" int heat_step(bsk_handle* h, void* u, const void* q, int nsteps, cons
         report->status = st;
         report->elapsed_ms = 1e3 * seconds_since(t0);
         report->kernel_launches = h->launches;
+        report->iter_ms = h->iter_ms;
+    }
+    return st;
+}
+
+extern "C" int bsk_net_forward(bsk_net* net, const float* r, const uint8_t* mask, float* z);
+
+// Iterative refinement around the preconditioned inner FCG solve (fcg.cu).
+extern "C" int fcg_solve(bsk_handle* h, bsk_net* net, const void* bv, void* xv, const bsk_cg_opts* opts,
+                         bsk_cg_report* rep)
+{
+    auto t0 = std::chrono::steady_clock::now();
+    if (int rc = check_handle(h)) return rc;
+    if (h->prec != BSK_F32_IR) return fail(BSK_EINVAL, "fcg_solve needs a BSK_F32_IR handle");
+    if (!bv || !xv) return fail(BSK_EINVAL, "null vector");
+    if (overlaps(bv, xv, h->len * sizeof(double))) return fail(BSK_EINVAL, "b and x overlap");
+    const Opts o = resolve(opts);
+    if (rep) memset(rep, 0, sizeof *rep);
+    h->launches = 0;
+    const double* b = (const double*)bv;
+    double* x = (double*)xv;
+    if (!h->fcg_ws) {
+        cudaError_t e = cudaMalloc((void**)&h->fcg_ws, 3 * h->len * sizeof(float));
+        if (e == cudaSuccess) e = cudaMalloc((void**)&h->fcg_partials, 3 * 1216 * sizeof(double));
+        if (e == cudaSuccess) e = cudaMalloc(&h->fcg_state, bsk::fcg_state_bytes());
+        if (e != cudaSuccess) {
+            cudaGetLastError();
+            return fail(BSK_ENOMEM, "FCG work vectors: %s", cudaGetErrorString(e));
+        }
+        BSK_CUDA(cudaMemsetAsync(h->fcg_state, 0, bsk::fcg_state_bytes(), h->stream));
+    }
+    bsk::FcgVectors V;
+    V.b = static_cast<const float*>(h->r);   // the scaled residual is written here, then copied to r
+    V.x = static_cast<float*>(h->x);
+    V.r = static_cast<float*>(h->r);
+    V.p = static_cast<float*>(h->p0);
+    V.q = static_cast<float*>(h->q);
+    V.z = h->fcg_ws;
+    V.rn = h->fcg_ws + h->len;
+    V.zn = h->fcg_ws + 2 * h->len;
+    V.partials = h->fcg_partials;
+    V.state = h->fcg_state;
+    auto op = [&](const float* p, float* q) -> int {
+        cudaError_t e;
+        if (tma_ok(h, sizeof(float), {p, q})) {
+            bsk::TmaLaunch T;
+            fill_tma(h, T, bsk::TMODE_OP);
+            T.in[0] = p;
+            T.out0 = q;
+            T.fin = bsk::FIN_NONE;
+            e = bsk::launch_tma<float>(T, h->stream);
+        } else {
+            bsk::OpLaunch L;
+            fill_launch(h, L, bsk::MODE_OP);
+            L.in0 = p;
+            L.out0 = q;
+            L.fin = bsk::FIN_NONE;
+            e = bsk::launch_op<float>(L, h->stream);
+        }
+        if (e != cudaSuccess) return cuda_fail(e, "operator launch");
+        h->launches += 1;
+        return BSK_OK;
+    };
+    auto netf = [&](bsk_net* n, const float* r, const uint8_t* m, float* z) -> int {
+        h->launches += 5;
+        return bsk_net_forward(n, r, m, z);
+    };
+    int rc;
+    int total_iters = 0, outer = 0, st = BSK_NOT_CONVERGED, fb = -1;
+    double rel = 0.0;
+    BSK_LAUNCH(h, bsk::launch_copy_masked<double>(x, x, h->len, h->mask, h->stream));
+    for (;; outer++) {
+        bsk::OpLaunch L;
+        fill_launch(h, L, bsk::MODE_RES);
+        L.in0 = x;
+        L.b = b;
+        L.out0 = h->r64;
+        L.sc = h->sc64;
+        L.partials = h->partials;
+        L.fin = bsk::FIN_RES_TRUE;
+        BSK_LAUNCH(h, op_launch<double>(L, h->stream));
+        if ((rc = sync_scalars(h, h->sc64))) return rc;
+        const double rr = h->h_sc->rr_true, bb = h->h_sc->bb_true;
+        if (!std::isfinite(rr) || !std::isfinite(bb)) return fail(BSK_EBREAKDOWN, "non-finite residual");
+        if (bb == 0.0) {
+            BSK_CUDA(cudaMemsetAsync(x, 0, h->len * sizeof(double), h->stream));
+            rel = 0.0;
+            st = BSK_OK;
+            break;
+        }
+        rel = std::sqrt(rr / bb);
+        if (rel <= o.tol) { st = BSK_OK; break; }
+        if (outer >= o.max_outer || total_iters >= o.max_iter) { st = BSK_NOT_CONVERGED; break; }
+        double inner = std::max(o.inner_tol, 0.3 * o.tol / rel);
+        if (inner > 0.5) inner = 0.5;
+        BSK_LAUNCH(h, bsk::launch_ir_scale_down(h->r64, static_cast<float*>(h->r), h->len, h->sc64, h->stream));
+        int it = 0, fbi = -1;
+        // the network predicts errors in units of 1 / (hx hy hz), the inverse mass scale
+        const double out_scale = 1.0 / (h->h[0] * h->h[1] * h->h[2]);
+        int ist = bsk::fcg_inner(V, h->len, h->mask, inner, o.max_iter - total_iters, o.stall_window,
+                                 out_scale, 0.0, op, net, netf, h->stream, &it, &fbi, o.time_limit, t0);
+        h->launches += 6LL * it;
+        total_iters += it;
+        if (fbi >= 0) fb = fbi;
+        if (ist == BSK_ETIMEOUT || ist == BSK_ECUDA) return ist;
+        if (ist == BSK_EBREAKDOWN && it == 0) return ist;
+        BSK_LAUNCH(h, bsk::launch_ir_update(x, static_cast<const float*>(h->x), h->len, h->sc64, h->stream));
+    }
+    if (rep) {
+        rep->status = st;
+        rep->iterations = total_iters;
+        rep->outer_iterations = outer;
+        rep->rel_residual = rel;
+        rep->elapsed_ms = 1e3 * seconds_since(t0);
+        rep->kernel_launches = h->launches;
+        rep->fallback_iter = fb;
     }
     return st;
 }

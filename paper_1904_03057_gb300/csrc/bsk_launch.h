@@ -6,7 +6,12 @@
 #include <stddef.h>
 #include <stdint.h>
 
+#include <chrono>
+#include <functional>
+
 #include "bsk_device.cuh"
+
+struct bsk_net;
 
 namespace bsk {
 
@@ -108,6 +113,20 @@ cudaError_t fill_batch_problem(void* host_desc, int degree, int nx, int ny, int 
                                float* const p[2], float* x, Scalars* sc, double* partials,
                                unsigned int* items_done, int timing, int* nitems_out);
 cudaError_t launch_tma_batch(const TmaBatchLaunch& L, cudaStream_t s);
+
+// ---- flexible CG with the learned preconditioner (fcg.cu, net.cu) ----
+struct FcgVectors {
+    const float* b;      // right-hand side of the inner solve
+    float *x, *r, *p, *q, *z, *rn, *zn;
+    double* partials;    // 3 doubles per block of the vector kernels (1216 blocks at most)
+    void* state;         // fcg_state_bytes()
+};
+size_t fcg_state_bytes();
+int fcg_inner(const FcgVectors& V, size_t n, const uint8_t* mask, double tol, int max_iter, int stall_window,
+              double out_scale, double jac, const std::function<int(const float*, float*)>& op, bsk_net* net,
+              const std::function<int(bsk_net*, const float*, const uint8_t*, float*)>& net_forward,
+              cudaStream_t s, int* iters, int* fallback_iter, double time_limit,
+              std::chrono::steady_clock::time_point t0);
 
 cudaError_t launch_ir_scale_down(const double* r64, float* r32, size_t len, const Scalars* outer,
                                  cudaStream_t s);
