@@ -81,6 +81,9 @@ struct TGeo {
     static constexpr int BX = kTX + 2 * HL + 4;         // box width; +4 columns spread smem banks
     static constexpr int HY = kTY + 2 * N;              // box height (tile rows + y halo)
     static constexpr int MXP = kTX + 4;                 // row pitch of the x-sweep results
+    // interior box (b or x) width = row pitch of it and of the ring: 16 bytes over the tile,
+    // so that threads on consecutive rows hit distinct shared-memory banks
+    static constexpr int IP = kTX + 16 / (int)sizeof(T);
     static constexpr int WIN = 8 + 2 * HL;              // x-window loaded per 8 outputs
 };
 
@@ -91,7 +94,7 @@ struct TLayout {
     static constexpr int NINT = MODE == TMODE_OP ? 0 : 1;
     static constexpr size_t rnd(size_t b) { return (b + 127) / 128 * 128; }
     static constexpr size_t in_bytes = rnd(sizeof(T) * G::HY * G::BX);
-    static constexpr size_t int_bytes = rnd(sizeof(T) * kTY * kTX);
+    static constexpr size_t int_bytes = rnd(sizeof(T) * kTY * G::IP);
     static constexpr size_t stage_bytes = NIN * in_bytes + NINT * int_bytes;
     static constexpr int S = MODE == TMODE_OP ? 4 : 2;   // pipeline stages
     static constexpr size_t off_mx = S * stage_bytes;
@@ -101,7 +104,7 @@ struct TLayout {
     static constexpr size_t off_bar = off_ring + ring_bytes;
     static constexpr size_t total = off_bar + 64;
     static constexpr uint32_t tx_bytes =
-        (uint32_t)(NIN * sizeof(T) * G::HY * G::BX + NINT * sizeof(T) * kTY * kTX);
+        (uint32_t)(NIN * sizeof(T) * G::HY * G::BX + NINT * sizeof(T) * kTY * G::IP);
 };
 
 // Packed pair arithmetic: f32x2 instructions for FP32, two scalar operations for FP64.
@@ -270,7 +273,7 @@ __global__ void __launch_bounds__(kTNT, (sizeof(T) == 4 && N <= 4 && !BATCH) ? 2
     using LY = TLayout<T, N, MODE>;
     using PP = P2<T>;
     using T2 = typename PP::t;
-    constexpr int L = G::L, HY = G::HY, BX = G::BX, MXP = G::MXP, HL = G::HL, WIN = G::WIN;
+    constexpr int L = G::L, HY = G::HY, BX = G::BX, MXP = G::MXP, HL = G::HL, WIN = G::WIN, IP = G::IP;
     constexpr int S = LY::S;
     constexpr int NIN = LY::NIN;
     static_assert(LY::total <= 227 * 1024, "shared memory budget");
@@ -482,8 +485,8 @@ __global__ void __launch_bounds__(kTNT, (sizeof(T) == 4 && N <= 4 && !BATCH) ? 2
                         }
                         if (interior) {
                             const int gy = y0 + row - N;
-                            const T* xin = inint + (row - N) * kTX + 8 * g;
-                            T* rg = ring + rslot * (kTY * kTX) + (row - N) * kTX + 8 * g;
+                            const T* xin = inint + (row - N) * IP + 8 * g;
+                            T* rg = ring + rslot * (kTY * IP) + (row - N) * IP + 8 * g;
                             T xi8[8];
                             load_window<T, 8>(xi8, xin);
 #pragma unroll
@@ -529,8 +532,8 @@ __global__ void __launch_bounds__(kTNT, (sizeof(T) == 4 && N <= 4 && !BATCH) ? 2
                     } else if (MODE == TMODE_RES && interior) {
                         // keep b of this plane for the residual of output plane z
                         T b8[8];
-                        load_window<T, 8>(b8, inint + (row - N) * kTX + 8 * g);
-                        T* rg = ring + rslot * (kTY * kTX) + (row - N) * kTX + 8 * g;
+                        load_window<T, 8>(b8, inint + (row - N) * IP + 8 * g);
+                        T* rg = ring + rslot * (kTY * IP) + (row - N) * IP + 8 * g;
                         if constexpr (sizeof(T) == 4) {
                             reinterpret_cast<float4*>(rg)[0] = make_float4(b8[0], b8[1], b8[2], b8[3]);
                             reinterpret_cast<float4*>(rg)[1] = make_float4(b8[4], b8[5], b8[6], b8[7]);
@@ -640,7 +643,7 @@ __global__ void __launch_bounds__(kTNT, (sizeof(T) == 4 && N <= 4 && !BATCH) ? 2
                                 *reinterpret_cast<T2*>(out0 + o) = q[t];
                             } else {
                                 const T2 rg = *reinterpret_cast<const T2*>(
-                                    ring + oslot * (kTY * kTX) + (3 * warp + t) * kTX + c2);
+                                    ring + oslot * (kTY * IP) + (3 * warp + t) * IP + c2);
                                 if constexpr (MODE == TMODE_RES) {
                                     T2 r;
                                     r.x = rg.x - q[t].x;

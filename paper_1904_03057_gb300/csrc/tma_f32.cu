@@ -109,7 +109,7 @@ cudaError_t fill_batch_problem(void* host_desc, int degree, int nx, int ny, int 
         P.out1[par] = r[1 - par];
         P.out2[par] = p[1 - par];
     }
-    if ((e = enc(&P.tint, x, kTX, kTY)) != cudaSuccess) return e;
+    if ((e = enc(&P.tint, x, TGeo<float, 1>::IP, kTY)) != cudaSuccess) return e;
     P.xvec = x;
     P.nx = nx;
     P.ny = ny;

@@ -117,7 +117,7 @@ cudaError_t launch_one(const TmaLaunch& L, cudaStream_t s)
     for (int i = 0; i < nin; i++)
         if ((e = encode_box(&a.tin[i], L.in[i], L.nx, L.ny, L.nz, G::BX, G::HY)) != cudaSuccess) return e;
     if (MODE != TMODE_OP)
-        if ((e = encode_box(&a.tint, L.inint, L.nx, L.ny, L.nz, kTX, kTY)) != cudaSuccess) return e;
+        if ((e = encode_box(&a.tint, L.inint, L.nx, L.ny, L.nz, G::IP, kTY)) != cudaSuccess) return e;
     a.out0 = static_cast<BSK_T*>(L.out0);
     a.out1 = static_cast<BSK_T*>(L.out1);
     a.out2 = static_cast<BSK_T*>(L.out2);
