@@ -4,12 +4,13 @@
 Workload (the paper's ~0.8 G-node scale, synthetic): 928^3 = 799,178,752 unknowns on the unit
 cube, cubic B-splines, zero Dirichlet faces, dt = 5e-4, initial coefficients = 64 seeded sine
 modes (k in {1..16}^3, amplitudes N(0,1)/|k|^2), one implicit Euler step per benchmark step,
-solved to a 1e-8 true relative residual by CG with FP32 operator sweeps and FP64 iterative
-refinement (FP64 residual, FP64 CG scalars).
+solved to a 1e-8 true relative residual by CG with FP32 operator sweeps and iterative
+refinement (FP64-accurate true residual -- double-float arithmetic on the FP32 pipes, FP64
+input and output -- FP64 update and CG scalars).
 
 value = operator throughput inside the solve: unknowns x operator applications / time, summed
 over ranks, where every application of the full operator counts (inner FP32 CG iterations and
-FP64 true residuals; the mass-only right-hand side is not counted). Each rank solves its own
+the true residuals; the mass-only right-hand side is not counted). Each rank solves its own
 problem (weak scaling, no collective on the data path).
 
 --impl reference runs the FP64 CPU oracle (the test-suite's reference implementation) on a
@@ -160,6 +161,72 @@ def run_reference(args, rank, world):
     print(json.dumps(line), flush=True)
 
 
+def fcg_race():
+    """The 512^3 union-of-40-spheres race (config 5): one implicit Euler step from u = 0 with a
+    Gaussian source, dt = 1e-3, each solver from x = 0 to a 1e-8 true relative residual: plain
+    FP64 CG, FP32 CG with FP64 refinement, and flexible CG preconditioned by the trained linear
+    network inside FP64 refinement. The network is trained first (32^3 crops at the same h and
+    dt; its time is reported separately); solves are timed with CUDA events after a warm-up."""
+    import torch
+
+    from paper_1904_03057_gb300 import api, inputs, learned
+    N, dt, tol = 512, 1e-3, 1e-8
+    h = 1.0 / (N + 1)
+    t0 = time.perf_counter()
+    problems = learned.make_problems(40, crop=32, h=h, dt=dt, seed=2, noise_fraction=0.25)
+    pairs = learned.make_pairs(440, crop=32, h=h, dt=dt, problems=problems,
+                               ks=(0, 1, 2, 3, 4, 6, 8, 12, 16, 24, 32))
+    tr = api.Net(32, 32, 32, activation="linear")
+    tr.set_params(learned.init_params(0, h=h, dt=dt))
+    learned.train_on_policy(tr, pairs, problems[:12], rounds=3)
+    params = tr.get_params()
+    tr.close()
+    del pairs, problems
+    torch.cuda.synchronize()
+    train_s = time.perf_counter() - t0
+
+    centers, radii = inputs.random_spheres(5, 40, 0.05, 0.2)
+    mask = inputs.union_of_spheres_mask(N, N, N, centers, radii, h=h, device="cuda")
+    q = inputs.gaussian_source(N, N, N, inputs.gaussian_centers(5, 32), sigma=0.03, h=h, mask=mask,
+                               device="cuda")
+    H64 = api.Handle(N, N, N, DEGREE, h, dt, mask=mask, precision="f64")
+    b = H64.mass_apply(q) * dt          # (M + dt K) u1 = M (u0 + dt q), u0 = 0
+    del q
+    stream = torch.cuda.current_stream()
+
+    def timed(fn):
+        x = torch.zeros_like(b)
+        fn(x, 1e-3)                      # warm-up: graphs, work vectors
+        x.zero_()
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        rep = fn(x, tol)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        return {"ms": e0.elapsed_time(e1), "iterations": rep["iterations"],
+                "outer_iterations": rep["outer_iterations"], "rel_residual": rep["rel_residual"],
+                "status": rep["status"], "fallback_iter": rep["fallback_iter"]}
+
+    out = {"workload": "union40spheres_512cube_cubic_dt1e-3_one_step", "tol": tol,
+           "active_unknowns": int(mask.sum().item())}
+    out["fp64_cg"] = timed(lambda x, t: H64.cg_solve(b, x, tol=t))
+    H64.close()
+    H32 = api.Handle(N, N, N, DEGREE, h, dt, mask=mask, precision="f32_ir")
+    out["f32_ir_cg"] = timed(lambda x, t: H32.cg_solve(b, x, tol=t))
+    out["fcg_plain_ir"] = timed(lambda x, t: H32.fcg_solve(b, x, None, tol=t))
+    net = api.Net(N, N, N, activation="linear")
+    net.set_params(params)
+    out["fcg_net_ir"] = timed(lambda x, t: H32.fcg_solve(b, x, net, tol=t))
+    net.close()
+    H32.close()
+    out["training_s"] = train_s
+    out["speedup_fcg_net_vs_fp64_cg"] = out["fp64_cg"]["ms"] / out["fcg_net_ir"]["ms"]
+    out["iterations_fcg_net_vs_fcg_plain"] = (out["fcg_net_ir"]["iterations"]
+                                              / max(out["fcg_plain_ir"]["iterations"], 1))
+    return out
+
+
 def run_ours(args, rank, world, dist):
     import torch
 
@@ -201,7 +268,7 @@ def run_ours(args, rank, world, dist):
         elapsed_ms = float(t.item())
     inner = sum(r["iterations"] for r in reps)
     outer = sum(r["outer_iterations"] for r in reps)
-    op_apps = inner + outer + len(reps)          # inner CG + FP64 residuals (one per outer + final)
+    op_apps = inner + outer + len(reps)          # inner CG + true residuals (one per outer + final)
     launches = sum(r["kernel_launches"] for r in reps)
     value = world * dofs * op_apps / (elapsed_ms * 1e-3) / 1e9
     ms_step = elapsed_ms / args.steps
@@ -243,7 +310,25 @@ def run_ours(args, rank, world, dist):
     ms_op = H.time_kernel(api.KERNEL_OP, reps=10)
     bytes_op = 8.0 * dofs       # read x, write y (FP32)
     ms_res64 = H.time_kernel(api.KERNEL_RES64, reps=3)
+    ms_resdf = H.time_kernel(api.KERNEL_RES_DF, reps=5)
     ms_upd = H.time_kernel(api.KERNEL_CG_UPDATE, reps=10)
+    # BF16-storage operator variant (BSK_BF16S): its speed, and what BF16 storage costs in
+    # accuracy against the FP64 operator of the same (unrounded) field
+    Hb = api.Handle(N, N, N, DEGREE, h, DT, precision="bf16s", stream=stream)
+    ub = u.to(torch.bfloat16)
+    yb = Hb.op_apply(ub)
+    torch.cuda.synchronize()
+    eb0, eb1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    eb0.record(stream)
+    for _ in range(3):
+        Hb.op_apply(ub, yb)
+    eb1.record(stream)
+    torch.cuda.synchronize()
+    ms_bf16 = eb0.elapsed_time(eb1) / 3
+    y64 = H.op_apply(u)
+    bf16_err = (torch.linalg.vector_norm(yb.double() - y64) / torch.linalg.vector_norm(y64)).item()
+    del y64, yb, ub
+    Hb.close()
     ach = bytes_fused / (ms_fused_live * 1e-3) / 1e9
     traffic = None
     if CG_TRAFFIC_BYTES_PER_UNKNOWN is not None and cg_kernel_sources_sha256() == CG_TRAFFIC_SOURCES_SHA256:
@@ -257,7 +342,8 @@ def run_ours(args, rank, world, dist):
         "config": {
             "workload": WORKLOAD if N == N_GRID else WORKLOAD.replace(str(N_GRID), str(N)),
             "grid": f"{N}^3", "unknowns": dofs, "degree": DEGREE, "dt": DT,
-            "tol": TOL, "precision": "FP32 operator sweeps, FP64 true residual + CG scalars",
+            "tol": TOL, "precision": "FP32 operator sweeps; true residual in double-float "
+                                     "(FP64-accurate) on FP64 vectors; FP64 update and CG scalars",
             "l2": f"inputs larger than L2 ({4 * dofs / 1e9:.2f} GB FP32 / {8 * dofs / 1e9:.2f} GB FP64 vectors)",
             "op_applications_per_step": op_apps / len(reps),
             "cg_iterations_per_step": inner / len(reps),
@@ -265,10 +351,13 @@ def run_ours(args, rank, world, dist):
             "max_true_rel_residual": worst_res,
             "kernel_ms": {"cg_fused_f32_in_timed_region": ms_fused_live,
                           "cg_fused_f32_alone": ms_fused, "cg_update_f32": ms_upd, "op_f32": ms_op,
-                          "residual_f64": ms_res64},
+                          "residual_f64": ms_res64, "residual_double_float": ms_resdf},
             "cg_iteration_share_of_timed_region": iter_ms / elapsed_ms if world == 1 else None,
             "op_apply_gdofs": dofs / (ms_op * 1e-3) / 1e9,
             "op_apply_hbm_frac": bytes_op / (ms_op * 1e-3) / 1e9 / hbm,
+            "op_apply_bf16_storage": {"gdofs": dofs / (ms_bf16 * 1e-3) / 1e9, "ms": ms_bf16,
+                                      "rel_l2_error_vs_fp64": bf16_err,
+                                      "kernel": "general kernel, FP32 arithmetic, BF16 in/out"},
             "parallelism": f"{world} independent problems (one per GPU)",
         },
         "roofline": {"kernel": "k_op_tma<float,3,CG>: one CG iteration (p, r, x updates + A p + "
@@ -283,11 +372,14 @@ def run_ours(args, rank, world, dist):
     }
     if e2e is not None:
         line["e2e"] = e2e
+    H.close()
+    del u
+    if rank == 0 and not args.no_fcg_race and args.grid == N_GRID:
+        line["fcg_race"] = fcg_race()
     if rank == 0 and not args.no_cpu_baseline:
         v, cores, secs, desc = cpu_oracle_sample()
         line["cpu_baseline"] = {"value": v, "unit": "GDoF/s", "cores": cores, "kind": "oracle",
                                 "sample": desc}
-    H.close()
     if rank == 0:
         print(json.dumps(line), flush=True)
 
@@ -300,6 +392,8 @@ def main():
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-fcg-race", action="store_true",
+                    help="skip the 512^3 union-of-spheres time-to-1e-8 race (learned FCG vs CG)")
     ap.add_argument("--grid", type=int, default=N_GRID,
                     help="grid edge (default: the benchmark workload; smaller grids are the "
                          "profiler's small case)")

@@ -55,6 +55,10 @@ extern "C" {
 #define BSK_F32 1     /* vectors float; operator in FP32; CG scalars and reductions in FP64       */
 #define BSK_F32_IR 2  /* vectors double; FP64 true residual b - A x and FP64 update of x around an
                          inner FP32 CG (iterative refinement); CG scalars in FP64                 */
+#define BSK_BF16S 3   /* BF16 storage: op_apply / mass_apply only, vectors bfloat16 (uint16 bit
+                         patterns), arithmetic FP32, each output rounded to nearest BF16 once.
+                         An operator variant for measuring what BF16 storage costs in accuracy
+                         (about 2^-9 relative per stored value); the solvers reject it           */
 
 /* Galerkin kernels of degree-n B-splines on a grid of step h (Table tblBsplines, scalar-product
  * and derivative rows):
@@ -80,8 +84,9 @@ typedef struct bsk_handle bsk_handle;
 /* Creates a solver handle: validates the problem, uploads the kernels and the mask, allocates
  * every work vector the handle needs for op_apply, mass_apply, cg_solve and heat_step (the hot
  * loop never allocates), and binds the handle to `stream` (a cudaStream_t; NULL = the legacy
- * default stream). precision is BSK_F64, BSK_F32 or BSK_F32_IR. On success *out receives the
- * handle, to be released with bsk_destroy. */
+ * default stream). precision is BSK_F64, BSK_F32, BSK_F32_IR or BSK_BF16S (operator only, no
+ * work vectors; cg_solve, heat_step and fcg_solve return BSK_EINVAL). On success *out receives
+ * the handle, to be released with bsk_destroy. */
 int bsk_create(const bsk_problem* prob, int precision, void* stream, bsk_handle** out);
 
 /* Releases the handle and its device memory (after synchronising its stream). NULL is a no-op. */
@@ -105,9 +110,12 @@ typedef struct bsk_cg_opts {
     int check_every;       /* iterations per device-side chunk between host polls [16]          */
     int stall_window;      /* stop with BSK_STALLED when ||r|| has not reached a new minimum for
                               this many iterations [0 = off]                                     */
-    double inner_tol;      /* BSK_F32_IR: relative tolerance of each inner FP32 solve [1e-4]    */
+    double inner_tol;      /* BSK_F32_IR: relative tolerance of each inner FP32 solve [1e-5]    */
     int max_outer;         /* BSK_F32_IR: refinement steps [30]                                 */
     double time_limit_s;   /* wall-clock limit of one call [0 = none]                            */
+    int residual_fp64;     /* BSK_F32_IR: 1 = evaluate the true residual b - A x in FP64
+                              arithmetic; 0 = double-float arithmetic on the FP32 pipes where
+                              the grid allows it (bsk_residual), the default                    */
 } bsk_cg_opts;
 
 /* What a solve did. */
@@ -146,6 +154,16 @@ int heat_step(bsk_handle* h, void* u, const void* q, int nsteps, const bsk_cg_op
 /* Device-side sum of squares of a handle vector (FP64 accumulation); *out is written on the
  * host after synchronising the stream. Used to check results without a host copy. */
 int bsk_norm2(bsk_handle* h, const void* x, double* out);
+
+/* r = b - A x with the handle's true-residual kernel, and ||r||^2, ||b||^2 (FP64, written on the
+ * host after the stream is synchronised; either pointer may be NULL). b, x, r: DEVICE vectors of
+ * the handle's element type; entries of b off the mask are ignored, x must be zero there.
+ * BSK_F32_IR handles evaluate A x in double-float arithmetic (hi + lo float pairs, exact
+ * products and two-sums: about 2^-44 relative per operation, so r agrees with an FP64
+ * evaluation to about 1e-13 of the |A||x| scale) on the FP32 pipes when the grid takes the TMA
+ * kernels (16-byte rows, degree <= 3); fp64 != 0 forces FP64 arithmetic. This is the residual the
+ * refinement of cg_solve / heat_step / fcg_solve uses. */
+int bsk_residual(bsk_handle* h, const void* b, const void* x, void* r, int fp64, double* rr, double* bb);
 
 /* ---- batches of independent problems ------------------------------------------------------
  * Many unmasked box problems (any sizes, degrees 1..5, one shared dt) solved together: each CG
@@ -241,12 +259,14 @@ int fcg_solve(bsk_handle* h, bsk_net* net, const void* b, void* x, const bsk_cg_
  *   BSK_KERNEL_OP        y = A x in the CG precision (FP32 for BSK_F32 and BSK_F32_IR)
  *   BSK_KERNEL_CG_FUSED  the fused CG pass: p = r + beta p, x += alpha p_old, q = A p, p.q
  *   BSK_KERNEL_CG_UPDATE the CG residual pass: r -= alpha q, r.r
- *   BSK_KERNEL_RES64     the FP64 true residual b - A x of iterative refinement (BSK_F32_IR)
- * Returns BSK_EINVAL for an unknown kernel or reps < 1. */
+ *   BSK_KERNEL_RES64     the true residual b - A x in FP64 arithmetic (BSK_F32_IR)
+ *   BSK_KERNEL_RES_DF    the same residual in double-float arithmetic (BSK_F32_IR; TMA grids)
+ * Returns BSK_EINVAL for an unknown kernel, a kernel the handle does not have, or reps < 1. */
 #define BSK_KERNEL_OP 0
 #define BSK_KERNEL_CG_FUSED 1
 #define BSK_KERNEL_CG_UPDATE 2
 #define BSK_KERNEL_RES64 3
+#define BSK_KERNEL_RES_DF 4
 int bsk_time_kernel(bsk_handle* h, int kernel, int reps, double* ms);
 
 /* Allocation-free residual: r = b - A x, with *rr = r.r and *bb = b.b reduced in FP64 (the

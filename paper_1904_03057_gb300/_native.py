@@ -26,6 +26,7 @@ class CgOpts(ctypes.Structure):
         ("tol", ctypes.c_double), ("max_iter", ctypes.c_int), ("check_every", ctypes.c_int),
         ("stall_window", ctypes.c_int), ("inner_tol", ctypes.c_double),
         ("max_outer", ctypes.c_int), ("time_limit_s", ctypes.c_double),
+        ("residual_fp64", ctypes.c_int),
     ]
 
 
@@ -54,6 +55,9 @@ SIGNATURES = {
                                  ctypes.POINTER(CgOpts), ctypes.POINTER(CgReport)]),
     "bsk_norm2": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p,
                                  ctypes.POINTER(ctypes.c_double)]),
+    "bsk_residual": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p,
+                                     ctypes.c_int, ctypes.POINTER(ctypes.c_double),
+                                     ctypes.POINTER(ctypes.c_double)]),
     "bsk_time_kernel": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int, ctypes.c_int,
                                        ctypes.POINTER(ctypes.c_double)]),
     "residual_noalloc": (ctypes.c_int, [ctypes.POINTER(Problem), ctypes.c_int, ctypes.c_void_p,

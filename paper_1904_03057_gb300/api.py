@@ -13,11 +13,12 @@ import torch
 
 from . import _native
 
-F64, F32, F32_IR = 0, 1, 2
-_PREC = {"f64": F64, "f32": F32, "f32_ir": F32_IR, F64: F64, F32: F32, F32_IR: F32_IR}
+F64, F32, F32_IR, BF16S = 0, 1, 2, 3
+_PREC = {"f64": F64, "f32": F32, "f32_ir": F32_IR, "bf16s": BF16S,
+         F64: F64, F32: F32, F32_IR: F32_IR, BF16S: BF16S}
 
 OK, NOT_CONVERGED, STALLED = 0, 1, 2
-KERNEL_OP, KERNEL_CG_FUSED, KERNEL_CG_UPDATE, KERNEL_RES64 = 0, 1, 2, 3
+KERNEL_OP, KERNEL_CG_FUSED, KERNEL_CG_UPDATE, KERNEL_RES64, KERNEL_RES_DF = 0, 1, 2, 3, 4
 EINVAL, ECUDA, ENOMEM, ETIMEOUT, EBREAKDOWN = -1, -2, -3, -4, -5
 
 
@@ -31,7 +32,7 @@ def bspline_kernels(n: int, h: float):
 
 
 def _opts(tol=None, max_iter=None, check_every=None, stall_window=None, inner_tol=None,
-          max_outer=None, time_limit_s=None):
+          max_outer=None, time_limit_s=None, residual_fp64=None):
     o = _native.CgOpts()
     o.tol = float(tol or 0.0)
     o.max_iter = int(max_iter or 0)
@@ -40,6 +41,7 @@ def _opts(tol=None, max_iter=None, check_every=None, stall_window=None, inner_to
     o.inner_tol = float(inner_tol or 0.0)
     o.max_outer = int(max_outer or 0)
     o.time_limit_s = float(time_limit_s or 0.0)
+    o.residual_fp64 = int(bool(residual_fp64))
     return o
 
 
@@ -62,7 +64,7 @@ class Handle:
         self.shape = (int(nz), int(ny), int(nx))
         self.degree = int(degree)
         self.precision = _PREC[precision]
-        self.dtype = torch.float32 if self.precision == F32 else torch.float64
+        self.dtype = {F32: torch.float32, BF16S: torch.bfloat16}.get(self.precision, torch.float64)
         self.stream = stream if stream is not None else torch.cuda.current_stream()
         prob = _native.Problem(int(nx), int(ny), int(nz), int(degree), hx, hy, hz, float(dt), None)
         self._mask = None
@@ -152,6 +154,17 @@ class Handle:
         out = ctypes.c_double(0.0)
         _native.check(self._lib.bsk_norm2(self._ptr, self._vec(x, "x"), ctypes.byref(out)))
         return out.value
+
+    def residual(self, b: torch.Tensor, x: torch.Tensor, r: Optional[torch.Tensor] = None,
+                 fp64: bool = False):
+        """(r, ||r||^2, ||b||^2) with r = b - A x by the handle's true-residual kernel
+        (bsk_residual)."""
+        r = self.empty() if r is None else r
+        rr, bb = ctypes.c_double(0.0), ctypes.c_double(0.0)
+        _native.check(self._lib.bsk_residual(self._ptr, self._vec(b, "b"), self._vec(x, "x"),
+                                             self._vec(r, "r"), int(bool(fp64)), ctypes.byref(rr),
+                                             ctypes.byref(bb)))
+        return r, rr.value, bb.value
 
 
 class BatchHandle:

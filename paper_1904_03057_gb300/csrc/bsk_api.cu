@@ -106,8 +106,10 @@ struct bsk_handle {
     // CG vectors in the CG element type (double for BSK_F64, float otherwise). The single-pass
     // TMA iteration ping-pongs r, q and p (r/r2, q/q2, p0/p1); the general one uses r, q, p0/p1.
     void *x, *r, *p0, *p1, *q, *bvec, *r2, *q2;
-    bool use_tma;     // CG vectors go through the TMA kernels (unmasked, 16-byte rows)
+    bool use_tma;     // CG vectors go through the TMA kernels (16-byte rows; a mask only zeroes
+                      // outputs, the solvers' vectors being zero on inactive nodes)
     bool tma64;       // FP64 operator passes (op_apply / residual) may use the TMA kernels
+    bool res_df;      // BSK_F32_IR: the true residual may use the double-float TMA kernel
     // iterative refinement (FP64 outer vectors)
     double *r64, *b64;
     Scalars *sc, *sc64, *sc_aux;
@@ -126,7 +128,10 @@ struct bsk_handle {
 
 namespace {
 
-size_t user_es(const bsk_handle* h) { return h->prec == BSK_F32 ? sizeof(float) : sizeof(double); }
+size_t user_es(const bsk_handle* h)
+{
+    return h->prec == BSK_BF16S ? 2 : h->prec == BSK_F32 ? sizeof(float) : sizeof(double);
+}
 size_t cg_es(const bsk_handle* h) { return h->prec == BSK_F64 ? sizeof(double) : sizeof(float); }
 
 void fill_tma(const bsk_handle* h, bsk::TmaLaunch& L, int mode)
@@ -138,6 +143,7 @@ void fill_tma(const bsk_handle* h, bsk::TmaLaunch& L, int mode)
     L.nx = h->nx;
     L.ny = h->ny;
     L.nz = h->nz;
+    L.mask = h->mask;
     for (int d = 0; d < 3; d++)
         for (int j = 0; j < bsk::kMaxTaps; j++) {
             L.M[d][j] = h->M[d][j];
@@ -222,7 +228,7 @@ int init_scalars(bsk_handle* h, Scalars* dev, double tol, int max_iter, int stal
 
 struct Opts {
     double tol, inner_tol, time_limit;
-    int max_iter, check_every, stall_window, max_outer;
+    int max_iter, check_every, stall_window, max_outer, residual_fp64;
 };
 
 Opts resolve(const bsk_cg_opts* o)
@@ -236,7 +242,37 @@ Opts resolve(const bsk_cg_opts* o)
     r.inner_tol = (o && o->inner_tol > 0) ? o->inner_tol : 1e-5;
     r.max_outer = (o && o->max_outer > 0) ? o->max_outer : 30;
     r.time_limit = (o && o->time_limit_s > 0) ? o->time_limit_s : 0.0;
+    r.residual_fp64 = (o && o->residual_fp64) ? 1 : 0;
     return r;
+}
+
+// Enqueues the true residual r = b - A x of FP64 vectors (FIN_RES_TRUE: r.r and b.b into sc):
+// double-float TMA kernel (BSK_F32_IR, unless fp64), FP64 TMA kernel, or the general kernel.
+int enqueue_residual64(bsk_handle* h, const double* b, const double* x, double* r, Scalars* sc, bool fp64)
+{
+    if (tma_ok(h, sizeof(double), {b, x, r})) {
+        bsk::TmaLaunch R;
+        fill_tma(h, R, bsk::TMODE_RES);
+        R.in[0] = x;
+        R.inint = b;
+        R.out0 = r;
+        R.sc = sc;
+        R.partials = h->partials;
+        R.fin = bsk::FIN_RES_TRUE;
+        if (h->res_df && !fp64) BSK_LAUNCH(h, bsk::launch_tma<bsk::dfl>(R, h->stream));
+        else BSK_LAUNCH(h, bsk::launch_tma<double>(R, h->stream));
+    } else {
+        bsk::OpLaunch L;
+        fill_launch(h, L, bsk::MODE_RES);
+        L.in0 = x;
+        L.b = b;
+        L.out0 = r;
+        L.sc = sc;
+        L.partials = h->partials;
+        L.fin = bsk::FIN_RES_TRUE;
+        BSK_LAUNCH(h, op_launch<double>(L, h->stream));
+    }
+    return BSK_OK;
 }
 
 // The device-resident CG chunk: `chunk` iterations of (fused p-update + operator + p.Ap, then
@@ -427,27 +463,7 @@ int cg_ir(bsk_handle* h, const double* b, double* x, const Opts& o, bsk_cg_repor
     double rel = 0.0;
     BSK_LAUNCH(h, bsk::launch_copy_masked<double>(x, x, h->len, h->mask, h->stream));
     for (;; outer++) {
-        if (tma_ok(h, sizeof(double), {b, x})) {
-            bsk::TmaLaunch R;
-            fill_tma(h, R, bsk::TMODE_RES);
-            R.in[0] = x;
-            R.inint = b;
-            R.out0 = h->r64;
-            R.sc = h->sc64;
-            R.partials = h->partials;
-            R.fin = bsk::FIN_RES_TRUE;
-            BSK_LAUNCH(h, bsk::launch_tma<double>(R, h->stream));
-        } else {
-            bsk::OpLaunch L;
-            fill_launch(h, L, bsk::MODE_RES);
-            L.in0 = x;
-            L.b = b;
-            L.out0 = h->r64;
-            L.sc = h->sc64;
-            L.partials = h->partials;
-            L.fin = bsk::FIN_RES_TRUE;
-            BSK_LAUNCH(h, op_launch<double>(L, h->stream));
-        }
+        if ((rc = enqueue_residual64(h, b, x, h->r64, h->sc64, o.residual_fp64))) return rc;
         if ((rc = sync_scalars(h, h->sc64))) return rc;
         const double rr = h->h_sc->rr_true, bb = h->h_sc->bb_true;
         if (!std::isfinite(rr) || !std::isfinite(bb))
@@ -532,7 +548,7 @@ extern "C" int bsk_create(const bsk_problem* prob, int precision, void* stream, 
         !std::isfinite(prob->hy) || !std::isfinite(prob->hz))
         return fail(BSK_EINVAL, "grid steps must be finite and > 0");
     if (!(prob->dt >= 0) || !std::isfinite(prob->dt)) return fail(BSK_EINVAL, "dt must be finite and >= 0");
-    if (precision != BSK_F64 && precision != BSK_F32 && precision != BSK_F32_IR)
+    if (precision != BSK_F64 && precision != BSK_F32 && precision != BSK_F32_IR && precision != BSK_BF16S)
         return fail(BSK_EINVAL, "unknown precision %d", precision);
     const size_t len = (size_t)prob->nx * prob->ny * prob->nz;
     if ((size_t)prob->nx * prob->ny > (size_t)1 << 31 || len > ((size_t)1 << 40))
@@ -581,18 +597,23 @@ extern "C" int bsk_create(const bsk_problem* prob, int precision, void* stream, 
     if (e == cudaSuccess) e = bsk::prepare_op<double>(n);
     if (e != cudaSuccess) return cleanup(cuda_fail(e, "kernel set-up"));
     {
-        // the TMA kernels need unmasked grids whose rows are whole 16-byte units
+        // the TMA kernels need grids whose rows are whole 16-byte units
         const size_t ces_ = precision == BSK_F64 ? sizeof(double) : sizeof(float);
-        h->use_tma = !prob->mask && n <= (ces_ == 8 ? bsk::tma_max_degree<double>() : bsk::tma_max_degree<float>()) &&
-                     (prob->nx * ces_) % 16 == 0;
-        h->tma64 = !prob->mask && n <= bsk::tma_max_degree<double>() && (prob->nx * sizeof(double)) % 16 == 0 &&
-                   precision != BSK_F32;
+        h->use_tma = n <= (ces_ == 8 ? bsk::tma_max_degree<double>() : bsk::tma_max_degree<float>()) &&
+                     (prob->nx * ces_) % 16 == 0 && precision != BSK_BF16S;
+        h->tma64 = n <= bsk::tma_max_degree<double>() && (prob->nx * sizeof(double)) % 16 == 0 &&
+                   precision != BSK_F32 && precision != BSK_BF16S;
         if (h->use_tma || precision == BSK_F32) {
             e = bsk::prepare_tma<float>(n > bsk::tma_max_degree<float>() ? 1 : n);
             if (e != cudaSuccess) return cleanup(cuda_fail(e, "TMA kernel set-up"));
         }
         if (h->tma64 || (h->use_tma && ces_ == 8)) {
             e = bsk::prepare_tma<double>(n);
+            if (e != cudaSuccess) return cleanup(cuda_fail(e, "TMA kernel set-up"));
+        }
+        h->res_df = precision == BSK_F32_IR && h->tma64 && n <= bsk::tma_max_degree<bsk::dfl>();
+        if (h->res_df) {
+            e = bsk::prepare_tma<bsk::dfl>(n);
             if (e != cudaSuccess) return cleanup(cuda_fail(e, "TMA kernel set-up"));
         }
     }
@@ -608,20 +629,22 @@ extern "C" int bsk_create(const bsk_problem* prob, int precision, void* stream, 
         if (e != cudaSuccess) return cleanup(cuda_fail(e, "mask copy"));
     }
     const size_t ces = cg_es(h);
-    BSK_ALLOC(h->x, len * ces);
-    BSK_ALLOC(h->r, len * ces);
-    BSK_ALLOC(h->p0, len * ces);
-    BSK_ALLOC(h->p1, len * ces);
-    BSK_ALLOC(h->q, len * ces);
-    if (h->use_tma) {
-        BSK_ALLOC(h->r2, len * ces);
-        BSK_ALLOC(h->q2, len * ces);
-    }
-    if (precision == BSK_F32_IR) {
-        BSK_ALLOC(h->r64, len * sizeof(double));
-        BSK_ALLOC(h->b64, len * sizeof(double));
-    } else {
-        BSK_ALLOC(h->bvec, len * ces);
+    if (precision != BSK_BF16S) {   // the BF16-storage variant has no solver
+        BSK_ALLOC(h->x, len * ces);
+        BSK_ALLOC(h->r, len * ces);
+        BSK_ALLOC(h->p0, len * ces);
+        BSK_ALLOC(h->p1, len * ces);
+        BSK_ALLOC(h->q, len * ces);
+        if (h->use_tma) {
+            BSK_ALLOC(h->r2, len * ces);
+            BSK_ALLOC(h->q2, len * ces);
+        }
+        if (precision == BSK_F32_IR) {
+            BSK_ALLOC(h->r64, len * sizeof(double));
+            BSK_ALLOC(h->b64, len * sizeof(double));
+        } else {
+            BSK_ALLOC(h->bvec, len * ces);
+        }
     }
     BSK_ALLOC(h->sc, sizeof(Scalars));
     BSK_ALLOC(h->sc64, sizeof(Scalars));
@@ -688,7 +711,9 @@ static int apply_common(bsk_handle* h, const void* x, void* y, int mode)
     const size_t es = user_es(h);
     if (overlaps(x, y, h->len * es)) return fail(BSK_EINVAL, "x and y overlap");
     cudaError_t e;
-    if (mode == bsk::MODE_OP && tma_ok(h, es, {x, y})) {
+    // op_apply's x is the caller's and may be non-zero off the mask: masked grids take the
+    // general kernel, which masks its input
+    if (mode == bsk::MODE_OP && !h->mask && tma_ok(h, es, {x, y})) {
         bsk::TmaLaunch T;
         fill_tma(h, T, bsk::TMODE_OP);
         T.in[0] = x;
@@ -701,7 +726,12 @@ static int apply_common(bsk_handle* h, const void* x, void* y, int mode)
         L.in0 = x;
         L.out0 = y;
         L.fin = bsk::FIN_NONE;
-        e = op_launch_es(es, L, h->stream);
+        if (h->prec == BSK_BF16S) {   // FP32 arithmetic on bfloat16 vectors
+            L.bf16io = 1;
+            e = bsk::launch_op<float>(L, h->stream);
+        } else {
+            e = op_launch_es(es, L, h->stream);
+        }
     }
     if (e != cudaSuccess) return cuda_fail(e, "operator launch");
     h->launches += 1;
@@ -724,6 +754,7 @@ extern "C" int cg_solve(bsk_handle* h, const void* b, void* x, const bsk_cg_opts
     auto t0 = std::chrono::steady_clock::now();
     if (int rc = check_handle(h)) return rc;
     if (!b || !x) return fail(BSK_EINVAL, "null vector");
+    if (h->prec == BSK_BF16S) return fail(BSK_EINVAL, "BF16 storage is an operator-only variant");
     if (overlaps(b, x, h->len * user_es(h))) return fail(BSK_EINVAL, "b and x overlap");
     const Opts o = resolve(opts);
     if (report) memset(report, 0, sizeof *report);
@@ -746,6 +777,7 @@ extern "C" int heat_step(bsk_handle* h, void* u, const void* q, int nsteps, cons
     if (int rc = check_handle(h)) return rc;
     if (!u) return fail(BSK_EINVAL, "null vector");
     if (nsteps < 0) return fail(BSK_EINVAL, "nsteps < 0");
+    if (h->prec == BSK_BF16S) return fail(BSK_EINVAL, "BF16 storage is an operator-only variant");
     const size_t es = user_es(h);
     if (q && overlaps(u, q, h->len * es)) return fail(BSK_EINVAL, "u and q overlap");
     const Opts o = resolve(opts);
@@ -845,15 +877,7 @@ extern "C" int fcg_solve(bsk_handle* h, bsk_net* net, const void* bv, void* xv, 
     double rel = 0.0;
     BSK_LAUNCH(h, bsk::launch_copy_masked<double>(x, x, h->len, h->mask, h->stream));
     for (;; outer++) {
-        bsk::OpLaunch L;
-        fill_launch(h, L, bsk::MODE_RES);
-        L.in0 = x;
-        L.b = b;
-        L.out0 = h->r64;
-        L.sc = h->sc64;
-        L.partials = h->partials;
-        L.fin = bsk::FIN_RES_TRUE;
-        BSK_LAUNCH(h, op_launch<double>(L, h->stream));
+        if ((rc = enqueue_residual64(h, b, x, h->r64, h->sc64, o.residual_fp64))) return rc;
         if ((rc = sync_scalars(h, h->sc64))) return rc;
         const double rr = h->h_sc->rr_true, bb = h->h_sc->bb_true;
         if (!std::isfinite(rr) || !std::isfinite(bb)) return fail(BSK_EBREAKDOWN, "non-finite residual");
@@ -897,8 +921,11 @@ extern "C" int bsk_time_kernel(bsk_handle* h, int kernel, int reps, double* ms)
 {
     if (int rc = check_handle(h)) return rc;
     if (!ms || reps < 1) return fail(BSK_EINVAL, "bad arguments");
-    if (kernel < BSK_KERNEL_OP || kernel > BSK_KERNEL_RES64) return fail(BSK_EINVAL, "unknown kernel %d", kernel);
-    if (kernel == BSK_KERNEL_RES64 && h->prec != BSK_F32_IR)
+    if (h->prec == BSK_BF16S) return fail(BSK_EINVAL, "a BF16-storage handle has no solver kernels to time");
+    if (kernel < BSK_KERNEL_OP || kernel > BSK_KERNEL_RES_DF) return fail(BSK_EINVAL, "unknown kernel %d", kernel);
+    if (kernel == BSK_KERNEL_RES_DF && !h->res_df)
+        return fail(BSK_EINVAL, "this handle has no double-float residual kernel");
+    if (kernel >= BSK_KERNEL_RES64 && h->prec != BSK_F32_IR)
         return fail(BSK_EINVAL, "the FP64 residual kernel exists only for BSK_F32_IR handles");
     const size_t ces = cg_es(h);
     for (void* p : {h->x, h->r, h->p0, h->p1, h->q, h->r2, h->q2})
@@ -958,7 +985,7 @@ extern "C" int bsk_time_kernel(bsk_handle* h, int kernel, int reps, double* ms)
                                                        h->sc_aux, h->partials, bsk::FIN_NORM, h->stream)
                        : bsk::launch_cg_update<float>((float*)h->r, (const float*)h->q, h->len,
                                                       h->sc_aux, h->partials, bsk::FIN_NORM, h->stream);
-        default:  // BSK_KERNEL_RES64
+        default:  // BSK_KERNEL_RES64, BSK_KERNEL_RES_DF
             if (tma_ok(h, sizeof(double), {h->b64, h->r64})) {
                 fill_tma(h, T, bsk::TMODE_RES);
                 T.in[0] = h->b64;
@@ -967,7 +994,8 @@ extern "C" int bsk_time_kernel(bsk_handle* h, int kernel, int reps, double* ms)
                 T.sc = h->sc_aux;
                 T.partials = h->partials;
                 T.fin = bsk::FIN_RES_TRUE;
-                return bsk::launch_tma<double>(T, h->stream);
+                return kernel == BSK_KERNEL_RES_DF ? bsk::launch_tma<bsk::dfl>(T, h->stream)
+                                                   : bsk::launch_tma<double>(T, h->stream);
             }
             fill_launch(h, L, bsk::MODE_RES);
             L.in0 = h->b64;
@@ -997,10 +1025,51 @@ extern "C" int bsk_time_kernel(bsk_handle* h, int kernel, int reps, double* ms)
     return BSK_OK;
 }
 
+extern "C" int bsk_residual(bsk_handle* h, const void* b, const void* x, void* r, int fp64, double* rr,
+                            double* bb)
+{
+    if (int rc = check_handle(h)) return rc;
+    if (!b || !x || !r) return fail(BSK_EINVAL, "null vector");
+    if (h->prec == BSK_BF16S) return fail(BSK_EINVAL, "BF16 storage is an operator-only variant");
+    const size_t es = user_es(h);
+    if (overlaps(r, x, h->len * es) || overlaps(r, b, h->len * es)) return fail(BSK_EINVAL, "r overlaps b or x");
+    h->launches = 0;
+    int rc;
+    if (es == sizeof(double)) {
+        if ((rc = enqueue_residual64(h, (const double*)b, (const double*)x, (double*)r, h->sc_aux, fp64 != 0)))
+            return rc;
+    } else if (tma_ok(h, sizeof(float), {b, x, r})) {
+        bsk::TmaLaunch R;
+        fill_tma(h, R, bsk::TMODE_RES);
+        R.in[0] = x;
+        R.inint = b;
+        R.out0 = r;
+        R.sc = h->sc_aux;
+        R.partials = h->partials;
+        R.fin = bsk::FIN_RES_TRUE;
+        BSK_LAUNCH(h, bsk::launch_tma<float>(R, h->stream));
+    } else {
+        bsk::OpLaunch L;
+        fill_launch(h, L, bsk::MODE_RES);
+        L.in0 = x;
+        L.b = b;
+        L.out0 = r;
+        L.sc = h->sc_aux;
+        L.partials = h->partials;
+        L.fin = bsk::FIN_RES_TRUE;
+        BSK_LAUNCH(h, op_launch<float>(L, h->stream));
+    }
+    if ((rc = sync_scalars(h, h->sc_aux))) return rc;
+    if (rr) *rr = h->h_sc->rr_true;
+    if (bb) *bb = h->h_sc->bb_true;
+    return BSK_OK;
+}
+
 extern "C" int bsk_norm2(bsk_handle* h, const void* x, double* out)
 {
     if (int rc = check_handle(h)) return rc;
     if (!x || !out) return fail(BSK_EINVAL, "null argument");
+    if (h->prec == BSK_BF16S) return fail(BSK_EINVAL, "bsk_norm2 takes FP32 or FP64 vectors");
     cudaError_t e = user_es(h) == sizeof(double)
                         ? bsk::launch_norm2<double>((const double*)x, h->len, h->sc_aux, h->partials, h->stream)
                         : bsk::launch_norm2<float>((const float*)x, h->len, h->sc_aux, h->partials, h->stream);

@@ -36,6 +36,7 @@ struct OpLaunch {
     double* partials;
     int fin;
     int p_parity;
+    int bf16io;                  // FP32 kernels, MODE_OP / MODE_MASS: in0, in1, out0 hold bfloat16
 };
 
 // Grid of the operator kernel for a problem; partial-sum buffers hold 2 doubles per block.
@@ -79,11 +80,13 @@ struct TmaLaunch {
     void* out1;                  // CG r
     void* out2;                  // CG p
     void* xvec;                  // CG x (in place)
+    const uint8_t* mask;         // node mask or null (outputs zeroed where 0; inputs must be)
     Scalars* sc;
     double* partials;            // 3 doubles per block of the resident grid
     unsigned int* work;          // 2 counters, zero between launches (dynamic item queue)
     int fin;
 };
+struct dfl;   // double-float element (dfloat.cuh): the FP64-accurate residual on the FP32 pipes
 template <typename T>
 int tma_max_degree();
 template <typename T>

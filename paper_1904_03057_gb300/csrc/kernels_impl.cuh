@@ -61,6 +61,7 @@ static cudaError_t launch_generic(const OpLaunch& L, cudaStream_t s)
     a.partials = L.partials;
     a.fin = L.fin;
     a.p_parity = L.p_parity;
+    a.bf16io = L.bf16io;
     k_op_generic<T, N, MODE><<<grid, kGenNT, smem, s>>>(a);
     return cudaGetLastError();
 }

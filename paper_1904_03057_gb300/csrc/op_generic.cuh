@@ -14,6 +14,8 @@
 // while staging, the deferred x update, the residual b - A x, and the p.Ap / r.r reductions.
 #pragma once
 
+#include <cuda_bf16.h>
+
 #include "bsk_device.cuh"
 
 namespace bsk {
@@ -33,7 +35,29 @@ struct OpArgs {
     double* partials;
     int fin;
     int p_parity;
+    int bf16io;       // FP32, OP / MASS: in0, in1 and out0 are bfloat16 arrays (BF16 storage)
 };
+
+// Element o of an input / output array that holds T, or bfloat16 when bf (FP32 kernels only).
+template <typename T>
+__device__ __forceinline__ T ld_io(const T* p, size_t o, int bf)
+{
+    if constexpr (sizeof(T) == 4) {
+        if (bf) return __bfloat162float(reinterpret_cast<const __nv_bfloat16*>(p)[o]);
+    }
+    return p[o];
+}
+template <typename T>
+__device__ __forceinline__ void st_io(T* p, size_t o, T v, int bf)
+{
+    if constexpr (sizeof(T) == 4) {
+        if (bf) {
+            reinterpret_cast<__nv_bfloat16*>(p)[o] = __float2bfloat16_rn(v);
+            return;
+        }
+    }
+    p[o] = v;
+}
 
 template <typename T, int N>
 constexpr size_t generic_smem_bytes()
@@ -89,7 +113,9 @@ __global__ void __launch_bounds__(kGenNT) k_op_generic(const __grid_constant__ O
                 if (!mask || mask[o]) {
                     T u;
                     if (MODE == MODE_CGP) u = a.in0[o] + beta * a.in1[o];
-                    else if (MODE == MODE_MASS) u = a.in0[o] + (a.in1 ? (T)a.s * a.in1[o] : T(0));
+                    else if (MODE == MODE_MASS)
+                        u = ld_io(a.in0, o, a.bf16io) + (a.in1 ? (T)a.s * ld_io(a.in1, o, a.bf16io) : T(0));
+                    else if (MODE == MODE_OP) u = ld_io(a.in0, o, a.bf16io);
                     else u = a.in0[o];
                     v = s > 0 ? u : -u;
                 }
@@ -153,7 +179,7 @@ __global__ void __launch_bounds__(kGenNT) k_op_generic(const __grid_constant__ O
             const bool act = !mask || mask[o];
             if (!act) y = T(0);
             if (MODE == MODE_OP || MODE == MODE_MASS) {
-                a.out0[o] = y;
+                st_io(a.out0, o, y, a.bf16io);
             } else if (MODE == MODE_RES) {
                 const T bv = act ? a.b[o] : T(0);
                 const T r = bv - y;

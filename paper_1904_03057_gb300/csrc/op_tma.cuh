@@ -15,13 +15,19 @@
 //   4. z-sweep as a push: the plane's U, V are added, with the 2n+1 z taps, into a ring of 2n+1
 //      per-thread accumulators of the output planes z-n .. z+n; output plane z-n is complete and
 //      leaves the kernel straight from registers.
+// A node mask (principal submatrix of the box operator) needs no staging: every input the
+// kernel reads is zero on inactive nodes already (the solvers keep their vectors masked), so
+// only the operator outputs are multiplied by the mask, read straight from global memory.
 // Blocks are persistent and walk a static list of (tile, z-chunk) items. In CG mode the staged
 // value is the new search direction p_m = (r - alpha q) + beta p of the previous iteration's
 // vectors, and the pass also writes r_m, p_m, x_m = x + alpha p and reduces r.r, p.Ap, Ap.Ap
 // (single-synchronisation CG, see finalize_cg1).
 #pragma once
 
+#include <type_traits>
+
 #include "bsk_device.cuh"
+#include "dfloat.cuh"
 #include "tma_util.cuh"
 
 namespace bsk {
@@ -38,6 +44,8 @@ struct TmaArgs {
     T* out1;              // CG r_m
     T* out2;              // CG p_m
     T* xvec;              // CG x, updated in place
+    const uint8_t* mask;  // node mask [nz][ny][nx] or null: outputs (q, r) are zeroed where it is 0;
+                          // the inputs must already be zero there (principal submatrix)
     int nx, ny, nz;
     int pitch;            // elements per row in memory (>= nx; rows of 16-byte multiples)
     int tiles_x, tiles_y, tz, nitems;
@@ -127,6 +135,17 @@ template <> struct P2<double> {
     static __device__ __forceinline__ t zero() { return make_double2(0.0, 0.0); }
 };
 
+// Double-float pairs (the FP64-accurate residual on the FP32 pipes, T = dfl): boxes arrive as
+// FP64 and are split in shared memory; every tap is an exact product plus a two-sum.
+template <> struct P2<dfl> {
+    using t = dfl2;
+    static __device__ __forceinline__ t mk(dfl a) { return dfl2{a, a}; }
+    static __device__ __forceinline__ t fma(t a, t b, t c) { return dfl2{df_fma(a.x, b.x, c.x), df_fma(a.y, b.y, c.y)}; }
+    static __device__ __forceinline__ t add(t a, t b) { return dfl2{df_add(a.x, b.x), df_add(a.y, b.y)}; }
+    static __device__ __forceinline__ t zero() { return dfl2{dfl(0.f, 0.f), dfl(0.f, 0.f)}; }
+};
+__device__ __forceinline__ dfl operator+(dfl a, dfl b) { return df_add(a, b); }
+
 // Compensated (Kahan) running sum in the element precision; converted to FP64 once per block.
 template <typename T>
 struct KSum {
@@ -153,10 +172,11 @@ __device__ __forceinline__ void load_window(T (&v)[W], const T* src)
             v[4 * q] = f.x; v[4 * q + 1] = f.y; v[4 * q + 2] = f.z; v[4 * q + 3] = f.w;
         }
     } else {
+        struct alignas(16) Pair { T a, b; };
 #pragma unroll
         for (int q = 0; q < W / 2; q++) {
-            const double2 f = reinterpret_cast<const double2*>(src)[q];
-            v[2 * q] = f.x; v[2 * q + 1] = f.y;
+            const Pair f = reinterpret_cast<const Pair*>(src)[q];
+            v[2 * q] = f.a; v[2 * q + 1] = f.b;
         }
     }
 }
@@ -329,8 +349,10 @@ __global__ void __launch_bounds__(kTNT, (sizeof(T) == 4 && N <= 4 && !BATCH) ? 2
     int nx = a.nx, ny = a.ny, nz = a.nz, pitch = a.pitch;
     int tiles_x = a.tiles_x, tiles_y = a.tiles_y, tz = a.tz, item0 = 0;
     Scalars* sc = a.sc;
+    constexpr bool DF = std::is_same<T, dfl>::value;   // double-float residual (RES only)
+    static_assert(!DF || (MODE == TMODE_RES && !BATCH), "double-float: residual passes only");
     T alpha = T(0), beta = T(0);
-    if (!BATCH && MODE == TMODE_CG) {
+    if constexpr (!BATCH && MODE == TMODE_CG) {
         alpha = (T)a.sc->alpha;
         beta = (T)a.sc->beta;
     }
@@ -359,7 +381,9 @@ __global__ void __launch_bounds__(kTNT, (sizeof(T) == 4 && N <= 4 && !BATCH) ? 2
     const T* mxb = MXs + 3 * warp * MXP + 2 * lane;
     const T* kxb = KXs + 3 * warp * MXP + 2 * lane;
 
-    KSum<T> d0, d1, d2;
+    using Acc = std::conditional_t<DF, float, T>;
+    KSum<Acc> d0, d1, d2;
+    double s0 = 0.0, s1 = 0.0;   // DF: plain FP64 sums of r.r and b.b
     uint32_t cnt = 0;   // planes consumed by this block before the current item
 
     for (;;) {
@@ -387,8 +411,10 @@ __global__ void __launch_bounds__(kTNT, (sizeof(T) == 4 && N <= 4 && !BATCH) ? 2
                 nx = P.nx; ny = P.ny; nz = P.nz; pitch = P.pitch;
                 tiles_x = P.tiles_x; tiles_y = P.tiles_y; tz = P.tz; item0 = P.item0;
                 sc = P.sc;
-                alpha = (T)P.sc->alpha;
-                beta = (T)P.sc->beta;
+                if constexpr (BATCH) {
+                    alpha = (T)P.sc->alpha;
+                    beta = (T)P.sc->beta;
+                }
                 load_taps(P.M, P.K);
             }
         }
@@ -446,20 +472,39 @@ __global__ void __launch_bounds__(kTNT, (sizeof(T) == 4 && N <= 4 && !BATCH) ? 2
             __syncthreads();
             if (s_abort) goto abort;
 
-            if (patch_y) {
-                patch_rows<T, N>(in0, y0, ny);
-                if (NIN > 1) { patch_rows<T, N>(in1, y0, ny); patch_rows<T, N>(in2, y0, ny); }
+            if constexpr (DF) {
+                // the box holds FP64 as loaded: reflect in FP64, then split in place
+                double* bd = reinterpret_cast<double*>(in0);
+                if (patch_y) {
+                    patch_rows<double, N>(bd, y0, ny);
+                    __syncthreads();
+                }
+                if (patch_x) {
+                    patch_cols<double, N>(bd, x0, nx);
+                    __syncthreads();
+                }
+                for (int i = tid; i < HY * BX; i += kTNT) {
+                    const double dv = bd[i];
+                    in0[i] = df_from_double(dv);
+                }
                 __syncthreads();
-            }
-            if (patch_x) {
-                patch_cols<T, N>(in0, x0, nx);
-                if (NIN > 1) { patch_cols<T, N>(in1, x0, nx); patch_cols<T, N>(in2, x0, nx); }
-                __syncthreads();
+            } else {
+                if (patch_y) {
+                    patch_rows<T, N>(in0, y0, ny);
+                    if (NIN > 1) { patch_rows<T, N>(in1, y0, ny); patch_rows<T, N>(in2, y0, ny); }
+                    __syncthreads();
+                }
+                if (patch_x) {
+                    patch_cols<T, N>(in0, x0, nx);
+                    if (NIN > 1) { patch_cols<T, N>(in1, x0, nx); patch_cols<T, N>(in2, x0, nx); }
+                    __syncthreads();
+                }
             }
 
             {
                 int zsrc = 0;
-                const T zsgn = (T)reflect_index(z, nz, zsrc);   // 1, -1 (mirror plane) or 0 (face)
+                const int zsi = reflect_index(z, nz, zsrc);   // 1, -1 (mirror plane) or 0 (face)
+                const T zsgn = (T)zsi;
                 const bool zint = (z >= z0 && z < z1);
                 const int rslot = zint ? (z - z0) % (N + 1) : 0;
                 // ---- x-sweep: task = (row, group of 8 output columns) ----
@@ -567,7 +612,7 @@ __global__ void __launch_bounds__(kTNT, (sizeof(T) == 4 && N <= 4 && !BATCH) ? 2
                         mo[i / 2] = m;
                         ko[i / 2] = k2;
                     }
-                    if (zsgn != T(1)) {   // mirrored plane (-1) or a face plane (0)
+                    if (zsi != 1) {   // mirrored plane (-1) or a face plane (0)
                         const T2 sg = PP::mk(zsgn);
 #pragma unroll
                         for (int i = 0; i < 4; i++) {
@@ -638,14 +683,39 @@ __global__ void __launch_bounds__(kTNT, (sizeof(T) == 4 && N <= 4 && !BATCH) ? 2
                         const int gy = y0 + 3 * warp + t, gx = x0 + c2;
                         if (gy < ny && gx < nx) {
                             const size_t o = ((size_t)zo * ny + gy) * pitch + gx;
+                            unsigned mm = 0x0101u;
+                            if (!BATCH && a.mask)   // masked grids have even nx: whole pairs
+                                mm = *reinterpret_cast<const uint16_t*>(a.mask + ((size_t)zo * ny + gy) * nx + gx);
+                            if constexpr (DF) {
+                                // r = b - A x in FP64 from the double-float A x; b is still FP64
+                                const double2 bq = *reinterpret_cast<const double2*>(
+                                    ring + oslot * (kTY * IP) + (3 * warp + t) * IP + c2);
+                                const double bx = (mm & 0xffu) ? bq.x : 0.0, by = (mm >> 8) ? bq.y : 0.0;
+                                const double qx = (mm & 0xffu) ? df_to_double(q[t].x) : 0.0;
+                                const double qy = (mm >> 8) ? df_to_double(q[t].y) : 0.0;
+                                const double2 r = make_double2(bx - qx, by - qy);
+                                *reinterpret_cast<double2*>(reinterpret_cast<double*>(out0) + o) = r;
+                                const double wyd = (gx + 1 < nx) ? 1.0 : 0.0;
+                                s0 = ::fma(r.x, r.x, ::fma(wyd * r.y, r.y, s0));
+                                s1 = ::fma(bx, bx, ::fma(wyd * by, by, s1));
+                            } else {
                             const T wy = (gx + 1 < nx) ? T(1) : T(0);   // second of the pair in range?
+                            T2 mk2 = PP::mk(T(1));
+                            if (mm != 0x0101u) {
+                                mk2.x = (mm & 0xffu) ? T(1) : T(0);
+                                mk2.y = (mm >> 8) ? T(1) : T(0);
+                                q[t].x *= mk2.x;
+                                q[t].y *= mk2.y;
+                            }
                             if constexpr (MODE == TMODE_OP) {
                                 *reinterpret_cast<T2*>(out0 + o) = q[t];
                             } else {
-                                const T2 rg = *reinterpret_cast<const T2*>(
+                                T2 rg = *reinterpret_cast<const T2*>(
                                     ring + oslot * (kTY * IP) + (3 * warp + t) * IP + c2);
                                 if constexpr (MODE == TMODE_RES) {
                                     T2 r;
+                                    rg.x *= mk2.x;   // b off the mask is ignored
+                                    rg.y *= mk2.y;
                                     r.x = rg.x - q[t].x;
                                     r.y = rg.y - q[t].y;
                                     *reinterpret_cast<T2*>(out0 + o) = r;
@@ -657,6 +727,7 @@ __global__ void __launch_bounds__(kTNT, (sizeof(T) == 4 && N <= 4 && !BATCH) ? 2
                                     d2.add(fma(q[t].x, q[t].x, wy * q[t].y * q[t].y));
                                 }
                             }
+                            }   // not DF
                         }
                     }
                 }
@@ -733,6 +804,9 @@ __global__ void __launch_bounds__(kTNT, (sizeof(T) == 4 && N <= 4 && !BATCH) ? 2
         if constexpr (MODE == TMODE_CG) {
             double v3[3] = {d0.value(), d1.value(), d2.value()};
             grid_reduce_k<kTNT, 3>(v3, a.partials, a.sc, a.fin);
+        } else if constexpr (DF) {
+            double v2[2] = {s0, s1};
+            grid_reduce_k<kTNT, 2>(v2, a.partials, a.sc, a.fin);
         } else {
             double v2[2] = {d0.value(), d1.value()};
             grid_reduce_k<kTNT, 2>(v2, a.partials, a.sc, a.fin);

@@ -1,6 +1,9 @@
 // tma_impl.cuh -- host launchers of the TMA operator kernel for one element type. Included once
-// by tma_f32.cu (BSK_T = float) and once by tma_f64.cu (BSK_T = double).
+// by tma_f32.cu (BSK_T = float), once by tma_f64.cu (BSK_T = double) and once by tma_df.cu
+// (BSK_T = dfl, the double-float residual; BSK_TMA_RES_ONLY).
 #pragma once
+
+#include <type_traits>
 
 #include <cudaTypedefs.h>
 
@@ -41,6 +44,18 @@ cudaError_t encode_box(CUtensorMap* m, const void* base, int nx, int ny, int nz,
     return r == CUDA_SUCCESS ? cudaSuccess : cudaErrorInvalidValue;
 }
 
+#ifndef BSK_TMA_RES_ONLY
+#define BSK_TMA_RES_ONLY 0
+#endif
+
+// kernel coefficient of the element type (double-float: split on the host)
+template <typename U>
+U coef_cast(double v)
+{
+    if constexpr (std::is_same<U, dfl>::value) return dfl::from_double_host(v);
+    else return (U)v;
+}
+
 struct TmaInfo {
     bool ready = false;
     int grid = 0;   // resident blocks on the whole GPU
@@ -76,10 +91,14 @@ cudaError_t prepare_one()
 template <int N>
 cudaError_t prepare_degree_tma()
 {
+#if BSK_TMA_RES_ONLY
+    return prepare_one<N, TMODE_RES>();
+#else
     cudaError_t e = prepare_one<N, TMODE_OP>();
     if (e == cudaSuccess) e = prepare_one<N, TMODE_RES>();
     if (e == cudaSuccess) e = prepare_one<N, TMODE_CG>();
     return e;
+#endif
 }
 
 // Items = tiles x z-chunks. Chooses the z-chunk count that minimises rounds x planes per item
@@ -122,6 +141,7 @@ cudaError_t launch_one(const TmaLaunch& L, cudaStream_t s)
     a.out1 = static_cast<BSK_T*>(L.out1);
     a.out2 = static_cast<BSK_T*>(L.out2);
     a.xvec = static_cast<BSK_T*>(L.xvec);
+    a.mask = L.mask;
     a.nx = L.nx;
     a.ny = L.ny;
     a.nz = L.nz;
@@ -129,8 +149,8 @@ cudaError_t launch_one(const TmaLaunch& L, cudaStream_t s)
     plan(L.nx, L.ny, L.nz, N, info.grid, a.tiles_x, a.tiles_y, a.tz, a.nitems);
     for (int d = 0; d < 3; d++)
         for (int j = 0; j < kMaxTaps; j++) {
-            a.M[d][j] = (BSK_T)L.M[d][j];
-            a.K[d][j] = (BSK_T)L.Kdt[d][j];
+            a.M[d][j] = coef_cast<BSK_T>(L.M[d][j]);
+            a.K[d][j] = coef_cast<BSK_T>(L.Kdt[d][j]);
         }
     a.sc = L.sc;
     a.partials = L.partials;
@@ -145,9 +165,11 @@ template <int N>
 cudaError_t launch_degree(const TmaLaunch& L, cudaStream_t s)
 {
     switch (L.mode) {
+#if !BSK_TMA_RES_ONLY
     case TMODE_OP: return launch_one<N, TMODE_OP>(L, s);
-    case TMODE_RES: return launch_one<N, TMODE_RES>(L, s);
     case TMODE_CG: return launch_one<N, TMODE_CG>(L, s);
+#endif
+    case TMODE_RES: return launch_one<N, TMODE_RES>(L, s);
     default: return cudaErrorInvalidValue;
     }
 }
