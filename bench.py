@@ -37,10 +37,11 @@ WORKLOAD = "heat3d_928cube_cubic_f32sweeps_f64refinement"
 
 # DRAM bytes per unknown of one fused CG-iteration launch (dram__bytes_read.sum +
 # dram__bytes_write.sum over the unknowns of the launch), from the ncu capture summarised in
-# profiles/; valid only while the kernel's sources hash to CG_TRAFFIC_SOURCES_SHA256.
-CG_TRAFFIC_BYTES_PER_UNKNOWN = None
-CG_TRAFFIC_SOURCES_SHA256 = None
-CG_KERNEL_SOURCES = ("op_tma.cuh", "tma_impl.cuh", "tma_util.cuh", "bsk_device.cuh", "tma_f32.cu")
+# profiles/k_op_tma_cg_f32_928cube_dram.md; valid only while the kernel's sources hash to
+# CG_TRAFFIC_SOURCES_SHA256.
+CG_TRAFFIC_BYTES_PER_UNKNOWN = 39.82   # 928^3, two launches: 19.07 GB read + 12.76 GB written
+CG_TRAFFIC_SOURCES_SHA256 = "8c008737f36872082d46a761ae8ce25f6c6b56713914c3aef0a18de0fc70d4a7"
+CG_KERNEL_SOURCES = ("op_tma.cuh", "tma_impl.cuh", "tma_util.cuh", "bsk_device.cuh", "tma_f32.cu", "dfloat.cuh")
 
 
 def cg_kernel_sources_sha256() -> str:

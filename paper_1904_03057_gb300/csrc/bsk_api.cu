@@ -787,14 +787,31 @@ extern "C" int heat_step(bsk_handle* h, void* u, const void* q, int nsteps, cons
     h->launches = 0;
     h->iter_ms = 0.0;
     for (int s = 0; s < nsteps; s++) {
-        bsk::OpLaunch L;
-        fill_launch(h, L, bsk::MODE_MASS);
-        L.in0 = u;
-        L.in1 = q;
-        L.s = h->dt;
-        L.out0 = b;
-        L.fin = bsk::FIN_NONE;
-        cudaError_t e = op_launch_es(es, L, h->stream);
+        cudaError_t e;
+        if (!q && h->res_df && tma_ok(h, sizeof(double), {u, b})) {
+            // M u as the double-float operator with the stiffness weight set to zero; the TMA
+            // kernels take inputs that are zero off the mask (the solve below masks u anyway)
+            if (h->mask)
+                BSK_LAUNCH(h, bsk::launch_copy_masked<double>(static_cast<const double*>(u), static_cast<double*>(u),
+                                                         h->len, h->mask, h->stream));
+            bsk::TmaLaunch T;
+            fill_tma(h, T, bsk::TMODE_OP);
+            for (int d = 0; d < 3; d++)
+                for (int j = 0; j < bsk::kMaxTaps; j++) T.Kdt[d][j] = 0.0;
+            T.in[0] = u;
+            T.out0 = b;
+            T.fin = bsk::FIN_NONE;
+            e = bsk::launch_tma<bsk::dfl>(T, h->stream);
+        } else {
+            bsk::OpLaunch L;
+            fill_launch(h, L, bsk::MODE_MASS);
+            L.in0 = u;
+            L.in1 = q;
+            L.s = h->dt;
+            L.out0 = b;
+            L.fin = bsk::FIN_NONE;
+            e = op_launch_es(es, L, h->stream);
+        }
         if (e != cudaSuccess) return cuda_fail(e, "right-hand side launch");
         h->launches += 1;
         int rs = solve_dispatch(h, b, u, o, report, t0);

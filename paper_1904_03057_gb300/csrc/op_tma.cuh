@@ -349,8 +349,8 @@ __global__ void __launch_bounds__(kTNT, (sizeof(T) == 4 && N <= 4 && !BATCH) ? 2
     int nx = a.nx, ny = a.ny, nz = a.nz, pitch = a.pitch;
     int tiles_x = a.tiles_x, tiles_y = a.tiles_y, tz = a.tz, item0 = 0;
     Scalars* sc = a.sc;
-    constexpr bool DF = std::is_same<T, dfl>::value;   // double-float residual (RES only)
-    static_assert(!DF || (MODE == TMODE_RES && !BATCH), "double-float: residual passes only");
+    constexpr bool DF = std::is_same<T, dfl>::value;   // double-float passes (FP64 vectors)
+    static_assert(!DF || (MODE != TMODE_CG && !BATCH), "double-float: operator and residual passes only");
     T alpha = T(0), beta = T(0);
     if constexpr (!BATCH && MODE == TMODE_CG) {
         alpha = (T)a.sc->alpha;
@@ -686,7 +686,12 @@ __global__ void __launch_bounds__(kTNT, (sizeof(T) == 4 && N <= 4 && !BATCH) ? 2
                             unsigned mm = 0x0101u;
                             if (!BATCH && a.mask)   // masked grids have even nx: whole pairs
                                 mm = *reinterpret_cast<const uint16_t*>(a.mask + ((size_t)zo * ny + gy) * nx + gx);
-                            if constexpr (DF) {
+                            if constexpr (DF && MODE == TMODE_OP) {
+                                // y = A x rounded once to FP64
+                                const double yx = (mm & 0xffu) ? df_to_double(q[t].x) : 0.0;
+                                const double yy = (mm >> 8) ? df_to_double(q[t].y) : 0.0;
+                                *reinterpret_cast<double2*>(reinterpret_cast<double*>(out0) + o) = make_double2(yx, yy);
+                            } else if constexpr (DF) {
                                 // r = b - A x in FP64 from the double-float A x; b is still FP64
                                 const double2 bq = *reinterpret_cast<const double2*>(
                                     ring + oslot * (kTY * IP) + (3 * warp + t) * IP + c2);

@@ -1,6 +1,6 @@
 // tma_impl.cuh -- host launchers of the TMA operator kernel for one element type. Included once
 // by tma_f32.cu (BSK_T = float), once by tma_f64.cu (BSK_T = double) and once by tma_df.cu
-// (BSK_T = dfl, the double-float residual; BSK_TMA_RES_ONLY).
+// (BSK_T = dfl, the double-float operator and residual; BSK_TMA_NO_CG).
 #pragma once
 
 #include <type_traits>
@@ -44,8 +44,8 @@ cudaError_t encode_box(CUtensorMap* m, const void* base, int nx, int ny, int nz,
     return r == CUDA_SUCCESS ? cudaSuccess : cudaErrorInvalidValue;
 }
 
-#ifndef BSK_TMA_RES_ONLY
-#define BSK_TMA_RES_ONLY 0
+#ifndef BSK_TMA_NO_CG
+#define BSK_TMA_NO_CG 0
 #endif
 
 // kernel coefficient of the element type (double-float: split on the host)
@@ -91,18 +91,22 @@ cudaError_t prepare_one()
 template <int N>
 cudaError_t prepare_degree_tma()
 {
-#if BSK_TMA_RES_ONLY
-    return prepare_one<N, TMODE_RES>();
-#else
     cudaError_t e = prepare_one<N, TMODE_OP>();
     if (e == cudaSuccess) e = prepare_one<N, TMODE_RES>();
+#if !BSK_TMA_NO_CG
     if (e == cudaSuccess) e = prepare_one<N, TMODE_CG>();
-    return e;
 #endif
+    return e;
 }
 
 // Items = tiles x z-chunks. Chooses the z-chunk count that minimises rounds x planes per item
-// (halo planes included) for the resident grid.
+// (halo planes included) for the resident grid, with chunks of at most kMaxChunk planes: the
+// blocks of one wave of items drift apart in z as they march, and once neighbouring tiles are
+// far apart their shared halo rows no longer meet in L2 (a whole-column item at 928^3 read
+// 30 B/unknown from DRAM for 16 B of algorithmic reads; chunks of <= 128 planes cut the CG
+// iteration from 6.65 to 5.98 ms on GB300).
+constexpr int kMaxChunk = 128;
+
 void plan(int nx, int ny, int nz, int n, int grid, int& tiles_x, int& tiles_y, int& tz, int& nitems)
 {
     tiles_x = (nx + kTX - 1) / kTX;
@@ -110,8 +114,10 @@ void plan(int nx, int ny, int nz, int n, int grid, int& tiles_x, int& tiles_y, i
     const long long tiles = (long long)tiles_x * tiles_y;
     long long best = -1;
     int best_tz = nz;
-    for (int nzc = 1; nzc <= 64 && nzc <= nz; nzc++) {
+    for (int nzc = 1; nzc <= nz; nzc++) {
         const int t = (nz + nzc - 1) / nzc;
+        if (t > kMaxChunk && t > 1) continue;
+        if (best >= 0 && t < kMaxChunk / 4) break;   // no finer chunking than needed
         const int chunks = (nz + t - 1) / t;
         const long long items = tiles * chunks;
         const long long rounds = (items + grid - 1) / grid;
@@ -165,8 +171,8 @@ template <int N>
 cudaError_t launch_degree(const TmaLaunch& L, cudaStream_t s)
 {
     switch (L.mode) {
-#if !BSK_TMA_RES_ONLY
     case TMODE_OP: return launch_one<N, TMODE_OP>(L, s);
+#if !BSK_TMA_NO_CG
     case TMODE_CG: return launch_one<N, TMODE_CG>(L, s);
 #endif
     case TMODE_RES: return launch_one<N, TMODE_RES>(L, s);
