@@ -39,8 +39,8 @@ WORKLOAD = "heat3d_928cube_cubic_f32sweeps_f64refinement"
 # dram__bytes_write.sum over the unknowns of the launch), from the ncu capture summarised in
 # profiles/k_op_tma_cg_f32_928cube_dram.md; valid only while the kernel's sources hash to
 # CG_TRAFFIC_SOURCES_SHA256.
-CG_TRAFFIC_BYTES_PER_UNKNOWN = 39.82   # 928^3, two launches: 19.07 GB read + 12.76 GB written
-CG_TRAFFIC_SOURCES_SHA256 = "8c008737f36872082d46a761ae8ce25f6c6b56713914c3aef0a18de0fc70d4a7"
+CG_TRAFFIC_BYTES_PER_UNKNOWN = 40.12   # 928^3, two launches: 19.31 GB read + 12.75 GB written
+CG_TRAFFIC_SOURCES_SHA256 = "1e77c52d0845c2defff52733ef1878f5af1cb7dea1987b89eb64dc3a2603a7e0"
 CG_KERNEL_SOURCES = ("op_tma.cuh", "tma_impl.cuh", "tma_util.cuh", "bsk_device.cuh", "tma_f32.cu", "dfloat.cuh")
 
 
@@ -51,6 +51,22 @@ def cg_kernel_sources_sha256() -> str:
         with open(os.path.join(ROOT, "paper_1904_03057_gb300", "csrc", name), "rb") as f:
             d.update(f.read())
     return d.hexdigest()
+
+
+def max_over_ranks(value: float, dist, device="cuda") -> float:
+    """The largest value over all ranks (the job's wall time is its slowest rank's)."""
+    if dist is None:
+        return float(value)
+    import torch
+    t = torch.tensor([float(value)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def whole_job_gdofs(world: int, dofs_per_rank: int, op_apps_per_rank: float, seconds: float) -> float:
+    """Weak scaling: every rank solves its own problem of the same size; the job's throughput is
+    all ranks' unknowns x operator applications over the slowest rank's time."""
+    return world * dofs_per_rank * op_apps_per_rank / seconds / 1e9
 
 
 def peaks():
@@ -262,16 +278,12 @@ def run_ours(args, rank, world, dist):
     e1.record(stream)
     barrier()
     clocks = sampler.stop()
-    elapsed_ms = e0.elapsed_time(e1)
-    if dist is not None:
-        t = torch.tensor([elapsed_ms], device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        elapsed_ms = float(t.item())
+    elapsed_ms = max_over_ranks(e0.elapsed_time(e1), dist)
     inner = sum(r["iterations"] for r in reps)
     outer = sum(r["outer_iterations"] for r in reps)
     op_apps = inner + outer + len(reps)          # inner CG + true residuals (one per outer + final)
     launches = sum(r["kernel_launches"] for r in reps)
-    value = world * dofs * op_apps / (elapsed_ms * 1e-3) / 1e9
+    value = whole_job_gdofs(world, dofs, op_apps, elapsed_ms * 1e-3)
     ms_step = elapsed_ms / args.steps
     worst_res = max(r["rel_residual"] for r in reps)
 
@@ -290,12 +302,8 @@ def run_ours(args, rank, world, dist):
             uh.copy_(u, non_blocking=True)
             torch.cuda.current_stream().synchronize()
             e2e_apps += r["iterations"] + r["outer_iterations"] + 1
-        t_e2e = time.perf_counter() - t0
-        if dist is not None:
-            t = torch.tensor([t_e2e], device="cuda")
-            dist.all_reduce(t, op=dist.ReduceOp.MAX)
-            t_e2e = float(t.item())
-        e2e = {"value": world * dofs * e2e_apps / t_e2e / 1e9, "unit": "GDoF/s",
+        t_e2e = max_over_ranks(time.perf_counter() - t0, dist)
+        e2e = {"value": whole_job_gdofs(world, dofs, e2e_apps, t_e2e), "unit": "GDoF/s",
                "h2d_bytes_per_step": dofs * 8, "d2h_bytes_per_step": dofs * 8}
         del uh
 

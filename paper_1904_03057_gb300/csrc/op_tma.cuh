@@ -554,13 +554,15 @@ __global__ void __launch_bounds__(kTNT, (sizeof(T) == 4 && N <= 4 && !BATCH) ? 2
                                 }
                                 if (gy < ny && gx < nx) {
                                     // rows are padded to 16-byte multiples: a partial group of
-                                    // four writes into the padding, which no kernel reads
+                                    // four writes into the padding, which no kernel reads. The
+                                    // outputs are streamed (evict-first), so that they do not push
+                                    // the halo rows neighbouring tiles still read out of L2.
                                     const size_t o = ((size_t)z * ny + gy) * pitch + gx;
                                     d0.add(part);
                                     if constexpr (sizeof(T) == 4) {
-                                        *reinterpret_cast<float4*>(out1 + o) = make_float4(rn4[0], rn4[1], rn4[2], rn4[3]);
-                                        *reinterpret_cast<float4*>(out2 + o) = make_float4(pn4[0], pn4[1], pn4[2], pn4[3]);
-                                        *reinterpret_cast<float4*>(xvec + o) = make_float4(xn4[0], xn4[1], xn4[2], xn4[3]);
+                                        __stcs(reinterpret_cast<float4*>(out1 + o), make_float4(rn4[0], rn4[1], rn4[2], rn4[3]));
+                                        __stcs(reinterpret_cast<float4*>(out2 + o), make_float4(pn4[0], pn4[1], pn4[2], pn4[3]));
+                                        __stcs(reinterpret_cast<float4*>(xvec + o), make_float4(xn4[0], xn4[1], xn4[2], xn4[3]));
                                     } else {
 #pragma unroll
                                         for (int e = 0; e < 4; e += 2) {
@@ -713,7 +715,7 @@ __global__ void __launch_bounds__(kTNT, (sizeof(T) == 4 && N <= 4 && !BATCH) ? 2
                                 q[t].y *= mk2.y;
                             }
                             if constexpr (MODE == TMODE_OP) {
-                                *reinterpret_cast<T2*>(out0 + o) = q[t];
+                                __stcs(reinterpret_cast<T2*>(out0 + o), q[t]);
                             } else {
                                 T2 rg = *reinterpret_cast<const T2*>(
                                     ring + oslot * (kTY * IP) + (3 * warp + t) * IP + c2);
@@ -727,7 +729,7 @@ __global__ void __launch_bounds__(kTNT, (sizeof(T) == 4 && N <= 4 && !BATCH) ? 2
                                     d0.add(fma(r.x, r.x, wy * r.y * r.y));
                                     d1.add(fma(rg.x, rg.x, wy * rg.y * rg.y));
                                 } else {
-                                    *reinterpret_cast<T2*>(out0 + o) = q[t];
+                                    __stcs(reinterpret_cast<T2*>(out0 + o), q[t]);
                                     d1.add(fma(rg.x, q[t].x, wy * rg.y * q[t].y));
                                     d2.add(fma(q[t].x, q[t].x, wy * q[t].y * q[t].y));
                                 }
