@@ -178,6 +178,90 @@ def run_reference(args, rank, world):
     print(json.dumps(line), flush=True)
 
 
+def _timed_ms(fn):
+    """Device time of fn() on the current stream (CUDA events, synchronised on both sides)."""
+    import torch
+    stream = torch.cuda.current_stream()
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    out = fn()
+    e1.record(stream)
+    torch.cuda.synchronize()
+    return e0.elapsed_time(e1), out
+
+
+def batch_config4():
+    """Config 4: 64 independent boxes (dims U{48..160} per axis, degrees 2..5, 8 Gaussian
+    sources each, dt = 1e-3), one implicit Euler step of every box to a 1e-8 true residual:
+    the batched persistent solver (autotuned decomposition) against the same problems solved one
+    after another through single handles. Throughput counts unknowns x operator applications."""
+    import torch
+
+    from paper_1904_03057_gb300 import api, inputs
+    dt, tol = 1e-3, 1e-8
+    specs = inputs.batch_problems(seed=4)
+    qs = [inputs.gaussian_source(s.nx, s.ny, s.nz, s.centers, 0.03, h=s.h, device="cuda") for s in specs]
+    B = api.BatchHandle(specs, dt)
+    tune = B.autotune(3)
+    dofs = [s.nx * s.ny * s.nz for s in specs]
+
+    def fresh():
+        return [torch.zeros((s.nz, s.ny, s.nx), dtype=torch.float64, device="cuda") for s in specs]
+
+    B.heat_step(fresh(), qs, 1, tol=tol)                 # warm-up (graphs)
+    us = fresh()
+    ms_b, reps_b = _timed_ms(lambda: B.heat_step(us, qs, 1, tol=tol))
+    apps_b = sum(d * (r["iterations"] + r["outer_iterations"] + 1) for d, r in zip(dofs, reps_b))
+    B.close()
+    hs = [api.Handle(s.nx, s.ny, s.nz, s.degree, s.h, dt, precision="f32_ir") for s in specs]
+    for H, q, u in zip(hs, qs, fresh()):                 # warm-up
+        H.heat_step(u, q, 1, tol=tol)
+    us2 = fresh()
+    ms_s, reps_s = _timed_ms(lambda: [H.heat_step(u, q, 1, tol=tol) for H, q, u in zip(hs, qs, us2)])
+    apps_s = sum(d * (r["iterations"] + r["outer_iterations"] + 1) for d, r in zip(dofs, reps_s))
+    diff = max((torch.linalg.vector_norm(a - b) / torch.linalg.vector_norm(b)).item() for a, b in zip(us, us2))
+    for H in hs:
+        H.close()
+    return {"workload": "64 boxes, dims U{48..160}^3, degrees 2-5, one heat step, tol 1e-8",
+            "unknowns": sum(dofs), "batched_ms": ms_b, "sequential_ms": ms_s,
+            "speedup_batched_vs_sequential": ms_s / ms_b,
+            "batched_gdofs": apps_b / (ms_b * 1e-3) / 1e9, "sequential_gdofs": apps_s / (ms_s * 1e-3) / 1e9,
+            "max_rel_residual": max(r["rel_residual"] for r in reps_b),
+            "max_rel_diff_batched_vs_sequential": diff, "autotune": tune}
+
+
+def mixed_precision_config2(steps: int = 50):
+    """Config 2: 256^3, sphere mask r = 0.45 at the centre, 32 Gaussian sources (sigma 0.03,
+    centres U[0.2,0.8]^3, seed 2), u0 = 0, dt = 1e-3, `steps` implicit Euler steps to a 1e-8 true
+    residual, FP64 CG against FP32 CG with FP64-accurate refinement: time per step, iterations,
+    and the relative difference of the final fields."""
+    import torch
+
+    from paper_1904_03057_gb300 import api, inputs
+    N, dt, tol = 256, 1e-3, 1e-8
+    h = 1.0 / (N + 1)
+    mask = inputs.sphere_mask(N, N, N, (0.5, 0.5, 0.5), 0.45, h=h, device="cuda")
+    q = inputs.gaussian_source(N, N, N, inputs.gaussian_centers(2, 32), sigma=0.03, h=h, mask=mask,
+                               device="cuda")
+    out = {"workload": f"256^3 sphere r=0.45, 32 Gaussian sources, dt=1e-3, {steps} steps, tol 1e-8",
+           "active_unknowns": int(mask.sum().item())}
+    us = {}
+    for prec in ("f64", "f32_ir"):
+        H = api.Handle(N, N, N, DEGREE, h, dt, mask=mask, precision=prec)
+        H.heat_step(torch.zeros((N, N, N), dtype=torch.float64, device="cuda"), q, 1, tol=tol)   # warm-up
+        u = torch.zeros((N, N, N), dtype=torch.float64, device="cuda")
+        ms, rep = _timed_ms(lambda: H.heat_step(u, q, steps, tol=tol))
+        out[prec] = {"ms_per_step": ms / steps, "iterations_per_step": rep["iterations"] / steps,
+                     "last_rel_residual": rep["rel_residual"]}
+        us[prec] = u
+        H.close()
+    out["speedup_f32_ir_vs_f64"] = out["f64"]["ms_per_step"] / out["f32_ir"]["ms_per_step"]
+    out["rel_diff_f32_ir_vs_f64"] = (torch.linalg.vector_norm(us["f32_ir"] - us["f64"])
+                                     / torch.linalg.vector_norm(us["f64"])).item()
+    return out
+
+
 def fcg_race():
     """The 512^3 union-of-40-spheres race (config 5): one implicit Euler step from u = 0 with a
     Gaussian source, dt = 1e-3, each solver from x = 0 to a 1e-8 true relative residual: plain
@@ -385,6 +469,9 @@ def run_ours(args, rank, world, dist):
     del u
     if rank == 0 and not args.no_fcg_race and args.grid == N_GRID:
         line["fcg_race"] = fcg_race()
+    if rank == 0 and not args.no_extra_configs and args.grid == N_GRID:
+        line["batch_config4"] = batch_config4()
+        line["mixed_precision_config2"] = mixed_precision_config2()
     if rank == 0 and not args.no_cpu_baseline:
         v, cores, secs, desc = cpu_oracle_sample()
         line["cpu_baseline"] = {"value": v, "unit": "GDoF/s", "cores": cores, "kind": "oracle",
@@ -401,6 +488,8 @@ def main():
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-extra-configs", action="store_true",
+                    help="skip the batched (64 boxes) and the 256^3 mixed-precision measurements")
     ap.add_argument("--no-fcg-race", action="store_true",
                     help="skip the 512^3 union-of-spheres time-to-1e-8 race (learned FCG vs CG)")
     ap.add_argument("--grid", type=int, default=N_GRID,
