@@ -5,10 +5,13 @@
 //
 // The error-free transformations are the classical ones: the exact product a*b = p + e with
 // e = fma(a, b, -p) (one rounding of the fused multiply-add), and Knuth's two-sum
-// s + e = a + b (six additions, no ordering requirement), followed by a renormalisation. Every
-// operation uses the explicitly rounded intrinsics (__fadd_rn, __fmul_rn, __fmaf_rn) so that
-// the compiler cannot contract a multiply and an add into one fused operation, which would
-// break the transformations.
+// s + e = a + b (six additions, no ordering requirement). Sums are left unnormalised (hi is the
+// rounded leading sum, lo collects the exact errors and may exceed half an ulp of hi): over the
+// few dozen taps of one output lo stays a few ulps of the largest partial sum, which costs no
+// accuracy (its own rounding is 2^-24 of that) and saves the three-operation renormalisation per
+// tap. Every operation uses the explicitly rounded intrinsics (__fadd_rn, __fmul_rn, __fmaf_rn)
+// so that the compiler cannot contract a multiply and an add into one fused operation, which
+// would break the transformations.
 #pragma once
 
 #include <cstdint>
@@ -16,7 +19,7 @@
 namespace bsk {
 
 struct __align__(8) dfl {
-    float hi, lo;
+    float hi, lo;   // value hi + lo (not necessarily normalised)
     dfl() = default;
     __host__ __device__ constexpr dfl(float h, float l) : hi(h), lo(l) {}
     __host__ __device__ constexpr dfl(int v) : hi((float)v), lo(0.f) {}   // exact for |v| < 2^24
@@ -32,12 +35,6 @@ struct __align__(16) dfl2 {
     dfl x, y;
 };
 
-__device__ __forceinline__ dfl df_renorm(float s, float e)
-{
-    const float hi = __fadd_rn(s, e);
-    return dfl(hi, __fsub_rn(e, __fsub_rn(hi, s)));
-}
-
 // (s, e) with s + e = a + b exactly (Knuth)
 __device__ __forceinline__ void two_sum(float a, float b, float& s, float& e)
 {
@@ -46,7 +43,7 @@ __device__ __forceinline__ void two_sum(float a, float b, float& s, float& e)
     e = __fadd_rn(__fsub_rn(a, __fsub_rn(s, bb)), __fsub_rn(b, bb));
 }
 
-// c + a * b
+// c + a * b (a.lo * b.lo, below 2^-48 of the product, is dropped)
 __device__ __forceinline__ dfl df_fma(dfl a, dfl b, dfl c)
 {
     const float p = __fmul_rn(a.hi, b.hi);
@@ -55,16 +52,14 @@ __device__ __forceinline__ dfl df_fma(dfl a, dfl b, dfl c)
     pe = __fmaf_rn(a.lo, b.hi, pe);
     float s, se;
     two_sum(c.hi, p, s, se);
-    se = __fadd_rn(se, __fadd_rn(pe, c.lo));
-    return df_renorm(s, se);
+    return dfl(s, __fadd_rn(se, __fadd_rn(pe, c.lo)));
 }
 
 __device__ __forceinline__ dfl df_add(dfl a, dfl b)
 {
     float s, e;
     two_sum(a.hi, b.hi, s, e);
-    e = __fadd_rn(e, __fadd_rn(a.lo, b.lo));
-    return df_renorm(s, e);
+    return dfl(s, __fadd_rn(e, __fadd_rn(a.lo, b.lo)));
 }
 
 __device__ __forceinline__ dfl df_neg(dfl a) { return dfl(-a.hi, -a.lo); }

@@ -130,6 +130,27 @@ def test_fcg_without_network_is_cg(mods):
     assert d <= 1e-5
 
 
+def test_identity_network_reproduces_cg(mods):
+    """A linear network that is the identity (only the full-resolution filter's centre tap, 1)
+    gives z = c r, for which flexible CG is plain CG: same iteration count and solution."""
+    api, inputs, learned = mods
+    n, h, dt, tol = 40, 1.0 / 513, 1e-3, 1e-8
+    mask, b = _masked_problem(inputs, n, 11, h)
+    H = api.Handle(n, n, n, 3, h, dt, mask=mask, precision="f32_ir")
+    net = api.Net(n, n, n, activation="linear")
+    p = torch.zeros(nr.NPARAM)
+    p[-27 + 13] = 1.0
+    net.set_params(p)
+    x1 = torch.zeros_like(b)
+    r1 = H.fcg_solve(b, x1, None, tol=tol)
+    x2 = torch.zeros_like(b)
+    r2 = H.fcg_solve(b, x2, net, tol=tol)
+    assert r1["status"] == 0 and r2["status"] == 0 and r2["fallback_iter"] == -1
+    assert abs(r2["iterations"] - r1["iterations"]) <= 2, (r1, r2)
+    d = (torch.linalg.vector_norm(x1 - x2) / torch.linalg.vector_norm(x1)).item()
+    assert d <= 1e-6
+
+
 def test_bad_network_falls_back_and_converges(mods):
     api, inputs, learned = mods
     n, h, dt, tol = 32, 1.0 / 513, 1e-3, 1e-8
