@@ -55,17 +55,26 @@ class CropProblem:
 
 def make_problems(count: int, crop: int = 48, h: float = 1.0 / 513, dt: float = 1e-3, seed: int = 0,
                   degree: int = 3, device="cuda", signed: bool = True,
-                  noise_fraction: float = 0.0) -> list:
+                  noise_fraction: float = 0.0, domain_mask=None) -> list:
     """`count` random masked crop^3 problems with their solutions. The right-hand side is a few
     Gaussian sources plus a little noise, or (a fraction noise_fraction of the problems) white
     noise, which gives residuals rich in high frequencies. With `signed` each source gets a random
     sign and amplitude, so that the network learns no sign bias (a preconditioner has to act on
-    r and -r alike)."""
+    r and -r alike). With domain_mask (a [nz][ny][nx] uint8 tensor of the target domain) the
+    masks are random crop^3 windows of it that contain active nodes, so that the network sees
+    the geometry it will precondition; otherwise unions of random spheres inside the crop."""
     rng = np.random.default_rng(seed)
     n = crop
     out = []
     for _ in range(count):
-        mask = _random_crop_mask(n, rng, device)
+        if domain_mask is not None:
+            for _try in range(100):
+                z0, y0, x0 = (int(rng.integers(0, d - n + 1)) for d in domain_mask.shape)
+                mask = domain_mask[z0:z0 + n, y0:y0 + n, x0:x0 + n].contiguous()
+                if int(mask.sum().item()) > n ** 3 // 20:
+                    break
+        else:
+            mask = _random_crop_mask(n, rng, device)
         cs = [tuple(c) for c in rng.uniform(0.1, 0.9, size=(int(rng.integers(1, 6)), 3)) * (n + 1) * h]
         sigma = float(rng.uniform(3, 10)) * h
         b = torch.zeros((n, n, n), dtype=torch.float64, device=device)
