@@ -45,6 +45,21 @@ struct FcgState {
     int pad;
 };
 
+// Per-thread compensated FP32 sum (Kahan): the element products stay on the FP32 pipes (GB300
+// runs FP64 at 1/62 of the FP32 rate); each thread's sum is widened to FP64 once for the
+// deterministic block and grid reduction.
+struct FSum {
+    float s = 0.f, c = 0.f;
+    __device__ __forceinline__ void add(float v)
+    {
+        const float y = __fsub_rn(v, c);
+        const float t = __fadd_rn(s, y);
+        c = __fsub_rn(__fsub_rn(t, s), y);
+        s = t;
+    }
+    __device__ __forceinline__ double value() const { return (double)s - (double)c; }
+};
+
 template <int K, typename F>
 __device__ void reduce_then(double (&v)[K], double* partials, unsigned int* counter, F fin)
 {
@@ -107,15 +122,15 @@ __global__ void __launch_bounds__(NT) k_fcg_init(const float* __restrict__ b, fl
                                                  float* __restrict__ x, size_t n, const uint8_t* __restrict__ mask,
                                                  FcgState* st, double* partials)
 {
-    double acc = 0.0;
+    FSum acc;
     GRID_STRIDE(i, n)
     {
         const float v = (!mask || mask[i]) ? b[i] : 0.f;
         r[i] = v;
         x[i] = 0.f;
-        acc += (double)v * v;
+        acc.add(v * v);
     }
-    double v1[1] = {acc};
+    double v1[1] = {acc.value()};
     reduce_then<1>(v1, partials, &st->counter, [&](double* t) {
         st->rr = t[0];
         st->bb = t[0];
@@ -147,16 +162,16 @@ __global__ void __launch_bounds__(NT) k_fcg_direction(const float* __restrict__ 
     if (st->done) return;
     const float s = (float)(st->zscale * st->out_scale);
     const float jac = (float)st->jac;
-    double zq = 0.0, zr = 0.0, rq = 0.0;
+    FSum zq, zr, rq;
     GRID_STRIDE(i, n)
     {
         const float zv = fmaf(s, zn[i], jac * r[i]);   // jac = 0 unless a fixed diagonal part is set
         z[i] = zv;
-        zq += (double)zv * q[i];
-        zr += (double)zv * r[i];
-        rq += (double)r[i] * q[i];
+        zq.add(zv * q[i]);
+        zr.add(zv * r[i]);
+        rq.add(r[i] * q[i]);
     }
-    double v3[3] = {zq, zr, rq};
+    double v3[3] = {zq.value(), zr.value(), rq.value()};
     reduce_then<3>(v3, partials, &st->counter, [&](double* t) {
         const bool finite = isfinite(t[0]) && isfinite(t[1]);
         if (!finite && !st->use_r) {
@@ -191,13 +206,13 @@ __global__ void __launch_bounds__(NT) k_fcg_alpha(const float* __restrict__ r, c
                                                   double* partials)
 {
     if (st->done) return;
-    double rp = 0.0, pq = 0.0;
+    FSum rp, pq;
     GRID_STRIDE(i, n)
     {
-        rp += (double)r[i] * p[i];
-        pq += (double)p[i] * q[i];
+        rp.add(r[i] * p[i]);
+        pq.add(p[i] * q[i]);
     }
-    double v2[2] = {rp, pq};
+    double v2[2] = {rp.value(), pq.value()};
     reduce_then<2>(v2, partials, &st->counter, [&](double* t) {
         if (!(t[1] > 0.0) || !isfinite(t[0]) || !isfinite(t[1])) {
             st->done = 1;
@@ -218,15 +233,15 @@ __global__ void __launch_bounds__(NT) k_fcg_update(float* __restrict__ x, float*
 {
     if (st->done) return;
     const float alpha = (float)st->alpha;
-    double acc = 0.0;
+    FSum acc;
     GRID_STRIDE(i, n)
     {
         x[i] = fmaf(alpha, p[i], x[i]);
         const float rv = fmaf(-alpha, q[i], r[i]);
         r[i] = rv;
-        acc += (double)rv * rv;
+        acc.add(rv * rv);
     }
-    double v1[1] = {acc};
+    double v1[1] = {acc.value()};
     reduce_then<1>(v1, partials, &st->counter, [&](double* t) {
         const double rr = t[0];
         st->iter += 1;

@@ -1,5 +1,5 @@
 // vec_kernels.cuh -- streaming CG vector kernels (section 2.5 of arXiv:1904.03057) with fused
-// FP64 reductions.
+// reductions (FP64 across threads and blocks).
 #pragma once
 
 #include "bsk_device.cuh"
@@ -7,6 +7,28 @@
 namespace bsk {
 
 constexpr int kVecNT = 256;
+
+// Per-thread sum of squares: compensated FP32 for float vectors (GB300 runs FP64 at 1/62 of
+// the FP32 rate, so FP64 per-element arithmetic would dominate these streaming kernels), plain
+// FP64 for double vectors; widened to FP64 once per thread for the deterministic reduction.
+template <typename T>
+struct SqSum {
+    double s = 0.0;
+    __device__ __forceinline__ void add(T v) { s = fma((double)v, (double)v, s); }
+    __device__ __forceinline__ double value() const { return s; }
+};
+template <>
+struct SqSum<float> {
+    float s = 0.f, c = 0.f;
+    __device__ __forceinline__ void add(float v)
+    {
+        const float y = __fsub_rn(__fmul_rn(v, v), c);
+        const float t = __fadd_rn(s, y);
+        c = __fsub_rn(__fsub_rn(t, s), y);
+        s = t;
+    }
+    __device__ __forceinline__ double value() const { return (double)s - (double)c; }
+};
 
 // r -= alpha q; reduction r.r; finaliser `fin` (FIN_UPD in a solve: beta, convergence).
 template <typename T>
@@ -16,14 +38,14 @@ __global__ void __launch_bounds__(kVecNT) k_cg_update(T* __restrict__ r, const T
 {
     if (*(volatile int*)&sc->done) return;
     const T alpha = (T)sc->alpha;
-    double acc = 0.0;
+    SqSum<T> acc;
     for (size_t i = blockIdx.x * (size_t)kVecNT + threadIdx.x; i < len;
          i += (size_t)gridDim.x * kVecNT) {
         const T v = fma(-alpha, q[i], r[i]);
         r[i] = v;
-        acc += (double)v * (double)v;
+        acc.add(v);
     }
-    grid_reduce2<kVecNT>(acc, 0.0, partials, sc, fin, 0);
+    grid_reduce2<kVecNT>(acc.value(), 0.0, partials, sc, fin, 0);
 }
 
 // x += alpha_prev p[p_cur]: applies the last deferred update once the iteration has stopped.
@@ -47,15 +69,15 @@ __global__ void __launch_bounds__(kVecNT) k_cg_init_zero(const T* __restrict__ b
                                                          const uint8_t* __restrict__ mask,
                                                          Scalars* sc, double* partials)
 {
-    double acc = 0.0;
+    SqSum<T> acc;
     for (size_t i = blockIdx.x * (size_t)kVecNT + threadIdx.x; i < len;
          i += (size_t)gridDim.x * kVecNT) {
         const T v = (!mask || mask[i]) ? b[i] : T(0);
         r[i] = v;
         x[i] = T(0);
-        acc += (double)v * (double)v;
+        acc.add(v);
     }
-    grid_reduce2<kVecNT>(acc, acc, partials, sc, FIN_RES_INIT, 0);
+    grid_reduce2<kVecNT>(acc.value(), acc.value(), partials, sc, FIN_RES_INIT, 0);
 }
 
 // dst = mask ? src : 0 (src == dst allowed)
@@ -68,16 +90,17 @@ __global__ void __launch_bounds__(kVecNT) k_copy_masked(const T* src, T* dst, si
         dst[i] = (!mask || mask[i]) ? src[i] : T(0);
 }
 
-// reduction x.x; finaliser FIN_NORM (rr_true).
+// reduction x.x; finaliser FIN_NORM (rr_true). Not on a solver path: FP64 per element, so the
+// result is a reference value for checks (bsk_norm2).
 template <typename T>
 __global__ void __launch_bounds__(kVecNT) k_norm2(const T* __restrict__ x, size_t len, Scalars* sc,
                                                   double* partials)
 {
-    double acc = 0.0;
+    SqSum<double> acc;
     for (size_t i = blockIdx.x * (size_t)kVecNT + threadIdx.x; i < len;
          i += (size_t)gridDim.x * kVecNT)
-        acc += (double)x[i] * (double)x[i];
-    grid_reduce2<kVecNT>(acc, 0.0, partials, sc, FIN_NORM, 0);
+        acc.add(x[i]);
+    grid_reduce2<kVecNT>(acc.value(), 0.0, partials, sc, FIN_NORM, 0);
 }
 
 }  // namespace bsk
