@@ -465,12 +465,13 @@ __global__ void __launch_bounds__(kTNT, (sizeof(T) == 4 && N <= 4 && !BATCH) ? 2
             T* in2 = reinterpret_cast<T*>(st + 2 * LY::in_bytes);
             T* inint = reinterpret_cast<T*>(st + NIN * LY::in_bytes);
 
+            // every thread waits on the stage's mbarrier itself (which also makes the TMA data
+            // visible to it), so no block barrier is needed here; a wait that gives up is
+            // reported after the x-sweep's barrier, which every thread still reaches
             if (!mbar_wait_bounded(&bars[c % S], (c / S) & 1u, 2000000000ull)) {
                 s_abort = 1;
                 s_wait_from = c;
             }
-            __syncthreads();
-            if (s_abort) goto abort;
 
             if constexpr (DF) {
                 // the box holds FP64 as loaded: reflect in FP64, then split in place
@@ -639,6 +640,7 @@ __global__ void __launch_bounds__(kTNT, (sizeof(T) == 4 && N <= 4 && !BATCH) ? 2
                 }
             }
             __syncthreads();
+            if (s_abort) goto abort;
             // the stage is consumed: refill it with plane k + S
             if (tid == 0) {
                 if (k + S < np) {
