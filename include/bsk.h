@@ -53,12 +53,13 @@ extern "C" {
 /* ---- precision modes --------------------------------------------------------------------- */
 #define BSK_F64 0     /* vectors double; operator and reductions in FP64                         */
 #define BSK_F32 1     /* vectors float; operator in FP32; CG scalars and reductions in FP64       */
-#define BSK_F32_IR 2  /* vectors double; FP64 true residual b - A x and FP64 update of x around an
-                         inner FP32 CG (iterative refinement); CG scalars in FP64                 */
+#define BSK_F32_IR 2  /* vectors double; FP64-accurate true residual b - A x (double-float
+                         arithmetic where the grid allows, see bsk_residual) and FP64 update of
+                         x around an inner FP32 CG (iterative refinement); CG scalars in FP64     */
 #define BSK_BF16S 3   /* BF16 storage: op_apply / mass_apply only, vectors bfloat16 (uint16 bit
                          patterns), arithmetic FP32, each output rounded to nearest BF16 once.
                          An operator variant for measuring what BF16 storage costs in accuracy
-                         (about 2^-9 relative per stored value); the solvers reject it           */
+                         (at most 2^-8 relative per stored value); the solvers reject it         */
 
 /* Galerkin kernels of degree-n B-splines on a grid of step h (Table tblBsplines, scalar-product
  * and derivative rows):
@@ -129,6 +130,7 @@ typedef struct bsk_cg_report {
     long long kernel_launches; /* kernels this call launched on the GPU (graph nodes included) */
     int fallback_iter;     /* fcg_solve: inner iteration at which the last inner solve fell back
                               to plain CG, -1 if it never did; 0 for the other solvers            */
+    int net_rejected;      /* fcg_solve: iterations whose network direction was replaced by r   */
     double iter_ms;        /* cg_solve / heat_step: device time (CUDA events on the handle's
                               stream) from the first to the end of the last CUDA-graph launch of
                               the CG iterations, summed over the inner solves; iter_ms divided by
@@ -241,14 +243,16 @@ int bsk_net_adam(bsk_net* net, float lr, float grad_scale);
 /* Accumulated loss (host float) and, if grads is not NULL, the gradients (host floats). */
 int bsk_net_read_loss(bsk_net* net, float* loss, float* grads);
 
-/* Flexible CG (FCG(1)) preconditioned by the network, z = ||r|| N(r / ||r||) / (hx hy hz) (the
- * coarse path is a correction on top of the full-resolution 3^3 filter Wf), as the inner FP32
- * solver of iterative
- * refinement (handle precision BSK_F32_IR; b, x double). The network must have been created for
- * the handle's grid. Falls back to plain CG for the rest of an inner solve when the network's
- * direction is not a descent direction or the residual stops improving (stall_window,
- * default 8); the FP64 true residual decides convergence. net == NULL runs the same iteration
- * without preconditioner (plain CG). The first call allocates the handle's FCG work vectors. */
+/* Flexible CG (FCG(1), one previous direction kept A-orthogonal) preconditioned by the network,
+ * z = ||r|| N(r / ||r||) / (hx hy hz), as the inner FP32 solver of iterative refinement (handle
+ * precision BSK_F32_IR; b, x double). The network must have been created for the handle's grid.
+ * An iteration whose network direction is no descent direction (z.r <= 0) uses z = r for that
+ * iteration (counted in report->net_rejected); a non-finite network output, or a residual that
+ * has not dropped by 2 % within stall_window iterations (default 8), switches the rest of that
+ * inner solve to plain CG (report->fallback_iter). The FP64-accurate true residual outside
+ * decides convergence, so the network changes the speed, not the answer. net == NULL runs the
+ * same iteration without preconditioner (plain CG). The first call allocates the handle's FCG
+ * work vectors. */
 int fcg_solve(bsk_handle* h, bsk_net* net, const void* b, void* x, const bsk_cg_opts* opts,
               bsk_cg_report* report);
 

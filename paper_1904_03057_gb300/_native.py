@@ -35,7 +35,7 @@ class CgReport(ctypes.Structure):
         ("status", ctypes.c_int), ("iterations", ctypes.c_int),
         ("outer_iterations", ctypes.c_int), ("rel_residual", ctypes.c_double),
         ("elapsed_ms", ctypes.c_double), ("kernel_launches", ctypes.c_longlong),
-        ("fallback_iter", ctypes.c_int), ("iter_ms", ctypes.c_double),
+        ("fallback_iter", ctypes.c_int), ("net_rejected", ctypes.c_int), ("iter_ms", ctypes.c_double),
     ]
 
 

@@ -49,7 +49,8 @@ def _report(rep: _native.CgReport) -> dict:
     return {"status": rep.status, "iterations": rep.iterations,
             "outer_iterations": rep.outer_iterations, "rel_residual": rep.rel_residual,
             "elapsed_ms": rep.elapsed_ms, "kernel_launches": rep.kernel_launches,
-            "fallback_iter": rep.fallback_iter, "iter_ms": rep.iter_ms}
+            "fallback_iter": rep.fallback_iter, "net_rejected": rep.net_rejected,
+            "iter_ms": rep.iter_ms}
 
 
 class Handle:

@@ -890,7 +890,7 @@ extern "C" int fcg_solve(bsk_handle* h, bsk_net* net, const void* bv, void* xv, 
         return bsk_net_forward(n, r, m, z);
     };
     int rc;
-    int total_iters = 0, outer = 0, st = BSK_NOT_CONVERGED, fb = -1;
+    int total_iters = 0, outer = 0, st = BSK_NOT_CONVERGED, fb = -1, total_rejected = 0;
     double rel = 0.0;
     BSK_LAUNCH(h, bsk::launch_copy_masked<double>(x, x, h->len, h->mask, h->stream));
     for (;; outer++) {
@@ -910,13 +910,14 @@ extern "C" int fcg_solve(bsk_handle* h, bsk_net* net, const void* bv, void* xv, 
         double inner = std::max(o.inner_tol, 0.3 * o.tol / rel);
         if (inner > 0.5) inner = 0.5;
         BSK_LAUNCH(h, bsk::launch_ir_scale_down(h->r64, static_cast<float*>(h->r), h->len, h->sc64, h->stream));
-        int it = 0, fbi = -1;
+        int it = 0, fbi = -1, rej = 0;
         // the network predicts errors in units of 1 / (hx hy hz), the inverse mass scale
         const double out_scale = 1.0 / (h->h[0] * h->h[1] * h->h[2]);
         int ist = bsk::fcg_inner(V, h->len, h->mask, inner, o.max_iter - total_iters, o.stall_window,
-                                 out_scale, 0.0, op, net, netf, h->stream, &it, &fbi, o.time_limit, t0);
+                                 out_scale, 0.0, op, net, netf, h->stream, &it, &fbi, &rej, o.time_limit, t0);
         h->launches += 6LL * it;
         total_iters += it;
+        total_rejected += rej;
         if (fbi >= 0) fb = fbi;
         if (ist == BSK_ETIMEOUT || ist == BSK_ECUDA) return ist;
         if (ist == BSK_EBREAKDOWN && it == 0) return ist;
@@ -930,6 +931,7 @@ extern "C" int fcg_solve(bsk_handle* h, bsk_net* net, const void* bv, void* xv, 
         rep->elapsed_ms = 1e3 * seconds_since(t0);
         rep->kernel_launches = h->launches;
         rep->fallback_iter = fb;
+        rep->net_rejected = total_rejected;
     }
     return st;
 }

@@ -128,7 +128,7 @@ size_t fcg_state_bytes();
 int fcg_inner(const FcgVectors& V, size_t n, const uint8_t* mask, double tol, int max_iter, int stall_window,
               double out_scale, double jac, const std::function<int(const float*, float*)>& op, bsk_net* net,
               const std::function<int(bsk_net*, const float*, const uint8_t*, float*)>& net_forward,
-              cudaStream_t s, int* iters, int* fallback_iter, double time_limit,
+              cudaStream_t s, int* iters, int* fallback_iter, int* rejected, double time_limit,
               std::chrono::steady_clock::time_point t0);
 
 cudaError_t launch_ir_scale_down(const double* r64, float* r32, size_t len, const Scalars* outer,

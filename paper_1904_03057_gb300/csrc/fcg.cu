@@ -290,7 +290,7 @@ namespace bsk {
 int fcg_inner(const FcgVectors& V, size_t n, const uint8_t* mask, double tol, int max_iter, int stall_window,
               double out_scale, double jac, const std::function<int(const float*, float*)>& op, bsk_net* net,
               const std::function<int(bsk_net*, const float*, const uint8_t*, float*)>& net_forward,
-              cudaStream_t s, int* iters, int* fallback_iter, double time_limit,
+              cudaStream_t s, int* iters, int* fallback_iter, int* rejected, double time_limit,
               std::chrono::steady_clock::time_point t0)
 {
     FcgState* st = reinterpret_cast<FcgState*>(V.state);
@@ -336,6 +336,7 @@ int fcg_inner(const FcgVectors& V, size_t n, const uint8_t* mask, double tol, in
     }
     *iters = h.iter;
     *fallback_iter = h.fallback_iter;
+    *rejected = h.rejected;
     switch (h.status) {
     case 0: return BSK_OK;
     case 1: return BSK_NOT_CONVERGED;
