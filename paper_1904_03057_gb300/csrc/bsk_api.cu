@@ -101,6 +101,7 @@ struct bsk_handle {
     cudaStream_t cap_stream;   // private stream used only to capture the CG graph (the legacy
                                // default stream cannot be captured; the graph runs on `stream`)
     uint8_t* mask;
+    uint8_t* occ;                 // tile occupancy per plane of the mask (TMA grids), or null
     double M[3][bsk::kMaxTaps];   // per-axis mass kernels
     double K[3][bsk::kMaxTaps];   // per-axis stiffness kernels (not yet multiplied by dt)
     // CG vectors in the CG element type (double for BSK_F64, float otherwise). The single-pass
@@ -144,6 +145,7 @@ void fill_tma(const bsk_handle* h, bsk::TmaLaunch& L, int mode)
     L.ny = h->ny;
     L.nz = h->nz;
     L.mask = h->mask;
+    L.occ = h->occ;
     for (int d = 0; d < 3; d++)
         for (int j = 0; j < bsk::kMaxTaps; j++) {
             L.M[d][j] = h->M[d][j];
@@ -627,6 +629,13 @@ extern "C" int bsk_create(const bsk_problem* prob, int precision, void* stream, 
         BSK_ALLOC(h->mask, len);
         e = cudaMemcpyAsync(h->mask, prob->mask, len, cudaMemcpyDeviceToDevice, h->stream);
         if (e != cudaSuccess) return cleanup(cuda_fail(e, "mask copy"));
+        if (h->use_tma || h->tma64) {
+            // brick occupancy of the mask: the TMA kernels skip the (tile, z-chunk) items that
+            // hold no active node
+            BSK_ALLOC(h->occ, (size_t)bsk::tma_tiles(prob->nx, prob->ny) * prob->nz);
+            e = bsk::launch_tile_occupancy(h->mask, prob->nx, prob->ny, prob->nz, h->occ, h->stream);
+            if (e != cudaSuccess) return cleanup(cuda_fail(e, "occupancy launch"));
+        }
     }
     const size_t ces = cg_es(h);
     if (precision != BSK_BF16S) {   // the BF16-storage variant has no solver
@@ -645,6 +654,20 @@ extern "C" int bsk_create(const bsk_problem* prob, int precision, void* stream, 
         } else {
             BSK_ALLOC(h->bvec, len * ces);
         }
+    }
+    if (h->occ) {
+        // items skipped by occupancy leave their outputs untouched: every work vector starts
+        // zero, so its inactive part stays zero
+        for (void* v : {h->x, h->r, h->p0, h->p1, h->q, h->r2, h->q2, h->bvec})
+            if (v) {
+                e = cudaMemsetAsync(v, 0, len * ces, h->stream);
+                if (e != cudaSuccess) return cleanup(cuda_fail(e, "memset"));
+            }
+        for (void* v : {(void*)h->r64, (void*)h->b64})
+            if (v) {
+                e = cudaMemsetAsync(v, 0, len * sizeof(double), h->stream);
+                if (e != cudaSuccess) return cleanup(cuda_fail(e, "memset"));
+            }
     }
     BSK_ALLOC(h->sc, sizeof(Scalars));
     BSK_ALLOC(h->sc64, sizeof(Scalars));
@@ -677,7 +700,7 @@ extern "C" void bsk_destroy(bsk_handle* h)
     if (!h) return;
     cudaStreamSynchronize(h->stream);
     if (h->graph) cudaGraphExecDestroy(h->graph);
-    void* ptrs[] = {h->mask, h->x, h->r, h->p0, h->p1, h->q, h->bvec, h->r2, h->q2, h->r64, h->b64,
+    void* ptrs[] = {h->mask, h->occ, h->x, h->r, h->p0, h->p1, h->q, h->bvec, h->r2, h->q2, h->r64, h->b64,
                     h->sc, h->sc64, h->sc_aux, h->partials, h->work};
     for (void* p : ptrs)
         if (p) cudaFree(p);
@@ -1054,6 +1077,9 @@ extern "C" int bsk_residual(bsk_handle* h, const void* b, const void* x, void* r
     if (overlaps(r, x, h->len * es) || overlaps(r, b, h->len * es)) return fail(BSK_EINVAL, "r overlaps b or x");
     h->launches = 0;
     int rc;
+    // the TMA kernels leave the items without active nodes unwritten: the caller's r is
+    // zeroed first so that it reads zero off the mask
+    if (h->occ) BSK_CUDA(cudaMemsetAsync(r, 0, h->len * es, h->stream));
     if (es == sizeof(double)) {
         if ((rc = enqueue_residual64(h, (const double*)b, (const double*)x, (double*)r, h->sc_aux, fp64 != 0)))
             return rc;

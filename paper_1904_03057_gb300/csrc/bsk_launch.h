@@ -81,11 +81,15 @@ struct TmaLaunch {
     void* out2;                  // CG p
     void* xvec;                  // CG x (in place)
     const uint8_t* mask;         // node mask or null (outputs zeroed where 0; inputs must be)
+    const uint8_t* occ;          // tile occupancy per plane (tile_occupancy), null without a mask
     Scalars* sc;
     double* partials;            // 3 doubles per block of the resident grid
     unsigned int* work;          // 2 counters, zero between launches (dynamic item queue)
     int fin;
 };
+// occ[z * tiles + tile] = 1 iff the 64 x 24 tile (x fastest) has an active node in plane z.
+cudaError_t launch_tile_occupancy(const uint8_t* mask, int nx, int ny, int nz, uint8_t* occ, cudaStream_t s);
+int tma_tiles(int nx, int ny);
 struct dfl;   // double-float element (dfloat.cuh): the FP64-accurate residual on the FP32 pipes
 template <typename T>
 int tma_max_degree();

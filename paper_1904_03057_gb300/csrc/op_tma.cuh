@@ -46,6 +46,8 @@ struct TmaArgs {
     T* xvec;              // CG x, updated in place
     const uint8_t* mask;  // node mask [nz][ny][nx] or null: outputs (q, r) are zeroed where it is 0;
                           // the inputs must already be zero there (principal submatrix)
+    const uint8_t* occ;   // with a mask: occ[z * tiles + tile] != 0 iff tile has an active node in
+                          // plane z; items with none are skipped (their outputs stay zero)
     int nx, ny, nz;
     int pitch;            // elements per row in memory (>= nx; rows of 16-byte multiples)
     int tiles_x, tiles_y, tz, nitems;
@@ -427,6 +429,18 @@ __global__ void __launch_bounds__(kTNT, (sizeof(T) == 4 && N <= 4 && !BATCH) ? 2
         const int np = (z1 - z0) + 2 * N;
         const bool patch_x = (x0 == 0) || (x0 + kTX + N > nx);
         const bool patch_y = (y0 == 0) || (y0 + kTY + N > ny);
+        if (!BATCH && a.occ) {
+            // brick occupancy: an item whose output box holds no active node is left out. Its
+            // outputs are zero and already zero in the solvers' vectors (which are zero off the
+            // mask from creation on), and it adds nothing to the dot products.
+            bool act = false;
+            for (int zt = z0 + tid; zt < z1; zt += kTNT) act |= a.occ[(size_t)zt * ntiles + tile] != 0;
+            if (!__syncthreads_or(act)) {
+                if (tid == 0) fetch();
+                __syncthreads();
+                continue;
+            }
+        }
 
         auto issue = [&](int k) {   // plane k of this item -> stage (cnt + k) % S
             const uint32_t c = cnt + (uint32_t)k;

@@ -148,6 +148,7 @@ cudaError_t launch_one(const TmaLaunch& L, cudaStream_t s)
     a.out2 = static_cast<BSK_T*>(L.out2);
     a.xvec = static_cast<BSK_T*>(L.xvec);
     a.mask = L.mask;
+    a.occ = L.mask ? L.occ : nullptr;
     a.nx = L.nx;
     a.ny = L.ny;
     a.nz = L.nz;

@@ -78,3 +78,41 @@ def test_refinement_with_either_residual(api):
     d = (torch.linalg.vector_norm(xs[0] - xs[1]) / torch.linalg.vector_norm(xs[1])).item()
     assert d <= 1e-8, d
     H.close()
+
+
+def test_sparse_mask_skips_empty_bricks(api):
+    """A mask whose active nodes fill a few of the 64 x 24 tiles: the TMA kernels skip the
+    empty (tile, z-chunk) items. Residual parity and zeros off the mask, and CG solves (FP64 and
+    FP32 with refinement) that the oracle confirms."""
+    from paper_1904_03057_gb300 import inputs
+    nx, ny, nz, n, dt = 200, 80, 64, 3, 1e-3
+    h = 1.0 / (nx + 1)
+    mask = inputs.union_of_spheres_mask(nx, ny, nz, [(0.2, 0.15, 0.15), (0.7, 0.25, 0.2)], [0.06, 0.08],
+                                        h=h)
+    m = mask.numpy()
+    tiles_active = sum(int(m[:, ty * 24:(ty + 1) * 24, tx * 64:(tx + 1) * 64].any())
+                       for ty in range((ny + 23) // 24) for tx in range((nx + 63) // 64))
+    assert 0 < tiles_active < 8            # most of the 16 tiles are empty
+    rng = np.random.default_rng(3)
+    x = rng.standard_normal((nz, ny, nx)) * m
+    b = rng.standard_normal((nz, ny, nx)) * m * h ** 3
+    P = oracle.Problem(nx, ny, nz, n, h, dt=dt, mask=m)
+    r_ref = b - oracle.op_stencil(P, x)
+    scale = np.max(oracle.abs_op(P, np.abs(x)) + np.abs(b))
+    H = api.Handle(nx, ny, nz, n, h, dt, mask=mask.cuda(), precision="f32_ir")
+    r, rr, bb = H.residual(torch.from_numpy(b).cuda(), torch.from_numpy(x).cuda())
+    r = r.cpu().numpy()
+    assert np.max(np.abs(r - r_ref)) <= 1e-12 * scale
+    assert np.all(r[m == 0] == 0)
+    tol = 1e-9
+    for prec in ("f32_ir", "f64"):
+        Hs = api.Handle(nx, ny, nz, n, h, dt, mask=mask.cuda(), precision=prec)
+        u = torch.zeros((nz, ny, nx), dtype=torch.float64, device="cuda")
+        rep = Hs.cg_solve(torch.from_numpy(b).cuda(), u, tol=tol)
+        assert rep["status"] == 0, rep
+        un = u.cpu().numpy()
+        assert np.all(un[m == 0] == 0)
+        res = b - oracle.op_stencil(P, un)
+        assert np.linalg.norm(res) <= 1.5 * tol * np.linalg.norm(b), prec
+        Hs.close()
+    H.close()
