@@ -39,8 +39,8 @@ WORKLOAD = "heat3d_928cube_cubic_f32sweeps_f64refinement"
 # dram__bytes_write.sum over the unknowns of the launch), from the ncu capture summarised in
 # profiles/k_op_tma_cg_f32_928cube_dram.md; valid only while the kernel's sources hash to
 # CG_TRAFFIC_SOURCES_SHA256.
-CG_TRAFFIC_BYTES_PER_UNKNOWN = 40.12   # 928^3, two launches: 19.31 GB read + 12.75 GB written
-CG_TRAFFIC_SOURCES_SHA256 = "1e77c52d0845c2defff52733ef1878f5af1cb7dea1987b89eb64dc3a2603a7e0"
+CG_TRAFFIC_BYTES_PER_UNKNOWN = 37.98   # 928^3, three launches: 17.60 GB read + 12.76 GB written
+CG_TRAFFIC_SOURCES_SHA256 = "d65b6c4b6e4c6cf1025fd273330d4b4509edb382f29da12f3fef2b15bbbb1e9d"
 CG_KERNEL_SOURCES = ("op_tma.cuh", "tma_impl.cuh", "tma_util.cuh", "bsk_device.cuh", "tma_f32.cu", "dfloat.cuh")
 
 
