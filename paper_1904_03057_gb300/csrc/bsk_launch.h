@@ -129,6 +129,8 @@ struct FcgVectors {
     void* state;         // fcg_state_bytes()
 };
 size_t fcg_state_bytes();
+// The network maps r linearly (BSK_ACT_LINEAR): N(r / ||r||) ||r|| = N(r), no normalisation.
+bool net_linear(const bsk_net* net);
 int fcg_inner(const FcgVectors& V, size_t n, const uint8_t* mask, double tol, int max_iter, int stall_window,
               double out_scale, double jac, const std::function<int(const float*, float*)>& op, bsk_net* net,
               const std::function<int(bsk_net*, const float*, const uint8_t*, float*)>& net_forward,

@@ -34,6 +34,7 @@ struct FcgState {
     double zscale;       // ||r_k||: the network sees r / ||r||
     double out_scale;    // the network's output unit: z = ||r|| out_scale N(r / ||r||) + jac r
     double jac;          // Jacobi part of the preconditioner: 1 / A_ii
+    int unit_input;      // linear network: it sees r itself (z = out_scale N(r)), no normalisation
     int iter, max_iter, done, status;
     int use_r;           // 1: plain CG direction for the rest of the solve (fallback engaged)
     int dir_r;           // 1: this iteration's direction is r (use_r, or z . r <= 0 this time)
@@ -160,7 +161,7 @@ __global__ void __launch_bounds__(NT) k_fcg_direction(const float* __restrict__ 
                                                       size_t n, FcgState* st, double* partials)
 {
     if (st->done) return;
-    const float s = (float)(st->zscale * st->out_scale);
+    const float s = (float)((st->unit_input ? 1.0 : st->zscale) * st->out_scale);
     const float jac = (float)st->jac;
     FSum zq, zr, rq;
     GRID_STRIDE(i, n)
@@ -300,6 +301,8 @@ int fcg_inner(const FcgVectors& V, size_t n, const uint8_t* mask, double tol, in
     h.max_iter = max_iter;
     h.stall_window = stall_window > 0 ? stall_window : 8;
     h.use_r = net ? 0 : 1;
+    const bool lin = net && net_linear(net);
+    h.unit_input = lin ? 1 : 0;
     h.fallback_iter = -1;
     h.out_scale = out_scale;
     h.jac = jac;
@@ -315,9 +318,11 @@ int fcg_inner(const FcgVectors& V, size_t n, const uint8_t* mask, double tol, in
         // a few iterations between polls
         for (int j = 0; j < 4; j++, k++) {
             if (net) {
-                k_fcg_normalise<<<gb, NT, 0, s>>>(V.r, V.rn, n, st);
-                FCUDA(cudaGetLastError());
-                if (int rc = net_forward(net, V.rn, mask, V.zn)) return rc;
+                if (!lin) {
+                    k_fcg_normalise<<<gb, NT, 0, s>>>(V.r, V.rn, n, st);
+                    FCUDA(cudaGetLastError());
+                }
+                if (int rc = net_forward(net, lin ? V.r : V.rn, mask, V.zn)) return rc;
             }
             k_fcg_direction<<<gb, NT, 0, s>>>(net ? V.zn : V.r, V.z, V.r, V.q, n, st, V.partials);
             k_fcg_p<<<gb, NT, 0, s>>>(V.z, V.r, V.p, n, st);

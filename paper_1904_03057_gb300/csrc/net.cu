@@ -194,58 +194,94 @@ __global__ void k_down1(const float* __restrict__ x, D3 din, __nv_bfloat16* __re
     }
 }
 
-// z[o] = mask * ( sum_{k valid} sum_c W[k][c] a[srcT(o,k)][c] + b + sum_k Wf[k] r[o + k - 1] ),
-// a coarse (BF16), z and r fine.
-__global__ void k_up1(const __nv_bfloat16* __restrict__ a, D3 din, float* __restrict__ z, D3 dout,
-                      const float* __restrict__ W, const float* __restrict__ bias,
-                      const uint8_t* __restrict__ mask, const float* __restrict__ r,
-                      const float* __restrict__ Wf)
+// Output layer, z[o] = mask * ( sum_{k valid} sum_c W[k][c] a[srcT(o,k)][c] + b
+//                                 + sum_k Wf[k] r[o + k - 1] ), a coarse (BF16), z and r fine.
+// One thread per 2 x 2 x 2 block of fine voxels (2m .. 2m+1 per axis), which gathers from the
+// 2 x 2 x 2 coarse voxels m .. m+1, so that each coarse voxel is loaded once for the eight
+// outputs it feeds. Along an axis, fine 2m + e
+// takes coarse m + d with tap k = e + 1 - 2d (the transposed stride-2 gather of src_index:
+// (e, d) = (0, 0) -> 1, (1, 0) -> 2, (1, 1) -> 0, (0, 1) none).
+__global__ void __launch_bounds__(128) k_up1b(const __nv_bfloat16* __restrict__ a, D3 din, float* __restrict__ z,
+                                              D3 dout, const float* __restrict__ W,
+                                              const float* __restrict__ bias, const uint8_t* __restrict__ mask,
+                                              const float* __restrict__ r, const float* __restrict__ Wf)
 {
     __shared__ float sW[KT * C];
     __shared__ float sF[KT];
     for (int i = threadIdx.x; i < KT * C; i += blockDim.x) sW[i] = W[i];
     for (int i = threadIdx.x; i < KT; i += blockDim.x) sF[i] = Wf[i];
     __syncthreads();
-    const long long n = (long long)dout.nx * dout.ny * dout.nz;
-    const long long o = blockIdx.x * (long long)blockDim.x + threadIdx.x;
-    if (o >= n) return;
-    if (mask && !mask[o]) { z[o] = 0.f; return; }
-    const int ox = (int)(o % dout.nx), oy = (int)((o / dout.nx) % dout.ny), oz = (int)(o / ((long long)dout.nx * dout.ny));
-    float acc = bias ? bias[0] : 0.f;
-    for (int kz = 0; kz < 3; kz++) {
-        const int iz = src_index(CONVT_S2, oz, kz, din.nz);
-        if (iz < 0) continue;
-        for (int ky = 0; ky < 3; ky++) {
-            const int iy = src_index(CONVT_S2, oy, ky, din.ny);
-            if (iy < 0) continue;
-            for (int kx = 0; kx < 3; kx++) {
-                const int ix = src_index(CONVT_S2, ox, kx, din.nx);
-                if (ix < 0) continue;
-                const __nv_bfloat162* av =
-                    reinterpret_cast<const __nv_bfloat162*>(a + (((long long)iz * din.ny + iy) * din.nx + ix) * C);
-                const float* w = sW + ((kz * 3 + ky) * 3 + kx) * C;
+    const long long nb = (long long)din.nx * din.ny * din.nz;
+    const long long b = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    if (b >= nb) return;
+    const int mx = (int)(b % din.nx), my = (int)((b / din.nx) % din.ny), mz = (int)(b / ((long long)din.nx * din.ny));
+    int act = 0;   // bit e: fine output e = (ez, ey, ex) exists and is active
 #pragma unroll
-                for (int c = 0; c < C; c += 2) {
-                    const float2 f = __bfloat1622float2(av[c / 2]);
-                    acc = fmaf(w[c], f.x, fmaf(w[c + 1], f.y, acc));
+    for (int e = 0; e < 8; e++) {
+        const int fz = 2 * mz + (e >> 2), fy = 2 * my + ((e >> 1) & 1), fx = 2 * mx + (e & 1);
+        if (fz < dout.nz && fy < dout.ny && fx < dout.nx) {
+            const long long o = ((long long)fz * dout.ny + fy) * dout.nx + fx;
+            if (!mask || mask[o]) act |= 1 << e;
+            else z[o] = 0.f;
+        }
+    }
+    if (!act) return;
+    float acc[8];
+#pragma unroll
+    for (int e = 0; e < 8; e++) acc[e] = 0.f;
+#pragma unroll
+    for (int d = 0; d < 8; d++) {
+        const int dz = d >> 2, dy = (d >> 1) & 1, dx = d & 1;
+        const int cz = mz + dz, cy = my + dy, cx = mx + dx;
+        if (cz >= din.nz || cy >= din.ny || cx >= din.nx) continue;
+        const uint4* av = reinterpret_cast<const uint4*>(a + (((long long)cz * din.ny + cy) * din.nx + cx) * C);
+        const uint4 v0 = av[0], v1 = av[1];   // 16 BF16 channels
+        const uint32_t wv[8] = {v0.x, v0.y, v0.z, v0.w, v1.x, v1.y, v1.z, v1.w};
+        float f[C];
+#pragma unroll
+        for (int c = 0; c < C / 2; c++) {
+            const float2 t = __bfloat1622float2(*reinterpret_cast<const __nv_bfloat162*>(&wv[c]));
+            f[2 * c] = t.x;
+            f[2 * c + 1] = t.y;
+        }
+#pragma unroll
+        for (int e = 0; e < 8; e++) {
+            const int ez = e >> 2, ey = (e >> 1) & 1, ex = e & 1;
+            if ((dz && !ez) || (dy && !ey) || (dx && !ex)) continue;   // no tap joins them
+            if (!(act & (1 << e))) continue;
+            const int kz = ez + 1 - 2 * dz, ky = ey + 1 - 2 * dy, kx = ex + 1 - 2 * dx;
+            const float* w = sW + ((kz * 3 + ky) * 3 + kx) * C;
+            float s0 = 0.f, s1 = 0.f;
+#pragma unroll
+            for (int c = 0; c < C; c += 2) {
+                s0 = fmaf(w[c], f[c], s0);
+                s1 = fmaf(w[c + 1], f[c + 1], s1);
+            }
+            acc[e] += s0 + s1;
+        }
+    }
+    const float b5 = bias ? bias[0] : 0.f;
+#pragma unroll
+    for (int e = 0; e < 8; e++) {
+        if (!(act & (1 << e))) continue;
+        const int fz = 2 * mz + (e >> 2), fy = 2 * my + ((e >> 1) & 1), fx = 2 * mx + (e & 1);
+        float fine = 0.f;   // the full-resolution filter of r
+        for (int kz = 0; kz < 3; kz++) {
+            const int iz = fz + kz - 1;
+            if (iz < 0 || iz >= dout.nz) continue;
+            for (int ky = 0; ky < 3; ky++) {
+                const int iy = fy + ky - 1;
+                if (iy < 0 || iy >= dout.ny) continue;
+                const float* rr = r + ((long long)iz * dout.ny + iy) * dout.nx;
+#pragma unroll
+                for (int kx = 0; kx < 3; kx++) {
+                    const int ix = fx + kx - 1;
+                    if (ix >= 0 && ix < dout.nx) fine = fmaf(sF[(kz * 3 + ky) * 3 + kx], rr[ix], fine);
                 }
             }
         }
+        z[((long long)fz * dout.ny + fy) * dout.nx + fx] = acc[e] + b5 + fine;
     }
-    for (int kz = 0; kz < 3; kz++) {
-        const int iz = src_index(CONV_S1, oz, kz, dout.nz);
-        if (iz < 0) continue;
-        for (int ky = 0; ky < 3; ky++) {
-            const int iy = src_index(CONV_S1, oy, ky, dout.ny);
-            if (iy < 0) continue;
-            for (int kx = 0; kx < 3; kx++) {
-                const int ix = src_index(CONV_S1, ox, kx, dout.nx);
-                if (ix < 0) continue;
-                acc = fmaf(sF[(kz * 3 + ky) * 3 + kx], r[((long long)iz * dout.ny + iy) * dout.nx + ix], acc);
-            }
-        }
-    }
-    z[o] = acc;
 }
 
 // dWf[k] += sum_o dz[o] r[o + k - 1] (fine grid, FP32)
@@ -526,8 +562,8 @@ int forward(bsk_net* N, const float* r, const uint8_t* mask, float* z)
     NCUDA(conv16<CONV_S2>(N->a1, N->d1, N->a2, N->d2, N->w2, bias(OFF_B2), nullptr, relu, N->stream));
     NCUDA(conv16<CONV_S1>(N->a2, N->d2, N->a3, N->d2, N->w3, bias(OFF_B3), nullptr, relu, N->stream));
     NCUDA(conv16<CONVT_S2>(N->a3, N->d2, N->a4, N->d1, N->w4, bias(OFF_B4), N->a1, relu, N->stream));
-    k_up1<<<blocks_for(vox(N->d0), 128), 128, 0, N->stream>>>(N->a4, N->d1, z, N->d0, R + OFF_W5, bias(OFF_B5), mask,
-                                                              r, P + OFF_WF);
+    k_up1b<<<blocks_for(vox(N->d1), 128), 128, 0, N->stream>>>(N->a4, N->d1, z, N->d0, R + OFF_W5, bias(OFF_B5),
+                                                               mask, r, P + OFF_WF);
     NCUDA(cudaGetLastError());
     return BSK_OK;
 }
@@ -607,6 +643,10 @@ extern "C" int bsk_net_set_activation(bsk_net* N, int act)
     N->linear = act == BSK_ACT_LINEAR;
     return BSK_OK;
 }
+
+namespace bsk {
+bool net_linear(const bsk_net* N) { return N && N->linear; }
+}  // namespace bsk
 
 extern "C" int bsk_net_get_params(bsk_net* N, float* params)
 {
