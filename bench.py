@@ -191,8 +191,8 @@ def _timed_ms(fn):
     return e0.elapsed_time(e1), out
 
 
-def batch_config4():
-    """Config 4: 64 independent boxes (dims U{48..160} per axis, degrees 2..5, 8 Gaussian
+def batch_64_boxes():
+    """64 independent boxes (dims U{48..160} per axis, degrees 2..5, 8 Gaussian
     sources each, dt = 1e-3), one implicit Euler step of every box to a 1e-8 true residual:
     the batched persistent solver (autotuned decomposition) against the same problems solved one
     after another through single handles. Throughput counts unknowns x operator applications."""
@@ -231,8 +231,8 @@ def batch_config4():
             "max_rel_diff_batched_vs_sequential": diff, "autotune": tune}
 
 
-def mixed_precision_config2(steps: int = 50):
-    """Config 2: 256^3, sphere mask r = 0.45 at the centre, 32 Gaussian sources (sigma 0.03,
+def mixed_precision_sphere256(steps: int = 50):
+    """256^3, sphere mask r = 0.45 at the centre, 32 Gaussian sources (sigma 0.03,
     centres U[0.2,0.8]^3, seed 2), u0 = 0, dt = 1e-3, `steps` implicit Euler steps to a 1e-8 true
     residual, FP64 CG against FP32 CG with FP64-accurate refinement: time per step, iterations,
     and the relative difference of the final fields."""
@@ -263,7 +263,7 @@ def mixed_precision_config2(steps: int = 50):
 
 
 def fcg_race():
-    """The 512^3 union-of-40-spheres race (config 5): one implicit Euler step from u = 0 with a
+    """The 512^3 union-of-40-spheres race: one implicit Euler step from u = 0 with a
     Gaussian source, dt = 1e-3, each solver from x = 0 to a 1e-8 true relative residual: plain
     FP64 CG, FP32 CG with FP64 refinement, and flexible CG preconditioned by the trained linear
     network inside FP64 refinement. The network is trained first (32^3 crops at the same h and
@@ -486,8 +486,8 @@ def run_ours(args, rank, world, dist):
     if rank == 0 and not args.no_fcg_race and args.grid == N_GRID:
         line["fcg_race"] = fcg_race()
     if rank == 0 and not args.no_extra_configs and args.grid == N_GRID:
-        line["batch_config4"] = batch_config4()
-        line["mixed_precision_config2"] = mixed_precision_config2()
+        line["batch_64_boxes"] = batch_64_boxes()
+        line["mixed_precision_sphere256"] = mixed_precision_sphere256()
     if rank == 0 and not args.no_cpu_baseline:
         v, cores, secs, desc = cpu_oracle_sample()
         line["cpu_baseline"] = {"value": v, "unit": "GDoF/s", "cores": cores, "kind": "oracle",

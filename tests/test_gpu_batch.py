@@ -96,8 +96,8 @@ def test_batch_autotune_then_solve(api, tmp_path):
     assert all(r["status"] == 0 and r["rel_residual"] <= tol for r in reps)
 
 
-def test_config4_batch_one_step(api):
-    """Config 4: 64 problems, dims U{48..160} per axis, degrees {2,3,4,5}, 8 Gaussian sources
+def test_batch_64_boxes_one_step(api):
+    """64 problems, dims U{48..160} per axis, degrees {2,3,4,5}, 8 Gaussian sources
     each, dt = 1e-3; one implicit Euler step of the whole batch to a 1e-8 true residual."""
     dt, tol = 1e-3, 1e-8
     specs = inputs.batch_problems(seed=4)

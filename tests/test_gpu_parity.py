@@ -152,7 +152,7 @@ def test_cg_solve_matches_oracle(api, orc, precision, tol, masked, nx):
         assert np.all(x[p.mask == 0] == 0)
 
 
-def test_heat_step_config1_closed_form(api, orc):
+def test_heat_step_32cube_closed_form(api, orc):
     """32^3, cubic, sin sin sin initial coefficients, dt = 1e-3, 10 steps, tol 1e-10, FP64."""
     N, n, dt, K, tol = 32, 3, 1e-3, 10, 1e-10
     h = 1 / (N + 1)
@@ -174,7 +174,7 @@ def test_heat_step_config1_closed_form(api, orc):
 
 
 def test_heat_step_masked_gaussian_sources_fp64_vs_ir(api, orc):
-    """Reduced config 2: sphere mask r = 0.45, 32 Gaussian sources (sigma 0.03, seed 2),
+    """A reduced sphere-masked heat problem: sphere mask r = 0.45, 32 Gaussian sources (sigma 0.03, seed 2),
     u0 = 0, dt = 1e-3, a few steps; FP64 CG vs FP32-sweep + FP64 refinement vs the oracle."""
     N, n, dt, K, tol = 48, 3, 1e-3, 3, 1e-10
     h = 1 / (N + 1)
@@ -280,7 +280,7 @@ def test_full_size_928_operator_sampled_and_eigen(api, orc):
 
 
 def test_full_size_928_heat_step_ir_closed_form(api):
-    """Config 3: 928^3, 64 seeded sine modes, dt = 5e-4, one implicit Euler step with FP32 sweeps
+    """928^3, 64 seeded sine modes, dt = 5e-4, one implicit Euler step with FP32 sweeps
     and FP64 refinement; each mode must decay by exactly its discrete factor g_k."""
     N, n, dt, tol = 928, 3, 5e-4, 1e-8
     h = 1 / (N + 1)
