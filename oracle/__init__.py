@@ -289,3 +289,52 @@ def abs_op(prob: Problem, x):
 def set_plant(mode: int) -> None:
     """Test hook: 0 = correct odd reflection, 1 = zero ghosts, 2 = even reflection."""
     lib().orc_set_plant(int(mode))
+
+
+def sampled_basis_1d(n: int, N: int, h: float = None) -> np.ndarray:
+    """B[j, i] = psi_i(x_j): the odd-reflected degree-n basis function of unknown i sampled at
+    node j of an axis with N unknowns (positions (j + 1) h, faces at 0 and (N + 1) h). The
+    reflected function is the B-spline centred at (i + 1) minus its mirror images about the
+    faces (Eq. expansion with the zero-Dirichlet reading); in units of h it does not depend on h.
+    This matrix is the indirect B-spline transform at the nodes along one axis (Fig.
+    figBspnSignProc, section 2.3)."""
+    P = 2 * (N + 1)                  # the odd extension is periodic with this period
+    B = np.zeros((N, N))
+    for i in range(N):
+        I = i + 1
+        for j in range(N):
+            J = j + 1
+            v = 0.0
+            # images of the odd, P-periodic extension: +I + m P and -(I) + m P, m = -1, 0, 1
+            for s, c in ((1.0, I), (1.0, I + P), (1.0, I - P), (-1.0, -I), (-1.0, -I + P),
+                         (-1.0, -I - P)):
+                if abs(J - c) < (n + 1) / 2.0:
+                    v += s * float(lib().orc_bspline(n, float(J - c)))
+            B[j, i] = v
+    return B
+
+
+def indirect_transform(prob: Problem, c) -> np.ndarray:
+    """u at the grid nodes from the coefficients c (indirect B-spline transform, section 2.3):
+    u = (Bz (x) By (x) Bx) c with the sampled reflected basis of each axis. The mask is not
+    applied (the transform acts on the whole box)."""
+    c = _f64(c).reshape(prob.shape)
+    Bx = sampled_basis_1d(prob.n, prob.nx)
+    By = sampled_basis_1d(prob.n, prob.ny)
+    Bz = sampled_basis_1d(prob.n, prob.nz)
+    return np.einsum("ck,bj,ai,kji->cba", Bz, By, Bx, c, optimize=True)
+
+
+def direct_transform(prob: Problem, f) -> np.ndarray:
+    """Coefficients c whose indirect transform reproduces the samples f at the nodes (direct
+    B-spline transform by interpolation, section 2.3): one linear solve per axis with the
+    sampled reflected basis, c = (Bz^-1 (x) By^-1 (x) Bx^-1) f."""
+    f = _f64(f).reshape(prob.shape)
+    Bx = sampled_basis_1d(prob.n, prob.nx)
+    By = sampled_basis_1d(prob.n, prob.ny)
+    Bz = sampled_basis_1d(prob.n, prob.nz)
+    t = np.linalg.solve(Bx, f.reshape(-1, prob.nx).T).T.reshape(prob.shape)
+    t = np.moveaxis(np.linalg.solve(By, np.moveaxis(t, 1, 0).reshape(prob.ny, -1)).reshape(
+        prob.ny, prob.nz, prob.nx), 0, 1)
+    t = np.linalg.solve(Bz, t.reshape(prob.nz, -1)).reshape(prob.shape)
+    return t

@@ -327,3 +327,60 @@ def test_planted_ghost_rule_mistakes_are_caught(orc):
     finally:
         orc.set_plant(0)
     assert _bruteforce_gap(orc, p) < 1e-13
+
+
+# ---- B-spline transforms at the nodes (section 2.3, Fig. figBspnSignProc) -----------------------
+
+def test_indirect_transform_matches_independent_evaluator():
+    """The sampled-basis transform equals the oracle's point evaluator (psi_1d in C) at the
+    nodes, for every degree and anisotropic steps."""
+    rng = np.random.default_rng(31)
+    for n in range(1, 6):
+        p = oracle.Problem(9, 7, 8, n, 1 / 10, hy=1 / 8, hz=1 / 9)
+        c = rng.standard_normal(p.shape)
+        xs = (np.arange(p.nx) + 1) * p.hx
+        ys = (np.arange(p.ny) + 1) * p.hy
+        zs = (np.arange(p.nz) + 1) * p.hz
+        assert np.max(np.abs(oracle.eval_tensor(p, c, xs, ys, zs) - oracle.indirect_transform(p, c))) <= 1e-13
+
+
+def test_direct_transform_sine_closed_form():
+    """Sine modes are eigenvectors of the sampled odd-reflected basis: the direct transform of
+    prod_d sin(pi k_d x_d) is the same field divided by prod_d sum_j beta^n(j) cos(pi k_d j h_d)."""
+    for n in (1, 2, 3, 4, 5):
+        N = (11, 9, 10)
+        p = oracle.Problem(N[0], N[1], N[2], n, 1 / (N[0] + 1), hy=1 / (N[1] + 1), hz=1 / (N[2] + 1))
+        k = (3, 2, 5)
+        hs = (p.hx, p.hy, p.hz)
+        axes = [np.sin(np.pi * k[d] * (np.arange(N[d]) + 1) * hs[d]) for d in range(3)]
+        f = axes[2][:, None, None] * axes[1][None, :, None] * axes[0][None, None, :]
+        lam = 1.0
+        for d in range(3):
+            js = np.arange(-3, 4)
+            lam *= float(np.sum(oracle.bspline(n, js) * np.cos(np.pi * k[d] * js * hs[d])))
+        c = oracle.direct_transform(p, f)
+        assert np.max(np.abs(c - f / lam)) <= 1e-12 * np.max(np.abs(f / lam)), n
+
+
+def test_direct_transform_degree_one_is_identity_and_round_trip():
+    rng = np.random.default_rng(32)
+    p1 = oracle.Problem(6, 5, 7, 1, 1 / 7)
+    f = rng.standard_normal(p1.shape)
+    assert np.max(np.abs(oracle.direct_transform(p1, f) - f)) <= 1e-15
+    p3 = oracle.Problem(12, 10, 11, 3, 1 / 13)
+    f = rng.standard_normal(p3.shape)
+    assert np.max(np.abs(oracle.indirect_transform(p3, oracle.direct_transform(p3, f)) - f)) <= 1e-12
+
+
+def test_planted_missing_reflection_in_transform_is_caught():
+    """A sampled basis without the mirror images (no zero-Dirichlet reflection) differs at the
+    nodes next to the faces, and the closed form catches it (degree 5, whose samples reach two
+    nodes: the cubic's vanish one node beyond the face)."""
+    n, N = 5, 10
+    B = oracle.sampled_basis_1d(n, N)
+    Bbad = np.array([[float(oracle.bspline(n, (j + 1) - (i + 1))[0]) for i in range(N)] for j in range(N)])
+    k, h = 2, 1 / (N + 1)
+    s = np.sin(np.pi * k * (np.arange(N) + 1) * h)
+    lam = float(np.sum(oracle.bspline(n, np.arange(-3, 4)) * np.cos(np.pi * k * np.arange(-3, 4) * h)))
+    assert np.max(np.abs(B @ s - lam * s)) <= 1e-13
+    assert np.max(np.abs(Bbad @ s - lam * s)) > 1e-3
