@@ -421,6 +421,14 @@ def run_ours(args, rank, world, dist):
     ms_res64 = H.time_kernel(api.KERNEL_RES64, reps=3)
     ms_resdf = H.time_kernel(api.KERNEL_RES_DF, reps=5)
     ms_upd = H.time_kernel(api.KERNEL_CG_UPDATE, reps=10)
+    # B-spline transforms at the nodes of the same field (direct: interpolation by banded line
+    # solves; indirect: the separable sampled-B-spline convolution), FP64 vectors
+    cf = H.to_coeffs(u)
+    uf = H.to_samples(cf)
+    ms_direct, _ = _timed_ms(lambda: H.to_coeffs(u, cf))
+    ms_indirect, _ = _timed_ms(lambda: H.to_samples(cf, uf))
+    tr_err = (torch.max(torch.abs(uf - u)) / torch.max(torch.abs(u))).item()
+    del cf, uf
     # BF16-storage operator variant (BSK_BF16S): its speed, and what BF16 storage costs in
     # accuracy against the FP64 operator of the same (unrounded) field
     Hb = api.Handle(N, N, N, DEGREE, h, DT, precision="bf16s", stream=stream)
@@ -464,6 +472,10 @@ def run_ours(args, rank, world, dist):
             "cg_iteration_share_of_timed_region": iter_ms / elapsed_ms if world == 1 else None,
             "op_apply_gdofs": dofs / (ms_op * 1e-3) / 1e9,
             "op_apply_hbm_frac": bytes_op / (ms_op * 1e-3) / 1e9 / hbm,
+            "transforms": {"direct_ms": ms_direct, "indirect_ms": ms_indirect,
+                           "direct_gdofs": dofs / (ms_direct * 1e-3) / 1e9,
+                           "indirect_gdofs": dofs / (ms_indirect * 1e-3) / 1e9,
+                           "round_trip_max_rel_error": tr_err},
             "op_apply_bf16_storage": {"gdofs": dofs / (ms_bf16 * 1e-3) / 1e9, "ms": ms_bf16,
                                       "rel_l2_error_vs_fp64": bf16_err,
                                       "kernel": "general kernel, FP32 arithmetic, BF16 in/out"},

@@ -157,6 +157,22 @@ int heat_step(bsk_handle* h, void* u, const void* q, int nsteps, const bsk_cg_op
  * host after synchronising the stream. Used to check results without a host copy. */
 int bsk_norm2(bsk_handle* h, const void* x, double* out);
 
+/* B-spline transforms at the grid nodes (section 2.3, Fig. figBspnSignProc), on the handle's
+ * grid and degree, over the whole box (the mask is not applied):
+ *   BSK_TO_SAMPLES  out = u, the values sum_i c_i psi_i(x_j) of the coefficients in = c at the
+ *                   nodes x_j (indirect transform): a separable convolution with the sampled
+ *                   B-spline beta^n(j), odd-reflected at the faces like the operator;
+ *   BSK_TO_COEFFS   out = c, the coefficients whose indirect transform is in = f (direct
+ *                   transform by interpolation): per axis the band system of the sampled
+ *                   basis (positive definite, half-width ceil((n+1)/2) - 1) is solved along every
+ *                   grid line with its Cholesky factor (computed and kept by the first call).
+ * in, out: DEVICE vectors of the handle's element type (float for BSK_F32, double otherwise),
+ * not overlapping. Enqueued on the handle's stream; returns without synchronising.
+ * BSK_BF16S handles and unknown directions give BSK_EINVAL. */
+#define BSK_TO_SAMPLES 0
+#define BSK_TO_COEFFS 1
+int bsk_transform(bsk_handle* h, int direction, const void* in, void* out);
+
 /* r = b - A x with the handle's true-residual kernel, and ||r||^2, ||b||^2 (FP64, written on the
  * host after the stream is synchronised; either pointer may be NULL). b, x, r: DEVICE vectors of
  * the handle's element type; entries of b off the mask are ignored, x must be zero there.

@@ -55,6 +55,7 @@ SIGNATURES = {
                                  ctypes.POINTER(CgOpts), ctypes.POINTER(CgReport)]),
     "bsk_norm2": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p,
                                  ctypes.POINTER(ctypes.c_double)]),
+    "bsk_transform": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int, ctypes.c_void_p, ctypes.c_void_p]),
     "bsk_residual": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p,
                                      ctypes.c_int, ctypes.POINTER(ctypes.c_double),
                                      ctypes.POINTER(ctypes.c_double)]),

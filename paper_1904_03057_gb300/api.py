@@ -156,6 +156,18 @@ class Handle:
         _native.check(self._lib.bsk_norm2(self._ptr, self._vec(x, "x"), ctypes.byref(out)))
         return out.value
 
+    def to_samples(self, c: torch.Tensor, out: Optional[torch.Tensor] = None) -> torch.Tensor:
+        """Values at the grid nodes of the B-spline coefficients c (indirect transform)."""
+        out = self.empty() if out is None else out
+        _native.check(self._lib.bsk_transform(self._ptr, 0, self._vec(c, "c"), self._vec(out, "out")))
+        return out
+
+    def to_coeffs(self, f: torch.Tensor, out: Optional[torch.Tensor] = None) -> torch.Tensor:
+        """B-spline coefficients interpolating the node values f (direct transform)."""
+        out = self.empty() if out is None else out
+        _native.check(self._lib.bsk_transform(self._ptr, 1, self._vec(f, "f"), self._vec(out, "out")))
+        return out
+
     def residual(self, b: torch.Tensor, x: torch.Tensor, r: Optional[torch.Tensor] = None,
                  fp64: bool = False):
         """(r, ||r||^2, ||b||^2) with r = b - A x by the handle's true-residual kernel

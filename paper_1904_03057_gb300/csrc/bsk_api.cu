@@ -3,6 +3,7 @@
 // implicit Euler stepping. Every arithmetic step of the path runs in the kernels of
 // kernels_f32.cu / kernels_f64.cu; this file only validates, allocates and sequences.
 #include <algorithm>
+#include <vector>
 #include <chrono>
 #include <cmath>
 #include <cstdarg>
@@ -60,6 +61,25 @@ long long bspline_odd_scaled(int m, int j)
         binom = binom * (m + 1 - k) / (k + 1);
     }
     return s;
+}
+
+// beta^m(j) at an integer j, exactly: m! 2^m beta^m(j) = sum_k (-1)^k C(m+1, k) (2j + m + 1 - 2k)_+^m
+// (the truncated-power form with every term an integer, for either parity of m).
+double bspline_at(int m, int j)
+{
+    long long s = 0, binom = 1;
+    for (int k = 0; k <= m + 1; k++) {
+        const long long t = 2LL * j + m + 1 - 2LL * k;
+        if (t > 0) {
+            long long pw = 1;
+            for (int e = 0; e < m; e++) pw *= t;
+            s += (k & 1) ? -binom * pw : binom * pw;
+        }
+        binom = binom * (m + 1 - k) / (k + 1);
+    }
+    double den = 1.0;
+    for (int i = 2; i <= m; i++) den *= i;
+    return (double)s / (den * (double)(1LL << m));
 }
 
 double factorial(int m)
@@ -122,6 +142,7 @@ struct bsk_handle {
     long long launches;   // kernels launched since the counter was last read
     cudaEvent_t it_ev[2]; // bracket the inner iterations on `stream` (bsk_cg_report.iter_ms)
     double iter_ms;       // device time of the inner iterations since the counter was last read
+    void* tr_L[3];        // Cholesky factors of the sampled basis per axis (first direct transform)
     float* fcg_ws;        // FCG work vectors z, rn, zn (allocated by the first fcg_solve)
     double* fcg_partials;
     void* fcg_state;
@@ -708,6 +729,8 @@ extern "C" void bsk_destroy(bsk_handle* h)
     if (h->fcg_ws) cudaFree(h->fcg_ws);
     if (h->fcg_partials) cudaFree(h->fcg_partials);
     if (h->fcg_state) cudaFree(h->fcg_state);
+    for (int d = 0; d < 3; d++)
+        if (h->tr_L[d]) cudaFree(h->tr_L[d]);
     if (h->cap_stream) cudaStreamDestroy(h->cap_stream);
     for (int i = 0; i < 2; i++)
         if (h->it_ev[i]) cudaEventDestroy(h->it_ev[i]);
@@ -1064,6 +1087,115 @@ extern "C" int bsk_time_kernel(bsk_handle* h, int kernel, int reps, double* ms)
     if (e1) cudaEventDestroy(e1);
     if (err != cudaSuccess) return cuda_fail(err, "bsk_time_kernel");
     *ms = (double)total / reps;
+    return BSK_OK;
+}
+
+// ---- B-spline transforms at the nodes -------------------------------------------------------
+
+namespace {
+
+int transform_halfwidth(int n) { return (n + 2) / 2 - 1; }   // ceil((n + 1) / 2) - 1
+
+// Banded Cholesky factor of the sampled odd-reflected basis of one axis with N unknowns:
+// B[j][i] = sum over the images of unknown i (i + 1 + m P with sign +, -(i + 1) + m P with sign
+// -, P = 2 (N + 1), m = -1, 0, 1) of beta^n(j + 1 - image). Row j of the output holds
+// { 1 / L[j][j], L[j][j-1], ..., L[j][j-p] }. Returns false if B is not positive definite.
+bool sampled_basis_cholesky(int n, int N, std::vector<double>& out)
+{
+    const int p = transform_halfwidth(n), w = p + 1;
+    const long long P = 2LL * (N + 1);
+    auto b = [&](int j, int i) {
+        const long long J = j + 1, I = i + 1;
+        const long long img[6] = {I, I + P, I - P, -I, -I + P, -I - P};
+        double v = 0.0;
+        for (int q = 0; q < 6; q++) {
+            const long long d = J - img[q];
+            if (d >= -p && d <= p) v += (q < 3 ? 1.0 : -1.0) * bspline_at(n, (int)d);
+        }
+        return v;
+    };
+    std::vector<double> Lf((size_t)N * w, 0.0);   // Lf[j * w + (j - k)] = L[j][k]
+    auto Lat = [&](int j, int k) -> double& { return Lf[(size_t)j * w + (j - k)]; };
+    for (int j = 0; j < N; j++) {
+        for (int k = std::max(0, j - p); k <= j; k++) {
+            double sum = b(j, k);
+            for (int m = std::max(0, j - p); m < k; m++)
+                if (m >= k - p) sum -= Lat(j, m) * Lat(k, m);
+            if (k == j) {
+                if (!(sum > 0.0)) return false;
+                Lat(j, j) = std::sqrt(sum);
+            } else {
+                Lat(j, k) = sum / Lat(k, k);
+            }
+        }
+    }
+    out.assign((size_t)N * w, 0.0);
+    for (int j = 0; j < N; j++) {
+        out[(size_t)j * w] = 1.0 / Lat(j, j);
+        for (int k = 1; k <= p && j - k >= 0; k++) out[(size_t)j * w + k] = Lat(j, j - k);
+    }
+    return true;
+}
+
+}  // namespace
+
+extern "C" int bsk_transform(bsk_handle* h, int direction, const void* in, void* out)
+{
+    if (int rc = check_handle(h)) return rc;
+    if (!in || !out) return fail(BSK_EINVAL, "null vector");
+    if (direction != BSK_TO_SAMPLES && direction != BSK_TO_COEFFS)
+        return fail(BSK_EINVAL, "unknown transform direction %d", direction);
+    if (h->prec == BSK_BF16S) return fail(BSK_EINVAL, "the transforms take FP32 or FP64 vectors");
+    const size_t es = user_es(h);
+    if (overlaps(in, out, h->len * es)) return fail(BSK_EINVAL, "in and out overlap");
+    const int n = h->n, p = transform_halfwidth(n);
+    if (direction == BSK_TO_SAMPLES) {
+        // u = (Bz (x) By (x) Bx) c: the mass-only sweeps with the sampled B-spline as taps
+        bsk::OpLaunch L;
+        fill_launch(h, L, bsk::MODE_MASS);
+        L.mask = nullptr;   // the transform acts on the whole box
+        for (int d = 0; d < 3; d++)
+            for (int j = 0; j < bsk::kMaxTaps; j++) {
+                const int off = j - n;
+                L.M[d][j] = (off >= -p && off <= p) ? bspline_at(n, off) : 0.0;
+                L.Kdt[d][j] = 0.0;
+            }
+        L.in0 = in;
+        L.in1 = nullptr;
+        L.s = 0.0;
+        L.out0 = out;
+        L.fin = bsk::FIN_NONE;
+        BSK_LAUNCH(h, op_launch_es(es, L, h->stream));
+        return BSK_OK;
+    }
+    // c = (Bz^-1 (x) By^-1 (x) Bx^-1) f: copy, then banded solves along x, y and z
+    const int dims[3] = {h->nx, h->ny, h->nz};
+    if (p > 0 && !h->tr_L[0]) {
+        for (int d = 0; d < 3; d++) {
+            std::vector<double> f;
+            if (!sampled_basis_cholesky(n, dims[d], f)) return fail(BSK_EBREAKDOWN, "sampled basis not positive definite");
+            void* dev = nullptr;
+            const size_t bytes = f.size() * es;
+            BSK_CUDA(cudaMalloc(&dev, bytes));
+            h->tr_L[d] = dev;
+            if (es == sizeof(double)) {
+                BSK_CUDA(cudaMemcpy(dev, f.data(), bytes, cudaMemcpyHostToDevice));
+            } else {
+                std::vector<float> ff(f.begin(), f.end());
+                BSK_CUDA(cudaMemcpy(dev, ff.data(), bytes, cudaMemcpyHostToDevice));
+            }
+        }
+    }
+    BSK_CUDA(cudaMemcpyAsync(out, in, h->len * es, cudaMemcpyDeviceToDevice, h->stream));
+    if (p > 0)
+        for (int d = 0; d < 3; d++) {
+            if (es == sizeof(double))
+                BSK_LAUNCH(h, bsk::launch_band_solve<double>(static_cast<double*>(out), h->nx, h->ny, h->nz, d, p,
+                                                            static_cast<const double*>(h->tr_L[d]), h->stream));
+            else
+                BSK_LAUNCH(h, bsk::launch_band_solve<float>(static_cast<float*>(out), h->nx, h->ny, h->nz, d, p,
+                                                           static_cast<const float*>(h->tr_L[d]), h->stream));
+        }
     return BSK_OK;
 }
 

@@ -87,6 +87,11 @@ struct TmaLaunch {
     unsigned int* work;          // 2 counters, zero between launches (dynamic item queue)
     int fin;
 };
+// In-place banded triangular solves along one axis (0 = x, 1 = y, 2 = z) of an nx*ny*nz grid,
+// one thread per line: L holds the Cholesky factor of the axis's sampled basis (transform.cu).
+template <typename T>
+cudaError_t launch_band_solve(T* d, int nx, int ny, int nz, int axis, int p, const T* L, cudaStream_t s);
+
 // occ[z * tiles + tile] = 1 iff the 64 x 24 tile (x fastest) has an active node in plane z.
 cudaError_t launch_tile_occupancy(const uint8_t* mask, int nx, int ny, int nz, uint8_t* occ, cudaStream_t s);
 int tma_tiles(int nx, int ny);
