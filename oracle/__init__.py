@@ -80,6 +80,11 @@ def lib():
             L.orc_eval_tensor.argtypes = [P, ctypes.c_int, _D, ctypes.c_int, _D, _D,
                                           ctypes.c_int, _D, _D, ctypes.c_int, _D, _D, _D]
             L.orc_axis_rule.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.c_double, _D, _D]
+            L.orc_triple_kernels_1d.argtypes = [ctypes.c_int, _D, _D]
+            for name in ("orc_op_var", "orc_abs_op_var", "orc_bruteforce_apply_var"):
+                getattr(L, name).argtypes = [P, _D, _D, _D, _D]
+            L.orc_op_var_points.argtypes = [P, _D, _D, ctypes.c_void_p, ctypes.c_int,
+                                            ctypes.c_longlong, ctypes.POINTER(ctypes.c_longlong), _D]
             _lib = L
     return _lib
 
@@ -287,7 +292,8 @@ def abs_op(prob: Problem, x):
 
 
 def set_plant(mode: int) -> None:
-    """Test hook: 0 = correct odd reflection, 1 = zero ghosts, 2 = even reflection."""
+    """Test hook: 0 = correct odd reflection, 1 = zero ghosts, 2 = even reflection (solution),
+    3 = zero ghosts for the coefficient fields of the variable-coefficient operator."""
     lib().orc_set_plant(int(mode))
 
 
@@ -338,3 +344,65 @@ def direct_transform(prob: Problem, f) -> np.ndarray:
         prob.ny, prob.nz, prob.nx), 0, 1)
     t = np.linalg.solve(Bz, t.reshape(prob.nz, -1)).reshape(prob.shape)
     return t
+
+
+# --- variable coefficients (Eq. RitzGalerkin / Eq. tensForm with D, mu_a in B-splines) -------
+
+def coef_shape(prob: Problem):
+    """Shape of a nodal coefficient field: the N + 2 nodes 0..N+1 of each axis, faces included
+    (unknown i sits at node i + 1)."""
+    return (prob.nz + 2, prob.ny + 2, prob.nx + 2)
+
+
+def triple_kernels_1d(n: int):
+    """(f1, w1), each (2n+1, 2n+1) indexed [a + n, b + n]: f1 = int beta(x) beta(x-a) beta(x-b),
+    w1 = int beta'(x) beta'(x-a) beta(x-b), the per-axis factors of f^{klm} and w^{klm}
+    (Eq. tensForm, section 2.4)."""
+    L = 2 * n + 1
+    f1 = np.zeros(L * L)
+    w1 = np.zeros(L * L)
+    _check(lib().orc_triple_kernels_1d(int(n), _dp(f1), _dp(w1)))
+    return f1.reshape(L, L), w1.reshape(L, L)
+
+
+def _var(name, prob: Problem, d, m, x):
+    d = _f64(d).reshape(coef_shape(prob))
+    m = _f64(m).reshape(coef_shape(prob))
+    x = _f64(x).reshape(prob.shape)
+    y = np.zeros(prob.shape)
+    _check(getattr(lib(), name)(ctypes.byref(prob._c()), _dp(d), _dp(m), _dp(x), _dp(y)))
+    return y
+
+
+def op_var(prob: Problem, d, m, x):
+    """y = A(d, m) x: the variable-coefficient operator sum_k sum_m x_k (dt d_m w^{klm} +
+    m_m f^{klm}) of Eq. tensForm (no boundary term), written as the plain double sum over the
+    solution and coefficient B-splines. d, m: nodal fields of shape coef_shape(prob), extended
+    evenly across the faces; x odd-reflected and masked as for the constant operator."""
+    return _var("orc_op_var", prob, d, m, x)
+
+
+def abs_op_var(prob: Problem, d, m, x):
+    """(|A(d, m)| |x|): every factor of every term replaced by its absolute value (error scale)."""
+    return _var("orc_abs_op_var", prob, d, m, x)
+
+
+def bruteforce_apply_var(prob: Problem, d, m, x):
+    """A(d, m) x by Gauss quadrature over [0,1]^3 of dt D grad psi_i . grad u + mu_a psi_i u,
+    every function evaluated pointwise (odd-reflected solution basis, even-reflected
+    coefficient basis). Tiny grids only."""
+    return _var("orc_bruteforce_apply_var", prob, d, m, x)
+
+
+def op_var_points(prob: Problem, d, m, x, points):
+    """(A(d, m) x) at the given flat indices only; x float32 or float64."""
+    d = _f64(d).reshape(coef_shape(prob))
+    m = _f64(m).reshape(coef_shape(prob))
+    x = np.ascontiguousarray(x)
+    assert x.dtype in (np.float32, np.float64) and x.size == prob.nx * prob.ny * prob.nz
+    pts = np.ascontiguousarray(points, dtype=np.int64)
+    out = np.zeros(pts.size)
+    _check(lib().orc_op_var_points(ctypes.byref(prob._c()), _dp(d), _dp(m), x.ctypes.data,
+                                   int(x.dtype == np.float32), pts.size,
+                                   pts.ctypes.data_as(ctypes.POINTER(ctypes.c_longlong)), _dp(out)))
+    return out

@@ -14,6 +14,9 @@
  *     constant coefficients, D = dt and mu_a = 1 (one implicit Euler step of the heat equation).
  *   - Separable shift-invariant kernels and the filtering algorithm: section 2.4 and
  *     Fig. FiltAlg (four chains of three 1-D convolutions summed into p).
+ *   - Variable coefficients: Eq. RitzGalerkin and Eq. tensForm with D(x) and mu_a(x) expanded
+ *     in B-splines (section 2.3), the on-the-fly strategy of section 2.4 written as the plain
+ *     double sum over solution and coefficient B-splines with 1-D triple-product factors.
  *   - Conjugate gradient: section 2.5 (Fig. figGenTenSolv, stage 3).
  *   - Indirect B-spline transform (evaluation): section 2.3, Fig. figBspnSignProc.
  *   - L2 norm: Appendix I.
@@ -160,7 +163,8 @@ static int reflect(int a, int N, int* src)
 }
 
 /* Deliberate-mistake switch for the test-suite's planted-error checks: 0 = correct odd
- * reflection (default), 1 = zero ghosts, 2 = even reflection. Tests set it, check that a pin
+ * reflection (default), 1 = zero ghosts, 2 = even reflection, 3 = zero ghosts for the
+ * coefficient fields of the variable-coefficient operator. Tests set it, check that a pin
  * fails, and reset it. */
 static int g_plant = 0;
 void orc_set_plant(int mode) { g_plant = mode; }
@@ -745,4 +749,310 @@ int orc_axis_rule(int n, int N, double h, double* xs, double* ws)
 {
     if (n < 1 || n > 7 || N < 1 || !(h > 0)) return -1;
     return axis_rule(n, N, h, xs, ws);
+}
+
+/* ------------------------------------------------------------------------------------------ */
+/* Variable coefficients: Eq. RitzGalerkin / Eq. tensForm with D(x) and mu_a(x) in B-splines  */
+/* ------------------------------------------------------------------------------------------ */
+
+/* 1-D triple-product integrals on a unit grid, the per-axis factors of the tensors w^{klm} and
+ * f^{klm} of Eq. tensForm. With a = k - l and b = m - l (offsets of the solution B-spline k and
+ * of the coefficient B-spline m from the test B-spline l):
+ *   f1[a][b] = integral beta^n(x) beta^n(x - a) beta^n(x - b) dx,
+ *   w1[a][b] = integral beta^n'(x) beta^n'(x - a) beta^n(x - b) dx,
+ * for a, b in [-n, n], stored at (a + n) * (2n + 1) + (b + n). Every knot of beta^n and of its
+ * integer shifts is an integer or a half-integer, so between consecutive half-integers the
+ * integrand is one polynomial of degree at most 3n, which (3n + 2) / 2 Gauss points integrate
+ * exactly; the sum runs over the half-unit intervals of the support of beta^n(x). */
+int orc_triple_kernels_1d(int n, double* f1, double* w1)
+{
+    if (n < 1 || n > 7) return -1;
+    int L = 2 * n + 1, q = (3 * n + 2) / 2;
+    double t[16], w[16];
+    gauss_legendre(q, t, w);
+    double half = 0.5 * (double)(n + 1);
+    for (int a = -n; a <= n; a++)
+        for (int b = -n; b <= n; b++) {
+            double sf = 0.0, sw = 0.0;
+            for (int c = 0; c < 2 * (n + 1); c++) {
+                double lo = -half + 0.5 * c, hi = lo + 0.5;
+                for (int g = 0; g < q; g++) {
+                    double x = 0.5 * (lo + hi) + 0.5 * (hi - lo) * t[g];
+                    double wg = 0.5 * (hi - lo) * w[g];
+                    double bm = orc_bspline(n, x - b);
+                    sf += wg * orc_bspline(n, x) * orc_bspline(n, x - a) * bm;
+                    sw += wg * orc_bspline_deriv(n, x) * orc_bspline_deriv(n, x - a) * bm;
+                }
+            }
+            f1[(a + n) * L + (b + n)] = sf;
+            w1[(a + n) * L + (b + n)] = sw;
+        }
+    return 0;
+}
+
+/* Coefficient fields are given at the N + 2 nodes 0..N+1 of each axis (the box faces included;
+ * unknown i of the solution sits at node i + 1) and are extended evenly across the faces:
+ * node -e takes the value of node e and node N+1+e that of node N+1-e, so that D and mu_a are
+ * even about each face, the symmetry under which the integrals of odd-reflected basis
+ * functions over the box equal their integrals over the whole space. Returns the source node
+ * in [0, N+1]. g_plant == 3 (test hook) replaces the even extension by zero ghosts. */
+static int reflect_even(int e, int N, int* zero)
+{
+    *zero = 0;
+    if (e < 0) { e = -e; *zero = (g_plant == 3); }
+    if (e > N + 1) { e = 2 * (N + 1) - e; *zero = (g_plant == 3); }
+    return e;
+}
+
+/* Checks that single reflections reach every ghost: n <= N + 1 on each axis. */
+static int var_ok(const orc_problem* p)
+{
+    return problem_ok(p) && p->n <= p->nx + 1 && p->n <= p->ny + 1 && p->n <= p->nz + 1;
+}
+
+typedef struct {
+    int n, L;
+    double f1[15 * 15], w1[15 * 15];
+} var_tables;
+
+static void var_tables_init(var_tables* t, int n, int absmode)
+{
+    t->n = n;
+    t->L = 2 * n + 1;
+    orc_triple_kernels_1d(n, t->f1, t->w1);
+    if (absmode)
+        for (int i = 0; i < t->L * t->L; i++) {
+            t->f1[i] = fabs(t->f1[i]);
+            t->w1[i] = fabs(t->w1[i]);
+        }
+}
+
+/* y_l for one active node l = (ix, iy, iz) of the variable-coefficient operator:
+ *   y_l = sum_k sum_m x~_k ( dt d~_m w^{klm} + m~_m f^{klm} ),
+ *   f^{klm} = hx hy hz f1(ax,bx) f1(ay,by) f1(az,bz),
+ *   w^{klm} = hx hy hz [ w1(ax,bx) f1(ay,by) f1(az,bz) / hx^2 + f1(ax,bx) w1(ay,by) f1(az,bz) / hy^2
+ *                        + f1(ax,bx) f1(ay,by) w1(az,bz) / hz^2 ],
+ * with a = k - l, b = m - l per axis, x~ the masked odd-reflected extension of x (as for the
+ * constant-coefficient operator) and d~, m~ the even extensions of the coefficient fields. The
+ * sum is the plain double sum over the (k, m) pairs of the support (Eq. tensForm, the
+ * on-the-fly strategy of section 2.4). x is read as float (x_is_f32) or double; with absmode
+ * every factor is replaced by its absolute value. */
+static double var_point(const orc_problem* p, const var_tables* t, const double* d, const double* m,
+                        const void* x, int x_is_f32, int ix, int iy, int iz, int absmode)
+{
+    int n = p->n, L = t->L;
+    int N[3] = {p->nx, p->ny, p->nz}, I[3] = {ix, iy, iz};
+    int cpx = p->nx + 2, cpy = p->ny + 2;   /* coefficient field pitches */
+    /* per axis and offset o in [-n, n]: source of the solution (odd) and coefficient (even) */
+    int xs[3][15], xsg[3][15], cs[3][15], cz[3][15];
+    for (int ax = 0; ax < 3; ax++)
+        for (int o = -n; o <= n; o++) {
+            int src = 0;
+            xsg[ax][o + n] = reflect(I[ax] + o, N[ax], &src);
+            xs[ax][o + n] = src;
+            cs[ax][o + n] = reflect_even(I[ax] + o + 1, N[ax], &cz[ax][o + n]);
+        }
+    const float* xf = (const float*)x;
+    const double* xd = (const double*)x;
+    double vol = p->hx * p->hy * p->hz, dt = absmode ? fabs(p->dt) : p->dt;
+    double ihx2 = 1.0 / (p->hx * p->hx), ihy2 = 1.0 / (p->hy * p->hy), ihz2 = 1.0 / (p->hz * p->hz);
+    double s = 0.0;
+    for (int az = -n; az <= n; az++) {
+        int sgz = xsg[2][az + n];
+        if (!sgz) continue;
+        for (int ay = -n; ay <= n; ay++) {
+            int sgy = xsg[1][ay + n];
+            if (!sgy) continue;
+            for (int axx = -n; axx <= n; axx++) {
+                int sgx = xsg[0][axx + n];
+                if (!sgx) continue;
+                size_t src = ((size_t)xs[2][az + n] * p->ny + xs[1][ay + n]) * p->nx + xs[0][axx + n];
+                if (p->mask && !p->mask[src]) continue;
+                double xv = (x_is_f32 ? (double)xf[src] : xd[src]) * (sgz * sgy * sgx);
+                if (absmode) xv = fabs(xv);
+                if (xv == 0.0) continue;
+                for (int bz = -n; bz <= n; bz++) {
+                    double fz = t->f1[(az + n) * L + (bz + n)], wz = t->w1[(az + n) * L + (bz + n)];
+                    if (fz == 0.0 && wz == 0.0) continue;
+                    for (int by = -n; by <= n; by++) {
+                        double fy = t->f1[(ay + n) * L + (by + n)], wy = t->w1[(ay + n) * L + (by + n)];
+                        if (fy == 0.0 && wy == 0.0) continue;
+                        for (int bx = -n; bx <= n; bx++) {
+                            double fxx = t->f1[(axx + n) * L + (bx + n)];
+                            double wx = t->w1[(axx + n) * L + (bx + n)];
+                            if (fxx == 0.0 && wx == 0.0) continue;
+                            size_t cm = ((size_t)cs[2][bz + n] * cpy + cs[1][by + n]) * cpx + cs[0][bx + n];
+                            int zero = cz[2][bz + n] || cz[1][by + n] || cz[0][bx + n];
+                            double dv = zero ? 0.0 : d[cm], mv = zero ? 0.0 : m[cm];
+                            if (absmode) { dv = fabs(dv); mv = fabs(mv); }
+                            double wf = vol * fxx * fy * fz;
+                            double ww = vol * (wx * fy * fz * ihx2 + fxx * wy * fz * ihy2 + fxx * fy * wz * ihz2);
+                            s += xv * (dt * dv * ww + mv * wf);
+                        }
+                    }
+                }
+            }
+        }
+    }
+    return s;
+}
+
+static int op_var(const orc_problem* p, const double* d, const double* m, const double* x,
+                  double* y, int absmode)
+{
+    if (!var_ok(p)) return -1;
+    var_tables t;
+    var_tables_init(&t, p->n, absmode);
+    size_t ntot = (size_t)p->nx * p->ny * p->nz;
+#pragma omp parallel for schedule(dynamic, 64)
+    for (long long I = 0; I < (long long)ntot; I++) {
+        int ix = (int)(I % p->nx), iy = (int)((I / p->nx) % p->ny);
+        int iz = (int)(I / ((long long)p->nx * p->ny));
+        y[I] = (p->mask && !p->mask[I]) ? 0.0 : var_point(p, &t, d, m, x, 0, ix, iy, iz, absmode);
+    }
+    return 0;
+}
+
+/* y = mask o A(d, m) (mask o x); d and m are (nz+2)(ny+2)(nx+2) nodal fields, x fastest. */
+int orc_op_var(const orc_problem* p, const double* d, const double* m, const double* x, double* y)
+{
+    return op_var(p, d, m, x, y, 0);
+}
+
+/* (|A(d, m)| |x|): every triple product, coefficient and ghost-extended value replaced by its
+ * absolute value; the scale of the terms summed into each output (error measure). */
+int orc_abs_op_var(const orc_problem* p, const double* d, const double* m, const double* x, double* y)
+{
+    return op_var(p, d, m, x, y, 1);
+}
+
+/* The same definition at selected flat indices only; x read as float or double. */
+int orc_op_var_points(const orc_problem* p, const double* d, const double* m, const void* x,
+                      int x_is_f32, long long npts, const long long* pts, double* out)
+{
+    if (!var_ok(p)) return -1;
+    var_tables t;
+    var_tables_init(&t, p->n, 0);
+#pragma omp parallel for schedule(dynamic, 4)
+    for (long long k = 0; k < npts; k++) {
+        long long I = pts[k];
+        int ix = (int)(I % p->nx), iy = (int)((I / p->nx) % p->ny);
+        int iz = (int)(I / ((long long)p->nx * p->ny));
+        out[k] = (p->mask && !p->mask[I]) ? 0.0 : var_point(p, &t, d, m, x, x_is_f32, ix, iy, iz, 0);
+    }
+    return 0;
+}
+
+/* 1-D coefficient basis: the B-spline centred at node e (position e h) plus its distinct mirror
+ * images in both faces (even, 2(N+1)h-periodic extension), e = 0..N+1. */
+static double phi_1d(int n, int N, double h, int e, double x)
+{
+    double u = x / h, s = 0.0;
+    for (int k = -1; k <= 1; k++) {
+        double shift = 2.0 * k * (N + 1);
+        s += orc_bspline(n, u - e - shift);
+        if (e != 0 && e != N + 1) s += orc_bspline(n, u + e - shift);
+    }
+    return s;
+}
+
+/* Brute-force reference for the variable-coefficient operator on tiny grids:
+ *   y_i = integral over [0,1]^3 of dt D grad psi_i . grad u_h + mu_a psi_i u_h  (active i),
+ *   u_h = sum_j x_j psi_j over active j,  D = sum_e d_e phi_e,  mu_a = sum_e m_e phi_e,
+ * (Eq. RitzGalerkin without the boundary term) by Gauss quadrature on the tensor grid of
+ * half-cells with (3n + 2) / 2 points each, every function evaluated pointwise from its
+ * definition (psi_1d, phi_1d): no kernels, no ghost arrays. */
+int orc_bruteforce_apply_var(const orc_problem* p, const double* d, const double* m,
+                             const double* x, double* y)
+{
+    if (!var_ok(p)) return -1;
+    int n = p->n, N[3] = {p->nx, p->ny, p->nz}, q = (3 * n + 2) / 2;
+    double h[3] = {p->hx, p->hy, p->hz};
+    double t[16], w[16];
+    gauss_legendre(q, t, w);
+    double *X[3], *W[3], *PS[3], *DP[3], *PH[3];
+    int nq[3];
+    for (int a = 0; a < 3; a++) {
+        nq[a] = 2 * (N[a] + 1) * q;
+        X[a] = (double*)malloc(sizeof(double) * nq[a]);
+        W[a] = (double*)malloc(sizeof(double) * nq[a]);
+        PS[a] = (double*)malloc(sizeof(double) * (size_t)nq[a] * N[a]);
+        DP[a] = (double*)malloc(sizeof(double) * (size_t)nq[a] * N[a]);
+        PH[a] = (double*)malloc(sizeof(double) * (size_t)nq[a] * (N[a] + 2));
+        for (int c = 0; c < 2 * (N[a] + 1); c++) {
+            double lo = 0.5 * h[a] * c, hi = lo + 0.5 * h[a];
+            for (int g = 0; g < q; g++) {
+                X[a][c * q + g] = 0.5 * (lo + hi) + 0.5 * (hi - lo) * t[g];
+                W[a][c * q + g] = 0.5 * (hi - lo) * w[g];
+            }
+        }
+        for (int k = 0; k < nq[a]; k++) {
+            for (int i = 0; i < N[a]; i++) {
+                PS[a][(size_t)k * N[a] + i] = psi_1d(n, N[a], h[a], i + 1, X[a][k], 0);
+                DP[a][(size_t)k * N[a] + i] = psi_1d(n, N[a], h[a], i + 1, X[a][k], 1);
+            }
+            for (int e = 0; e <= N[a] + 1; e++)
+                PH[a][(size_t)k * (N[a] + 2) + e] = phi_1d(n, N[a], h[a], e, X[a][k]);
+        }
+    }
+    size_t ntot = (size_t)N[0] * N[1] * N[2];
+    size_t npt = (size_t)nq[0] * nq[1] * nq[2];
+    /* point values: fluxes dt D grad u (3) and mu u, times the quadrature weight */
+    double* F = (double*)malloc(sizeof(double) * npt * 4);
+#pragma omp parallel for schedule(dynamic, 16)
+    for (long long P = 0; P < (long long)npt; P++) {
+        int kx = (int)(P % nq[0]), ky = (int)((P / nq[0]) % nq[1]), kz = (int)(P / ((size_t)nq[0] * nq[1]));
+        double u = 0, ux = 0, uy = 0, uz = 0, Dv = 0, Mv = 0;
+        for (size_t J = 0; J < ntot; J++) {
+            if (p->mask && !p->mask[J]) continue;
+            int jx = (int)(J % N[0]), jy = (int)((J / N[0]) % N[1]), jz = (int)(J / ((size_t)N[0] * N[1]));
+            double bx = PS[0][(size_t)kx * N[0] + jx], by = PS[1][(size_t)ky * N[1] + jy];
+            double bz = PS[2][(size_t)kz * N[2] + jz];
+            double gx = DP[0][(size_t)kx * N[0] + jx], gy = DP[1][(size_t)ky * N[1] + jy];
+            double gz = DP[2][(size_t)kz * N[2] + jz];
+            u += x[J] * bx * by * bz;
+            ux += x[J] * gx * by * bz;
+            uy += x[J] * bx * gy * bz;
+            uz += x[J] * bx * by * gz;
+        }
+        for (int ez = 0; ez < N[2] + 2; ez++)
+            for (int ey = 0; ey < N[1] + 2; ey++)
+                for (int ex = 0; ex < N[0] + 2; ex++) {
+                    size_t e = ((size_t)ez * (N[1] + 2) + ey) * (N[0] + 2) + ex;
+                    double ph = PH[0][(size_t)kx * (N[0] + 2) + ex] * PH[1][(size_t)ky * (N[1] + 2) + ey] *
+                                PH[2][(size_t)kz * (N[2] + 2) + ez];
+                    Dv += d[e] * ph;
+                    Mv += m[e] * ph;
+                }
+        double wq = W[0][kx] * W[1][ky] * W[2][kz];
+        F[P * 4 + 0] = wq * p->dt * Dv * ux;
+        F[P * 4 + 1] = wq * p->dt * Dv * uy;
+        F[P * 4 + 2] = wq * p->dt * Dv * uz;
+        F[P * 4 + 3] = wq * Mv * u;
+    }
+#pragma omp parallel for schedule(dynamic, 4)
+    for (long long I = 0; I < (long long)ntot; I++) {
+        if (p->mask && !p->mask[I]) { y[I] = 0.0; continue; }
+        int ix = (int)(I % N[0]), iy = (int)((I / N[0]) % N[1]), iz = (int)(I / ((size_t)N[0] * N[1]));
+        double s = 0.0;
+        for (size_t P = 0; P < npt; P++) {
+            int kx = (int)(P % nq[0]), ky = (int)((P / nq[0]) % nq[1]), kz = (int)(P / ((size_t)nq[0] * nq[1]));
+            double bx = PS[0][(size_t)kx * N[0] + ix], by = PS[1][(size_t)ky * N[1] + iy];
+            double bz = PS[2][(size_t)kz * N[2] + iz];
+            if (bx == 0.0 || by == 0.0 || bz == 0.0) {
+                double gx = DP[0][(size_t)kx * N[0] + ix], gy = DP[1][(size_t)ky * N[1] + iy];
+                double gz = DP[2][(size_t)kz * N[2] + iz];
+                if ((bx == 0.0 && gx == 0.0) || (by == 0.0 && gy == 0.0) || (bz == 0.0 && gz == 0.0))
+                    continue;
+            }
+            double gx = DP[0][(size_t)kx * N[0] + ix], gy = DP[1][(size_t)ky * N[1] + iy];
+            double gz = DP[2][(size_t)kz * N[2] + iz];
+            s += F[P * 4 + 0] * gx * by * bz + F[P * 4 + 1] * bx * gy * bz +
+                 F[P * 4 + 2] * bx * by * gz + F[P * 4 + 3] * bx * by * bz;
+        }
+        y[I] = s;
+    }
+    free(F);
+    for (int a = 0; a < 3; a++) { free(X[a]); free(W[a]); free(PS[a]); free(DP[a]); free(PH[a]); }
+    return 0;
 }
