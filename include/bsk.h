@@ -183,6 +183,34 @@ int bsk_transform(bsk_handle* h, int direction, const void* in, void* out);
  * refinement of cg_solve / heat_step / fcg_solve uses. */
 int bsk_residual(bsk_handle* h, const void* b, const void* x, void* r, int fp64, double* rr, double* bb);
 
+/* Variable coefficients (Eq. RitzGalerkin and Eq. tensForm, section 2.3: the diffusion D(x) and
+ * the absorption mu_a(x) expanded in the same B-splines as the solution). After this call the
+ * handle's operator is
+ *   (A x)_l = sum_k sum_m x_k ( dt d_m w^{klm} + m_m f^{klm} )
+ *           = integral of dt D grad psi_l . grad u + mu_a psi_l u,   u = sum_k x_k psi_k,
+ * with D = sum_m d_m beta_m, mu_a = sum_m m_m beta_m: for the heat equation
+ * u_t = div(D grad u) - mu_a u + g one implicit Euler step takes m = 1 + dt mu_a. d = m = 1
+ * gives back the constant-coefficient operator M + dt K. The operator is computed on the fly
+ * (strategy (c) of section 2.4) by exact Gauss quadrature per knot interval with sum
+ * factorisation, in the handle's CG precision, and every solver and residual of the handle uses
+ * it (heat_step keeps the constant mass matrix for its right-hand side M (u + dt q)).
+ *   d, m: DEVICE arrays of (nz+2)*(ny+2)*(nx+2) doubles, x fastest: the coefficients at the
+ *         nodes 0..N+1 of each axis, box faces included (unknown i sits at node i + 1). Beyond
+ *         the faces they are extended evenly (node -e takes node e's value), so that D and mu_a
+ *         are even about each face. Either may be NULL, meaning 1 everywhere; both NULL returns
+ *         the handle to the constant-coefficient operator. The fields are copied (converted to
+ *         FP32 for FP32 passes); the caller keeps ownership of d and m.
+ * Synchronises the handle's stream. BSK_BF16S handles give BSK_EINVAL; BSK_ENOMEM if the copies
+ * cannot be allocated. */
+int bsk_set_coefficients(bsk_handle* h, const double* d, const double* m);
+
+/* Floating-point operations per grid node of one operator application (FMA = 2): the
+ * algorithmic count of the method as implemented (the seven band convolutions of Fig. FiltAlg
+ * for constant coefficients; the per-cell Gauss quadrature with sum factorisation, without
+ * block-halo recomputation, for variable coefficients) and the count the kernel executes on this
+ * grid, recomputed halo cells included. Either pointer may be NULL. */
+int bsk_op_flops(bsk_handle* h, double* algorithmic, double* executed);
+
 /* ---- batches of independent problems ------------------------------------------------------
  * Many unmasked box problems (any sizes, degrees 1..5, one shared dt) solved together: each CG
  * iteration of the whole batch is one persistent launch per degree present, whose blocks take

@@ -83,7 +83,7 @@ def lib():
             L.orc_triple_kernels_1d.argtypes = [ctypes.c_int, _D, _D]
             for name in ("orc_op_var", "orc_abs_op_var", "orc_bruteforce_apply_var"):
                 getattr(L, name).argtypes = [P, _D, _D, _D, _D]
-            L.orc_op_var_points.argtypes = [P, _D, _D, ctypes.c_void_p, ctypes.c_int,
+            L.orc_op_var_points.argtypes = [P, _D, _D, ctypes.c_void_p, ctypes.c_int, ctypes.c_int,
                                             ctypes.c_longlong, ctypes.POINTER(ctypes.c_longlong), _D]
             _lib = L
     return _lib
@@ -394,8 +394,9 @@ def bruteforce_apply_var(prob: Problem, d, m, x):
     return _var("orc_bruteforce_apply_var", prob, d, m, x)
 
 
-def op_var_points(prob: Problem, d, m, x, points):
-    """(A(d, m) x) at the given flat indices only; x float32 or float64."""
+def op_var_points(prob: Problem, d, m, x, points, absolute=False):
+    """(A(d, m) x) at the given flat indices only; x float32 or float64. absolute=True gives
+    the (|A(d, m)| |x|) scale at those points instead."""
     d = _f64(d).reshape(coef_shape(prob))
     m = _f64(m).reshape(coef_shape(prob))
     x = np.ascontiguousarray(x)
@@ -403,6 +404,6 @@ def op_var_points(prob: Problem, d, m, x, points):
     pts = np.ascontiguousarray(points, dtype=np.int64)
     out = np.zeros(pts.size)
     _check(lib().orc_op_var_points(ctypes.byref(prob._c()), _dp(d), _dp(m), x.ctypes.data,
-                                   int(x.dtype == np.float32), pts.size,
+                                   int(x.dtype == np.float32), int(bool(absolute)), pts.size,
                                    pts.ctypes.data_as(ctypes.POINTER(ctypes.c_longlong)), _dp(out)))
     return out

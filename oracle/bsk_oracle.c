@@ -926,19 +926,20 @@ int orc_abs_op_var(const orc_problem* p, const double* d, const double* m, const
     return op_var(p, d, m, x, y, 1);
 }
 
-/* The same definition at selected flat indices only; x read as float or double. */
+/* The same definition at selected flat indices only; x read as float or double; with absmode
+ * the |A(d, m)| |x| scale at those points. */
 int orc_op_var_points(const orc_problem* p, const double* d, const double* m, const void* x,
-                      int x_is_f32, long long npts, const long long* pts, double* out)
+                      int x_is_f32, int absmode, long long npts, const long long* pts, double* out)
 {
     if (!var_ok(p)) return -1;
     var_tables t;
-    var_tables_init(&t, p->n, 0);
+    var_tables_init(&t, p->n, absmode);
 #pragma omp parallel for schedule(dynamic, 4)
     for (long long k = 0; k < npts; k++) {
         long long I = pts[k];
         int ix = (int)(I % p->nx), iy = (int)((I / p->nx) % p->ny);
         int iz = (int)(I / ((long long)p->nx * p->ny));
-        out[k] = (p->mask && !p->mask[I]) ? 0.0 : var_point(p, &t, d, m, x, x_is_f32, ix, iy, iz, 0);
+        out[k] = (p->mask && !p->mask[I]) ? 0.0 : var_point(p, &t, d, m, x, x_is_f32, ix, iy, iz, absmode);
     }
     return 0;
 }

@@ -179,6 +179,33 @@ class Handle:
                                              ctypes.byref(bb)))
         return r, rr.value, bb.value
 
+    @property
+    def coef_shape(self):
+        """Shape of a nodal coefficient field: the N + 2 nodes 0..N+1 of each axis."""
+        return (self.shape[0] + 2, self.shape[1] + 2, self.shape[2] + 2)
+
+    def set_coefficients(self, d: Optional[torch.Tensor] = None, m: Optional[torch.Tensor] = None):
+        """Variable coefficients (bsk_set_coefficients): D = sum d beta and mu_a = sum m beta from
+        float64 CUDA fields of shape coef_shape (None = 1 everywhere; both None = back to the
+        constant-coefficient operator). The handle copies them."""
+        ptrs = []
+        for name, f in (("d", d), ("m", m)):
+            if f is None:
+                ptrs.append(None)
+                continue
+            if not (isinstance(f, torch.Tensor) and f.is_cuda and f.dtype == torch.float64
+                    and f.is_contiguous() and tuple(f.shape) == self.coef_shape):
+                raise ValueError(f"{name} must be a contiguous CUDA float64 tensor of shape {self.coef_shape}")
+            ptrs.append(f.data_ptr())
+        _native.check(self._lib.bsk_set_coefficients(self._ptr, ptrs[0], ptrs[1]))
+
+    def op_flops(self):
+        """(algorithmic, executed) floating-point operations per node of one operator
+        application (bsk_op_flops)."""
+        a, e = ctypes.c_double(0.0), ctypes.c_double(0.0)
+        _native.check(self._lib.bsk_op_flops(self._ptr, ctypes.byref(a), ctypes.byref(e)))
+        return a.value, e.value
+
 
 class BatchHandle:
     """Many independent unmasked box problems solved together (bsk_batch_*). problems: a list of

@@ -143,6 +143,11 @@ struct bsk_handle {
     cudaEvent_t it_ev[2]; // bracket the inner iterations on `stream` (bsk_cg_report.iter_ms)
     double iter_ms;       // device time of the inner iterations since the counter was last read
     void* tr_L[3];        // Cholesky factors of the sampled basis per axis (first direct transform)
+    // variable coefficients (bsk_set_coefficients): D and mu_a at the (nz+2)(ny+2)(nx+2) nodes as
+    // float [0] (FP32 passes) and double [1] (FP64 passes); null = constant coefficients
+    void* cd[2];
+    void* cm[2];
+    bool use_tma0, tma640, res_df0;   // TMA eligibility of the constant-coefficient operator
     float* fcg_ws;        // FCG work vectors z, rn, zn (allocated by the first fcg_solve)
     double* fcg_partials;
     void* fcg_state;
@@ -205,6 +210,12 @@ void fill_launch(const bsk_handle* h, bsk::OpLaunch& L, int mode)
             L.M[d][j] = h->M[d][j];
             L.Kdt[d][j] = h->dt * h->K[d][j];
         }
+    for (int i = 0; i < 2; i++) {
+        L.vd[i] = h->cd[i];
+        L.vm[i] = h->cm[i];
+    }
+    for (int d = 0; d < 3; d++) L.h[d] = h->h[d];
+    L.dt = h->dt;
 }
 
 template <typename T>
@@ -618,6 +629,8 @@ extern "C" int bsk_create(const bsk_problem* prob, int precision, void* stream, 
 
     e = bsk::prepare_op<float>(n);
     if (e == cudaSuccess) e = bsk::prepare_op<double>(n);
+    if (e == cudaSuccess) e = bsk::prepare_var<float>(n);
+    if (e == cudaSuccess) e = bsk::prepare_var<double>(n);
     if (e != cudaSuccess) return cleanup(cuda_fail(e, "kernel set-up"));
     {
         // the TMA kernels need grids whose rows are whole 16-byte units
@@ -639,6 +652,9 @@ extern "C" int bsk_create(const bsk_problem* prob, int precision, void* stream, 
             e = bsk::prepare_tma<bsk::dfl>(n);
             if (e != cudaSuccess) return cleanup(cuda_fail(e, "TMA kernel set-up"));
         }
+        h->use_tma0 = h->use_tma;
+        h->tma640 = h->tma64;
+        h->res_df0 = h->res_df;
     }
     e = cudaStreamCreateWithFlags(&h->cap_stream, cudaStreamNonBlocking);
     if (e != cudaSuccess) return cleanup(cuda_fail(e, "cudaStreamCreate"));
@@ -694,6 +710,8 @@ extern "C" int bsk_create(const bsk_problem* prob, int precision, void* stream, 
     BSK_ALLOC(h->sc64, sizeof(Scalars));
     BSK_ALLOC(h->sc_aux, sizeof(Scalars));
     size_t nb = 2 * std::max(bsk::op_grid_blocks(h->nx, h->ny, h->nz, n), (size_t)bsk::vec_grid(len));
+    nb = std::max(nb, 2 * bsk::var_grid_blocks<float>(h->nx, h->ny, h->nz, n));
+    nb = std::max(nb, 2 * bsk::var_grid_blocks<double>(h->nx, h->ny, h->nz, n));
     for (int mode = 0; mode < 3; mode++) {
         nb = std::max(nb, 3 * (size_t)bsk::tma_grid<float>(n, mode));
         nb = std::max(nb, 3 * (size_t)bsk::tma_grid<double>(n, mode));
@@ -722,7 +740,7 @@ extern "C" void bsk_destroy(bsk_handle* h)
     cudaStreamSynchronize(h->stream);
     if (h->graph) cudaGraphExecDestroy(h->graph);
     void* ptrs[] = {h->mask, h->occ, h->x, h->r, h->p0, h->p1, h->q, h->bvec, h->r2, h->q2, h->r64, h->b64,
-                    h->sc, h->sc64, h->sc_aux, h->partials, h->work};
+                    h->sc, h->sc64, h->sc_aux, h->partials, h->work, h->cd[0], h->cd[1], h->cm[0], h->cm[1]};
     for (void* p : ptrs)
         if (p) cudaFree(p);
     if (h->h_sc) cudaFreeHost(h->h_sc);
@@ -747,6 +765,80 @@ extern "C" int bsk_set_dt(bsk_handle* h, double dt)
         h->graph = nullptr;
     }
     h->dt = dt;
+    return BSK_OK;
+}
+
+extern "C" int bsk_set_coefficients(bsk_handle* h, const double* d, const double* m)
+{
+    if (int rc = check_handle(h)) return rc;
+    if (h->prec == BSK_BF16S) return fail(BSK_EINVAL, "the BF16-storage variant has constant coefficients only");
+    // the captured CG graph holds the kernels of the previous operator
+    BSK_CUDA(cudaStreamSynchronize(h->stream));
+    if (h->graph) {
+        cudaGraphExecDestroy(h->graph);
+        h->graph = nullptr;
+    }
+    if (!d && !m) {
+        for (int i = 0; i < 2; i++) {
+            if (h->cd[i]) cudaFree(h->cd[i]);
+            if (h->cm[i]) cudaFree(h->cm[i]);
+            h->cd[i] = h->cm[i] = nullptr;
+        }
+        h->use_tma = h->use_tma0;
+        h->tma64 = h->tma640;
+        h->res_df = h->res_df0;
+        return BSK_OK;
+    }
+    const size_t clen = (size_t)(h->nx + 2) * (h->ny + 2) * (h->nz + 2);
+    for (int i = 0; i < 2; i++) {
+        // FP32 fields for the FP32 passes (BSK_F32, inner solves of BSK_F32_IR), FP64 fields
+        // for the FP64 passes (BSK_F64, true residuals of BSK_F32_IR)
+        const bool need = i == 0 ? h->prec != BSK_F64 : h->prec != BSK_F32;
+        if (!need) continue;
+        const size_t bytes = clen * (i == 0 ? sizeof(float) : sizeof(double));
+        for (void** f : {&h->cd[i], &h->cm[i]})
+            if (!*f) {
+                cudaError_t e = cudaMalloc(f, bytes);
+                if (e != cudaSuccess) {
+                    cudaGetLastError();
+                    return fail(BSK_ENOMEM, "coefficient fields: cudaMalloc(%zu) failed", bytes);
+                }
+            }
+        if (i == 0) {
+            BSK_LAUNCH(h, bsk::launch_coef_fill<float>(d, static_cast<float*>(h->cd[0]), clen, h->stream));
+            BSK_LAUNCH(h, bsk::launch_coef_fill<float>(m, static_cast<float*>(h->cm[0]), clen, h->stream));
+        } else {
+            BSK_LAUNCH(h, bsk::launch_coef_fill<double>(d, static_cast<double*>(h->cd[1]), clen, h->stream));
+            BSK_LAUNCH(h, bsk::launch_coef_fill<double>(m, static_cast<double*>(h->cm[1]), clen, h->stream));
+        }
+    }
+    // every pass takes the general path, where launch_op dispatches to the variable-coefficient
+    // kernel (the right-hand-side mass of heat_step stays the constant mass matrix)
+    h->use_tma = h->tma64 = h->res_df = false;
+    BSK_CUDA(cudaStreamSynchronize(h->stream));
+    return BSK_OK;
+}
+
+extern "C" int bsk_op_flops(bsk_handle* h, double* algorithmic, double* executed)
+{
+    if (int rc = check_handle(h)) return rc;
+    const int n = h->n;
+    double alg, exe;
+    if (h->cd[0] || h->cd[1]) {
+        // per node of an unbounded tile: z-pass 4(n+1) FMA per quad plane, y-pass 5(n+1) FMA per
+        // (qz, qy) node, x-pass 10(n+1) FMA + 8 products per quad point, transposed y- and
+        // z-passes 3 Q (n+1) + 2 (n+1) FMA per quad plane
+        const double q = (3 * n + 2) / 2, nb = n + 1;
+        alg = 2.0 * q * 4 * nb + 2.0 * q * q * 5 * nb + q * q * q * (2.0 * 10 * nb + 8) +
+              2.0 * q * (3.0 * q * nb + 2 * nb);
+        exe = cg_es(h) == sizeof(double) ? bsk::var_flops_per_node<double>(n, h->nx, h->ny, h->nz)
+                                         : bsk::var_flops_per_node<float>(n, h->nx, h->ny, h->nz);
+    } else {
+        // seven (2n+1)-tap band convolutions per node (the three sweeps of Fig. FiltAlg)
+        alg = exe = 14.0 * (2 * n + 1);
+    }
+    if (algorithmic) *algorithmic = alg;
+    if (executed) *executed = exe;
     return BSK_OK;
 }
 

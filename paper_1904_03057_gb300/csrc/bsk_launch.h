@@ -37,6 +37,12 @@ struct OpLaunch {
     int fin;
     int p_parity;
     int bf16io;                  // FP32 kernels, MODE_OP / MODE_MASS: in0, in1, out0 hold bfloat16
+    // Variable coefficients (op_var.cuh): nodal fields D and mu_a at the (nz+2)(ny+2)(nx+2) nodes,
+    // as float [0] and double [1]; null = the constant-coefficient operator. MODE_MASS ignores them.
+    const void* vd[2];
+    const void* vm[2];
+    double h[3];                 // grid steps (variable-coefficient tables)
+    double dt;                   // weight of the diffusion term (variable coefficients)
 };
 
 // Grid of the operator kernel for a problem; partial-sum buffers hold 2 doubles per block.
@@ -51,6 +57,21 @@ cudaError_t prepare_op(int degree);
 
 template <typename T>
 cudaError_t launch_op(const OpLaunch& L, cudaStream_t s);
+
+// Variable-coefficient operator (op_var.cuh, var_impl.cuh): MODE_OP, MODE_RES, MODE_CGP with the
+// fields L.vd / L.vm of the element type.
+template <typename T>
+cudaError_t launch_var(const OpLaunch& L, cudaStream_t s);
+template <typename T>
+cudaError_t prepare_var(int degree);
+template <typename T>
+size_t var_grid_blocks(int nx, int ny, int nz, int degree);
+// Floating-point operations the variable-coefficient kernel executes per node (halo included).
+template <typename T>
+double var_flops_per_node(int degree, int nx, int ny, int nz);
+// dst = src (converted), or 1 everywhere when src is null.
+template <typename T>
+cudaError_t launch_coef_fill(const double* src, T* dst, size_t len, cudaStream_t s);
 
 template <typename T>
 cudaError_t launch_cg_update(T* r, const T* q, size_t len, Scalars* sc, double* partials,

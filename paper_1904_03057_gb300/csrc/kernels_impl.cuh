@@ -81,6 +81,7 @@ static cudaError_t launch_mode(const OpLaunch& L, cudaStream_t s)
 template <>
 cudaError_t launch_op<BSK_T>(const OpLaunch& L, cudaStream_t s)
 {
+    if (L.vd[sizeof(BSK_T) == 8] && L.mode != MODE_MASS) return launch_var<BSK_T>(L, s);
     switch (L.degree) {
     case 1: return launch_mode<BSK_T, 1>(L, s);
     case 2: return launch_mode<BSK_T, 2>(L, s);

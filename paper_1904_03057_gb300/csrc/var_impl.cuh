@@ -1,0 +1,250 @@
+// var_impl.cuh -- host side of the variable-coefficient operator kernel (op_var.cuh) for one
+// element type: Gauss-point tables, grid, launch. Included once by var_f32.cu (T = float) and
+// once by var_f64.cu (T = double).
+#pragma once
+
+#include <cmath>
+
+#include "bsk_launch.h"
+#include "op_var.cuh"
+
+namespace bsk {
+namespace {
+
+// Centred B-spline beta^n(x) from its truncated-power form
+// beta^n(x) = (1/n!) sum_k (-1)^k C(n+1, k) (x + (n+1)/2 - k)_+^n (Table tblBsplines).
+double bspline_real(int n, double x)
+{
+    double s = 0.0, binom = 1.0, fact = 1.0;
+    for (int i = 2; i <= n; i++) fact *= i;
+    for (int k = 0; k <= n + 1; k++) {
+        const double t = x + 0.5 * (n + 1) - k;
+        if (t > 0.0) s += ((k & 1) ? -binom : binom) * std::pow(t, n);
+        binom = binom * (n + 1 - k) / (k + 1);
+    }
+    return s / fact;
+}
+
+// beta^n'(x) = beta^{n-1}(x + 1/2) - beta^{n-1}(x - 1/2) (Table tblBsplines, derivative row).
+double bspline_real_deriv(int n, double x)
+{
+    return bspline_real(n - 1, x + 0.5) - bspline_real(n - 1, x - 0.5);
+}
+
+// Gauss-Legendre rule of q points on [0, 1]: Newton iteration on the three-term recurrence of
+// the Legendre polynomials, weights 2 / ((1 - x^2) P_q'(x)^2), mapped from [-1, 1].
+void gauss_unit(int q, double* xi, double* w)
+{
+    const double pi = 3.14159265358979323846;
+    for (int i = 0; i < q; i++) {
+        double x = std::cos(pi * (i + 0.75) / (q + 0.5)), dp = 1.0;
+        for (int it = 0; it < 100; it++) {
+            double p0 = 1.0, p1 = x;
+            for (int k = 2; k <= q; k++) {
+                const double p2 = ((2.0 * k - 1.0) * x * p1 - (k - 1.0) * p0) / k;
+                p0 = p1;
+                p1 = p2;
+            }
+            dp = q * (x * p1 - p0) / (x * x - 1.0);
+            const double dx = p1 / dp;
+            x -= dx;
+            if (std::fabs(dx) < 1e-16) break;
+        }
+        double p0 = 1.0, p1 = x;
+        for (int k = 2; k <= q; k++) {
+            const double p2 = ((2.0 * k - 1.0) * x * p1 - (k - 1.0) * p0) / k;
+            p0 = p1;
+            p1 = p2;
+        }
+        dp = q * (x * p1 - p0) / (x * x - 1.0);
+        xi[i] = 0.5 * (1.0 - x);
+        w[i] = 1.0 / ((1.0 - x * x) * dp * dp);
+    }
+}
+
+// Tables of one cell: local coordinate xi in [0, 1] of a knot interval; the cell's n + 1
+// B-splines are centred at offsets lo + t (lo = -floor(n/2)) from the interval's reference
+// node, and the interval starts at offset 0 (odd n, integer knots) or -1/2 (even n).
+template <typename T>
+VarTabs<T> make_tabs(int n, const double h[3])
+{
+    VarTabs<T> tb{};
+    double xi[kVarMaxQ], w[kVarMaxQ];
+    const int q = (3 * n + 2) / 2, lo = -(n / 2);
+    const double o = (n & 1) ? 0.0 : -0.5;
+    gauss_unit(q, xi, w);
+    for (int g = 0; g < q; g++) {
+        tb.w[g] = (T)w[g];
+        for (int t = 0; t <= n; t++) {
+            const double u = o + xi[g] - lo - t;
+            tb.B[g][t] = (T)bspline_real(n, u);
+            const double du = bspline_real_deriv(n, u);
+            for (int ax = 0; ax < 3; ax++) tb.D[ax][g][t] = (T)(du / h[ax]);
+        }
+    }
+    return tb;
+}
+
+template <typename T, int N, int MODE>
+cudaError_t set_var_attr()
+{
+    return cudaFuncSetAttribute(k_op_var<T, N, MODE>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                (int)VarCfg<T, N>::smem);
+}
+
+template <typename T, int N>
+cudaError_t prepare_var_degree()
+{
+    cudaError_t e = set_var_attr<T, N, MODE_OP>();
+    if (e == cudaSuccess) e = set_var_attr<T, N, MODE_RES>();
+    if (e == cudaSuccess) e = set_var_attr<T, N, MODE_CGP>();
+    return e;
+}
+
+template <typename T, int N>
+dim3 var_grid_n(int nx, int ny, int nz, int* tz)
+{
+    constexpr int TT = VarCfg<T, N>::TT;
+    const int bx = (nx + TT - 1) / TT, by = (ny + TT - 1) / TT;
+    const long long bxy = (long long)bx * by;
+    // about four blocks per SM, but at least 2n output planes per block so that the n extra
+    // z-cells each block recomputes stay a bounded overhead
+    const long long nzc = (608 + bxy - 1) / bxy;
+    int t = (int)((nz + nzc - 1) / nzc);
+    if (t < 2 * N) t = 2 * N;
+    if (t > nz) t = nz;
+    *tz = t;
+    return dim3(bx, by, (nz + t - 1) / t);
+}
+
+template <typename T>
+dim3 var_grid_t(int degree, int nx, int ny, int nz, int* tz)
+{
+    switch (degree) {
+    case 1: return var_grid_n<T, 1>(nx, ny, nz, tz);
+    case 2: return var_grid_n<T, 2>(nx, ny, nz, tz);
+    case 3: return var_grid_n<T, 3>(nx, ny, nz, tz);
+    case 4: return var_grid_n<T, 4>(nx, ny, nz, tz);
+    default: return var_grid_n<T, 5>(nx, ny, nz, tz);
+    }
+}
+
+template <typename T, int N, int MODE>
+cudaError_t launch_var_mode(const OpLaunch& L, cudaStream_t s)
+{
+    using Cfg = VarCfg<T, N>;
+    VarArgs<T> a;
+    int tz = 0;
+    const dim3 grid = var_grid_n<T, N>(L.nx, L.ny, L.nz, &tz);
+    a.g.nx = L.nx;
+    a.g.ny = L.ny;
+    a.g.nz = L.nz;
+    a.g.tz = tz;
+    a.g.mask = L.mask;
+    a.t = make_tabs<T>(N, L.h);
+    a.vol = (T)(L.h[0] * L.h[1] * L.h[2]);
+    a.dt = (T)L.dt;
+    a.d = static_cast<const T*>(L.vd[sizeof(T) == 8]);
+    a.m = static_cast<const T*>(L.vm[sizeof(T) == 8]);
+    a.in0 = static_cast<const T*>(L.in0);
+    a.in1 = static_cast<const T*>(L.in1);
+    a.out0 = static_cast<T*>(L.out0);
+    a.out1 = static_cast<T*>(L.out1);
+    a.xvec = static_cast<T*>(L.xvec);
+    a.b = static_cast<const T*>(L.b);
+    a.sc = L.sc;
+    a.partials = L.partials;
+    a.fin = L.fin;
+    a.p_parity = L.p_parity;
+    k_op_var<T, N, MODE><<<grid, Cfg::NT, Cfg::smem, s>>>(a);
+    return cudaGetLastError();
+}
+
+template <typename T, int N>
+cudaError_t launch_var_n(const OpLaunch& L, cudaStream_t s)
+{
+    switch (L.mode) {
+    case MODE_OP: return launch_var_mode<T, N, MODE_OP>(L, s);
+    case MODE_RES: return launch_var_mode<T, N, MODE_RES>(L, s);
+    case MODE_CGP: return launch_var_mode<T, N, MODE_CGP>(L, s);
+    default: return cudaErrorInvalidValue;
+    }
+}
+
+__global__ void k_coef_fill(const double* __restrict__ src, BSK_T* __restrict__ dst, size_t len)
+{
+    for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < len; i += (size_t)gridDim.x * blockDim.x)
+        dst[i] = src ? (BSK_T)src[i] : BSK_T(1);
+}
+
+}  // namespace
+
+template <>
+cudaError_t launch_coef_fill<BSK_T>(const double* src, BSK_T* dst, size_t len, cudaStream_t s)
+{
+    k_coef_fill<<<vec_grid(len), 256, 0, s>>>(src, dst, len);
+    return cudaGetLastError();
+}
+
+template <>
+cudaError_t launch_var<BSK_T>(const OpLaunch& L, cudaStream_t s)
+{
+    switch (L.degree) {
+    case 1: return launch_var_n<BSK_T, 1>(L, s);
+    case 2: return launch_var_n<BSK_T, 2>(L, s);
+    case 3: return launch_var_n<BSK_T, 3>(L, s);
+    case 4: return launch_var_n<BSK_T, 4>(L, s);
+    case 5: return launch_var_n<BSK_T, 5>(L, s);
+    default: return cudaErrorInvalidValue;
+    }
+}
+
+template <>
+cudaError_t prepare_var<BSK_T>(int degree)
+{
+    switch (degree) {
+    case 1: return prepare_var_degree<BSK_T, 1>();
+    case 2: return prepare_var_degree<BSK_T, 2>();
+    case 3: return prepare_var_degree<BSK_T, 3>();
+    case 4: return prepare_var_degree<BSK_T, 4>();
+    case 5: return prepare_var_degree<BSK_T, 5>();
+    default: return cudaErrorInvalidValue;
+    }
+}
+
+template <>
+size_t var_grid_blocks<BSK_T>(int nx, int ny, int nz, int degree)
+{
+    int tz = 0;
+    const dim3 g = var_grid_t<BSK_T>(degree, nx, ny, nz, &tz);
+    return (size_t)g.x * g.y * g.z;
+}
+
+template <>
+double var_flops_per_node<BSK_T>(int degree, int nx, int ny, int nz)
+{
+    // floating-point operations the kernel executes per output node (FMA = 2), counting the
+    // recomputed halo cells of each block: z-pass 4(n+1) FMA per halo node and quad plane;
+    // BC 5(n+1) FMA per y-pass node, 10(n+1) FMA + 8 products per x quad point;
+    // DE 3 Q (n+1) FMA per output column and quad plane plus 2(n+1) per z-transpose.
+    const int n = degree, q = (3 * n + 2) / 2, nb = n + 1;
+    int tile = 0;
+    switch (degree) {
+    case 1: tile = VarCfg<BSK_T, 1>::TT; break;
+    case 2: tile = VarCfg<BSK_T, 2>::TT; break;
+    case 3: tile = VarCfg<BSK_T, 3>::TT; break;
+    case 4: tile = VarCfg<BSK_T, 4>::TT; break;
+    default: tile = VarCfg<BSK_T, 5>::TT; break;
+    }
+    const double H = tile + 2 * n, C = tile + n, QC = q * C;
+    const double per_cell = 2.0 * (q * H * H * 4 * nb)                        // A
+                            + 2.0 * (q * QC * H * 5 * nb)                      // BC y-pass
+                            + q * QC * C * q * (2.0 * 10 * nb + 8)             // BC x-pass
+                            + 2.0 * tile * tile * q * (3.0 * q * nb + 2 * nb); // DE
+    int tz = 0;
+    const dim3 g = var_grid_t<BSK_T>(degree, nx, ny, nz, &tz);
+    const double cells = (double)g.x * g.y * ((double)nz + (double)g.z * n);
+    return per_cell * cells / ((double)nx * ny * nz);
+}
+
+}  // namespace bsk

@@ -119,6 +119,28 @@ def random_field(shape, seed: int, device="cpu", dtype=torch.float64, mask=None)
     return x
 
 
+def inclusion_coefficients(nx, ny, nz, seed: int, count: int = 8, base: float = 1.0,
+                           lo: float = 0.2, hi: float = 5.0, h=None, device="cpu",
+                           dtype=torch.float64):
+    """Nodal coefficient field on the N + 2 nodes 0..N+1 of each axis (faces included, node e at
+    position e h), shape (nz+2, ny+2, nx+2): the value base, overwritten inside `count` random
+    balls (radius ~ U[0.1, 0.25], centre ~ U[0, 1]^3) by a value ~ log-uniform on [lo, hi] --
+    a piecewise-constant material map such as tissue conductivities, with contrast up to hi/lo."""
+    hs = _steps(nx, ny, nz, h)
+    rng = np.random.default_rng(seed)
+    axes = [torch.arange(0, N + 2, device=device, dtype=torch.float64) * hh
+            for N, hh in zip((nx, ny, nz), hs)]
+    out = torch.full((nz + 2, ny + 2, nx + 2), float(base), dtype=torch.float64, device=device)
+    for _ in range(count):
+        c = rng.uniform(0.0, 1.0, size=3)
+        r = rng.uniform(0.1, 0.25)
+        v = float(np.exp(rng.uniform(np.log(lo), np.log(hi))))
+        d2 = ((axes[2] - c[2]) ** 2)[:, None, None] + ((axes[1] - c[1]) ** 2)[None, :, None] + \
+             ((axes[0] - c[0]) ** 2)[None, None, :]
+        out[d2 <= r * r] = v
+    return out.to(dtype)
+
+
 @dataclass
 class BatchProblem:
     nx: int
