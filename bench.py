@@ -328,6 +328,89 @@ def fcg_race():
     return out
 
 
+# Per-SM FP32 lanes and SM count of a GB300 (152 SMs x 128 FP32 lanes, one FMA = 2 flops per
+# lane per clock): the ALU roofline of the variable-coefficient kernel at the sampled maximum SM
+# clock.
+FP32_LANES = 152 * 128
+
+
+def variable_coefficients():
+    """The variable-coefficient operator A(d, m) (D and mu_a as B-spline fields) on the grids
+    the paper times its on-the-fly operator on (240 x 240 x 960, degrees 1-3, FP32 and FP64;
+    522^3 cubic FP32), with inclusion fields D (contrast up to 25) and mu_a; one application per
+    timing, inputs larger than L2. Also one implicit Euler step (m = 1 + dt mu_a) solved to a
+    1e-8 true residual by FP32 CG inside FP64 refinement on a 256^3 sphere."""
+    import torch
+
+    from paper_1904_03057_gb300 import api, inputs
+    out = {"operator": [], "note": "flop counts per node from bsk_op_flops: algorithmic = per-cell "
+                                   "Gauss quadrature with sum factorisation, executed = with the "
+                                   "halo cells each block recomputes"}
+    sampler = ClockSampler(int(os.environ.get("LOCAL_RANK", "0")))
+    sampler.start()
+    cases = [(n, (240, 240, 960), p) for p in ("f32", "f64") for n in (1, 2, 3)]
+    cases.append((3, (522, 522, 522), "f32"))
+    for n, (nx, ny, nz), prec in cases:
+        h = 1.0 / (max(nx, ny, nz) + 1)
+        H = api.Handle(nx, ny, nz, n, h, 5e-4, precision=prec)
+        d = inputs.inclusion_coefficients(nx, ny, nz, seed=7, h=h, device="cuda")
+        m = 1.0 + 0.5 * inputs.inclusion_coefficients(nx, ny, nz, seed=8, h=h, base=0.3, device="cuda")
+        H.set_coefficients(d, m)
+        del d, m
+        ms = H.time_kernel(api.KERNEL_OP, reps=2 if prec == "f64" else 5)
+        alg, exe = H.op_flops()
+        nodes = nx * ny * nz
+        out["operator"].append({
+            "grid": f"{nx}x{ny}x{nz}", "degree": n, "precision": prec, "ms": ms,
+            "gnodes_per_s": nodes / (ms * 1e-3) / 1e9,
+            "flop_per_node": {"algorithmic": alg, "executed": exe},
+            "tflops": {"algorithmic": nodes * alg / (ms * 1e-3) / 1e12,
+                       "executed": nodes * exe / (ms * 1e-3) / 1e12}})
+        H.close()
+        torch.cuda.empty_cache()
+    # one implicit Euler step with variable coefficients, time to a 1e-8 true residual
+    N = 256
+    h = 1.0 / (N + 1)
+    dt = 5e-4
+    mask = inputs.sphere_mask(N, N, N, radius=0.45, h=h, device="cuda")
+    H = api.Handle(N, N, N, 3, h, dt, mask=mask, precision="f32_ir")
+    d = inputs.inclusion_coefficients(N, N, N, seed=7, h=h, device="cuda")
+    mu = 10.0 * inputs.inclusion_coefficients(N, N, N, seed=8, h=h, base=0.3, device="cuda")
+    H.set_coefficients(d, 1.0 + dt * mu)
+    del d, mu
+    u = torch.zeros((N, N, N), dtype=torch.float64, device="cuda")
+    q = inputs.gaussian_source(N, N, N, inputs.gaussian_centers(2, 32), sigma=0.03, h=h,
+                               mask=mask, device="cuda")
+    H.heat_step(u.clone(), q, 1, tol=1e-8)   # warm-up (graph capture)
+    ms, rep = _timed_ms(lambda: H.heat_step(u, q, 1, tol=1e-8))
+    out["heat_step_256_sphere"] = {"ms": ms, "cg_iterations": rep["iterations"],
+                                   "refinement_steps": rep["outer_iterations"],
+                                   "true_rel_residual": rep["rel_residual"],
+                                   "coefficients": "D inclusions (0.2-5 in background 1), "
+                                                   "m = 1 + dt mu_a"}
+    H.close()
+    del u, q, mask
+    torch.cuda.empty_cache()
+    clocks = sampler.stop()
+    top = next(r for r in out["operator"] if r["degree"] == 3 and r["precision"] == "f32"
+               and r["grid"] == "240x240x960")
+    mhz = clocks.get("sm_max_mhz") or 2070.0
+    peak = FP32_LANES * 2 * mhz * 1e6 / 1e12
+    ach = top["tflops"]["algorithmic"]
+    out["roofline"] = {"kernel": "k_op_var<float,3,OP> on 240x240x960", "bound": "alu",
+                       "achieved": ach, "peak": peak, "unit": "TFLOP/s", "frac": ach / peak,
+                       "executed_frac": top["tflops"]["executed"] / peak, "traffic": None,
+                       "note": "peak = 152 SMs x 128 FP32 lanes x 2 flop x the sampled maximum "
+                               "SM clock; achieved = algorithmic flops / kernel time"}
+    out["clocks"] = clocks
+    # the paper's own times for one application on the same grids (other hardware, context):
+    # Table tblPerformance (24-core CPU) and Table tblGpu (one GPU, 522^3)
+    out["paper_seconds"] = {"240x240x960 f32 n=1,2,3": [0.87, 3.65, 9.87],
+                            "240x240x960 f64 n=1,2,3": [1.07, 6.93, 15.11],
+                            "522x522x522 f32 n=3": 21.079}
+    return out
+
+
 def run_ours(args, rank, world, dist):
     import torch
 
@@ -500,6 +583,7 @@ def run_ours(args, rank, world, dist):
     if rank == 0 and not args.no_extra_configs and args.grid == N_GRID:
         line["batch_64_boxes"] = batch_64_boxes()
         line["mixed_precision_sphere256"] = mixed_precision_sphere256()
+        line["variable_coefficients"] = variable_coefficients()
     if rank == 0 and not args.no_cpu_baseline:
         v, cores, secs, desc = cpu_oracle_sample()
         line["cpu_baseline"] = {"value": v, "unit": "GDoF/s", "cores": cores, "kind": "oracle",
@@ -517,7 +601,8 @@ def main():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-extra-configs", action="store_true",
-                    help="skip the batched (64 boxes) and the 256^3 mixed-precision measurements")
+                    help="skip the batched (64 boxes), the 256^3 mixed-precision and the "
+                         "variable-coefficient measurements")
     ap.add_argument("--no-fcg-race", action="store_true",
                     help="skip the 512^3 union-of-spheres time-to-1e-8 race (learned FCG vs CG)")
     ap.add_argument("--grid", type=int, default=N_GRID,

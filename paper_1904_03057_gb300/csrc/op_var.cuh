@@ -79,12 +79,14 @@ struct VarCfg {
     static constexpr int C = TT + N;              // cells per axis
     static constexpr int QC = Q * C;              // quad points per axis
     static constexpr int R = Q * QC;              // rows of stage BC per z-cell
+    static constexpr int XP = TT + 1;             // padded row of the X buffers: consecutive
+                                                  // rows (threads) fall in different banks
     static constexpr int PASSES = (R + 511) / 512;
     static constexpr int NT0 = ((R + PASSES - 1) / PASSES + 31) / 32 * 32;
     static constexpr int NT = NT0 < 64 ? 64 : NT0;
     static constexpr int NPT = (TT * TT + NT - 1) / NT;   // output columns per thread
     static constexpr size_t smem =
-        sizeof(T) * ((size_t)3 * (N + 1) * H * H + (size_t)4 * Q * H * H + (size_t)3 * Q * QC * TT);
+        sizeof(T) * ((size_t)3 * (N + 1) * H * H + (size_t)4 * Q * H * H + (size_t)3 * Q * QC * XP);
     static_assert(smem <= 227 * 1024, "variable-coefficient tile exceeds shared memory");
 };
 
@@ -102,12 +104,12 @@ __global__ void __launch_bounds__(VarCfg<T, N>::NT, 1) k_op_var(const __grid_con
 {
     using Cfg = VarCfg<T, N>;
     constexpr int Q = Cfg::Q, NB = N + 1, TT = Cfg::TT, H = Cfg::H, C = Cfg::C, QC = Cfg::QC;
-    constexpr int NT = Cfg::NT, R = Cfg::R, NPT = Cfg::NPT;
-    constexpr int HH = H * H, XS = Q * QC * TT;   // plane size, stride between X fields
+    constexpr int NT = Cfg::NT, R = Cfg::R, NPT = Cfg::NPT, XP = Cfg::XP;
+    constexpr int HH = H * H, XS = Q * QC * XP;   // plane size, stride between X fields
     extern __shared__ __align__(16) unsigned char smem_raw[];
     T* ring = reinterpret_cast<T*>(smem_raw);   // [N + 1][3][HH]: c, d, m per node plane
     T* sZ = ring + (N + 1) * 3 * HH;            // [Q][4][HH]: cB, cD, dB, mB
-    T* sX = sZ + Q * 4 * HH;                    // [3][Q][QC][TT]: Xa, Xb, Xc
+    T* sX = sZ + Q * 4 * HH;                    // [3][Q][QC][XP]: Xa, Xb, Xc
 
     const int tid = threadIdx.x;
     const int nx = a.g.nx, ny = a.g.ny, nz = a.g.nz;
@@ -231,8 +233,9 @@ __global__ void __launch_bounds__(VarCfg<T, N>::NT, 1) k_op_var(const __grid_con
             for (int f = 0; f < 3; f++)
 #pragma unroll
                 for (int t = 0; t < NB; t++) xo[f][t] = T(0);
-            T* xrow = sX + (size_t)(qz * QC + yq) * TT;
-#pragma unroll 1
+            T* xrow = sX + (size_t)(qz * QC + yq) * XP;
+            // unrolled by the window length, the window shifts below are register renames
+#pragma unroll NB
             for (int cx = 0; cx < C; cx++) {
                 {
                     T v[5];
@@ -296,12 +299,12 @@ __global__ void __launch_bounds__(VarCfg<T, N>::NT, 1) k_op_var(const __grid_con
                     T Ya = T(0), Yc = T(0);
 #pragma unroll
                     for (int t = 0; t < NB; t++) {
-                        const T* xa = sX + (size_t)(qz * QC + (ly + N - t) * Q) * TT + lx;
+                        const T* xa = sX + (size_t)(qz * QC + (ly + N - t) * Q) * XP + lx;
 #pragma unroll
                         for (int qy = 0; qy < Q; qy++) {
                             const T b = a.t.B[qy][t], d = a.t.D[1][qy][t];
-                            Ya = fma(b, xa[qy * TT], fma(d, xa[XS + qy * TT], Ya));
-                            Yc = fma(b, xa[2 * XS + qy * TT], Yc);
+                            Ya = fma(b, xa[qy * XP], fma(d, xa[XS + qy * XP], Ya));
+                            Yc = fma(b, xa[2 * XS + qy * XP], Yc);
                         }
                     }
 #pragma unroll
