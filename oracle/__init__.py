@@ -81,6 +81,16 @@ def lib():
                                           ctypes.c_int, _D, _D, ctypes.c_int, _D, _D, _D]
             L.orc_axis_rule.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.c_double, _D, _D]
             L.orc_triple_kernels_1d.argtypes = [ctypes.c_int, _D, _D]
+            L.orc_robin_size.argtypes = [ctypes.c_int, ctypes.c_int]
+            L.orc_robin_1d.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.c_double, _D, _D, _D]
+            for name in ("orc_op_robin", "orc_abs_op_robin", "orc_bruteforce_apply_robin"):
+                getattr(L, name).argtypes = [P, ctypes.c_double, _D, _D]
+            L.orc_diag.argtypes = [P, ctypes.c_double, ctypes.c_int, _D]
+            L.orc_pcg.argtypes = [P, ctypes.c_double, ctypes.c_int, _D, _D, ctypes.c_double,
+                                  ctypes.c_int, _I, _D]
+            L.orc_transfer_1d.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.c_double,
+                                          ctypes.c_int, ctypes.c_double, _D]
+            L.orc_prolong_robin.argtypes = [P, P, _D, _D]
             for name in ("orc_op_var", "orc_abs_op_var", "orc_bruteforce_apply_var"):
                 getattr(L, name).argtypes = [P, _D, _D, _D, _D]
             L.orc_op_var_points.argtypes = [P, _D, _D, ctypes.c_void_p, ctypes.c_int, ctypes.c_int,
@@ -293,7 +303,8 @@ def abs_op(prob: Problem, x):
 
 def set_plant(mode: int) -> None:
     """Test hook: 0 = correct odd reflection, 1 = zero ghosts, 2 = even reflection (solution),
-    3 = zero ghosts for the coefficient fields of the variable-coefficient operator."""
+    3 = zero ghosts for the coefficient fields of the variable-coefficient operator, 4 = the far
+    face left out of the Robin boundary term."""
     lib().orc_set_plant(int(mode))
 
 
@@ -407,3 +418,79 @@ def op_var_points(prob: Problem, d, m, x, points, absolute=False):
                                    int(x.dtype == np.float32), int(bool(absolute)), pts.size,
                                    pts.ctypes.data_as(ctypes.POINTER(ctypes.c_longlong)), _dp(out)))
     return out
+
+
+# --- Robin (boundary penalty) problems on the box, Jacobi PCG, coarse-grid prolongation --------
+
+def robin_size(n: int, N: int) -> int:
+    """Unknowns per axis of the untruncated basis on a box of N interior nodes:
+    N + 2 + 2 floor(n/2) (every B-spline whose support meets the box)."""
+    return int(lib().orc_robin_size(int(n), int(N)))
+
+
+def robin_shape(prob: Problem):
+    return tuple(robin_size(prob.n, N) for N in (prob.nz, prob.ny, prob.nx))
+
+
+def robin_1d(n: int, N: int, h: float):
+    """(M, K, E): truncated Gram, stiffness and face matrices of one axis (dense Nt x Nt)."""
+    Nt = robin_size(n, N)
+    M, K, E = np.zeros(Nt * Nt), np.zeros(Nt * Nt), np.zeros(Nt * Nt)
+    _check(lib().orc_robin_1d(int(n), int(N), float(h), _dp(M), _dp(K), _dp(E)))
+    return M.reshape(Nt, Nt), K.reshape(Nt, Nt), E.reshape(Nt, Nt)
+
+
+def _robin(name, prob: Problem, pen, x):
+    x = _f64(x).reshape(robin_shape(prob))
+    y = np.zeros(robin_shape(prob))
+    _check(getattr(lib(), name)(ctypes.byref(prob._c()), float(pen), _dp(x), _dp(y)))
+    return y
+
+
+def op_robin(prob: Problem, pen, x):
+    """A_R x: M + dt K + pen E over the untruncated basis, integrals truncated to the box (Eq.
+    RitzGalerkin with the boundary term), x of shape robin_shape(prob)."""
+    return _robin("orc_op_robin", prob, pen, x)
+
+
+def abs_op_robin(prob: Problem, pen, x):
+    return _robin("orc_abs_op_robin", prob, pen, x)
+
+
+def bruteforce_apply_robin(prob: Problem, pen, x):
+    """A_R x by volume and surface Gauss quadrature of point values of the basis (tiny grids)."""
+    return _robin("orc_bruteforce_apply_robin", prob, pen, x)
+
+
+def diag(prob: Problem, pen=0.0, robin=False):
+    """Diagonal of the reflected (masked) operator, or of A_R with robin=True."""
+    shape = robin_shape(prob) if robin else prob.shape
+    d = np.zeros(shape)
+    _check(lib().orc_diag(ctypes.byref(prob._c()), float(pen), int(bool(robin)), _dp(d)))
+    return d
+
+
+def pcg(prob: Problem, b, x0=None, tol=1e-10, max_iter=10000, pen=0.0, robin=False):
+    """Jacobi-preconditioned CG. Returns (x, iterations, true relative residual, status)."""
+    shape = robin_shape(prob) if robin else prob.shape
+    b = _f64(b).reshape(shape)
+    x = np.zeros(shape) if x0 is None else _f64(x0).reshape(shape).copy()
+    it = ctypes.c_int(0)
+    rel = ctypes.c_double(0.0)
+    st = _check(lib().orc_pcg(ctypes.byref(prob._c()), float(pen), int(bool(robin)), _dp(b), _dp(x),
+                              float(tol), int(max_iter), ctypes.byref(it), ctypes.byref(rel)))
+    return x, it.value, rel.value, st
+
+
+def transfer_1d(n: int, Nf: int, hf: float, Nc: int, hc: float):
+    T = np.zeros(robin_size(n, Nf) * robin_size(n, Nc))
+    _check(lib().orc_transfer_1d(int(n), int(Nf), float(hf), int(Nc), float(hc), _dp(T)))
+    return T.reshape(robin_size(n, Nf), robin_size(n, Nc))
+
+
+def prolong_robin(fine: Problem, coarse: Problem, xc):
+    """L2 projection of the coarse Robin expansion onto the fine Robin basis of the same box."""
+    xc = _f64(xc).reshape(robin_shape(coarse))
+    xf = np.zeros(robin_shape(fine))
+    _check(lib().orc_prolong_robin(ctypes.byref(fine._c()), ctypes.byref(coarse._c()), _dp(xc), _dp(xf)))
+    return xf

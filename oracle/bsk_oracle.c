@@ -17,6 +17,9 @@
  *   - Variable coefficients: Eq. RitzGalerkin and Eq. tensForm with D(x) and mu_a(x) expanded
  *     in B-splines (section 2.3), the on-the-fly strategy of section 2.4 written as the plain
  *     double sum over solution and coefficient B-splines with 1-D triple-product factors.
+ *   - Boundary penalty (Robin) problems on the box: the boundary integral of Eq. RitzGalerkin
+ *     over the untruncated basis; the Jacobi-preconditioned CG and the coarse-grid
+ *     initialisation of the large run of section 3.
  *   - Conjugate gradient: section 2.5 (Fig. figGenTenSolv, stage 3).
  *   - Indirect B-spline transform (evaluation): section 2.3, Fig. figBspnSignProc.
  *   - L2 norm: Appendix I.
@@ -164,8 +167,8 @@ static int reflect(int a, int N, int* src)
 
 /* Deliberate-mistake switch for the test-suite's planted-error checks: 0 = correct odd
  * reflection (default), 1 = zero ghosts, 2 = even reflection, 3 = zero ghosts for the
- * coefficient fields of the variable-coefficient operator. Tests set it, check that a pin
- * fails, and reset it. */
+ * coefficient fields of the variable-coefficient operator, 4 = the far face left out of the
+ * Robin boundary term. Tests set it, check that a pin fails, and reset it. */
 static int g_plant = 0;
 void orc_set_plant(int mode) { g_plant = mode; }
 
@@ -1055,5 +1058,484 @@ int orc_bruteforce_apply_var(const orc_problem* p, const double* d, const double
     }
     free(F);
     for (int a = 0; a < 3; a++) { free(X[a]); free(W[a]); free(PS[a]); free(DP[a]); free(PH[a]); }
+    return 0;
+}
+
+/* ------------------------------------------------------------------------------------------ */
+/* Robin (boundary penalty) problems on the box: the untruncated B-spline basis                */
+/* ------------------------------------------------------------------------------------------ */
+
+/* With the boundary penalty method (section 3, Dirichlet data approximated by a Robin condition
+ * weighted by a penalty; the boundary integral of Eq. RitzGalerkin) the basis does not vanish on
+ * the faces: every B-spline beta(x/h - i) whose support meets the box (0, (N+1)h) is an unknown,
+ * i = i0 .. N+1-i0 with i0 = -floor(n/2), i.e. Nt = N + 2 + 2 floor(n/2) per axis, array
+ * position a = i - i0. */
+int orc_robin_size(int n, int N) { return N + 2 + 2 * (n / 2); }
+
+/* Dense Nt x Nt factors of one axis, integrals truncated to the box [0, (N+1)h]:
+ *   M_ab = int beta_a beta_b dx,  K_ab = int beta_a' beta_b' dx,
+ *   E_ab = beta_a(0) beta_b(0) + beta_a((N+1)h) beta_b((N+1)h)   (the two faces of the axis).
+ * Quadrature: n + 1 Gauss points per half-cell of the box (the rule of the brute-force matrix),
+ * exact for the degree-2n products. */
+int orc_robin_1d(int n, int N, double h, double* M, double* K, double* E)
+{
+    if (n < 1 || n > 7 || N < 1 || !(h > 0)) return -1;
+    int Nt = orc_robin_size(n, N), i0 = -(n / 2);
+    int cap = 2 * (N + 1) * (n + 1);
+    double* xs = (double*)malloc(sizeof(double) * cap);
+    double* ws = (double*)malloc(sizeof(double) * cap);
+    int nq = axis_rule(n, N, h, xs, ws);
+    for (int a = 0; a < Nt; a++)
+        for (int b = 0; b < Nt; b++) {
+            double sm = 0.0, sk = 0.0;
+            for (int q = 0; q < nq; q++) {
+                double u = xs[q] / h;
+                sm += ws[q] * orc_bspline(n, u - (a + i0)) * orc_bspline(n, u - (b + i0));
+                sk += ws[q] * orc_bspline_deriv(n, u - (a + i0)) * orc_bspline_deriv(n, u - (b + i0)) / (h * h);
+            }
+            M[a * Nt + b] = sm;
+            K[a * Nt + b] = sk;
+            E[a * Nt + b] = orc_bspline(n, 0.0 - (a + i0)) * orc_bspline(n, 0.0 - (b + i0)) +
+                            (g_plant == 4 ? 0.0 :   /* test hook: the far face left out */
+                             orc_bspline(n, (double)(N + 1) - (a + i0)) * orc_bspline(n, (double)(N + 1) - (b + i0)));
+        }
+    free(xs);
+    free(ws);
+    return 0;
+}
+
+typedef struct {
+    int Nt[3];
+    double *M[3], *K[3], *E[3];
+} robin_tabs;
+
+static void robin_free(robin_tabs* t)
+{
+    for (int d = 0; d < 3; d++) { free(t->M[d]); free(t->K[d]); free(t->E[d]); }
+}
+
+static int robin_init(const orc_problem* p, robin_tabs* t, int absmode)
+{
+    int N[3] = {p->nx, p->ny, p->nz};
+    double h[3] = {p->hx, p->hy, p->hz};
+    for (int d = 0; d < 3; d++) {
+        int Nt = orc_robin_size(p->n, N[d]);
+        t->Nt[d] = Nt;
+        t->M[d] = (double*)malloc(sizeof(double) * Nt * Nt);
+        t->K[d] = (double*)malloc(sizeof(double) * Nt * Nt);
+        t->E[d] = (double*)malloc(sizeof(double) * Nt * Nt);
+        if (orc_robin_1d(p->n, N[d], h[d], t->M[d], t->K[d], t->E[d])) return -1;
+        if (absmode)
+            for (int i = 0; i < Nt * Nt; i++) {
+                t->M[d][i] = fabs(t->M[d][i]);
+                t->K[d][i] = fabs(t->K[d][i]);
+                t->E[d][i] = fabs(t->E[d][i]);
+            }
+    }
+    return 0;
+}
+
+/* Weight of unknown k in output l of the Robin operator from the 1-D factors. */
+static double robin_weight(const robin_tabs* t, double dt, double pen, const int* l, const int* k)
+{
+    double m[3], s[3], e[3];
+    for (int d = 0; d < 3; d++) {
+        size_t o = (size_t)l[d] * t->Nt[d] + k[d];
+        m[d] = t->M[d][o];
+        s[d] = t->K[d][o];
+        e[d] = t->E[d][o];
+    }
+    return m[2] * m[1] * m[0] + dt * (s[2] * m[1] * m[0] + m[2] * s[1] * m[0] + m[2] * m[1] * s[0]) +
+           pen * (e[2] * m[1] * m[0] + m[2] * e[1] * m[0] + m[2] * m[1] * e[0]);
+}
+
+/* y = A_R x on the Nt^3 unknowns of the Robin basis (problem nx, ny, nz = interior nodes N of
+ * the box):
+ *   A_R = Mz My Mx + dt (Kz My Mx + Mz Ky Mx + Mz My Kx) + pen (Ez My Mx + Mz Ey Mx + Mz My Ex),
+ * Eq. RitzGalerkin with D = dt, mu_a = 1 and the boundary term weighted by pen (1/(2 gamma) in
+ * the paper's notation), summed directly over the (2n+1)^3 band of each output. No mask. */
+static int op_robin(const orc_problem* p, double pen, const double* x, double* y, int absmode)
+{
+    if (!problem_ok(p) || p->mask) return -1;
+    robin_tabs t;
+    memset(&t, 0, sizeof t);
+    if (robin_init(p, &t, absmode)) { robin_free(&t); return -1; }
+    int n = p->n, *Nt = t.Nt;
+    double dt = absmode ? fabs(p->dt) : p->dt, pw = absmode ? fabs(pen) : pen;
+    size_t len = (size_t)Nt[0] * Nt[1] * Nt[2];
+#pragma omp parallel for schedule(dynamic, 64)
+    for (long long I = 0; I < (long long)len; I++) {
+        int l[3] = {(int)(I % Nt[0]), (int)((I / Nt[0]) % Nt[1]), (int)(I / ((long long)Nt[0] * Nt[1]))};
+        double s = 0.0;
+        for (int kz = l[2] - n; kz <= l[2] + n; kz++) {
+            if (kz < 0 || kz >= Nt[2]) continue;
+            for (int ky = l[1] - n; ky <= l[1] + n; ky++) {
+                if (ky < 0 || ky >= Nt[1]) continue;
+                for (int kx = l[0] - n; kx <= l[0] + n; kx++) {
+                    if (kx < 0 || kx >= Nt[0]) continue;
+                    int k[3] = {kx, ky, kz};
+                    double xv = x[((size_t)kz * Nt[1] + ky) * Nt[0] + kx];
+                    s += robin_weight(&t, dt, pw, l, k) * (absmode ? fabs(xv) : xv);
+                }
+            }
+        }
+        y[I] = s;
+    }
+    robin_free(&t);
+    return 0;
+}
+
+int orc_op_robin(const orc_problem* p, double pen, const double* x, double* y)
+{
+    return op_robin(p, pen, x, y, 0);
+}
+
+int orc_abs_op_robin(const orc_problem* p, double pen, const double* x, double* y)
+{
+    return op_robin(p, pen, x, y, 1);
+}
+
+/* Brute-force reference for A_R on tiny grids: the volume integral of u psi_i + dt grad u . grad
+ * psi_i over the box on the tensor half-cell Gauss grid, plus pen times the surface integral of
+ * u psi_i over the six faces on the 2-D half-cell Gauss grid of each face, with u and every
+ * B-spline evaluated pointwise (no 1-D factors, no bands). */
+int orc_bruteforce_apply_robin(const orc_problem* p, double pen, const double* x, double* y)
+{
+    if (!problem_ok(p) || p->mask) return -1;
+    int n = p->n, N[3] = {p->nx, p->ny, p->nz}, Nt[3], i0 = -(n / 2);
+    double h[3] = {p->hx, p->hy, p->hz}, L[3];
+    double *X[3], *W[3], *B[3], *G[3], *F0[3], *F1[3];
+    int nq[3];
+    for (int a = 0; a < 3; a++) {
+        Nt[a] = orc_robin_size(n, N[a]);
+        L[a] = (N[a] + 1) * h[a];
+        int cap = 2 * (N[a] + 1) * (n + 1);
+        X[a] = (double*)malloc(sizeof(double) * cap);
+        W[a] = (double*)malloc(sizeof(double) * cap);
+        nq[a] = axis_rule(n, N[a], h[a], X[a], W[a]);
+        B[a] = (double*)malloc(sizeof(double) * (size_t)nq[a] * Nt[a]);
+        G[a] = (double*)malloc(sizeof(double) * (size_t)nq[a] * Nt[a]);
+        F0[a] = (double*)malloc(sizeof(double) * Nt[a]);
+        F1[a] = (double*)malloc(sizeof(double) * Nt[a]);
+        for (int i = 0; i < Nt[a]; i++) {
+            for (int q = 0; q < nq[a]; q++) {
+                double u = X[a][q] / h[a] - (i + i0);
+                B[a][(size_t)q * Nt[a] + i] = orc_bspline(n, u);
+                G[a][(size_t)q * Nt[a] + i] = orc_bspline_deriv(n, u) / h[a];
+            }
+            F0[a][i] = orc_bspline(n, 0.0 / h[a] - (i + i0));
+            F1[a][i] = orc_bspline(n, L[a] / h[a] - (i + i0));
+        }
+    }
+    size_t len = (size_t)Nt[0] * Nt[1] * Nt[2];
+    memset(y, 0, sizeof(double) * len);
+    /* volume: point values of u and grad u, then the projection onto every basis function */
+    size_t npt = (size_t)nq[0] * nq[1] * nq[2];
+    double* U = (double*)malloc(sizeof(double) * npt * 4);
+#pragma omp parallel for schedule(dynamic, 16)
+    for (long long P = 0; P < (long long)npt; P++) {
+        int q[3] = {(int)(P % nq[0]), (int)((P / nq[0]) % nq[1]), (int)(P / ((size_t)nq[0] * nq[1]))};
+        double u = 0, gx = 0, gy = 0, gz = 0;
+        for (size_t J = 0; J < len; J++) {
+            int j[3] = {(int)(J % Nt[0]), (int)((J / Nt[0]) % Nt[1]), (int)(J / ((size_t)Nt[0] * Nt[1]))};
+            double b0 = B[0][(size_t)q[0] * Nt[0] + j[0]], b1 = B[1][(size_t)q[1] * Nt[1] + j[1]];
+            double b2 = B[2][(size_t)q[2] * Nt[2] + j[2]];
+            if (b0 == 0.0 && G[0][(size_t)q[0] * Nt[0] + j[0]] == 0.0) continue;
+            double g0 = G[0][(size_t)q[0] * Nt[0] + j[0]], g1 = G[1][(size_t)q[1] * Nt[1] + j[1]];
+            double g2 = G[2][(size_t)q[2] * Nt[2] + j[2]];
+            u += x[J] * b0 * b1 * b2;
+            gx += x[J] * g0 * b1 * b2;
+            gy += x[J] * b0 * g1 * b2;
+            gz += x[J] * b0 * b1 * g2;
+        }
+        double w = W[0][q[0]] * W[1][q[1]] * W[2][q[2]];
+        U[P * 4 + 0] = w * u;
+        U[P * 4 + 1] = w * p->dt * gx;
+        U[P * 4 + 2] = w * p->dt * gy;
+        U[P * 4 + 3] = w * p->dt * gz;
+    }
+#pragma omp parallel for schedule(dynamic, 4)
+    for (long long I = 0; I < (long long)len; I++) {
+        int i[3] = {(int)(I % Nt[0]), (int)((I / Nt[0]) % Nt[1]), (int)(I / ((size_t)Nt[0] * Nt[1]))};
+        double s = 0.0;
+        for (size_t P = 0; P < npt; P++) {
+            int q[3] = {(int)(P % nq[0]), (int)((P / nq[0]) % nq[1]), (int)(P / ((size_t)nq[0] * nq[1]))};
+            double b0 = B[0][(size_t)q[0] * Nt[0] + i[0]], b1 = B[1][(size_t)q[1] * Nt[1] + i[1]];
+            double b2 = B[2][(size_t)q[2] * Nt[2] + i[2]];
+            double g0 = G[0][(size_t)q[0] * Nt[0] + i[0]], g1 = G[1][(size_t)q[1] * Nt[1] + i[1]];
+            double g2 = G[2][(size_t)q[2] * Nt[2] + i[2]];
+            s += U[P * 4 + 0] * b0 * b1 * b2 + U[P * 4 + 1] * g0 * b1 * b2 + U[P * 4 + 2] * b0 * g1 * b2 +
+                 U[P * 4 + 3] * b0 * b1 * g2;
+        }
+        y[I] = s;
+    }
+    free(U);
+    /* faces: axis a fixed at 0 or L[a]; the other two axes on their Gauss grids */
+    for (int a = 0; a < 3; a++) {
+        int b = (a + 1) % 3, c = (a + 2) % 3;
+        for (int side = 0; side < 2; side++) {
+            const double* Fa = side ? F1[a] : F0[a];
+            size_t nfp = (size_t)nq[b] * nq[c];
+            double* Uf = (double*)malloc(sizeof(double) * nfp);
+#pragma omp parallel for schedule(dynamic, 16)
+            for (long long P = 0; P < (long long)nfp; P++) {
+                int qb = (int)(P % nq[b]), qc = (int)(P / nq[b]);
+                double u = 0.0;
+                for (size_t J = 0; J < len; J++) {
+                    int j[3] = {(int)(J % Nt[0]), (int)((J / Nt[0]) % Nt[1]), (int)(J / ((size_t)Nt[0] * Nt[1]))};
+                    u += x[J] * Fa[j[a]] * B[b][(size_t)qb * Nt[b] + j[b]] * B[c][(size_t)qc * Nt[c] + j[c]];
+                }
+                Uf[P] = W[b][qb] * W[c][qc] * u;
+            }
+#pragma omp parallel for schedule(dynamic, 4)
+            for (long long I = 0; I < (long long)len; I++) {
+                int i[3] = {(int)(I % Nt[0]), (int)((I / Nt[0]) % Nt[1]), (int)(I / ((size_t)Nt[0] * Nt[1]))};
+                if (Fa[i[a]] == 0.0) continue;
+                double s = 0.0;
+                for (size_t P = 0; P < nfp; P++) {
+                    int qb = (int)(P % nq[b]), qc = (int)(P / nq[b]);
+                    s += Uf[P] * B[b][(size_t)qb * Nt[b] + i[b]] * B[c][(size_t)qc * Nt[c] + i[c]];
+                }
+                y[I] += pen * Fa[i[a]] * s;
+            }
+            free(Uf);
+        }
+    }
+    for (int a = 0; a < 3; a++) { free(X[a]); free(W[a]); free(B[a]); free(G[a]); free(F0[a]); free(F1[a]); }
+    return 0;
+}
+
+/* Diagonal of the system matrix: robin = 0, the odd-reflected (and masked) operator of
+ * orc_op_stencil (A_ii is the sum of the stencil weights whose reflected source is i itself,
+ * with the reflection's sign); robin = 1, A_R (products of the 1-D diagonals). The Jacobi
+ * preconditioner of the paper's large run (section 3) divides by it. Inactive nodes get 1. */
+int orc_diag(const orc_problem* p, double pen, int robin, double* d)
+{
+    if (!problem_ok(p)) return -1;
+    if (robin) {
+        if (p->mask) return -1;
+        robin_tabs t;
+        memset(&t, 0, sizeof t);
+        if (robin_init(p, &t, 0)) { robin_free(&t); return -1; }
+        size_t len = (size_t)t.Nt[0] * t.Nt[1] * t.Nt[2];
+        for (size_t I = 0; I < len; I++) {
+            int l[3] = {(int)(I % t.Nt[0]), (int)((I / t.Nt[0]) % t.Nt[1]), (int)(I / ((size_t)t.Nt[0] * t.Nt[1]))};
+            d[I] = robin_weight(&t, p->dt, pen, l, l);
+        }
+        robin_free(&t);
+        return 0;
+    }
+    int n = p->n, L = 2 * n + 1;
+    double kern[6 * 15];
+    if (orc_problem_kernels(p, kern)) return -1;
+    const double *Mx = kern, *Kx = kern + L, *My = kern + 2 * L, *Ky = kern + 3 * L;
+    const double *Mz = kern + 4 * L, *Kz = kern + 5 * L;
+    size_t len = (size_t)p->nx * p->ny * p->nz;
+#pragma omp parallel for schedule(static)
+    for (long long I = 0; I < (long long)len; I++) {
+        int ix = (int)(I % p->nx), iy = (int)((I / p->nx) % p->ny), iz = (int)(I / ((long long)p->nx * p->ny));
+        if (p->mask && !p->mask[I]) { d[I] = 1.0; continue; }
+        double s = 0.0;
+        for (int c = 0; c < L; c++) {
+            int sz, gz = reflect(iz + c - n, p->nz, &sz);
+            if (!gz || sz != iz) continue;
+            for (int b = 0; b < L; b++) {
+                int sy, gy = reflect(iy + b - n, p->ny, &sy);
+                if (!gy || sy != iy) continue;
+                for (int a = 0; a < L; a++) {
+                    int sx, gx = reflect(ix + a - n, p->nx, &sx);
+                    if (!gx || sx != ix) continue;
+                    double w = Mz[c] * My[b] * Mx[a] +
+                               p->dt * (Kz[c] * My[b] * Mx[a] + Mz[c] * Ky[b] * Mx[a] + Mz[c] * My[b] * Kx[a]);
+                    s += w * (gz * gy * gx);
+                }
+            }
+        }
+        d[I] = s;
+    }
+    return 0;
+}
+
+/* Jacobi-preconditioned conjugate gradient (the solver of the paper's large run, section 3):
+ * textbook PCG with z = r / diag(A), for the reflected operator (robin = 0, masked) or A_R
+ * (robin = 1). Stops when ||r|| <= tol ||b||; reports iterations and the true relative
+ * residual. */
+int orc_pcg(const orc_problem* p, double pen, int robin, const double* b, double* x, double tol,
+            int max_iter, int* iters, double* relres)
+{
+    if (!problem_ok(p)) return -1;
+    size_t len = robin ? (size_t)orc_robin_size(p->n, p->nx) * orc_robin_size(p->n, p->ny) *
+                             orc_robin_size(p->n, p->nz)
+                       : (size_t)p->nx * p->ny * p->nz;
+    double kern[6 * 15];
+    if (!robin && orc_problem_kernels(p, kern)) return -1;
+    double* dg = (double*)malloc(sizeof(double) * len);
+    double* r = (double*)malloc(sizeof(double) * len);
+    double* z = (double*)malloc(sizeof(double) * len);
+    double* pv = (double*)malloc(sizeof(double) * len);
+    double* q = (double*)malloc(sizeof(double) * len);
+    double* bm = (double*)malloc(sizeof(double) * len);
+    if (!dg || !r || !z || !pv || !q || !bm || orc_diag(p, pen, robin, dg)) {
+        free(dg); free(r); free(z); free(pv); free(q); free(bm);
+        return -1;
+    }
+    for (size_t i = 0; i < len; i++) {
+        int act = robin || !p->mask || p->mask[i];
+        bm[i] = act ? b[i] : 0.0;
+        if (!act) x[i] = 0.0;
+    }
+#define APPLY(in, out) (robin ? orc_op_robin(p, pen, in, out) : orc_op_separable(p, kern, in, out))
+    double bb = dot(bm, bm, len);
+    APPLY(x, q);
+    for (size_t i = 0; i < len; i++) { r[i] = bm[i] - q[i]; z[i] = r[i] / dg[i]; pv[i] = z[i]; }
+    double rz = dot(r, z, len), rr = dot(r, r, len);
+    int status = 1, it = 0;
+    if (bb == 0.0) {
+        memset(x, 0, sizeof(double) * len);
+        status = 0;
+    } else if (sqrt(rr) <= tol * sqrt(bb)) {
+        status = 0;
+    } else {
+        for (it = 1; it <= max_iter; it++) {
+            APPLY(pv, q);
+            double pq = dot(pv, q, len);
+            if (!(pq > 0.0)) { status = -5; break; }
+            double alpha = rz / pq;
+            for (size_t i = 0; i < len; i++) { x[i] += alpha * pv[i]; r[i] -= alpha * q[i]; }
+            rr = dot(r, r, len);
+            if (sqrt(rr) <= tol * sqrt(bb)) { status = 0; break; }
+            for (size_t i = 0; i < len; i++) z[i] = r[i] / dg[i];
+            double rz_new = dot(r, z, len);
+            double beta = rz_new / rz;
+            for (size_t i = 0; i < len; i++) pv[i] = z[i] + beta * pv[i];
+            rz = rz_new;
+        }
+        if (it > max_iter) it = max_iter;
+    }
+    *iters = it;
+    APPLY(x, q);
+    for (size_t i = 0; i < len; i++) r[i] = bm[i] - q[i];
+    *relres = bb > 0 ? sqrt(dot(r, r, len) / bb) : 0.0;
+#undef APPLY
+    free(dg); free(r); free(z); free(pv); free(q); free(bm);
+    return status;
+}
+
+/* 1-D transfer between the Robin bases of two grids on the same interval [0, L],
+ * L = (Nf+1) hf = (Nc+1) hc:  T_fc = int_0^L beta(x/hf - f) beta(x/hc - c) dx (dense Ntf x Ntc).
+ * The integrand is a polynomial of degree 2n between consecutive breakpoints of either grid (the
+ * half-multiples of hf and of hc), so n + 1 Gauss points per piece integrate it exactly. */
+int orc_transfer_1d(int n, int Nf, double hf, int Nc, double hc, double* T)
+{
+    if (n < 1 || n > 7 || Nf < 1 || Nc < 1 || !(hf > 0) || !(hc > 0)) return -1;
+    double L = (Nf + 1) * hf;
+    if (fabs((Nc + 1) * hc - L) > 1e-12 * L) return -1;
+    int Ntf = orc_robin_size(n, Nf), Ntc = orc_robin_size(n, Nc), i0 = -(n / 2);
+    int nbf = 2 * (Nf + 1), nbc = 2 * (Nc + 1), nb = 0;
+    double* br = (double*)malloc(sizeof(double) * (nbf + nbc + 2));
+    for (int k = 0; k <= nbf; k++) br[nb++] = 0.5 * hf * k;
+    for (int k = 0; k <= nbc; k++) br[nb++] = 0.5 * hc * k;
+    for (int i = 1; i < nb; i++)   /* insertion sort */
+        for (int j = i; j > 0 && br[j - 1] > br[j]; j--) { double t = br[j]; br[j] = br[j - 1]; br[j - 1] = t; }
+    double t[16], w[16];
+    gauss_legendre(n + 1, t, w);
+    memset(T, 0, sizeof(double) * (size_t)Ntf * Ntc);
+    for (int s = 0; s + 1 < nb; s++) {
+        double a = br[s], b = br[s + 1];
+        if (!(b - a > 1e-14 * L)) continue;
+        for (int g = 0; g <= n; g++) {
+            double x = 0.5 * (a + b) + 0.5 * (b - a) * t[g], wg = 0.5 * (b - a) * w[g];
+            for (int f = 0; f < Ntf; f++) {
+                double vf = orc_bspline(n, x / hf - (f + i0));
+                if (vf == 0.0) continue;
+                for (int c = 0; c < Ntc; c++)
+                    T[(size_t)f * Ntc + c] += wg * vf * orc_bspline(n, x / hc - (c + i0));
+            }
+        }
+    }
+    free(br);
+    return 0;
+}
+
+/* Solves the dense system A X = B (A n x n, B n x m, both row-major, overwritten) by Gaussian
+ * elimination with partial pivoting; X is left in B. */
+static int dense_solve(int n, int m, double* A, double* B)
+{
+    for (int k = 0; k < n; k++) {
+        int piv = k;
+        for (int i = k + 1; i < n; i++) if (fabs(A[i * n + k]) > fabs(A[piv * n + k])) piv = i;
+        if (A[piv * n + k] == 0.0) return -1;
+        if (piv != k) {
+            for (int j = 0; j < n; j++) { double t = A[k * n + j]; A[k * n + j] = A[piv * n + j]; A[piv * n + j] = t; }
+            for (int j = 0; j < m; j++) { double t = B[k * m + j]; B[k * m + j] = B[piv * m + j]; B[piv * m + j] = t; }
+        }
+        for (int i = k + 1; i < n; i++) {
+            double f = A[i * n + k] / A[k * n + k];
+            for (int j = k; j < n; j++) A[i * n + j] -= f * A[k * n + j];
+            for (int j = 0; j < m; j++) B[i * m + j] -= f * B[k * m + j];
+        }
+    }
+    for (int k = n - 1; k >= 0; k--) {
+        for (int j = 0; j < m; j++) {
+            double s = B[k * m + j];
+            for (int i = k + 1; i < n; i++) s -= A[k * n + i] * B[i * m + j];
+            B[k * m + j] = s / A[k * n + k];
+        }
+    }
+    return 0;
+}
+
+/* L2 projection of a coarse Robin expansion onto the fine Robin basis of the same box (the
+ * coarse-grid initialisation of the paper's large run, section 3): xf = M_f^{-1} T xc, with the
+ * fine Gram matrix and the transfer factorising per axis, so xf = (Pz Py Px) xc with
+ * P_d = M_d^{-1} T_d (dense 1-D solves). fine / coarse: problems with nx, ny, nz = interior nodes. */
+int orc_prolong_robin(const orc_problem* fine, const orc_problem* coarse, const double* xc, double* xf)
+{
+    if (!problem_ok(fine) || !problem_ok(coarse) || fine->n != coarse->n) return -1;
+    int n = fine->n;
+    int Nf[3] = {fine->nx, fine->ny, fine->nz}, Nc[3] = {coarse->nx, coarse->ny, coarse->nz};
+    double hf[3] = {fine->hx, fine->hy, fine->hz}, hc[3] = {coarse->hx, coarse->hy, coarse->hz};
+    int tf[3], tc[3];
+    double* P[3];
+    for (int d = 0; d < 3; d++) {
+        tf[d] = orc_robin_size(n, Nf[d]);
+        tc[d] = orc_robin_size(n, Nc[d]);
+        double* M = (double*)malloc(sizeof(double) * tf[d] * tf[d]);
+        double* K = (double*)malloc(sizeof(double) * tf[d] * tf[d]);
+        double* E = (double*)malloc(sizeof(double) * tf[d] * tf[d]);
+        P[d] = (double*)malloc(sizeof(double) * (size_t)tf[d] * tc[d]);
+        int rc = orc_robin_1d(n, Nf[d], hf[d], M, K, E);
+        if (!rc) rc = orc_transfer_1d(n, Nf[d], hf[d], Nc[d], hc[d], P[d]);
+        if (!rc) rc = dense_solve(tf[d], tc[d], M, P[d]);
+        free(M); free(K); free(E);
+        if (rc) { for (int e = 0; e <= d; e++) free(P[e]); return -1; }
+    }
+    /* apply P along x, then y, then z */
+    size_t s1 = (size_t)tf[0] * tc[1] * tc[2], s2 = (size_t)tf[0] * tf[1] * tc[2];
+    double* t1 = (double*)calloc(s1, sizeof(double));
+    double* t2 = (double*)calloc(s2, sizeof(double));
+    for (int z = 0; z < tc[2]; z++)
+        for (int y = 0; y < tc[1]; y++)
+            for (int f = 0; f < tf[0]; f++) {
+                double s = 0.0;
+                for (int c = 0; c < tc[0]; c++) s += P[0][(size_t)f * tc[0] + c] * xc[((size_t)z * tc[1] + y) * tc[0] + c];
+                t1[((size_t)z * tc[1] + y) * tf[0] + f] = s;
+            }
+    for (int z = 0; z < tc[2]; z++)
+        for (int f = 0; f < tf[1]; f++)
+            for (int x = 0; x < tf[0]; x++) {
+                double s = 0.0;
+                for (int c = 0; c < tc[1]; c++) s += P[1][(size_t)f * tc[1] + c] * t1[((size_t)z * tc[1] + c) * tf[0] + x];
+                t2[((size_t)z * tf[1] + f) * tf[0] + x] = s;
+            }
+    for (int f = 0; f < tf[2]; f++)
+        for (int y = 0; y < tf[1]; y++)
+            for (int x = 0; x < tf[0]; x++) {
+                double s = 0.0;
+                for (int c = 0; c < tc[2]; c++) s += P[2][(size_t)f * tc[2] + c] * t2[((size_t)c * tf[1] + y) * tf[0] + x];
+                xf[((size_t)f * tf[1] + y) * tf[0] + x] = s;
+            }
+    free(t1); free(t2);
+    for (int d = 0; d < 3; d++) free(P[d]);
     return 0;
 }
