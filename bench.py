@@ -411,6 +411,68 @@ def variable_coefficients():
     return out
 
 
+def robin_large_run(iters: int = 200):
+    """A synthetic analogue of the paper's large run (section 3): 600 x 600 x 2400 unknowns
+    (0.86 G), linear B-splines, Robin boundary penalty, FP64 Jacobi-preconditioned CG, started
+    from a 120 x 120 x 480 solution prolonged to the fine grid. The steady problem here is
+    M + K + pen E (perfusion-like mass term, unit conductivity) with 8 Gaussian heat sources
+    (seed 6); pen = 1e3. Reports the time per PCG iteration, and the residual after a fixed
+    number of iterations from zero and from the prolonged coarse solution (the paper ran a
+    fixed 1000 iterations, in 4 h 4 min on its 24-core CPU)."""
+    import numpy as np
+    import torch
+
+    from paper_1904_03057_gb300 import api, inputs
+    n, pen, dt = 1, 1.0e3, 1.0
+    nt_f, nt_c = (600, 600, 2400), (120, 120, 480)
+    hf = 1.0 / (nt_f[2] - 1)            # box [0, 1] along z: (N + 1) h = 1 with N = nt - 2
+    hc = 1.0 / (nt_c[2] - 1)
+    # the coarse grid covers the same box: (nt_c - 1) hc = (nt_f - 1) hf per axis
+    hcs = tuple((f - 1) * hf / (c - 1) for f, c in zip(nt_f, nt_c))
+    out = {"grid": "600x600x2400", "coarse": "120x120x480", "degree": n, "penalty": pen,
+           "precision": "FP64", "iterations": iters}
+    Hc = api.Handle(*nt_c, n, hcs, dt, precision="f64")
+    Hf = api.Handle(*nt_f, n, hf, dt, precision="f64")
+    for H in (Hc, Hf):
+        H.set_boundary("robin", pen)
+        H.set_preconditioner("jacobi")
+    rng = np.random.default_rng(6)
+    cs = [tuple(rng.uniform(0.2, 0.8, size=3) * np.array([(c - 1) * hf for c in nt_f])) for _ in range(8)]
+
+    def load(H, nt, h3):
+        # a Gaussian field sampled at the B-spline centres (generator nodes are offset by one
+        # step for the linear Robin basis), loaded with the grid's mass matrix
+        q = inputs.gaussian_source(*nt, [(c[0] + h3[0], c[1] + h3[1], c[2] + h3[2]) for c in cs],
+                                   sigma=0.03, h=h3, device="cuda")
+        b = H.mass_apply(q)
+        del q
+        return b
+    bc = load(Hc, nt_c, hcs)
+    xc = torch.zeros(bc.shape, dtype=torch.float64, device="cuda")
+    ms_c, rep_c = _timed_ms(lambda: Hc.cg_solve(bc, xc, tol=1e-8, max_iter=20000))
+    bf = load(Hf, nt_f, (hf, hf, hf))
+    ms_p, x0 = _timed_ms(lambda: api.prolong(Hf, Hc, xc))
+    res = {}
+    for name, start in (("from_zero", None), ("from_coarse", x0)):
+        x = torch.zeros_like(bf) if start is None else start
+        ms, rep = _timed_ms(lambda: Hf.cg_solve(bf, x, tol=1e-14, max_iter=iters))
+        res[name] = {"ms": ms, "iterations": rep["iterations"], "rel_residual": rep["rel_residual"]}
+        del x
+    ms_it = res["from_zero"]["ms"] / max(res["from_zero"]["iterations"], 1)
+    nodes = nt_f[0] * nt_f[1] * nt_f[2]
+    out.update({"coarse_solve": {"ms": ms_c, "iterations": rep_c["iterations"],
+                                 "rel_residual": rep_c["rel_residual"]},
+                "prolong_ms": ms_p, "fine": res, "ms_per_pcg_iteration": ms_it,
+                "gdofs_per_pcg_iteration": nodes / (ms_it * 1e-3) / 1e9,
+                "projected_1000_iterations_s": ms_it * 1000 / 1e3,
+                "paper_1000_iterations_s": 4 * 3600 + 4 * 60})
+    Hf.close()
+    Hc.close()
+    del bf, bc, xc, x0
+    torch.cuda.empty_cache()
+    return out
+
+
 def run_ours(args, rank, world, dist):
     import torch
 
@@ -584,6 +646,7 @@ def run_ours(args, rank, world, dist):
         line["batch_64_boxes"] = batch_64_boxes()
         line["mixed_precision_sphere256"] = mixed_precision_sphere256()
         line["variable_coefficients"] = variable_coefficients()
+        line["robin_large_run"] = robin_large_run()
     if rank == 0 and not args.no_cpu_baseline:
         v, cores, secs, desc = cpu_oracle_sample()
         line["cpu_baseline"] = {"value": v, "unit": "GDoF/s", "cores": cores, "kind": "oracle",
@@ -601,8 +664,8 @@ def main():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-extra-configs", action="store_true",
-                    help="skip the batched (64 boxes), the 256^3 mixed-precision and the "
-                         "variable-coefficient measurements")
+                    help="skip the batched (64 boxes), the 256^3 mixed-precision, the "
+                         "variable-coefficient and the Robin large-run measurements")
     ap.add_argument("--no-fcg-race", action="store_true",
                     help="skip the 512^3 union-of-spheres time-to-1e-8 race (learned FCG vs CG)")
     ap.add_argument("--grid", type=int, default=N_GRID,

@@ -204,6 +204,54 @@ int bsk_residual(bsk_handle* h, const void* b, const void* x, void* r, int fp64,
  * cannot be allocated. */
 int bsk_set_coefficients(bsk_handle* h, const double* d, const double* m);
 
+/* Boundary treatment (Eq. RitzGalerkin, section 2.3; the boundary penalty method of section 3).
+ *   BSK_BC_DIRICHLET  (default) zero Dirichlet faces: the B-splines odd-reflected at the faces
+ *                     (they vanish there); unknown i sits at node i + 1 of an axis of nx + 2 nodes.
+ *   BSK_BC_ROBIN      the boundary penalty method: the untruncated B-splines, every beta(x/h - i)
+ *                     whose support meets the box, with the integrals truncated to the box and
+ *                     the boundary term penalty * integral over the faces of phi psi ds added:
+ *                       A = M + dt K + penalty E,  E = sum over faces of (face values outer
+ *                       product) x (the other two axes' mass),
+ *                     which approximates zero Dirichlet data as penalty grows (the paper's
+ *                     1/(2 gamma)). The handle's nx, ny, nz are then the UNKNOWNS per axis: for a box
+ *                     of N interior nodes (h = box length / (N + 1)) that is N + 2 + 2 floor(n/2),
+ *                     unknown a being the B-spline centred at (a - floor(n/2)) h; every vector of
+ *                     the handle has nx*ny*nz entries in that order. Needs no mask, constant
+ *                     coefficients, and at least 2 (n + 1) unknowns per axis.
+ * The untruncated basis is ill-conditioned for n >= 2 (the outermost B-splines meet the box in a
+ * short interval), and more so for large penalties: the Jacobi preconditioner offsets the first
+ * part. Synchronises the handle's stream. BSK_EINVAL on an unknown kind, a negative or
+ * non-finite penalty, or a handle that does not meet the conditions above. bsk_transform takes
+ * Dirichlet handles only. */
+#define BSK_BC_DIRICHLET 0
+#define BSK_BC_ROBIN 1
+int bsk_set_boundary(bsk_handle* h, int kind, double penalty);
+
+/* Preconditioner of the handle's CG solves (cg_solve, heat_step, and the inner solves of
+ * BSK_F32_IR refinement):
+ *   BSK_PC_NONE    plain CG (default);
+ *   BSK_PC_JACOBI  Jacobi-preconditioned CG, z = r / diag(A) (the solver of the paper's large run,
+ *                  section 3); the diagonal of the separable operator is formed on the fly from
+ *                  per-axis diagonals (with the reflection terms of the Dirichlet basis, or the
+ *                  Robin rows). The CG iteration then takes the two-pass general kernels.
+ * Needs constant coefficients (BSK_EINVAL after bsk_set_coefficients). Synchronises the stream. */
+#define BSK_PC_NONE 0
+#define BSK_PC_JACOBI 1
+int bsk_set_preconditioner(bsk_handle* h, int kind);
+
+/* Coarse-grid initialisation (section 3: the large run starts from a solution computed on a
+ * grid five times coarser): xf = the L2 projection onto the fine handle's Robin basis of the
+ * function sum_c xc_c beta_c of the coarse handle's Robin basis. Both handles: BSK_BC_ROBIN, the
+ * same degree and element type, grids covering the same box (box length = (nx - 1 - 2 floor(n/2)) h
+ * per axis, equal to 1e-12). Per axis the projection is M_f^{-1} T with T_fc the integral over the
+ * box of the product of a fine and a coarse B-spline (exact Gauss quadrature between the
+ * breakpoints of both grids) and M_f the fine Gram matrix (banded Cholesky), applied as three
+ * banded transfer passes and three passes of line solves. Where the coarse space lies in the fine
+ * one (odd degree, coarse step a multiple of the fine step) the function is reproduced exactly.
+ * xc: DEVICE vector of the coarse handle's size, xf: of the fine handle's (not overlapping).
+ * Runs on the fine handle's stream and returns after it is synchronised. */
+int bsk_prolong(bsk_handle* fine, bsk_handle* coarse, const void* xc, void* xf);
+
 /* Floating-point operations per grid node of one operator application (FMA = 2): the
  * algorithmic count of the method as implemented (the seven band convolutions of Fig. FiltAlg
  * for constant coefficients; the per-cell Gauss quadrature with sum factorisation, without

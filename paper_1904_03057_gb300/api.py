@@ -199,12 +199,36 @@ class Handle:
             ptrs.append(f.data_ptr())
         _native.check(self._lib.bsk_set_coefficients(self._ptr, ptrs[0], ptrs[1]))
 
+    def set_boundary(self, kind: str = "dirichlet", penalty: float = 0.0):
+        """'dirichlet' (odd reflection) or 'robin' (untruncated basis with the boundary penalty
+        term; the handle's dimensions are then the unknowns per axis, see robin_size)."""
+        k = {"dirichlet": 0, "robin": 1}[kind]
+        _native.check(self._lib.bsk_set_boundary(self._ptr, k, float(penalty)))
+
+    def set_preconditioner(self, kind: str = "none"):
+        """'none' or 'jacobi' (Jacobi-preconditioned CG)."""
+        k = {"none": 0, "jacobi": 1}[kind]
+        _native.check(self._lib.bsk_set_preconditioner(self._ptr, k))
+
     def op_flops(self):
         """(algorithmic, executed) floating-point operations per node of one operator
         application (bsk_op_flops)."""
         a, e = ctypes.c_double(0.0), ctypes.c_double(0.0)
         _native.check(self._lib.bsk_op_flops(self._ptr, ctypes.byref(a), ctypes.byref(e)))
         return a.value, e.value
+
+
+def robin_size(degree: int, N: int) -> int:
+    """Unknowns per axis of a Robin handle on a box of N interior nodes: N + 2 + 2 floor(n/2)."""
+    return int(N) + 2 + 2 * (int(degree) // 2)
+
+
+def prolong(fine: "Handle", coarse: "Handle", xc: torch.Tensor,
+            xf: Optional[torch.Tensor] = None) -> torch.Tensor:
+    """L2 projection of a coarse Robin expansion onto the fine Robin basis (bsk_prolong)."""
+    xf = fine.empty() if xf is None else xf
+    _native.check(fine._lib.bsk_prolong(fine._ptr, coarse._ptr, coarse._vec(xc, "xc"), fine._vec(xf, "xf")))
+    return xf
 
 
 class BatchHandle:

@@ -15,6 +15,7 @@
 
 #include "bsk.h"
 #include "bsk_launch.h"
+#include "host_bspline.h"
 
 using bsk::Scalars;
 
@@ -148,6 +149,12 @@ struct bsk_handle {
     void* cd[2];
     void* cm[2];
     bool use_tma0, tma640, res_df0;   // TMA eligibility of the constant-coefficient operator
+    int bc;               // BSK_BC_DIRICHLET (odd reflection) or BSK_BC_ROBIN (untruncated basis)
+    double pen;           // Robin: weight of the boundary term
+    void* rb[2];          // Robin: band rows near the faces, float [0] / double [1]
+    int pc;               // BSK_PC_NONE or BSK_PC_JACOBI
+    void* jac[2];         // Jacobi: per-axis diagonals [3][2][jn], float [0] / double [1]
+    int jn;
     float* fcg_ws;        // FCG work vectors z, rn, zn (allocated by the first fcg_solve)
     double* fcg_partials;
     void* fcg_state;
@@ -216,6 +223,11 @@ void fill_launch(const bsk_handle* h, bsk::OpLaunch& L, int mode)
     }
     for (int d = 0; d < 3; d++) L.h[d] = h->h[d];
     L.dt = h->dt;
+    for (int i = 0; i < 2; i++) {
+        L.rb[i] = h->rb[i];
+        L.jac[i] = h->pc ? h->jac[i] : nullptr;
+    }
+    L.jn = h->jn;
 }
 
 template <typename T>
@@ -250,6 +262,7 @@ int init_scalars(bsk_handle* h, Scalars* dev, double tol, int max_iter, int stal
     s.tol2 = tol * tol;
     s.max_iter = max_iter;
     s.stall_window = stall_window;
+    s.pc = h->pc != BSK_PC_NONE;
     // the pinned mirror is reused as the staging buffer: wait for earlier copies out of it
     BSK_CUDA(cudaStreamSynchronize(h->stream));
     *h->h_sc = s;
@@ -352,9 +365,25 @@ int enqueue_chunk(bsk_handle* h, int chunk)
         L.fin = bsk::FIN_CGP;
         L.p_parity = (it + 1) & 1;
         BSK_CUDA(op_launch<T>(L, s));
-        BSK_CUDA(bsk::launch_cg_update<T>(static_cast<T*>(h->r), static_cast<const T*>(h->q),
-                                          h->len, h->sc, h->partials, bsk::FIN_UPD, s));
+        if (h->pc)
+            BSK_CUDA(bsk::launch_cg_update_pc<T>(static_cast<T*>(h->r), static_cast<const T*>(h->q), h->len,
+                                                 h->nx, h->ny, static_cast<const T*>(h->jac[sizeof(T) == 8]),
+                                                 h->jn, h->sc, h->partials, bsk::FIN_UPD_PC, s));
+        else
+            BSK_CUDA(bsk::launch_cg_update<T>(static_cast<T*>(h->r), static_cast<const T*>(h->q),
+                                              h->len, h->sc, h->partials, bsk::FIN_UPD, s));
     }
+    return BSK_OK;
+}
+
+// Preconditioned CG: r.z of the starting residual (after the init kernel has set r and rr).
+template <typename T>
+int pc_start(bsk_handle* h)
+{
+    if (!h->pc) return BSK_OK;
+    BSK_LAUNCH(h, bsk::launch_pc_dot<T>(static_cast<const T*>(h->r), h->len, h->nx, h->ny,
+                                        static_cast<const T*>(h->jac[sizeof(T) == 8]), h->jn, h->sc,
+                                        h->partials, h->stream));
     return BSK_OK;
 }
 
@@ -452,6 +481,7 @@ int cg_plain(bsk_handle* h, const T* b, T* x, const Opts& o, bsk_cg_report* rep,
         L.fin = bsk::FIN_RES_INIT;
         BSK_LAUNCH(h, op_launch<T>(L, h->stream));
     }
+    if ((rc = pc_start<T>(h))) return rc;
     BSK_CUDA(cudaMemsetAsync(h->p0, 0, h->len * sizeof(T), h->stream));
     if (h->use_tma) BSK_CUDA(cudaMemsetAsync(h->q, 0, h->len * sizeof(T), h->stream));
     int iters = 0;
@@ -524,6 +554,7 @@ int cg_ir(bsk_handle* h, const double* b, double* x, const Opts& o, bsk_cg_repor
         BSK_LAUNCH(h, bsk::launch_cg_init_zero<float>(static_cast<const float*>(h->r),
                                                  static_cast<float*>(h->r), static_cast<float*>(h->x),
                                                  h->len, h->mask, h->sc, h->partials, h->stream));
+        if ((rc = pc_start<float>(h))) return rc;
         BSK_CUDA(cudaMemsetAsync(h->p0, 0, h->len * sizeof(float), h->stream));
         if (h->use_tma) BSK_CUDA(cudaMemsetAsync(h->q, 0, h->len * sizeof(float), h->stream));
         int it = 0;
@@ -740,7 +771,8 @@ extern "C" void bsk_destroy(bsk_handle* h)
     cudaStreamSynchronize(h->stream);
     if (h->graph) cudaGraphExecDestroy(h->graph);
     void* ptrs[] = {h->mask, h->occ, h->x, h->r, h->p0, h->p1, h->q, h->bvec, h->r2, h->q2, h->r64, h->b64,
-                    h->sc, h->sc64, h->sc_aux, h->partials, h->work, h->cd[0], h->cd[1], h->cm[0], h->cm[1]};
+                    h->sc, h->sc64, h->sc_aux, h->partials, h->work, h->cd[0], h->cd[1], h->cm[0], h->cm[1],
+                    h->rb[0], h->rb[1], h->jac[0], h->jac[1]};
     for (void* p : ptrs)
         if (p) cudaFree(p);
     if (h->h_sc) cudaFreeHost(h->h_sc);
@@ -755,6 +787,149 @@ extern "C" void bsk_destroy(bsk_handle* h)
     delete h;
 }
 
+namespace {
+
+// Which kernels the handle may use: the TMA kernels implement the constant-coefficient operator
+// with odd reflection only, and the single-pass TMA iteration has no preconditioner. Drops the
+// captured CG graph (its kernels change).
+void refresh_paths(bsk_handle* h)
+{
+    const bool plain = !h->cd[0] && !h->cd[1] && h->bc == BSK_BC_DIRICHLET;
+    h->use_tma = h->use_tma0 && plain && h->pc == BSK_PC_NONE;
+    h->tma64 = h->tma640 && plain;
+    h->res_df = h->res_df0 && plain;
+    if (h->graph) {
+        cudaStreamSynchronize(h->stream);
+        cudaGraphExecDestroy(h->graph);
+        h->graph = nullptr;
+    }
+}
+
+// Integral over [lo, hi] (units of h, ends on the half-integer grid) of f by (n + 1)-point Gauss
+// rules on half-unit pieces: every knot of beta^n and of its integer shifts lies on that grid,
+// so products of two B-splines (degree 2n) are integrated exactly.
+template <typename F>
+double half_unit_integral(double lo, double hi, int n, F f)
+{
+    if (!(hi > lo)) return 0.0;
+    return bsk::host::integrate(lo, hi, (int)std::lround(2.0 * (hi - lo)), n + 1, f);
+}
+
+int dims_of(const bsk_handle* h, int ax) { return ax == 0 ? h->nx : ax == 1 ? h->ny : h->nz; }
+
+// Robin problems: the unknowns of an axis with nt entries are the B-splines beta(x/h - i),
+// i = i0 .. nt - 1 + i0 (i0 = -floor(n/2)), on the box [0, L h], L = nt - 1 + 2 i0: all those whose
+// support meets the box. Band rows of the N + 1 positions nearest each face,
+// [2 (mass, stiffness)][3 axes][2 ends][N + 1][2N + 1]: mass h int beta_a beta_b, stiffness
+// dt / h int beta_a' beta_b' + pen (beta_a beta_b at the two faces), integrals over the box.
+void robin_rows(const bsk_handle* h, std::vector<double>& out)
+{
+    const int n = h->n, NR = n + 1, W = 2 * n + 1, i0 = -(n / 2);
+    const double s = 0.5 * (n + 1);
+    out.assign((size_t)2 * 3 * 2 * NR * W, 0.0);
+    auto at = [&](int m, int ax, int end, int r, int c) -> double& {
+        return out[((((size_t)m * 3 + ax) * 2 + end) * NR + r) * W + c];
+    };
+    for (int ax = 0; ax < 3; ax++) {
+        const int nt = dims_of(h, ax);
+        const double L = nt - 1 + 2 * i0, hh = h->h[ax];
+        for (int end = 0; end < 2; end++)
+            for (int r = 0; r < NR; r++) {
+                const int a = end == 0 ? r : nt - NR + r;
+                const double ia = a + i0;
+                for (int c = 0; c < W; c++) {
+                    const int b = a + c - n;
+                    if (b < 0 || b >= nt) continue;
+                    const double ib = b + i0;
+                    const double lo = std::max(0.0, std::max(ia, ib) - s);
+                    const double hi = std::min(L, std::min(ia, ib) + s);
+                    const double m = half_unit_integral(lo, hi, n, [&](double u) {
+                        return bsk::host::bspline(n, u - ia) * bsk::host::bspline(n, u - ib);
+                    });
+                    const double k = half_unit_integral(lo, hi, n, [&](double u) {
+                        return bsk::host::bspline_deriv(n, u - ia) * bsk::host::bspline_deriv(n, u - ib);
+                    });
+                    const double e = bsk::host::bspline(n, -ia) * bsk::host::bspline(n, -ib) +
+                                     bsk::host::bspline(n, L - ia) * bsk::host::bspline(n, L - ib);
+                    at(0, ax, end, r, c) = hh * m;
+                    at(1, ax, end, r, c) = h->dt * k / hh + h->pen * e;
+                }
+            }
+    }
+}
+
+// Per-axis diagonals of the band matrices, [3 axes][2 (mass, dt-weighted stiffness)][jn]: the
+// diagonal of the separable operator is their product sum (op_generic.cuh, jacobi_inv). With odd
+// reflection a row's own mirror images subtract their taps; Robin rows come from robin_rows.
+void jacobi_diagonals(const bsk_handle* h, const std::vector<double>& rows, std::vector<double>& out)
+{
+    const int n = h->n, NR = n + 1, W = 2 * n + 1;
+    out.assign((size_t)6 * h->jn, 1.0);
+    for (int ax = 0; ax < 3; ax++) {
+        const int nt = dims_of(h, ax);
+        for (int pos = 0; pos < nt; pos++) {
+            double dm = h->M[ax][n], dk = h->dt * h->K[ax][n];
+            if (h->bc == BSK_BC_ROBIN) {
+                int end = -1, r = 0;
+                if (pos < NR) { end = 0; r = pos; }
+                else if (pos >= nt - NR) { end = 1; r = pos - (nt - NR); }
+                if (end >= 0) {
+                    dm = rows[((((size_t)0 * 3 + ax) * 2 + end) * NR + r) * W + n];
+                    dk = rows[((((size_t)1 * 3 + ax) * 2 + end) * NR + r) * W + n];
+                }
+            } else {
+                for (int img : {-2 - pos, 2 * nt - pos}) {
+                    const int off = img - pos;
+                    if (off >= -n && off <= n) {
+                        dm -= h->M[ax][n + off];
+                        dk -= h->dt * h->K[ax][n + off];
+                    }
+                }
+            }
+            out[((size_t)ax * 2 + 0) * h->jn + pos] = dm;
+            out[((size_t)ax * 2 + 1) * h->jn + pos] = dk;
+        }
+    }
+}
+
+// Copies v into dst[0] (float) and dst[1] (double), allocating them on first use.
+int upload_both(const std::vector<double>& v, void** dst)
+{
+    std::vector<float> f(v.begin(), v.end());
+    const size_t bytes[2] = {v.size() * sizeof(float), v.size() * sizeof(double)};
+    const void* src[2] = {f.data(), v.data()};
+    for (int i = 0; i < 2; i++) {
+        if (!dst[i]) {
+            cudaError_t e = cudaMalloc(&dst[i], bytes[i]);
+            if (e != cudaSuccess) {
+                cudaGetLastError();
+                return fail(BSK_ENOMEM, "table allocation failed");
+            }
+        }
+        BSK_CUDA(cudaMemcpy(dst[i], src[i], bytes[i], cudaMemcpyHostToDevice));
+    }
+    return BSK_OK;
+}
+
+// Rebuilds the Robin rows and Jacobi diagonals after a change of boundary, dt or preconditioner.
+int refresh_tables(bsk_handle* h)
+{
+    BSK_CUDA(cudaStreamSynchronize(h->stream));
+    std::vector<double> rows;
+    if (h->bc == BSK_BC_ROBIN) {
+        robin_rows(h, rows);
+        if (int rc = upload_both(rows, h->rb)) return rc;
+    }
+    if (h->pc == BSK_PC_JACOBI) {
+        std::vector<double> dg;
+        jacobi_diagonals(h, rows, dg);
+        if (int rc = upload_both(dg, h->jac)) return rc;
+    }
+    return BSK_OK;
+}
+
+}  // namespace
+
 extern "C" int bsk_set_dt(bsk_handle* h, double dt)
 {
     if (int rc = check_handle(h)) return rc;
@@ -765,13 +940,50 @@ extern "C" int bsk_set_dt(bsk_handle* h, double dt)
         h->graph = nullptr;
     }
     h->dt = dt;
+    if (h->bc == BSK_BC_ROBIN || h->pc) return refresh_tables(h);   // their rows carry dt too
     return BSK_OK;
+}
+
+extern "C" int bsk_set_boundary(bsk_handle* h, int kind, double penalty)
+{
+    if (int rc = check_handle(h)) return rc;
+    if (kind != BSK_BC_DIRICHLET && kind != BSK_BC_ROBIN) return fail(BSK_EINVAL, "unknown boundary kind %d", kind);
+    if (kind == BSK_BC_ROBIN) {
+        if (!(penalty >= 0) || !std::isfinite(penalty)) return fail(BSK_EINVAL, "penalty must be finite and >= 0");
+        if (h->mask) return fail(BSK_EINVAL, "the Robin boundary is defined on the whole box (no mask)");
+        if (h->cd[0] || h->cd[1]) return fail(BSK_EINVAL, "variable coefficients take the Dirichlet boundary");
+        if (h->prec == BSK_BF16S) return fail(BSK_EINVAL, "the BF16-storage variant has the Dirichlet boundary only");
+        for (int ax = 0; ax < 3; ax++)
+            if (dims_of(h, ax) < 2 * (h->n + 1))
+                return fail(BSK_EINVAL, "a Robin axis needs at least 2 (degree + 1) unknowns");
+    }
+    h->bc = kind;
+    h->pen = kind == BSK_BC_ROBIN ? penalty : 0.0;
+    refresh_paths(h);
+    return refresh_tables(h);
+}
+
+extern "C" int bsk_set_preconditioner(bsk_handle* h, int kind)
+{
+    if (int rc = check_handle(h)) return rc;
+    if (kind != BSK_PC_NONE && kind != BSK_PC_JACOBI) return fail(BSK_EINVAL, "unknown preconditioner %d", kind);
+    if (kind == BSK_PC_JACOBI && (h->cd[0] || h->cd[1]))
+        return fail(BSK_EINVAL, "the Jacobi preconditioner needs constant coefficients (separable diagonal)");
+    if (kind == BSK_PC_JACOBI && h->prec == BSK_BF16S) return fail(BSK_EINVAL, "BF16 storage has no solver");
+    h->pc = kind;
+    h->jn = std::max(h->nx, std::max(h->ny, h->nz));
+    refresh_paths(h);
+    return refresh_tables(h);
 }
 
 extern "C" int bsk_set_coefficients(bsk_handle* h, const double* d, const double* m)
 {
     if (int rc = check_handle(h)) return rc;
     if (h->prec == BSK_BF16S) return fail(BSK_EINVAL, "the BF16-storage variant has constant coefficients only");
+    if ((d || m) && h->bc == BSK_BC_ROBIN)
+        return fail(BSK_EINVAL, "variable coefficients take the Dirichlet boundary");
+    if ((d || m) && h->pc == BSK_PC_JACOBI)
+        return fail(BSK_EINVAL, "the Jacobi preconditioner needs constant coefficients");
     // the captured CG graph holds the kernels of the previous operator
     BSK_CUDA(cudaStreamSynchronize(h->stream));
     if (h->graph) {
@@ -784,9 +996,7 @@ extern "C" int bsk_set_coefficients(bsk_handle* h, const double* d, const double
             if (h->cm[i]) cudaFree(h->cm[i]);
             h->cd[i] = h->cm[i] = nullptr;
         }
-        h->use_tma = h->use_tma0;
-        h->tma64 = h->tma640;
-        h->res_df = h->res_df0;
+        refresh_paths(h);
         return BSK_OK;
     }
     const size_t clen = (size_t)(h->nx + 2) * (h->ny + 2) * (h->nz + 2);
@@ -814,7 +1024,7 @@ extern "C" int bsk_set_coefficients(bsk_handle* h, const double* d, const double
     }
     // every pass takes the general path, where launch_op dispatches to the variable-coefficient
     // kernel (the right-hand-side mass of heat_step stays the constant mass matrix)
-    h->use_tma = h->tma64 = h->res_df = false;
+    refresh_paths(h);
     BSK_CUDA(cudaStreamSynchronize(h->stream));
     return BSK_OK;
 }
@@ -1234,6 +1444,7 @@ bool sampled_basis_cholesky(int n, int N, std::vector<double>& out)
 extern "C" int bsk_transform(bsk_handle* h, int direction, const void* in, void* out)
 {
     if (int rc = check_handle(h)) return rc;
+    if (h->bc == BSK_BC_ROBIN) return fail(BSK_EINVAL, "the transforms take the Dirichlet (reflected) basis");
     if (!in || !out) return fail(BSK_EINVAL, "null vector");
     if (direction != BSK_TO_SAMPLES && direction != BSK_TO_COEFFS)
         return fail(BSK_EINVAL, "unknown transform direction %d", direction);
@@ -1289,6 +1500,188 @@ extern "C" int bsk_transform(bsk_handle* h, int direction, const void* in, void*
                                                            static_cast<const float*>(h->tr_L[d]), h->stream));
         }
     return BSK_OK;
+}
+
+// ---- coarse-to-fine prolongation of Robin problems --------------------------------------------
+
+namespace {
+
+// 1-D transfer between the Robin bases of a fine and a coarse grid on the same interval [0, L]:
+// T[f][c] = int_0^L beta(x/hf - if) beta(x/hc - ic) dx for the coarse columns c0[f] .. c0[f]+w-1
+// whose supports meet that of fine function f. Between consecutive breakpoints of either grid (the
+// half-multiples of hf and of hc) the integrand is one polynomial of degree 2n, integrated exactly
+// by n + 1 Gauss points.
+void transfer_1d(int n, int ntf, double hf, int ntc, double hc, std::vector<double>& tab, std::vector<int>& c0,
+                 int& w)
+{
+    const int i0 = -(n / 2);
+    const double s = 0.5 * (n + 1), L = (ntf - 1 + 2 * i0) * hf;
+    std::vector<int> lo(ntf, 0), hi(ntf, 0);
+    w = 1;
+    for (int f = 0; f < ntf; f++) {
+        const double xf = (f + i0) * hf;
+        int cl = ntc, ch = -1;
+        for (int c = 0; c < ntc; c++)
+            if (std::fabs(xf - (c + i0) * hc) < s * (hf + hc)) {
+                cl = std::min(cl, c);
+                ch = std::max(ch, c);
+            }
+        if (ch < cl) cl = ch = 0;
+        lo[f] = cl;
+        hi[f] = ch;
+        w = std::max(w, ch - cl + 1);
+    }
+    tab.assign((size_t)ntf * w, 0.0);
+    c0 = lo;
+    double xi[16], wt[16];
+    bsk::host::gauss_unit(n + 1, xi, wt);
+    std::vector<double> br;
+    for (int f = 0; f < ntf; f++) {
+        const double xf = (f + i0) * hf;
+        for (int c = lo[f]; c <= hi[f]; c++) {
+            const double xc = (c + i0) * hc;
+            const double a = std::max(0.0, std::max(xf - s * hf, xc - s * hc));
+            const double b = std::min(L, std::min(xf + s * hf, xc + s * hc));
+            if (!(b > a)) continue;
+            br.assign({a, b});
+            for (double step : {0.5 * hf, 0.5 * hc})
+                for (long long k = (long long)std::ceil(a / step); k * step < b; k++)
+                    if (k * step > a) br.push_back(k * step);
+            std::sort(br.begin(), br.end());
+            double acc = 0.0;
+            for (size_t j = 0; j + 1 < br.size(); j++) {
+                const double p0 = br[j], len = br[j + 1] - br[j];
+                if (!(len > 1e-15 * L)) continue;
+                for (int g = 0; g <= n; g++) {
+                    const double x = p0 + len * xi[g];
+                    acc += len * wt[g] * bsk::host::bspline(n, x / hf - (f + i0)) * bsk::host::bspline(n, x / hc - (c + i0));
+                }
+            }
+            tab[(size_t)f * w + (c - lo[f])] = acc;
+        }
+    }
+}
+
+// Banded Cholesky factor of the 1-D Robin Gram matrix of one axis (half-width n): interior rows the
+// shift-invariant mass kernel, the N + 1 rows at each end from robin_rows. Row j of the output is
+// { 1 / L[j][j], L[j][j-1], ..., L[j][j-n] }. False if not positive definite.
+bool robin_gram_cholesky(const bsk_handle* h, int ax, const std::vector<double>& rows, std::vector<double>& out)
+{
+    const int n = h->n, nt = dims_of(h, ax), NR = n + 1, W = 2 * n + 1, w = n + 1;
+    auto Mab = [&](int a, int b) -> double {   // |a - b| <= n
+        const int c = b - a + n;
+        if (a < NR) return rows[((((size_t)0 * 3 + ax) * 2 + 0) * NR + a) * W + c];
+        if (a >= nt - NR) return rows[((((size_t)0 * 3 + ax) * 2 + 1) * NR + (a - (nt - NR))) * W + c];
+        return h->M[ax][c];
+    };
+    std::vector<double> Lf((size_t)nt * w, 0.0);
+    auto Lat = [&](int j, int k) -> double& { return Lf[(size_t)j * w + (j - k)]; };
+    for (int j = 0; j < nt; j++)
+        for (int k = std::max(0, j - n); k <= j; k++) {
+            double sum = Mab(j, k);
+            for (int m = std::max(0, j - n); m < k; m++)
+                if (m >= k - n) sum -= Lat(j, m) * Lat(k, m);
+            if (k == j) {
+                if (!(sum > 0.0)) return false;
+                Lat(j, j) = std::sqrt(sum);
+            } else {
+                Lat(j, k) = sum / Lat(k, k);
+            }
+        }
+    out.assign((size_t)nt * w, 0.0);
+    for (int j = 0; j < nt; j++) {
+        out[(size_t)j * w] = 1.0 / Lat(j, j);
+        for (int k = 1; k <= n && j - k >= 0; k++) out[(size_t)j * w + k] = Lat(j, j - k);
+    }
+    return true;
+}
+
+template <typename T>
+int prolong_impl(bsk_handle* fh, bsk_handle* ch, const T* xc, T* xf)
+{
+    const int n = fh->n;
+    std::vector<double> rows;
+    robin_rows(fh, rows);
+    int nf[3], nc[3], w[3];
+    std::vector<void*> dev;
+    auto cleanup = [&]() {
+        cudaStreamSynchronize(fh->stream);
+        for (void* p : dev) cudaFree(p);
+    };
+    auto put = [&](const void* src, size_t bytes) -> void* {
+        void* d = nullptr;
+        if (cudaMalloc(&d, bytes) != cudaSuccess) {
+            cudaGetLastError();
+            return nullptr;
+        }
+        dev.push_back(d);
+        if (src && cudaMemcpy(d, src, bytes, cudaMemcpyHostToDevice) != cudaSuccess) return nullptr;
+        return d;
+    };
+    T* tab[3];
+    int* c0d[3];
+    T* Ld[3];
+    for (int ax = 0; ax < 3; ax++) {
+        nf[ax] = dims_of(fh, ax);
+        nc[ax] = dims_of(ch, ax);
+        std::vector<double> t, lr;
+        std::vector<int> c0;
+        transfer_1d(n, nf[ax], fh->h[ax], nc[ax], ch->h[ax], t, c0, w[ax]);
+        if (!robin_gram_cholesky(fh, ax, rows, lr)) {
+            cleanup();
+            return fail(BSK_EINVAL, "the fine Gram matrix is not positive definite");
+        }
+        std::vector<T> tt(t.begin(), t.end()), ll(lr.begin(), lr.end());
+        tab[ax] = static_cast<T*>(put(tt.data(), tt.size() * sizeof(T)));
+        c0d[ax] = static_cast<int*>(put(c0.data(), c0.size() * sizeof(int)));
+        Ld[ax] = static_cast<T*>(put(ll.data(), ll.size() * sizeof(T)));
+        if (!tab[ax] || !c0d[ax] || !Ld[ax]) {
+            cleanup();
+            return fail(BSK_ENOMEM, "prolongation tables");
+        }
+    }
+    T* t1 = static_cast<T*>(put(nullptr, (size_t)nf[0] * nc[1] * nc[2] * sizeof(T)));
+    T* t2 = static_cast<T*>(put(nullptr, (size_t)nf[0] * nf[1] * nc[2] * sizeof(T)));
+    if (!t1 || !t2) {
+        cleanup();
+        return fail(BSK_ENOMEM, "prolongation work arrays");
+    }
+    cudaStream_t s = fh->stream;
+    cudaError_t e = bsk::launch_transfer<T>(xc, t1, nc[0], nc[1], nc[2], 0, nf[0], w[0], tab[0], c0d[0], s);
+    if (e == cudaSuccess) e = bsk::launch_transfer<T>(t1, t2, nf[0], nc[1], nc[2], 1, nf[1], w[1], tab[1], c0d[1], s);
+    if (e == cudaSuccess) e = bsk::launch_transfer<T>(t2, xf, nf[0], nf[1], nc[2], 2, nf[2], w[2], tab[2], c0d[2], s);
+    for (int ax = 0; ax < 3 && e == cudaSuccess; ax++)
+        e = bsk::launch_band_solve<T>(xf, nf[0], nf[1], nf[2], ax, n, Ld[ax], s);
+    fh->launches += 6;
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    cleanup();
+    if (e != cudaSuccess) return cuda_fail(e, "prolongation");
+    return BSK_OK;
+}
+
+}  // namespace
+
+extern "C" int bsk_prolong(bsk_handle* fine, bsk_handle* coarse, const void* xc, void* xf)
+{
+    if (int rc = check_handle(fine)) return rc;
+    if (int rc = check_handle(coarse)) return rc;
+    if (!xc || !xf) return fail(BSK_EINVAL, "null vector");
+    if (fine->bc != BSK_BC_ROBIN || coarse->bc != BSK_BC_ROBIN)
+        return fail(BSK_EINVAL, "bsk_prolong takes two Robin handles");
+    if (fine->n != coarse->n) return fail(BSK_EINVAL, "the two handles have different degrees");
+    if (user_es(fine) != user_es(coarse)) return fail(BSK_EINVAL, "the two handles have different element types");
+    const int i0 = -(fine->n / 2);
+    for (int ax = 0; ax < 3; ax++) {
+        const double lf = (dims_of(fine, ax) - 1 + 2 * i0) * fine->h[ax];
+        const double lc = (dims_of(coarse, ax) - 1 + 2 * i0) * coarse->h[ax];
+        if (!(std::fabs(lf - lc) <= 1e-12 * lf)) return fail(BSK_EINVAL, "the two grids cover different boxes");
+    }
+    // the coarse handle's stream must be done with xc before the fine stream reads it
+    BSK_CUDA(cudaStreamSynchronize(coarse->stream));
+    fine->launches = 0;
+    return user_es(fine) == sizeof(double)
+               ? prolong_impl<double>(fine, coarse, static_cast<const double*>(xc), static_cast<double*>(xf))
+               : prolong_impl<float>(fine, coarse, static_cast<const float*>(xc), static_cast<float*>(xf));
 }
 
 extern "C" int bsk_residual(bsk_handle* h, const void* b, const void* x, void* r, int fp64, double* rr,

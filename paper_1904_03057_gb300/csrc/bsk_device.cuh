@@ -25,6 +25,8 @@ enum Fin : int {
     FIN_UPD = 4,        // rr_new = s0 -> beta, convergence, iteration count
     FIN_NORM = 5,       // rr_true = s0
     FIN_CG1 = 6,        // single-pass CG: s0 = r.r, s1 = p.Ap, s2 = Ap.Ap -> alpha, beta, status
+    FIN_PC_INIT = 7,    // preconditioned CG start: rz = s0 (r.z, z = r / diag A)
+    FIN_UPD_PC = 8,     // preconditioned update: rr_new = s0 (convergence), rz_new = s1 -> beta
 };
 
 // Operator kernel modes.
@@ -60,6 +62,8 @@ struct Scalars {
     int zero_b;         // b == 0: the solution is x = 0
     unsigned int counter;  // arrival counter of the last-block reduction
     int pass;           // single-pass CG: passes completed (pass m produces x_m, r_m)
+    double rz;          // preconditioned CG: r.z of the current residual (z = r / diag A)
+    int pc;             // non-zero: Jacobi-preconditioned CG (alpha and beta from rz)
 };
 
 // Per-axis kernels in compute precision: M[d][j + n], K[d][j + n] with K already scaled by dt.
@@ -149,14 +153,19 @@ __device__ __forceinline__ void finalize(Scalars* sc, int fin, double s0, double
             sc->alpha = 0.0;
             sc->alpha_prev = 0.0;
         } else {
-            sc->alpha = sc->rr / s0;
+            sc->alpha = (sc->pc ? sc->rz : sc->rr) / s0;
             sc->alpha_prev = sc->alpha;
         }
         break;
-    case FIN_UPD: {
+    case FIN_PC_INIT:
+        sc->rz = s0;
+        if (!isfinite(s0)) { sc->done = 1; sc->status = -5; }
+        break;
+    case FIN_UPD:
+    case FIN_UPD_PC: {
         const double rr_new = s0;
         sc->iter += 1;
-        if (!isfinite(rr_new)) { sc->done = 1; sc->status = -5; break; }
+        if (!isfinite(rr_new) || (fin == FIN_UPD_PC && !isfinite(s1))) { sc->done = 1; sc->status = -5; break; }
         if (rr_new <= sc->tol2 * sc->bb) { sc->done = 1; sc->status = 0; }
         else if (sc->iter >= sc->max_iter) { sc->done = 1; sc->status = 1; }
         else if (rr_new < sc->best_rr) { sc->best_rr = rr_new; sc->since_best = 0; }
@@ -164,7 +173,12 @@ __device__ __forceinline__ void finalize(Scalars* sc, int fin, double s0, double
             sc->done = 1;
             sc->status = 2;
         }
-        sc->beta = rr_new / sc->rr;
+        if (fin == FIN_UPD_PC) {
+            sc->beta = s1 / sc->rz;
+            sc->rz = s1;
+        } else {
+            sc->beta = rr_new / sc->rr;
+        }
         sc->rr = rr_new;
         break;
     }

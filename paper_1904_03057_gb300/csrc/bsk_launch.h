@@ -43,6 +43,13 @@ struct OpLaunch {
     const void* vm[2];
     double h[3];                 // grid steps (variable-coefficient tables)
     double dt;                   // weight of the diffusion term (variable coefficients)
+    // Robin problems: band rows near the faces (op_generic.cuh, robin_row), float [0] / double
+    // [1]; null = odd reflection at the faces
+    const void* rb[2];
+    // MODE_CGP: Jacobi diagonal factors (op_generic.cuh, jacobi_inv), float [0] / double [1];
+    // null = no preconditioner
+    const void* jac[2];
+    int jn;                      // row length of the jac tables
 };
 
 // Grid of the operator kernel for a problem; partial-sum buffers hold 2 doubles per block.
@@ -76,6 +83,20 @@ cudaError_t launch_coef_fill(const double* src, T* dst, size_t len, cudaStream_t
 template <typename T>
 cudaError_t launch_cg_update(T* r, const T* q, size_t len, Scalars* sc, double* partials,
                              int fin, cudaStream_t s);
+// Jacobi-preconditioned CG (vec_kernels.cuh): r -= alpha q with r.r and r.z (FIN_UPD_PC), and
+// the starting r.z (FIN_PC_INIT).
+template <typename T>
+cudaError_t launch_cg_update_pc(T* r, const T* q, size_t len, int nx, int ny, const T* jac, int jn,
+                                Scalars* sc, double* partials, int fin, cudaStream_t s);
+template <typename T>
+cudaError_t launch_pc_dot(const T* r, size_t len, int nx, int ny, const T* jac, int jn, Scalars* sc,
+                          double* partials, cudaStream_t s);
+// Banded transfer along one axis (transform.cu): out[.., f, ..] = sum_k T[f][k] in[.., c0[f] + k, ..]
+// for f < nout, the other two extents unchanged (dims are those of `in`, x fastest).
+template <typename T>
+cudaError_t launch_transfer(const T* in, T* out, int nx, int ny, int nz, int axis, int nout, int w,
+                            const T* tab, const int* c0, cudaStream_t s);
+
 template <typename T>
 cudaError_t launch_cg_flush(T* x, const T* p0, const T* p1, size_t len, const Scalars* sc,
                             cudaStream_t s);
@@ -109,7 +130,7 @@ struct TmaLaunch {
     int fin;
 };
 // In-place banded triangular solves along one axis (0 = x, 1 = y, 2 = z) of an nx*ny*nz grid,
-// one thread per line: L holds the Cholesky factor of the axis's sampled basis (transform.cu).
+// one thread per line: L holds a banded Cholesky factor of half-width p <= 5 (transform.cu).
 template <typename T>
 cudaError_t launch_band_solve(T* d, int nx, int ny, int nz, int axis, int p, const T* L, cudaStream_t s);
 

@@ -23,8 +23,13 @@ static Coef<T> make_coef(const OpLaunch& L)
 template <typename T, int N, int MODE>
 static cudaError_t set_smem_attr()
 {
-    return cudaFuncSetAttribute(k_op_generic<T, N, MODE>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                (int)generic_smem_bytes<T, N>());
+    cudaError_t e = cudaFuncSetAttribute(k_op_generic<T, N, MODE, false>,
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)generic_smem_bytes<T, N>());
+    if (e == cudaSuccess)
+        e = cudaFuncSetAttribute(k_op_generic<T, N, MODE, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 (int)generic_smem_bytes<T, N>());
+    return e;
 }
 
 template <typename T, int N>
@@ -62,7 +67,11 @@ static cudaError_t launch_generic(const OpLaunch& L, cudaStream_t s)
     a.fin = L.fin;
     a.p_parity = L.p_parity;
     a.bf16io = L.bf16io;
-    k_op_generic<T, N, MODE><<<grid, kGenNT, smem, s>>>(a);
+    a.rb = static_cast<const T*>(L.rb[sizeof(T) == 8]);
+    a.jac = MODE == MODE_CGP ? static_cast<const T*>(L.jac[sizeof(T) == 8]) : nullptr;
+    a.jn = L.jn;
+    if (a.rb) k_op_generic<T, N, MODE, true><<<grid, kGenNT, smem, s>>>(a);
+    else k_op_generic<T, N, MODE, false><<<grid, kGenNT, smem, s>>>(a);
     return cudaGetLastError();
 }
 
@@ -110,6 +119,22 @@ cudaError_t launch_cg_update<BSK_T>(BSK_T* r, const BSK_T* q, size_t len, Scalar
                                     double* partials, int fin, cudaStream_t s)
 {
     k_cg_update<BSK_T><<<vec_grid(len), kVecNT, 0, s>>>(r, q, len, sc, partials, fin);
+    return cudaGetLastError();
+}
+
+template <>
+cudaError_t launch_cg_update_pc<BSK_T>(BSK_T* r, const BSK_T* q, size_t len, int nx, int ny, const BSK_T* jac,
+                                       int jn, Scalars* sc, double* partials, int fin, cudaStream_t s)
+{
+    k_cg_update_pc<BSK_T><<<vec_grid(len), kVecNT, 0, s>>>(r, q, len, nx, ny, jac, jn, sc, partials, fin);
+    return cudaGetLastError();
+}
+
+template <>
+cudaError_t launch_pc_dot<BSK_T>(const BSK_T* r, size_t len, int nx, int ny, const BSK_T* jac, int jn,
+                                 Scalars* sc, double* partials, cudaStream_t s)
+{
+    k_pc_dot<BSK_T><<<vec_grid(len), kVecNT, 0, s>>>(r, len, nx, ny, jac, jn, sc, partials);
     return cudaGetLastError();
 }
 

@@ -36,7 +36,44 @@ struct OpArgs {
     int fin;
     int p_parity;
     int bf16io;       // FP32, OP / MASS: in0, in1 and out0 are bfloat16 arrays (BF16 storage)
+    const T* rb;      // Robin problems: band rows near the faces (robin_row), null otherwise
+    const T* jac;     // CGP: Jacobi diagonal factors (jacobi_inv), null = no preconditioner
+    int jn;           // row length of jac
 };
+
+// Robin (boundary penalty) problems use the untruncated basis with integrals truncated to the
+// box, so the 1-D band matrices differ from the shift-invariant kernels in the first and last
+// N + 1 rows of each axis. rb holds those rows: [2 (mass, stiffness + penalty)][3 axes][2 ends]
+// [N + 1 rows][2N + 1 taps], the stiffness rows already weighted by dt and including the face
+// term penalty * (beta_a beta_b at the face). Returns the row of axis ax at position pos, or null
+// where the shift-invariant taps apply (and for positions outside the grid).
+template <typename T, int N>
+__device__ __forceinline__ const T* robin_row(const T* rb, int m, int ax, int pos, int len)
+{
+    constexpr int NR = N + 1, W = 2 * N + 1;
+    int end, row;
+    if (pos < NR) {
+        end = 0;
+        row = pos;
+    } else if (pos >= len - NR && pos < len) {
+        end = 1;
+        row = pos - (len - NR);
+    } else {
+        return nullptr;
+    }
+    return rb + ((((size_t)m * 3 + ax) * 2 + end) * NR + row) * W;
+}
+
+// 1 / diag(A) at node (x, y, z) from the per-axis diagonals of the band matrices:
+// jac = [3 axes][2 (mass, stiffness incl. dt and penalty)][jn], so that
+// diag = mz my mx + kz my mx + mz ky mx + mz my kx (the diagonal of the separable operator).
+template <typename T>
+__device__ __forceinline__ T jacobi_inv(const T* j, int jn, int x, int y, int z)
+{
+    const T mx = j[x], kx = j[jn + x], my = j[2 * jn + y], ky = j[3 * jn + y];
+    const T mz = j[4 * jn + z], kz = j[5 * jn + z];
+    return T(1) / (mz * my * (mx + kx) + (kz * my + mz * ky) * mx);
+}
 
 // Element o of an input / output array that holds T, or bfloat16 when bf (FP32 kernels only).
 template <typename T>
@@ -66,7 +103,7 @@ constexpr size_t generic_smem_bytes()
     return sizeof(T) * (size_t)(L * HY * HX + 2 * HY * HX + 2 * kGenTY * HX);
 }
 
-template <typename T, int N, int MODE>
+template <typename T, int N, int MODE, bool RB>
 __global__ void __launch_bounds__(kGenNT) k_op_generic(const __grid_constant__ OpArgs<T> a)
 {
     constexpr int L = 2 * N + 1;
@@ -99,20 +136,33 @@ __global__ void __launch_bounds__(kGenNT) k_op_generic(const __grid_constant__ O
     auto load_plane = [&](int gz) {
         T* dst = ring + ((gz - zbase) % L) * (HY * HX);
         int sz = 0;
-        const int sgz = reflect_index(gz, nz, sz);
+        int sgz;
+        if (RB) {
+            sz = gz;
+            sgz = (unsigned)gz < (unsigned)nz;
+        } else {
+            sgz = reflect_index(gz, nz, sz);
+        }
         for (int i = tid; i < HY * HX; i += NT) {
             const int hy = i / HX, hx = i - hy * HX;
             const int gy = y0 - N + hy, gx = x0 - N + hx;
             int sy = 0, sx = 0;
             int s = sgz;
-            if (s) s *= reflect_index(gy, ny, sy);
-            if (s) s *= reflect_index(gx, nx, sx);
+            if (RB) {   // no reflection: the basis does not vanish on the faces, ghosts are zero
+                sy = gy;
+                sx = gx;
+                s = s && (unsigned)gy < (unsigned)ny && (unsigned)gx < (unsigned)nx;
+            } else {
+                if (s) s *= reflect_index(gy, ny, sy);
+                if (s) s *= reflect_index(gx, nx, sx);
+            }
             T v = T(0);
             if (s) {
                 const size_t o = ((size_t)sz * ny + sy) * nx + sx;
                 if (!mask || mask[o]) {
                     T u;
-                    if (MODE == MODE_CGP) u = a.in0[o] + beta * a.in1[o];
+                    if (MODE == MODE_CGP)
+                        u = (a.jac ? a.in0[o] * jacobi_inv(a.jac, a.jn, sx, sy, sz) : a.in0[o]) + beta * a.in1[o];
                     else if (MODE == MODE_MASS)
                         u = ld_io(a.in0, o, a.bf16io) + (a.in1 ? (T)a.s * ld_io(a.in1, o, a.bf16io) : T(0));
                     else if (MODE == MODE_OP) u = ld_io(a.in0, o, a.bf16io);
@@ -131,13 +181,15 @@ __global__ void __launch_bounds__(kGenNT) k_op_generic(const __grid_constant__ O
         load_plane(z + N);
         __syncthreads();
         // z-sweep on the (TY + 2N) x (TX + 2N) halo tile
+        const T* rzm = RB ? robin_row<T, N>(a.rb, 0, 2, z, nz) : nullptr;
+        const T* rzk = RB ? robin_row<T, N>(a.rb, 1, 2, z, nz) : nullptr;
         for (int i = tid; i < HY * HX; i += NT) {
             T P = T(0), Q = T(0);
 #pragma unroll
             for (int c = 0; c < L; c++) {
                 const T v = ring[((z - N + c - zbase) % L) * (HY * HX) + i];
-                P = fma(a.c.M[2][c], v, P);
-                if (!MASS_ONLY) Q = fma(a.c.K[2][c], v, Q);
+                P = fma(RB && rzm ? rzm[c] : a.c.M[2][c], v, P);
+                if (!MASS_ONLY) Q = fma(RB && rzk ? rzk[c] : a.c.K[2][c], v, Q);
             }
             sP[i] = P;
             if (!MASS_ONLY) sQ[i] = Q;
@@ -146,14 +198,17 @@ __global__ void __launch_bounds__(kGenNT) k_op_generic(const __grid_constant__ O
         // y-sweep on the TY x (TX + 2N) tile
         for (int i = tid; i < TY * HX; i += NT) {
             const int ty = i / HX, hx = i - ty * HX;
+            const T* rym = RB ? robin_row<T, N>(a.rb, 0, 1, y0 + ty, ny) : nullptr;
+            const T* ryk = RB ? robin_row<T, N>(a.rb, 1, 1, y0 + ty, ny) : nullptr;
             T A = T(0), B = T(0);
 #pragma unroll
             for (int b = 0; b < L; b++) {
                 const T pv = sP[(ty + b) * HX + hx];
-                A = fma(a.c.M[1][b], pv, A);
+                const T my = RB && rym ? rym[b] : a.c.M[1][b];
+                A = fma(my, pv, A);
                 if (!MASS_ONLY) {
-                    B = fma(a.c.K[1][b], pv, B);
-                    B = fma(a.c.M[1][b], sQ[(ty + b) * HX + hx], B);
+                    B = fma(RB && ryk ? ryk[b] : a.c.K[1][b], pv, B);
+                    B = fma(my, sQ[(ty + b) * HX + hx], B);
                 }
             }
             sA[i] = A;
@@ -165,14 +220,17 @@ __global__ void __launch_bounds__(kGenNT) k_op_generic(const __grid_constant__ O
             const int ty = i / TX, tx = i - ty * TX;
             const int gy = y0 + ty, gx = x0 + tx;
             if (gx >= nx || gy >= ny) continue;
+            const T* rxm = RB ? robin_row<T, N>(a.rb, 0, 0, gx, nx) : nullptr;
+            const T* rxk = RB ? robin_row<T, N>(a.rb, 1, 0, gx, nx) : nullptr;
             T y = T(0);
 #pragma unroll
             for (int c = 0; c < L; c++) {
+                const T mx = RB && rxm ? rxm[c] : a.c.M[0][c];
                 if (MASS_ONLY) {
-                    y = fma(a.c.M[0][c], sA[ty * HX + tx + c], y);
+                    y = fma(mx, sA[ty * HX + tx + c], y);
                 } else {
-                    y = fma(a.c.M[0][c], sS[ty * HX + tx + c], y);
-                    y = fma(a.c.K[0][c], sA[ty * HX + tx + c], y);
+                    y = fma(mx, sS[ty * HX + tx + c], y);
+                    y = fma(RB && rxk ? rxk[c] : a.c.K[0][c], sA[ty * HX + tx + c], y);
                 }
             }
             const size_t o = ((size_t)z * ny + gy) * nx + gx;

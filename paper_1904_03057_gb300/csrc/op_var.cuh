@@ -19,8 +19,9 @@
 //       D, mu), x-pass to the Q points of each x cell, point fluxes dt D grad u and mu u times
 //       the quadrature weight, and the transposed x-pass into the TT output columns (Xa, Xb,
 //       Xc), all on rolling register windows;
-//   DE  one thread per output column: transposed y-pass, then transposed z-pass into N + 1
-//       plane accumulators; the oldest plane is complete after its last cell and is written.
+//   D   one thread per (output column, quad plane): transposed y-pass;
+//   E   one thread per output column: transposed z-pass into N + 1 plane accumulators; the
+//       oldest plane is complete after its last cell and is written.
 // The epilogue fuses the same CG vector work as the constant-coefficient kernels (residual,
 // search-direction update, deferred x update, reductions).
 #pragma once
@@ -79,15 +80,18 @@ struct VarCfg {
     static constexpr int C = TT + N;              // cells per axis
     static constexpr int QC = Q * C;              // quad points per axis
     static constexpr int R = Q * QC;              // rows of stage BC per z-cell
-    static constexpr int XP = TT + 1;             // padded row of the X buffers: consecutive
-                                                  // rows (threads) fall in different banks
+    // X buffers are stored column-major, [field][qz][lx][RP]: the BC threads (consecutive rows)
+    // store contiguously, and with RP = 2 (mod 32) the D warps (16 columns x 2 rows Q apart)
+    // read 32 distinct banks
+    static constexpr int RP = (QC + 29) / 32 * 32 + 2;
     static constexpr int PASSES = (R + 511) / 512;
     static constexpr int NT0 = ((R + PASSES - 1) / PASSES + 31) / 32 * 32;
     static constexpr int NT = NT0 < 64 ? 64 : NT0;
     static constexpr int NPT = (TT * TT + NT - 1) / NT;   // output columns per thread
     static constexpr size_t smem =
-        sizeof(T) * ((size_t)3 * (N + 1) * H * H + (size_t)4 * Q * H * H + (size_t)3 * Q * QC * XP);
+        sizeof(T) * ((size_t)3 * (N + 1) * H * H + (size_t)4 * Q * H * H + (size_t)3 * Q * TT * RP);
     static_assert(smem <= 227 * 1024, "variable-coefficient tile exceeds shared memory");
+    static_assert(2 * Q * TT * TT <= 4 * Q * H * H, "the y-transposed planes reuse the quad planes");
 };
 
 // Coefficient node after even reflection across the faces at nodes 0 and n + 1. Positions more
@@ -104,12 +108,12 @@ __global__ void __launch_bounds__(VarCfg<T, N>::NT, 1) k_op_var(const __grid_con
 {
     using Cfg = VarCfg<T, N>;
     constexpr int Q = Cfg::Q, NB = N + 1, TT = Cfg::TT, H = Cfg::H, C = Cfg::C, QC = Cfg::QC;
-    constexpr int NT = Cfg::NT, R = Cfg::R, NPT = Cfg::NPT, XP = Cfg::XP;
-    constexpr int HH = H * H, XS = Q * QC * XP;   // plane size, stride between X fields
+    constexpr int NT = Cfg::NT, R = Cfg::R, NPT = Cfg::NPT, RP = Cfg::RP;
+    constexpr int HH = H * H, XS = Q * TT * RP;   // plane size, stride between X fields
     extern __shared__ __align__(16) unsigned char smem_raw[];
     T* ring = reinterpret_cast<T*>(smem_raw);   // [N + 1][3][HH]: c, d, m per node plane
     T* sZ = ring + (N + 1) * 3 * HH;            // [Q][4][HH]: cB, cD, dB, mB
-    T* sX = sZ + Q * 4 * HH;                    // [3][Q][QC][XP]: Xa, Xb, Xc
+    T* sX = sZ + Q * 4 * HH;                    // [3][Q][TT][RP]: Xa, Xb, Xc
 
     const int tid = threadIdx.x;
     const int nx = a.g.nx, ny = a.g.ny, nz = a.g.nz;
@@ -233,7 +237,7 @@ __global__ void __launch_bounds__(VarCfg<T, N>::NT, 1) k_op_var(const __grid_con
             for (int f = 0; f < 3; f++)
 #pragma unroll
                 for (int t = 0; t < NB; t++) xo[f][t] = T(0);
-            T* xrow = sX + (size_t)(qz * QC + yq) * XP;
+            T* xrow = sX + (size_t)qz * TT * RP + yq;   // column lx at xrow[lx * RP]
             // unrolled by the window length, the window shifts below are register renames
 #pragma unroll NB
             for (int cx = 0; cx < C; cx++) {
@@ -271,9 +275,9 @@ __global__ void __launch_bounds__(VarCfg<T, N>::NT, 1) k_op_var(const __grid_con
                 // output cx - N has now received all its cells
                 const int lx = cx - N;
                 if (lx >= 0 && lx < TT) {
-                    xrow[lx] = xo[0][0];
-                    xrow[XS + lx] = xo[1][0];
-                    xrow[2 * XS + lx] = xo[2][0];
+                    xrow[lx * RP] = xo[0][0];
+                    xrow[XS + lx * RP] = xo[1][0];
+                    xrow[2 * XS + lx * RP] = xo[2][0];
                 }
 #pragma unroll
                 for (int f = 0; f < 3; f++) {
@@ -288,25 +292,35 @@ __global__ void __launch_bounds__(VarCfg<T, N>::NT, 1) k_op_var(const __grid_con
             }
         }
         __syncthreads();
-        // ---- DE: transposed y- and z-passes per output column ----
+        // ---- D: transposed y-pass per (output column, quad plane), all threads; the results go
+        // to sY, which reuses sZ (read for the last time in BC) ----
+        T* sY = sZ;   // [2][Q][TT * TT]: Ya, Yc
+        for (int i = tid; i < Q * TT * TT; i += NT) {
+            const int qz = i / (TT * TT), node = i - qz * (TT * TT);
+            const int ly = node / TT, lx = node - ly * TT;
+            T Ya = T(0), Yc = T(0);
+#pragma unroll
+            for (int t = 0; t < NB; t++) {
+                const T* xa = sX + ((size_t)qz * TT + lx) * RP + (ly + N - t) * Q;
+#pragma unroll
+                for (int qy = 0; qy < Q; qy++) {
+                    const T b = a.t.B[qy][t], d = a.t.D[1][qy][t];
+                    Ya = fma(b, xa[qy], fma(d, xa[XS + qy], Ya));
+                    Yc = fma(b, xa[2 * XS + qy], Yc);
+                }
+            }
+            sY[i] = Ya;
+            sY[Q * TT * TT + i] = Yc;
+        }
+        __syncthreads();
+        // ---- E: transposed z-pass into the plane accumulators of each output column ----
 #pragma unroll
         for (int k = 0; k < NPT; k++) {
             const int node = tid + k * NT;
             if (node < TT * TT) {
-                const int ly = node / TT, lx = node - ly * TT;
 #pragma unroll
                 for (int qz = 0; qz < Q; qz++) {
-                    T Ya = T(0), Yc = T(0);
-#pragma unroll
-                    for (int t = 0; t < NB; t++) {
-                        const T* xa = sX + (size_t)(qz * QC + (ly + N - t) * Q) * XP + lx;
-#pragma unroll
-                        for (int qy = 0; qy < Q; qy++) {
-                            const T b = a.t.B[qy][t], d = a.t.D[1][qy][t];
-                            Ya = fma(b, xa[qy * XP], fma(d, xa[XS + qy * XP], Ya));
-                            Yc = fma(b, xa[2 * XS + qy * XP], Yc);
-                        }
-                    }
+                    const T Ya = sY[qz * TT * TT + node], Yc = sY[(Q + qz) * TT * TT + node];
 #pragma unroll
                     for (int t = 0; t < NB; t++)
                         acc[k][t] = fma(a.t.B[qz][t], Ya, fma(a.t.D[2][qz][t], Yc, acc[k][t]));

@@ -6,61 +6,11 @@
 #include <cmath>
 
 #include "bsk_launch.h"
+#include "host_bspline.h"
 #include "op_var.cuh"
 
 namespace bsk {
 namespace {
-
-// Centred B-spline beta^n(x) from its truncated-power form
-// beta^n(x) = (1/n!) sum_k (-1)^k C(n+1, k) (x + (n+1)/2 - k)_+^n (Table tblBsplines).
-double bspline_real(int n, double x)
-{
-    double s = 0.0, binom = 1.0, fact = 1.0;
-    for (int i = 2; i <= n; i++) fact *= i;
-    for (int k = 0; k <= n + 1; k++) {
-        const double t = x + 0.5 * (n + 1) - k;
-        if (t > 0.0) s += ((k & 1) ? -binom : binom) * std::pow(t, n);
-        binom = binom * (n + 1 - k) / (k + 1);
-    }
-    return s / fact;
-}
-
-// beta^n'(x) = beta^{n-1}(x + 1/2) - beta^{n-1}(x - 1/2) (Table tblBsplines, derivative row).
-double bspline_real_deriv(int n, double x)
-{
-    return bspline_real(n - 1, x + 0.5) - bspline_real(n - 1, x - 0.5);
-}
-
-// Gauss-Legendre rule of q points on [0, 1]: Newton iteration on the three-term recurrence of
-// the Legendre polynomials, weights 2 / ((1 - x^2) P_q'(x)^2), mapped from [-1, 1].
-void gauss_unit(int q, double* xi, double* w)
-{
-    const double pi = 3.14159265358979323846;
-    for (int i = 0; i < q; i++) {
-        double x = std::cos(pi * (i + 0.75) / (q + 0.5)), dp = 1.0;
-        for (int it = 0; it < 100; it++) {
-            double p0 = 1.0, p1 = x;
-            for (int k = 2; k <= q; k++) {
-                const double p2 = ((2.0 * k - 1.0) * x * p1 - (k - 1.0) * p0) / k;
-                p0 = p1;
-                p1 = p2;
-            }
-            dp = q * (x * p1 - p0) / (x * x - 1.0);
-            const double dx = p1 / dp;
-            x -= dx;
-            if (std::fabs(dx) < 1e-16) break;
-        }
-        double p0 = 1.0, p1 = x;
-        for (int k = 2; k <= q; k++) {
-            const double p2 = ((2.0 * k - 1.0) * x * p1 - (k - 1.0) * p0) / k;
-            p0 = p1;
-            p1 = p2;
-        }
-        dp = q * (x * p1 - p0) / (x * x - 1.0);
-        xi[i] = 0.5 * (1.0 - x);
-        w[i] = 1.0 / ((1.0 - x * x) * dp * dp);
-    }
-}
 
 // Tables of one cell: local coordinate xi in [0, 1] of a knot interval; the cell's n + 1
 // B-splines are centred at offsets lo + t (lo = -floor(n/2)) from the interval's reference
@@ -72,13 +22,13 @@ VarTabs<T> make_tabs(int n, const double h[3])
     double xi[kVarMaxQ], w[kVarMaxQ];
     const int q = (3 * n + 2) / 2, lo = -(n / 2);
     const double o = (n & 1) ? 0.0 : -0.5;
-    gauss_unit(q, xi, w);
+    host::gauss_unit(q, xi, w);
     for (int g = 0; g < q; g++) {
         tb.w[g] = (T)w[g];
         for (int t = 0; t <= n; t++) {
             const double u = o + xi[g] - lo - t;
-            tb.B[g][t] = (T)bspline_real(n, u);
-            const double du = bspline_real_deriv(n, u);
+            tb.B[g][t] = (T)host::bspline(n, u);
+            const double du = host::bspline_deriv(n, u);
             for (int ax = 0; ax < 3; ax++) tb.D[ax][g][t] = (T)(du / h[ax]);
         }
     }

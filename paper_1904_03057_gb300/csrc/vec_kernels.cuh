@@ -48,6 +48,76 @@ __global__ void __launch_bounds__(kVecNT) k_cg_update(T* __restrict__ r, const T
     grid_reduce2<kVecNT>(acc.value(), 0.0, partials, sc, fin, 0);
 }
 
+// Compensated running sum of arbitrary terms: Kahan in FP32 for float kernels, plain FP64 for
+// double kernels (widened once per thread for the grid reduction).
+template <typename T>
+struct TermSum {
+    double s = 0.0;
+    __device__ __forceinline__ void add(T v) { s += (double)v; }
+    __device__ __forceinline__ double value() const { return s; }
+};
+template <>
+struct TermSum<float> {
+    float s = 0.f, c = 0.f;
+    __device__ __forceinline__ void add(float v)
+    {
+        const float y = __fsub_rn(v, c);
+        const float t = __fadd_rn(s, y);
+        c = __fsub_rn(__fsub_rn(t, s), y);
+        s = t;
+    }
+    __device__ __forceinline__ double value() const { return (double)s - (double)c; }
+};
+
+// Jacobi factors of flat index i of an nx * ny * nz grid (op_generic.cuh, jacobi_inv).
+template <typename T>
+__device__ __forceinline__ T jacobi_inv_flat(const T* jac, int jn, size_t i, int nx, int ny)
+{
+    const size_t xy = (size_t)nx * ny;
+    const int z = (int)(i / xy);
+    const size_t rem = i - (size_t)z * xy;
+    const int y = (int)(rem / nx), x = (int)(rem - (size_t)y * nx);
+    const T mx = jac[x], kx = jac[jn + x], my = jac[2 * jn + y], ky = jac[3 * jn + y];
+    const T mz = jac[4 * jn + z], kz = jac[5 * jn + z];
+    return T(1) / (mz * my * (mx + kx) + (kz * my + mz * ky) * mx);
+}
+
+// Preconditioned CG residual pass: r -= alpha q; reductions r.r (convergence) and r.z with
+// z = r / diag A (Jacobi); finaliser FIN_UPD_PC.
+template <typename T>
+__global__ void __launch_bounds__(kVecNT) k_cg_update_pc(T* __restrict__ r, const T* __restrict__ q,
+                                                         size_t len, int nx, int ny, const T* __restrict__ jac,
+                                                         int jn, Scalars* sc, double* partials, int fin)
+{
+    if (*(volatile int*)&sc->done) return;
+    const T alpha = (T)sc->alpha;
+    SqSum<T> rr;
+    TermSum<T> rz;
+    for (size_t i = blockIdx.x * (size_t)kVecNT + threadIdx.x; i < len;
+         i += (size_t)gridDim.x * kVecNT) {
+        const T v = fma(-alpha, q[i], r[i]);
+        r[i] = v;
+        rr.add(v);
+        rz.add(v * v * jacobi_inv_flat(jac, jn, i, nx, ny));
+    }
+    grid_reduce2<kVecNT>(rr.value(), rz.value(), partials, sc, fin, 0);
+}
+
+// r.z with z = r / diag A: the starting value of the preconditioned iteration (FIN_PC_INIT).
+template <typename T>
+__global__ void __launch_bounds__(kVecNT) k_pc_dot(const T* __restrict__ r, size_t len, int nx, int ny,
+                                                   const T* __restrict__ jac, int jn, Scalars* sc,
+                                                   double* partials)
+{
+    TermSum<T> rz;
+    for (size_t i = blockIdx.x * (size_t)kVecNT + threadIdx.x; i < len;
+         i += (size_t)gridDim.x * kVecNT) {
+        const T v = r[i];
+        rz.add(v * v * jacobi_inv_flat(jac, jn, i, nx, ny));
+    }
+    grid_reduce2<kVecNT>(rz.value(), 0.0, partials, sc, FIN_PC_INIT, 0);
+}
+
 // x += alpha_prev p[p_cur]: applies the last deferred update once the iteration has stopped.
 template <typename T>
 __global__ void __launch_bounds__(kVecNT) k_cg_flush(T* __restrict__ x, const T* __restrict__ p0,
