@@ -39,8 +39,8 @@ WORKLOAD = "heat3d_928cube_cubic_f32sweeps_f64refinement"
 # dram__bytes_write.sum over the unknowns of the launch), from the ncu capture summarised in
 # profiles/k_op_tma_cg_f32_928cube_dram.md; valid only while the kernel's sources hash to
 # CG_TRAFFIC_SOURCES_SHA256.
-CG_TRAFFIC_BYTES_PER_UNKNOWN = 37.98   # 928^3, three launches: 17.60 GB read + 12.76 GB written
-CG_TRAFFIC_SOURCES_SHA256 = "d65b6c4b6e4c6cf1025fd273330d4b4509edb382f29da12f3fef2b15bbbb1e9d"
+CG_TRAFFIC_BYTES_PER_UNKNOWN = 38.03   # 928^3, three launches: 17.63 GB read + 12.76 GB written
+CG_TRAFFIC_SOURCES_SHA256 = "bba51d31b6ab9701861aedcaf7dd3aed5ad91567ed43c4f534c0eec6a6b364fd"
 CG_KERNEL_SOURCES = ("op_tma.cuh", "tma_impl.cuh", "tma_util.cuh", "bsk_device.cuh", "tma_f32.cu", "dfloat.cuh")
 
 
@@ -473,6 +473,26 @@ def robin_large_run(iters: int = 200):
     return out
 
 
+def profile_case(name: str):
+    """Small cases for the profiler: `var240` runs the variable-coefficient operator (cubic, FP32,
+    240 x 240 x 960, the inclusion fields of `variable_coefficients`) three times."""
+    import torch
+
+    from paper_1904_03057_gb300 import api, inputs
+    if name != "var240":
+        raise ValueError(name)
+    nx, ny, nz = 240, 240, 960
+    h = 1.0 / 961
+    H = api.Handle(nx, ny, nz, 3, h, 5e-4, precision="f32")
+    d = inputs.inclusion_coefficients(nx, ny, nz, seed=7, h=h, device="cuda")
+    m = 1.0 + 0.5 * inputs.inclusion_coefficients(nx, ny, nz, seed=8, h=h, base=0.3, device="cuda")
+    H.set_coefficients(d, m)
+    x = inputs.random_field((nz, ny, nx), 9, device="cuda", dtype=torch.float32)
+    y = torch.empty_like(x)
+    ms = [_timed_ms(lambda: H.op_apply(x, y))[0] for _ in range(3)]
+    print(json.dumps({"profile_case": name, "ms": ms, "max_abs_y": float(y.abs().max())}), flush=True)
+
+
 def run_ours(args, rank, world, dist):
     import torch
 
@@ -671,7 +691,12 @@ def main():
     ap.add_argument("--grid", type=int, default=N_GRID,
                     help="grid edge (default: the benchmark workload; smaller grids are the "
                          "profiler's small case)")
+    ap.add_argument("--profile-case", choices=["var240"], default=None,
+                    help="run one small case for the profiler instead of the benchmark")
     args = ap.parse_args()
+    if args.profile_case:
+        profile_case(args.profile_case)
+        return
     if args.grid < 16 or args.grid % 4:
         ap.error("--grid must be a multiple of 4 (16-byte FP32 rows for the TMA kernels), >= 16")
     world = int(os.environ.get("WORLD_SIZE", "1"))
