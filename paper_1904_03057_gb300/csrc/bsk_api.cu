@@ -1035,11 +1035,13 @@ extern "C" int bsk_op_flops(bsk_handle* h, double* algorithmic, double* executed
     const int n = h->n;
     double alg, exe;
     if (h->cd[0] || h->cd[1]) {
-        // per node of an unbounded tile: z-pass 4(n+1) FMA per quad plane, y-pass 5(n+1) FMA per
-        // (qz, qy) node, x-pass 10(n+1) FMA + 8 products per quad point, transposed y- and
-        // z-passes 3 Q (n+1) + 2 (n+1) FMA per quad plane
+        // per node of an unbounded tile: z-pass 4(n+1) FMA per quad plane, y-pass 5(n+1) FMA + 2
+        // products per (qz, qy) node, x-pass 10(n+1) FMA + 4 products per quad point, transposed
+        // y- and z-passes 3 Q (n+1) + 2 (n+1) FMA per quad plane
+        // (degrees <= 3 fold the quadrature weights: 2 products per y node, 4 per point; else 0, 8)
         const double q = (3 * n + 2) / 2, nb = n + 1;
-        alg = 2.0 * q * 4 * nb + 2.0 * q * q * 5 * nb + q * q * q * (2.0 * 10 * nb + 8) +
+        const double ny_prod = n <= 3 ? 2 : 0, pt_prod = n <= 3 ? 4 : 8;
+        alg = 2.0 * q * 4 * nb + q * q * (2.0 * 5 * nb + ny_prod) + q * q * q * (2.0 * 10 * nb + pt_prod) +
               2.0 * q * (3.0 * q * nb + 2 * nb);
         exe = cg_es(h) == sizeof(double) ? bsk::var_flops_per_node<double>(n, h->nx, h->ny, h->nz)
                                          : bsk::var_flops_per_node<float>(n, h->nx, h->ny, h->nz);

@@ -38,6 +38,8 @@ struct VarTabs {
     T B[kVarMaxQ][kMaxDeg + 1];       // beta^n at Gauss point q for local basis t of the cell
     T D[3][kVarMaxQ][kMaxDeg + 1];    // beta^n' / h_axis (physical derivative), axis 0 = x
     T w[kVarMaxQ];                    // Gauss weights on the unit cell
+    T Bw[kVarMaxQ][kMaxDeg + 1];      // w[q] B[q][t]: the transposed x-pass carries the x weight
+    T Dxw[kVarMaxQ][kMaxDeg + 1];     // w[q] D[0][q][t]
 };
 
 template <typename T>
@@ -68,7 +70,7 @@ constexpr int var_q() { return (3 * N + 2) / 2; }
 template <typename T, int N>
 constexpr int var_tile()
 {
-    if (sizeof(T) == 4) return N <= 3 ? 16 : 8;
+    if (sizeof(T) == 4) return N <= 3 ? 16 : N == 4 ? 12 : 10;
     return N == 1 ? 16 : N == 2 ? 12 : N <= 4 ? 8 : 4;
 }
 
@@ -88,6 +90,9 @@ struct VarCfg {
     static constexpr int NT0 = ((R + PASSES - 1) / PASSES + 31) / 32 * 32;
     static constexpr int NT = NT0 < 64 ? 64 : NT0;
     static constexpr int NPT = (TT * TT + NT - 1) / NT;   // output columns per thread
+    // quadrature weights folded into the y-passed fields and the transposed x tables (4 instead
+    // of 8 products per point); above degree 3 the extra live values spill, so it is left out
+    static constexpr bool FOLD = N <= 3;
     static constexpr size_t smem =
         sizeof(T) * ((size_t)3 * (N + 1) * H * H + (size_t)4 * Q * H * H + (size_t)3 * Q * TT * RP);
     static_assert(smem <= 227 * 1024, "variable-coefficient tile exceeds shared memory");
@@ -109,6 +114,7 @@ __global__ void __launch_bounds__(VarCfg<T, N>::NT, 1) k_op_var(const __grid_con
     using Cfg = VarCfg<T, N>;
     constexpr int Q = Cfg::Q, NB = N + 1, TT = Cfg::TT, H = Cfg::H, C = Cfg::C, QC = Cfg::QC;
     constexpr int NT = Cfg::NT, R = Cfg::R, NPT = Cfg::NPT, RP = Cfg::RP;
+    constexpr bool FOLD = Cfg::FOLD;
     constexpr int HH = H * H, XS = Q * TT * RP;   // plane size, stride between X fields
     extern __shared__ __align__(16) unsigned char smem_raw[];
     T* ring = reinterpret_cast<T*>(smem_raw);   // [N + 1][3][HH]: c, d, m per node plane
@@ -223,6 +229,10 @@ __global__ void __launch_bounds__(VarCfg<T, N>::NT, 1) k_op_var(const __grid_con
                     v[3] = fma(by[t], zq[2 * HH + k], v[3]);
                     v[4] = fma(by[t], zq[3 * HH + k], v[4]);
                 }
+                if (FOLD) {   // the y and z weights (and dt) of the row's points, once per node
+                    v[3] *= wyzdt;
+                    v[4] *= wyz;
+                }
             };
             T win[5][NB];   // y-passed node values of the current x cell: nodes cx .. cx + N
             T xo[3][NB];    // transposed x-pass accumulators of outputs cx - N .. cx
@@ -260,16 +270,22 @@ __global__ void __launch_bounds__(VarCfg<T, N>::NT, 1) k_op_var(const __grid_con
                         Dv = fma(bx, win[3][t], Dv);
                         Mv = fma(bx, win[4][t], Mv);
                     }
-                    const T wq = a.t.w[qx];
-                    const T G = (wq * wyzdt) * Dv;       // dt D times the point weight
-                    const T S = (wq * wyz) * (Mv * U);   // mu u times the point weight
+                    // point fluxes dt D grad u and mu u times the point weight; with FOLD the y, z
+                    // weights are already in Dv, Mv and the x weight is in the Bw, Dxw tables
+                    T G = Dv, S = Mv * U;
+                    if (!FOLD) {
+                        const T wq = a.t.w[qx];
+                        G = (wq * wyzdt) * Dv;
+                        S = (wq * wyz) * S;
+                    }
                     const T Fx = G * Ux, Fy = G * Uy, Fz = G * Uz;
 #pragma unroll
                     for (int t = 0; t < NB; t++) {
-                        const T bx = a.t.B[qx][t], dx = a.t.D[0][qx][t];
-                        xo[0][t] = fma(dx, Fx, fma(bx, S, xo[0][t]));
-                        xo[1][t] = fma(bx, Fy, xo[1][t]);
-                        xo[2][t] = fma(bx, Fz, xo[2][t]);
+                        const T bw = FOLD ? a.t.Bw[qx][t] : a.t.B[qx][t];
+                        const T dw = FOLD ? a.t.Dxw[qx][t] : a.t.D[0][qx][t];
+                        xo[0][t] = fma(dw, Fx, fma(bw, S, xo[0][t]));
+                        xo[1][t] = fma(bw, Fy, xo[1][t]);
+                        xo[2][t] = fma(bw, Fz, xo[2][t]);
                     }
                 }
                 // output cx - N has now received all its cells

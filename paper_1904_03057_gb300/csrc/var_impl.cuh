@@ -27,9 +27,11 @@ VarTabs<T> make_tabs(int n, const double h[3])
         tb.w[g] = (T)w[g];
         for (int t = 0; t <= n; t++) {
             const double u = o + xi[g] - lo - t;
-            tb.B[g][t] = (T)host::bspline(n, u);
-            const double du = host::bspline_deriv(n, u);
+            const double b = host::bspline(n, u), du = host::bspline_deriv(n, u);
+            tb.B[g][t] = (T)b;
             for (int ax = 0; ax < 3; ax++) tb.D[ax][g][t] = (T)(du / h[ax]);
+            tb.Bw[g][t] = (T)(w[g] * b);
+            tb.Dxw[g][t] = (T)(w[g] * du / h[0]);
         }
     }
     return tb;
@@ -175,9 +177,11 @@ double var_flops_per_node<BSK_T>(int degree, int nx, int ny, int nz)
 {
     // floating-point operations the kernel executes per output node (FMA = 2), counting the
     // recomputed halo cells of each block: z-pass 4(n+1) FMA per halo node and quad plane;
-    // BC 5(n+1) FMA per y-pass node, 10(n+1) FMA + 8 products per x quad point;
+    // BC 5(n+1) FMA (+ 2 products with folded weights) per y-pass node, 10(n+1) FMA + 4 (folded)
+    // or 8 products per x quad point;
     // DE 3 Q (n+1) FMA per output column and quad plane plus 2(n+1) per z-transpose.
     const int n = degree, q = (3 * n + 2) / 2, nb = n + 1;
+    const double ny_prod = n <= 3 ? 2 : 0, pt_prod = n <= 3 ? 4 : 8;   // VarCfg::FOLD
     int tile = 0;
     switch (degree) {
     case 1: tile = VarCfg<BSK_T, 1>::TT; break;
@@ -188,8 +192,8 @@ double var_flops_per_node<BSK_T>(int degree, int nx, int ny, int nz)
     }
     const double H = tile + 2 * n, C = tile + n, QC = q * C;
     const double per_cell = 2.0 * (q * H * H * 4 * nb)                        // A
-                            + 2.0 * (q * QC * H * 5 * nb)                      // BC y-pass
-                            + q * QC * C * q * (2.0 * 10 * nb + 8)             // BC x-pass
+                            + q * QC * H * (2.0 * 5 * nb + ny_prod)            // BC y-pass
+                            + q * QC * C * q * (2.0 * 10 * nb + pt_prod)       // BC x-pass
                             + 2.0 * tile * tile * q * (3.0 * q * nb + 2 * nb); // DE
     int tz = 0;
     const dim3 g = var_grid_t<BSK_T>(degree, nx, ny, nz, &tz);
