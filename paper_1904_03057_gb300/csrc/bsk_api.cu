@@ -1,7 +1,9 @@
 // bsk_api.cu -- the C ABI declared in include/bsk.h: kernel tables, solver handles, the CG
-// driver (device-resident iteration in CUDA graphs, host polling), iterative refinement and
-// implicit Euler stepping. Every arithmetic step of the path runs in the kernels of
-// kernels_f32.cu / kernels_f64.cu; this file only validates, allocates and sequences.
+// loop (device-resident iteration in CUDA graphs, host polling), iterative refinement,
+// implicit Euler stepping, boundary and preconditioner set-up and the coarse-to-fine
+// prolongation. Every arithmetic step of the path runs in the library's kernels; this file
+// computes the small host tables (kernels, band rows, quadrature), validates, allocates and
+// sequences.
 #include <algorithm>
 #include <vector>
 #include <chrono>

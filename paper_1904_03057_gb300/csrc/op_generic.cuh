@@ -72,7 +72,7 @@ __device__ __forceinline__ T jacobi_inv(const T* j, int jn, int x, int y, int z)
 {
     const T mx = j[x], kx = j[jn + x], my = j[2 * jn + y], ky = j[3 * jn + y];
     const T mz = j[4 * jn + z], kz = j[5 * jn + z];
-    return T(1) / (mz * my * (mx + kx) + (kz * my + mz * ky) * mx);
+    return recip_pc(mz * my * (mx + kx) + (kz * my + mz * ky) * mx);
 }
 
 // Element o of an input / output array that holds T, or bfloat16 when bf (FP32 kernels only).

@@ -96,6 +96,9 @@ struct VarCfg {
     static constexpr size_t smem =
         sizeof(T) * ((size_t)3 * (N + 1) * H * H + (size_t)4 * Q * H * H + (size_t)3 * Q * TT * RP);
     static_assert(smem <= 227 * 1024, "variable-coefficient tile exceeds shared memory");
+    // blocks per SM the register allocation must allow: two where two FP32 blocks' shared memory
+    // fits (the FP64 kernels are bound by the FP64 pipe; capping their registers only spills)
+    static constexpr int MINB = sizeof(T) == 4 && 2 * (smem + 1024) <= 228 * 1024 ? 2 : 1;
     static_assert(2 * Q * TT * TT <= 4 * Q * H * H, "the y-transposed planes reuse the quad planes");
 };
 
@@ -109,7 +112,7 @@ __device__ __forceinline__ int coef_node(int e, int n)
 }
 
 template <typename T, int N, int MODE>
-__global__ void __launch_bounds__(VarCfg<T, N>::NT, 1) k_op_var(const __grid_constant__ VarArgs<T> a)
+__global__ void __launch_bounds__(VarCfg<T, N>::NT, VarCfg<T, N>::MINB) k_op_var(const __grid_constant__ VarArgs<T> a)
 {
     using Cfg = VarCfg<T, N>;
     constexpr int Q = Cfg::Q, NB = N + 1, TT = Cfg::TT, H = Cfg::H, C = Cfg::C, QC = Cfg::QC;
@@ -139,12 +142,18 @@ __global__ void __launch_bounds__(VarCfg<T, N>::NT, 1) k_op_var(const __grid_con
     const int cpx = nx + 2, cpy = ny + 2;
     auto slot = [&](int gz) { return ring + ((gz - pz0) % (N + 1)) * (3 * HH); };
 
-    auto load_plane = [&](int gz) {
-        T* dst = slot(gz);
+    // One node plane of the halo tile (solution value, D, mu_a) into registers, and from there
+    // into its ring slot. The next plane is fetched before the long stages of the current cell
+    // and stored at the start of the next one, so its loads are in flight meanwhile.
+    constexpr int PRE = (HH + NT - 1) / NT;
+    auto fetch_plane = [&](int gz, T (&pv)[PRE][3]) {
         int sz = 0;
         const int sgz = reflect_index(gz, nz, sz);
         const size_t ez = (size_t)coef_node(gz + 1, nz) * cpy;
-        for (int i = tid; i < HH; i += NT) {
+#pragma unroll
+        for (int k = 0; k < PRE; k++) {
+            const int i = tid + k * NT;
+            if (i >= HH) break;
             const int hy = i / H, hx = i - hy * H;
             const int gy = y0 - N + hy, gx = x0 - N + hx;
             int sy = 0, sx = 0;
@@ -154,19 +163,36 @@ __global__ void __launch_bounds__(VarCfg<T, N>::NT, 1) k_op_var(const __grid_con
             T v = T(0);
             if (s) {
                 const size_t o = ((size_t)sz * ny + sy) * nx + sx;
-                if (!mask || mask[o]) {
-                    const T u = MODE == MODE_CGP ? a.in0[o] + beta * a.in1[o] : a.in0[o];
-                    v = s > 0 ? u : -u;
-                }
+                const T u = MODE == MODE_CGP ? a.in0[o] + beta * a.in1[o] : a.in0[o];
+                v = (mask && !mask[o]) ? T(0) : (s > 0 ? u : -u);
             }
-            dst[i] = v;
             const size_t e = (ez + coef_node(gy + 1, ny)) * cpx + coef_node(gx + 1, nx);
-            dst[HH + i] = a.d[e];
-            dst[2 * HH + i] = a.m[e];
+            pv[k][0] = v;
+            pv[k][1] = a.d[e];
+            pv[k][2] = a.m[e];
+        }
+    };
+    auto store_plane = [&](int gz, const T (&pv)[PRE][3]) {
+        T* dst = slot(gz);
+#pragma unroll
+        for (int k = 0; k < PRE; k++) {
+            const int i = tid + k * NT;
+            if (i >= HH) break;
+            dst[i] = pv[k][0];
+            dst[HH + i] = pv[k][1];
+            dst[2 * HH + i] = pv[k][2];
         }
     };
 
-    for (int gz = pz0; gz < pz0 + N; gz++) load_plane(gz);
+    // prefetching pays for FP32 from degree 3 up (1 %); for FP64 the values held across the
+    // stages spill
+    constexpr bool PREFETCH = N >= 3 && sizeof(T) == 4;
+    T pre[PRE][3];
+    for (int gz = pz0; gz < pz0 + N; gz++) {
+        fetch_plane(gz, pre);
+        store_plane(gz, pre);
+    }
+    if (PREFETCH) fetch_plane(pz0 + N, pre);
 
     T acc[NPT][NB];
 #pragma unroll
@@ -179,8 +205,10 @@ __global__ void __launch_bounds__(VarCfg<T, N>::NT, 1) k_op_var(const __grid_con
     for (int kc = 0; kc < ncells; kc++) {
         const int pz = pz0 + kc;   // plane of local basis 0 of this z-cell
         __syncthreads();           // the previous epilogue read the slot reloaded here
-        load_plane(pz + N);
+        if (!PREFETCH) fetch_plane(pz + N, pre);
+        store_plane(pz + N, pre);
         __syncthreads();
+        if (PREFETCH && kc + 1 < ncells) fetch_plane(pz + N + 1, pre);
         // ---- A: z-pass on the halo tile ----
         for (int i = tid; i < Q * HH; i += NT) {
             const int qz = i / HH, k = i - qz * HH;

@@ -79,7 +79,7 @@ __device__ __forceinline__ T jacobi_inv_flat(const T* jac, int jn, size_t i, int
     const int y = (int)(rem / nx), x = (int)(rem - (size_t)y * nx);
     const T mx = jac[x], kx = jac[jn + x], my = jac[2 * jn + y], ky = jac[3 * jn + y];
     const T mz = jac[4 * jn + z], kz = jac[5 * jn + z];
-    return T(1) / (mz * my * (mx + kx) + (kz * my + mz * ky) * mx);
+    return recip_pc(mz * my * (mx + kx) + (kz * my + mz * ky) * mx);
 }
 
 // Preconditioned CG residual pass: r -= alpha q; reductions r.r (convergence) and r.z with

@@ -1,5 +1,6 @@
-"""bench.py's reference arm on the host: one JSON line with the contract's keys, the oracle's
-throughput in the benchmark's unit, and the fields the driver reads."""
+"""bench.py's reference arm on the host: one JSON line with the benchmark contract's keys, the
+oracle's throughput in the benchmark's unit, and the reference-arm fields (impl, e2e,
+cpu_baseline)."""
 import json
 import os
 import subprocess
