@@ -460,13 +460,26 @@ def robin_large_run(iters: int = 200):
         del x
     ms_it = res["from_zero"]["ms"] / max(res["from_zero"]["iterations"], 1)
     nodes = nt_f[0] * nt_f[1] * nt_f[2]
+    Hf.close()
+    torch.cuda.empty_cache()
+    # the same problem and start with FP32 inner PCG inside FP64 refinement (the library's
+    # mixed-precision path), for the same number of inner iterations
+    Hm = api.Handle(*nt_f, n, hf, dt, precision="f32_ir")
+    Hm.set_boundary("robin", pen)
+    Hm.set_preconditioner("jacobi")
+    xm = x0.clone()
+    ms_m, rep_m = _timed_ms(lambda: Hm.cg_solve(bf, xm, tol=1e-14, max_iter=iters, inner_tol=1e-6))
+    res["from_coarse_f32_inner_f64_refinement"] = {"ms": ms_m, "iterations": rep_m["iterations"],
+                                                   "refinement_steps": rep_m["outer_iterations"],
+                                                   "rel_residual": rep_m["rel_residual"]}
+    Hm.close()
+    del xm
     out.update({"coarse_solve": {"ms": ms_c, "iterations": rep_c["iterations"],
                                  "rel_residual": rep_c["rel_residual"]},
                 "prolong_ms": ms_p, "fine": res, "ms_per_pcg_iteration": ms_it,
                 "gdofs_per_pcg_iteration": nodes / (ms_it * 1e-3) / 1e9,
                 "projected_1000_iterations_s": ms_it * 1000 / 1e3,
                 "paper_1000_iterations_s": 4 * 3600 + 4 * 60})
-    Hf.close()
     Hc.close()
     del bf, bc, xc, x0
     torch.cuda.empty_cache()

@@ -17,6 +17,7 @@
 #include <cuda_bf16.h>
 
 #include "bsk_device.cuh"
+#include "precond.cuh"
 
 namespace bsk {
 

@@ -3,6 +3,7 @@
 #pragma once
 
 #include "bsk_device.cuh"
+#include "precond.cuh"
 
 namespace bsk {
 
