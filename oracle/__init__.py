@@ -91,6 +91,8 @@ def lib():
             L.orc_transfer_1d.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.c_double,
                                           ctypes.c_int, ctypes.c_double, _D]
             L.orc_prolong_robin.argtypes = [P, P, _D, _D]
+            L.orc_diag_var.argtypes = [P, _D, _D, _D]
+            L.orc_pcg_var.argtypes = [P, _D, _D, _D, _D, ctypes.c_double, ctypes.c_int, _I, _D]
             for name in ("orc_op_var", "orc_abs_op_var", "orc_bruteforce_apply_var"):
                 getattr(L, name).argtypes = [P, _D, _D, _D, _D]
             L.orc_op_var_points.argtypes = [P, _D, _D, ctypes.c_void_p, ctypes.c_int, ctypes.c_int,
@@ -494,3 +496,25 @@ def prolong_robin(fine: Problem, coarse: Problem, xc):
     xf = np.zeros(robin_shape(fine))
     _check(lib().orc_prolong_robin(ctypes.byref(fine._c()), ctypes.byref(coarse._c()), _dp(xc), _dp(xf)))
     return xf
+
+
+def diag_var(prob: Problem, d, m):
+    """Diagonal of A(d, m) (inactive nodes: 1), each entry from the triple-sum definition."""
+    d = _f64(d).reshape(coef_shape(prob))
+    m = _f64(m).reshape(coef_shape(prob))
+    out = np.zeros(prob.shape)
+    _check(lib().orc_diag_var(ctypes.byref(prob._c()), _dp(d), _dp(m), _dp(out)))
+    return out
+
+
+def pcg_var(prob: Problem, d, m, b, x0=None, tol=1e-10, max_iter=10000):
+    """Jacobi-preconditioned CG on A(d, m). Returns (x, iterations, true relative residual, status)."""
+    d = _f64(d).reshape(coef_shape(prob))
+    m = _f64(m).reshape(coef_shape(prob))
+    b = _f64(b).reshape(prob.shape)
+    x = np.zeros(prob.shape) if x0 is None else _f64(x0).reshape(prob.shape).copy()
+    it = ctypes.c_int(0)
+    rel = ctypes.c_double(0.0)
+    st = _check(lib().orc_pcg_var(ctypes.byref(prob._c()), _dp(d), _dp(m), _dp(b), _dp(x), float(tol),
+                                  int(max_iter), ctypes.byref(it), ctypes.byref(rel)))
+    return x, it.value, rel.value, st

@@ -1539,3 +1539,92 @@ int orc_prolong_robin(const orc_problem* fine, const orc_problem* coarse, const 
     for (int d = 0; d < 3; d++) free(P[d]);
     return 0;
 }
+
+/* ------------------------------------------------------------------------------------------ */
+/* Jacobi preconditioning of the variable-coefficient operator                                 */
+/* ------------------------------------------------------------------------------------------ */
+
+/* Diagonal of A(d, m): A_ll = (A(d, m) e_l)_l, each entry evaluated from the triple-sum definition
+ * of var_point with x = e_l (whose odd-reflected extension carries the row's own mirror images).
+ * Inactive nodes get 1. */
+int orc_diag_var(const orc_problem* p, const double* d, const double* m, double* dg)
+{
+    if (!var_ok(p)) return -1;
+    var_tables t;
+    var_tables_init(&t, p->n, 0);
+    size_t len = (size_t)p->nx * p->ny * p->nz;
+    int failed = 0;
+#pragma omp parallel
+    {
+        double* e = (double*)calloc(len, sizeof(double));
+        if (!e) failed = 1;
+#pragma omp for schedule(dynamic, 16)
+        for (long long I = 0; I < (long long)len; I++) {
+            if (!e) continue;
+            if (p->mask && !p->mask[I]) { dg[I] = 1.0; continue; }
+            int ix = (int)(I % p->nx), iy = (int)((I / p->nx) % p->ny);
+            int iz = (int)(I / ((long long)p->nx * p->ny));
+            e[I] = 1.0;
+            dg[I] = var_point(p, &t, d, m, e, 0, ix, iy, iz, 0);
+            e[I] = 0.0;
+        }
+        free(e);
+    }
+    return failed ? -3 : 0;
+}
+
+/* Jacobi-preconditioned CG on A(d, m) x = b (textbook PCG, z = r / diag), masked. */
+int orc_pcg_var(const orc_problem* p, const double* d, const double* m, const double* b, double* x,
+                double tol, int max_iter, int* iters, double* relres)
+{
+    if (!var_ok(p)) return -1;
+    size_t len = (size_t)p->nx * p->ny * p->nz;
+    double* dg = (double*)malloc(sizeof(double) * len);
+    double* r = (double*)malloc(sizeof(double) * len);
+    double* z = (double*)malloc(sizeof(double) * len);
+    double* pv = (double*)malloc(sizeof(double) * len);
+    double* q = (double*)malloc(sizeof(double) * len);
+    double* bm = (double*)malloc(sizeof(double) * len);
+    if (!dg || !r || !z || !pv || !q || !bm || orc_diag_var(p, d, m, dg)) {
+        free(dg); free(r); free(z); free(pv); free(q); free(bm);
+        return -1;
+    }
+    for (size_t i = 0; i < len; i++) {
+        int act = !p->mask || p->mask[i];
+        bm[i] = act ? b[i] : 0.0;
+        if (!act) x[i] = 0.0;
+    }
+    double bb = dot(bm, bm, len);
+    orc_op_var(p, d, m, x, q);
+    for (size_t i = 0; i < len; i++) { r[i] = bm[i] - q[i]; z[i] = r[i] / dg[i]; pv[i] = z[i]; }
+    double rz = dot(r, z, len), rr = dot(r, r, len);
+    int status = 1, it = 0;
+    if (bb == 0.0) {
+        memset(x, 0, sizeof(double) * len);
+        status = 0;
+    } else if (sqrt(rr) <= tol * sqrt(bb)) {
+        status = 0;
+    } else {
+        for (it = 1; it <= max_iter; it++) {
+            orc_op_var(p, d, m, pv, q);
+            double pq = dot(pv, q, len);
+            if (!(pq > 0.0)) { status = -5; break; }
+            double alpha = rz / pq;
+            for (size_t i = 0; i < len; i++) { x[i] += alpha * pv[i]; r[i] -= alpha * q[i]; }
+            rr = dot(r, r, len);
+            if (sqrt(rr) <= tol * sqrt(bb)) { status = 0; break; }
+            for (size_t i = 0; i < len; i++) z[i] = r[i] / dg[i];
+            double rz_new = dot(r, z, len);
+            double beta = rz_new / rz;
+            for (size_t i = 0; i < len; i++) pv[i] = z[i] + beta * pv[i];
+            rz = rz_new;
+        }
+        if (it > max_iter) it = max_iter;
+    }
+    *iters = it;
+    orc_op_var(p, d, m, x, q);
+    for (size_t i = 0; i < len; i++) r[i] = bm[i] - q[i];
+    *relres = bb > 0 ? sqrt(dot(r, r, len) / bb) : 0.0;
+    free(dg); free(r); free(z); free(pv); free(q); free(bm);
+    return status;
+}
