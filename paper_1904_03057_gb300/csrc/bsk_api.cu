@@ -157,6 +157,7 @@ struct bsk_handle {
     int pc;               // BSK_PC_NONE or BSK_PC_JACOBI
     void* jac[2];         // Jacobi: per-axis diagonals [3][2][jn], float [0] / double [1]
     int jn;
+    void* jvec;           // Jacobi with variable coefficients: 1 / diag A per node, CG precision
     float* fcg_ws;        // FCG work vectors z, rn, zn (allocated by the first fcg_solve)
     double* fcg_partials;
     void* fcg_state;
@@ -227,7 +228,8 @@ void fill_launch(const bsk_handle* h, bsk::OpLaunch& L, int mode)
     L.dt = h->dt;
     for (int i = 0; i < 2; i++) {
         L.rb[i] = h->rb[i];
-        L.jac[i] = h->pc ? h->jac[i] : nullptr;
+        L.jac[i] = h->pc && !h->jvec ? h->jac[i] : nullptr;
+        L.jvec[i] = h->pc && (cg_es(h) == sizeof(double)) == (i == 1) ? h->jvec : nullptr;
     }
     L.jn = h->jn;
 }
@@ -370,7 +372,8 @@ int enqueue_chunk(bsk_handle* h, int chunk)
         if (h->pc)
             BSK_CUDA(bsk::launch_cg_update_pc<T>(static_cast<T*>(h->r), static_cast<const T*>(h->q), h->len,
                                                  h->nx, h->ny, static_cast<const T*>(h->jac[sizeof(T) == 8]),
-                                                 h->jn, h->sc, h->partials, bsk::FIN_UPD_PC, s));
+                                                 h->jn, static_cast<const T*>(h->jvec), h->sc, h->partials,
+                                                 bsk::FIN_UPD_PC, s));
         else
             BSK_CUDA(bsk::launch_cg_update<T>(static_cast<T*>(h->r), static_cast<const T*>(h->q),
                                               h->len, h->sc, h->partials, bsk::FIN_UPD, s));
@@ -384,8 +387,8 @@ int pc_start(bsk_handle* h)
 {
     if (!h->pc) return BSK_OK;
     BSK_LAUNCH(h, bsk::launch_pc_dot<T>(static_cast<const T*>(h->r), h->len, h->nx, h->ny,
-                                        static_cast<const T*>(h->jac[sizeof(T) == 8]), h->jn, h->sc,
-                                        h->partials, h->stream));
+                                        static_cast<const T*>(h->jac[sizeof(T) == 8]), h->jn,
+                                        static_cast<const T*>(h->jvec), h->sc, h->partials, h->stream));
     return BSK_OK;
 }
 
@@ -774,7 +777,7 @@ extern "C" void bsk_destroy(bsk_handle* h)
     if (h->graph) cudaGraphExecDestroy(h->graph);
     void* ptrs[] = {h->mask, h->occ, h->x, h->r, h->p0, h->p1, h->q, h->bvec, h->r2, h->q2, h->r64, h->b64,
                     h->sc, h->sc64, h->sc_aux, h->partials, h->work, h->cd[0], h->cd[1], h->cm[0], h->cm[1],
-                    h->rb[0], h->rb[1], h->jac[0], h->jac[1]};
+                    h->rb[0], h->rb[1], h->jac[0], h->jac[1], h->jvec};
     for (void* p : ptrs)
         if (p) cudaFree(p);
     if (h->h_sc) cudaFreeHost(h->h_sc);
@@ -913,7 +916,48 @@ int upload_both(const std::vector<double>& v, void** dst)
     return BSK_OK;
 }
 
-// Rebuilds the Robin rows and Jacobi diagonals after a change of boundary, dt or preconditioner.
+// 1 / diag A per node of the variable-coefficient operator, by probing: the operator is applied
+// to the indicator vectors of the (n+1)^3 classes of nodes congruent modulo n + 1 per axis; two
+// nodes of one class are more than n apart on some axis (and so are their mirror images), so
+// their B-splines do not overlap and each application returns A_ll at every node of its class.
+// Runs in the CG precision on the handle's work vectors.
+template <typename T>
+int probe_diagonal_t(bsk_handle* h)
+{
+    T* v = static_cast<T*>(h->p0);
+    T* y = static_cast<T*>(h->q);
+    T* jinv = static_cast<T*>(h->jvec);
+    const int s = h->n + 1;
+    for (int cz = 0; cz < s; cz++)
+        for (int cy = 0; cy < s; cy++)
+            for (int cx = 0; cx < s; cx++) {
+                BSK_CUDA(bsk::launch_probe<T>(v, y, jinv, 0, h->nx, h->ny, h->nz, s, cx, cy, cz, h->mask, h->stream));
+                bsk::OpLaunch L;
+                fill_launch(h, L, bsk::MODE_OP);
+                L.in0 = v;
+                L.out0 = y;
+                L.fin = bsk::FIN_NONE;
+                BSK_CUDA(bsk::launch_op<T>(L, h->stream));
+                BSK_CUDA(bsk::launch_probe<T>(v, y, jinv, 1, h->nx, h->ny, h->nz, s, cx, cy, cz, h->mask, h->stream));
+            }
+    BSK_CUDA(cudaStreamSynchronize(h->stream));
+    return BSK_OK;
+}
+
+int probe_diagonal(bsk_handle* h)
+{
+    const size_t es = cg_es(h);
+    cudaError_t e = cudaMalloc(&h->jvec, h->len * es);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        h->jvec = nullptr;
+        return fail(BSK_ENOMEM, "Jacobi diagonal: cudaMalloc(%zu) failed", h->len * es);
+    }
+    return es == sizeof(double) ? probe_diagonal_t<double>(h) : probe_diagonal_t<float>(h);
+}
+
+// Rebuilds the Robin rows and Jacobi diagonals after a change of boundary, dt, coefficients or
+// preconditioner.
 int refresh_tables(bsk_handle* h)
 {
     BSK_CUDA(cudaStreamSynchronize(h->stream));
@@ -927,6 +971,11 @@ int refresh_tables(bsk_handle* h)
         jacobi_diagonals(h, rows, dg);
         if (int rc = upload_both(dg, h->jac)) return rc;
     }
+    if (h->jvec) {
+        cudaFree(h->jvec);
+        h->jvec = nullptr;
+    }
+    if (h->pc == BSK_PC_JACOBI && (h->cd[0] || h->cd[1])) return probe_diagonal(h);
     return BSK_OK;
 }
 
@@ -969,8 +1018,6 @@ extern "C" int bsk_set_preconditioner(bsk_handle* h, int kind)
 {
     if (int rc = check_handle(h)) return rc;
     if (kind != BSK_PC_NONE && kind != BSK_PC_JACOBI) return fail(BSK_EINVAL, "unknown preconditioner %d", kind);
-    if (kind == BSK_PC_JACOBI && (h->cd[0] || h->cd[1]))
-        return fail(BSK_EINVAL, "the Jacobi preconditioner needs constant coefficients (separable diagonal)");
     if (kind == BSK_PC_JACOBI && h->prec == BSK_BF16S) return fail(BSK_EINVAL, "BF16 storage has no solver");
     h->pc = kind;
     h->jn = std::max(h->nx, std::max(h->ny, h->nz));
@@ -984,8 +1031,6 @@ extern "C" int bsk_set_coefficients(bsk_handle* h, const double* d, const double
     if (h->prec == BSK_BF16S) return fail(BSK_EINVAL, "the BF16-storage variant has constant coefficients only");
     if ((d || m) && h->bc == BSK_BC_ROBIN)
         return fail(BSK_EINVAL, "variable coefficients take the Dirichlet boundary");
-    if ((d || m) && h->pc == BSK_PC_JACOBI)
-        return fail(BSK_EINVAL, "the Jacobi preconditioner needs constant coefficients");
     // the captured CG graph holds the kernels of the previous operator
     BSK_CUDA(cudaStreamSynchronize(h->stream));
     if (h->graph) {
@@ -999,7 +1044,7 @@ extern "C" int bsk_set_coefficients(bsk_handle* h, const double* d, const double
             h->cd[i] = h->cm[i] = nullptr;
         }
         refresh_paths(h);
-        return BSK_OK;
+        return h->pc == BSK_PC_JACOBI ? refresh_tables(h) : BSK_OK;
     }
     const size_t clen = (size_t)(h->nx + 2) * (h->ny + 2) * (h->nz + 2);
     for (int i = 0; i < 2; i++) {
@@ -1028,6 +1073,7 @@ extern "C" int bsk_set_coefficients(bsk_handle* h, const double* d, const double
     // kernel (the right-hand-side mass of heat_step stays the constant mass matrix)
     refresh_paths(h);
     BSK_CUDA(cudaStreamSynchronize(h->stream));
+    if (h->pc == BSK_PC_JACOBI) return refresh_tables(h);   // the diagonal changed
     return BSK_OK;
 }
 

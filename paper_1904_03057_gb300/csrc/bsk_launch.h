@@ -50,6 +50,9 @@ struct OpLaunch {
     // null = no preconditioner
     const void* jac[2];
     int jn;                      // row length of the jac tables
+    // MODE_CGP of the variable-coefficient kernel: 1 / diag A per node (Jacobi), float [0] /
+    // double [1]; null = no preconditioner
+    const void* jvec[2];
 };
 
 // Grid of the operator kernel for a problem; partial-sum buffers hold 2 doubles per block.
@@ -85,12 +88,18 @@ cudaError_t launch_cg_update(T* r, const T* q, size_t len, Scalars* sc, double* 
                              int fin, cudaStream_t s);
 // Jacobi-preconditioned CG (vec_kernels.cuh): r -= alpha q with r.r and r.z (FIN_UPD_PC), and
 // the starting r.z (FIN_PC_INIT).
+// The inverse diagonal is jvec[i] when jvec is given, else formed from the per-axis tables jac.
 template <typename T>
-cudaError_t launch_cg_update_pc(T* r, const T* q, size_t len, int nx, int ny, const T* jac, int jn,
+cudaError_t launch_cg_update_pc(T* r, const T* q, size_t len, int nx, int ny, const T* jac, int jn, const T* jvec,
                                 Scalars* sc, double* partials, int fin, cudaStream_t s);
 template <typename T>
-cudaError_t launch_pc_dot(const T* r, size_t len, int nx, int ny, const T* jac, int jn, Scalars* sc,
-                          double* partials, cudaStream_t s);
+cudaError_t launch_pc_dot(const T* r, size_t len, int nx, int ny, const T* jac, int jn, const T* jvec,
+                          Scalars* sc, double* partials, cudaStream_t s);
+// Diagonal probing (var_impl.cuh): take = 0 fills v with the indicator of colour (cx, cy, cz)
+// modulo stride; take = 1 stores 1 / y at that colour's nodes into jinv.
+template <typename T>
+cudaError_t launch_probe(T* v, const T* y, T* jinv, int take, int nx, int ny, int nz, int stride, int cx,
+                         int cy, int cz, const uint8_t* mask, cudaStream_t s);
 // Banded transfer along one axis (transform.cu): out[.., f, ..] = sum_k T[f][k] in[.., c0[f] + k, ..]
 // for f < nout, the other two extents unchanged (dims are those of `in`, x fastest).
 template <typename T>

@@ -124,17 +124,18 @@ cudaError_t launch_cg_update<BSK_T>(BSK_T* r, const BSK_T* q, size_t len, Scalar
 
 template <>
 cudaError_t launch_cg_update_pc<BSK_T>(BSK_T* r, const BSK_T* q, size_t len, int nx, int ny, const BSK_T* jac,
-                                       int jn, Scalars* sc, double* partials, int fin, cudaStream_t s)
+                                       int jn, const BSK_T* jvec, Scalars* sc, double* partials, int fin,
+                                       cudaStream_t s)
 {
-    k_cg_update_pc<BSK_T><<<vec_grid(len), kVecNT, 0, s>>>(r, q, len, nx, ny, jac, jn, sc, partials, fin);
+    k_cg_update_pc<BSK_T><<<vec_grid(len), kVecNT, 0, s>>>(r, q, len, nx, ny, jac, jn, jvec, sc, partials, fin);
     return cudaGetLastError();
 }
 
 template <>
 cudaError_t launch_pc_dot<BSK_T>(const BSK_T* r, size_t len, int nx, int ny, const BSK_T* jac, int jn,
-                                 Scalars* sc, double* partials, cudaStream_t s)
+                                 const BSK_T* jvec, Scalars* sc, double* partials, cudaStream_t s)
 {
-    k_pc_dot<BSK_T><<<vec_grid(len), kVecNT, 0, s>>>(r, len, nx, ny, jac, jn, sc, partials);
+    k_pc_dot<BSK_T><<<vec_grid(len), kVecNT, 0, s>>>(r, len, nx, ny, jac, jn, jvec, sc, partials);
     return cudaGetLastError();
 }
 

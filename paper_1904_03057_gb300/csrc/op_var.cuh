@@ -56,6 +56,7 @@ struct VarArgs {
     T* out1;          // p (CGP)
     T* xvec;          // x, updated in place (CGP)
     const T* b;       // right-hand side (RES)
+    const T* jvec;    // CGP: 1 / diag A per node (Jacobi), null = no preconditioner
     Scalars* sc;
     double* partials;
     int fin;
@@ -163,7 +164,8 @@ __global__ void __launch_bounds__(VarCfg<T, N>::NT, VarCfg<T, N>::MINB) k_op_var
             T v = T(0);
             if (s) {
                 const size_t o = ((size_t)sz * ny + sy) * nx + sx;
-                const T u = MODE == MODE_CGP ? a.in0[o] + beta * a.in1[o] : a.in0[o];
+                const T u = MODE == MODE_CGP ? (a.jvec ? a.in0[o] * a.jvec[o] : a.in0[o]) + beta * a.in1[o]
+                                             : a.in0[o];
                 v = (mask && !mask[o]) ? T(0) : (s > 0 ? u : -u);
             }
             const size_t e = (ez + coef_node(gy + 1, ny)) * cpx + coef_node(gx + 1, nx);

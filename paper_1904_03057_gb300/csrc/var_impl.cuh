@@ -104,6 +104,7 @@ cudaError_t launch_var_mode(const OpLaunch& L, cudaStream_t s)
     a.out1 = static_cast<T*>(L.out1);
     a.xvec = static_cast<T*>(L.xvec);
     a.b = static_cast<const T*>(L.b);
+    a.jvec = MODE == MODE_CGP ? static_cast<const T*>(L.jvec[sizeof(T) == 8]) : nullptr;
     a.sc = L.sc;
     a.partials = L.partials;
     a.fin = L.fin;
@@ -129,7 +130,42 @@ __global__ void k_coef_fill(const double* __restrict__ src, BSK_T* __restrict__ 
         dst[i] = src ? (BSK_T)src[i] : BSK_T(1);
 }
 
+// Probing the diagonal of a banded operator: nodes whose coordinates equal (cx, cy, cz) modulo
+// `stride` (n + 1) are more than n apart on some axis, as are their mirror images, so one
+// application of A to their indicator vector returns A_ll at each of them.
+__global__ void k_probe_fill(BSK_T* __restrict__ v, int nx, int ny, size_t len, int stride, int cx, int cy,
+                             int cz, const uint8_t* __restrict__ mask)
+{
+    for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < len; i += (size_t)gridDim.x * blockDim.x) {
+        const int x = (int)(i % nx), y = (int)((i / nx) % ny), z = (int)(i / ((size_t)nx * ny));
+        const bool on = x % stride == cx && y % stride == cy && z % stride == cz && (!mask || mask[i]);
+        v[i] = on ? BSK_T(1) : BSK_T(0);
+    }
+}
+
+// jinv[i] = 1 / y[i] at the probed nodes; after every colour, every active node holds 1 / A_ii
+// (inactive nodes get 1: their residual is zero).
+__global__ void k_probe_take(const BSK_T* __restrict__ y, BSK_T* __restrict__ jinv, int nx, int ny, size_t len,
+                             int stride, int cx, int cy, int cz, const uint8_t* __restrict__ mask)
+{
+    for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < len; i += (size_t)gridDim.x * blockDim.x) {
+        const int x = (int)(i % nx), y2 = (int)((i / nx) % ny), z = (int)(i / ((size_t)nx * ny));
+        if (x % stride == cx && y2 % stride == cy && z % stride == cz)
+            jinv[i] = (!mask || mask[i]) ? BSK_T(1) / y[i] : BSK_T(1);
+    }
+}
+
 }  // namespace
+
+template <>
+cudaError_t launch_probe<BSK_T>(BSK_T* v, const BSK_T* y, BSK_T* jinv, int take, int nx, int ny, int nz,
+                                int stride, int cx, int cy, int cz, const uint8_t* mask, cudaStream_t s)
+{
+    const size_t len = (size_t)nx * ny * nz;
+    if (take) k_probe_take<<<vec_grid(len), 256, 0, s>>>(y, jinv, nx, ny, len, stride, cx, cy, cz, mask);
+    else k_probe_fill<<<vec_grid(len), 256, 0, s>>>(v, nx, ny, len, stride, cx, cy, cz, mask);
+    return cudaGetLastError();
+}
 
 template <>
 cudaError_t launch_coef_fill<BSK_T>(const double* src, BSK_T* dst, size_t len, cudaStream_t s)

@@ -88,7 +88,8 @@ __device__ __forceinline__ T jacobi_inv_flat(const T* jac, int jn, size_t i, int
 template <typename T>
 __global__ void __launch_bounds__(kVecNT) k_cg_update_pc(T* __restrict__ r, const T* __restrict__ q,
                                                          size_t len, int nx, int ny, const T* __restrict__ jac,
-                                                         int jn, Scalars* sc, double* partials, int fin)
+                                                         int jn, const T* __restrict__ jvec, Scalars* sc,
+                                                         double* partials, int fin)
 {
     if (*(volatile int*)&sc->done) return;
     const T alpha = (T)sc->alpha;
@@ -99,7 +100,7 @@ __global__ void __launch_bounds__(kVecNT) k_cg_update_pc(T* __restrict__ r, cons
         const T v = fma(-alpha, q[i], r[i]);
         r[i] = v;
         rr.add(v);
-        rz.add(v * v * jacobi_inv_flat(jac, jn, i, nx, ny));
+        rz.add(v * v * (jvec ? jvec[i] : jacobi_inv_flat(jac, jn, i, nx, ny)));
     }
     grid_reduce2<kVecNT>(rr.value(), rz.value(), partials, sc, fin, 0);
 }
@@ -107,14 +108,14 @@ __global__ void __launch_bounds__(kVecNT) k_cg_update_pc(T* __restrict__ r, cons
 // r.z with z = r / diag A: the starting value of the preconditioned iteration (FIN_PC_INIT).
 template <typename T>
 __global__ void __launch_bounds__(kVecNT) k_pc_dot(const T* __restrict__ r, size_t len, int nx, int ny,
-                                                   const T* __restrict__ jac, int jn, Scalars* sc,
-                                                   double* partials)
+                                                   const T* __restrict__ jac, int jn, const T* __restrict__ jvec,
+                                                   Scalars* sc, double* partials)
 {
     TermSum<T> rz;
     for (size_t i = blockIdx.x * (size_t)kVecNT + threadIdx.x; i < len;
          i += (size_t)gridDim.x * kVecNT) {
         const T v = r[i];
-        rz.add(v * v * jacobi_inv_flat(jac, jn, i, nx, ny));
+        rz.add(v * v * (jvec ? jvec[i] : jacobi_inv_flat(jac, jn, i, nx, ny)));
     }
     grid_reduce2<kVecNT>(rz.value(), 0.0, partials, sc, FIN_PC_INIT, 0);
 }

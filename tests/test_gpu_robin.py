@@ -176,8 +176,7 @@ def test_argument_errors(api):
     H2.set_coefficients(torch.ones(H2.coef_shape, dtype=torch.float64, device="cuda"), None)
     with pytest.raises(Exception):
         H2.set_boundary("robin", 1.0)
-    with pytest.raises(Exception):
-        H2.set_preconditioner("jacobi")
+    H2.set_preconditioner("jacobi")            # variable coefficients: probed diagonal
     H3 = api.Handle(20, 20, 20, 3, 1 / 17, 1e-3)
     H3.set_boundary("robin", 1.0)
     with pytest.raises(Exception):

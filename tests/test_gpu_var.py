@@ -4,8 +4,8 @@ FP64 oracle's plain triple sum, through the C ABI.
 Operator tolerances (max norm, relative to max_i (|A(d, m)| |x|)_i): 1e-12 in FP64 and 1e-5 in
 FP32, the FP32 case against the oracle applied to the FP32-rounded x, d and m that the kernel
 reads. Grids span several output tiles with ragged tails in x and y and several z-blocks
-(tiles: FP32 16 x 16 for degree <= 3 and 8 x 8 above; FP64 16, 12, 8, 8, 4 for degrees 1..5;
-z-blocks of at least 2n planes)."""
+(tiles: FP32 16 x 16 for degree <= 3, 12 x 12 and 10 x 10 for degrees 4 and 5; FP64 16, 12, 8,
+8, 4 for degrees 1..5; z-blocks of at least 2n planes)."""
 import numpy as np
 import pytest
 
@@ -199,3 +199,29 @@ def test_argument_errors_and_flops(api):
     B = api.Handle(16, 16, 16, 3, 1 / 17, 1e-3, precision="bf16s")
     with pytest.raises(Exception):
         B.set_coefficients(None, torch.ones(B.coef_shape, dtype=torch.float64, device="cuda"))
+
+
+@pytest.mark.parametrize("prec,tol", [("f64", 1e-10), ("f32_ir", 1e-8)])
+def test_jacobi_pcg_with_coefficients(api, prec, tol):
+    """Jacobi PCG on A(d, m): the diagonal comes from probing the operator; the iteration matches
+    the oracle's Jacobi PCG (whose diagonal is the triple-sum definition) and reaches the
+    tolerance in the oracle's FP64 residual."""
+    n, dims = 3, (30, 26, 22)
+    P, hs, d, m, _ = case(n, dims, 90, masked=True)
+    b = inputs.random_field(P.shape, 91, mask=torch.from_numpy(P.mask)).numpy()
+    H = make_handle(api, P, hs, prec)
+    set_fields(H, d, m)
+    H.set_preconditioner("jacobi")
+    x = torch.zeros(P.shape, dtype=torch.float64, device="cuda")
+    rep = H.cg_solve(torch.from_numpy(b).cuda(), x, tol=tol, max_iter=5000)
+    assert rep["status"] == 0 and rep["rel_residual"] <= tol, rep
+    r = b * P.mask - oracle.op_var(P, d, m, x.cpu().numpy())
+    assert np.linalg.norm(r) / np.linalg.norm(b * P.mask) <= 1.5 * tol
+    if prec == "f64":
+        _, it_ref, _, st = oracle.pcg_var(P, d, m, b, tol=tol)
+        assert st == 0 and abs(rep["iterations"] - it_ref) <= 3, (rep["iterations"], it_ref)
+        # plain CG on the same system takes more iterations (the fields vary by a factor 25)
+        x2 = torch.zeros_like(x)
+        H.set_preconditioner("none")
+        rep2 = H.cg_solve(torch.from_numpy(b).cuda(), x2, tol=tol, max_iter=5000)
+        assert rep2["status"] == 0 and rep["iterations"] < rep2["iterations"], (rep, rep2)
