@@ -381,6 +381,7 @@ def variable_coefficients():
     u = torch.zeros((N, N, N), dtype=torch.float64, device="cuda")
     q = inputs.gaussian_source(N, N, N, inputs.gaussian_centers(2, 32), sigma=0.03, h=h,
                                mask=mask, device="cuda")
+    u0 = u.clone()
     H.heat_step(u.clone(), q, 1, tol=1e-8)   # warm-up (graph capture)
     ms, rep = _timed_ms(lambda: H.heat_step(u, q, 1, tol=1e-8))
     out["heat_step_256_sphere"] = {"ms": ms, "cg_iterations": rep["iterations"],
@@ -388,6 +389,15 @@ def variable_coefficients():
                                    "true_rel_residual": rep["rel_residual"],
                                    "coefficients": "D inclusions (0.2-5 in background 1), "
                                                    "m = 1 + dt mu_a"}
+    # the same step with Jacobi-preconditioned CG (the diagonal probed once, timed apart)
+    ms_probe, _ = _timed_ms(lambda: H.set_preconditioner("jacobi"))
+    H.heat_step(u0.clone(), q, 1, tol=1e-8)
+    ms_j, rep_j = _timed_ms(lambda: H.heat_step(u0, q, 1, tol=1e-8))
+    out["heat_step_256_sphere_jacobi"] = {"ms": ms_j, "cg_iterations": rep_j["iterations"],
+                                          "refinement_steps": rep_j["outer_iterations"],
+                                          "true_rel_residual": rep_j["rel_residual"],
+                                          "diagonal_probe_ms": ms_probe}
+    del u0
     H.close()
     del u, q, mask
     torch.cuda.empty_cache()

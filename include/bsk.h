@@ -12,8 +12,15 @@
  * section 2.5). Md and Kd are the (2n+1)-tap mass and stiffness kernels of axis d,
  * Md = hd * beta^{2n+1}(j) and Kd = -(1/hd) * (beta^{2n-1}(j+1) - 2 beta^{2n-1}(j) +
  * beta^{2n-1}(j-1)), j = -n..n (scalar-product and derivative identities, Table tblBsplines).
+ * A handle can instead carry variable coefficients D(x), mu_a(x) expanded in B-splines
+ * (bsk_set_coefficients: the operator of Eq. tensForm computed on the fly), the boundary
+ * penalty of the paper's large run over the untruncated basis (bsk_set_boundary), and the
+ * Jacobi preconditioner (bsk_set_preconditioner); bsk_prolong starts a fine Robin solve from a
+ * coarse one, bsk_transform maps between B-spline coefficients and node values, and a learned
+ * preconditioner drives flexible CG (fcg_solve).
  *
- * Conventions shared by every entry point:
+ * Conventions shared by every entry point (the Robin boundary changes the second; see
+ * bsk_set_boundary):
  *   - Arrays are dense, x fastest: element (k, j, i) of an nx*ny*nz grid sits at
  *     ((k * ny) + j) * nx + i. Unknown i of an axis is the B-spline centred at (i + 1) h.
  *   - Zero Dirichlet data on the box faces: coefficients are odd-reflected about the faces,
