@@ -260,7 +260,9 @@ int bsk_set_preconditioner(bsk_handle* h, int kind);
  * banded transfer passes and three passes of line solves. Where the coarse space lies in the fine
  * one (odd degree, coarse step a multiple of the fine step) the function is reproduced exactly.
  * xc: DEVICE vector of the coarse handle's size, xf: of the fine handle's (not overlapping).
- * Runs on the fine handle's stream and returns after it is synchronised. */
+ * FP32 handles compute in FP64 internally (temporary FP64 copies; the untruncated Gram matrices
+ * are ill-conditioned for n >= 2) and round the result once. Runs on the fine handle's stream and
+ * returns after it is synchronised. */
 int bsk_prolong(bsk_handle* fine, bsk_handle* coarse, const void* xc, void* xf);
 
 /* Floating-point operations per grid node of one operator application (FMA = 2): the

@@ -1729,9 +1729,32 @@ extern "C" int bsk_prolong(bsk_handle* fine, bsk_handle* coarse, const void* xc,
     // the coarse handle's stream must be done with xc before the fine stream reads it
     BSK_CUDA(cudaStreamSynchronize(coarse->stream));
     fine->launches = 0;
-    return user_es(fine) == sizeof(double)
-               ? prolong_impl<double>(fine, coarse, static_cast<const double*>(xc), static_cast<double*>(xf))
-               : prolong_impl<float>(fine, coarse, static_cast<const float*>(xc), static_cast<float*>(xf));
+    if (user_es(fine) == sizeof(double))
+        return prolong_impl<double>(fine, coarse, static_cast<const double*>(xc), static_cast<double*>(xf));
+    // FP32 handles: the transfers and line solves run in FP64 (the Gram matrices of the
+    // untruncated basis are ill-conditioned for n >= 2: FP32 line solves lost 3 % at n = 3) and
+    // the result is rounded once
+    double *c64 = nullptr, *f64 = nullptr;
+    cudaError_t e = cudaMalloc((void**)&c64, coarse->len * sizeof(double));
+    if (e == cudaSuccess) e = cudaMalloc((void**)&f64, fine->len * sizeof(double));
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        if (c64) cudaFree(c64);
+        return fail(BSK_ENOMEM, "prolongation work arrays");
+    }
+    int rc = BSK_OK;
+    e = bsk::launch_convert_f32_f64(static_cast<const float*>(xc), c64, coarse->len, fine->stream);
+    if (e != cudaSuccess) rc = cuda_fail(e, "prolongation");
+    if (rc == BSK_OK) rc = prolong_impl<double>(fine, coarse, c64, f64);
+    if (rc == BSK_OK) {
+        e = bsk::launch_convert_f64_f32(f64, static_cast<float*>(xf), fine->len, fine->stream);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(fine->stream);
+        if (e != cudaSuccess) rc = cuda_fail(e, "prolongation");
+    }
+    cudaStreamSynchronize(fine->stream);
+    cudaFree(c64);
+    cudaFree(f64);
+    return rc;
 }
 
 extern "C" int bsk_residual(bsk_handle* h, const void* b, const void* x, void* r, int fp64, double* rr,

@@ -100,6 +100,9 @@ cudaError_t launch_pc_dot(const T* r, size_t len, int nx, int ny, const T* jac, 
 template <typename T>
 cudaError_t launch_probe(T* v, const T* y, T* jinv, int take, int nx, int ny, int nz, int stride, int cx,
                          int cy, int cz, const uint8_t* mask, cudaStream_t s);
+// Element type conversions (transform.cu).
+cudaError_t launch_convert_f32_f64(const float* src, double* dst, size_t len, cudaStream_t s);
+cudaError_t launch_convert_f64_f32(const double* src, float* dst, size_t len, cudaStream_t s);
 // Banded transfer along one axis (transform.cu): out[.., f, ..] = sum_k T[f][k] in[.., c0[f] + k, ..]
 // for f < nout, the other two extents unchanged (dims are those of `in`, x fastest).
 template <typename T>

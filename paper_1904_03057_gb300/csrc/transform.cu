@@ -98,7 +98,26 @@ __global__ void __launch_bounds__(256) k_transfer(const T* __restrict__ in, T* _
     }
 }
 
+template <typename S, typename D>
+__global__ void __launch_bounds__(256) k_convert(const S* __restrict__ src, D* __restrict__ dst, size_t len)
+{
+    for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < len; i += (size_t)gridDim.x * blockDim.x)
+        dst[i] = (D)src[i];
+}
+
 }  // namespace
+
+cudaError_t launch_convert_f32_f64(const float* src, double* dst, size_t len, cudaStream_t s)
+{
+    k_convert<float, double><<<vec_grid(len), 256, 0, s>>>(src, dst, len);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_convert_f64_f32(const double* src, float* dst, size_t len, cudaStream_t s)
+{
+    k_convert<double, float><<<vec_grid(len), 256, 0, s>>>(src, dst, len);
+    return cudaGetLastError();
+}
 
 template <typename T>
 cudaError_t launch_band_solve(T* d, int nx, int ny, int nz, int axis, int p, const T* L, cudaStream_t s)

@@ -185,3 +185,47 @@ def test_argument_errors(api):
         H3.set_boundary("robin", -1.0)
     H3.set_boundary("dirichlet")
     H3.to_samples(torch.zeros((20, 20, 20), dtype=torch.float64, device="cuda"))
+
+
+def test_robin_heat_step_and_mixed_precision(api):
+    """One implicit Euler step on a Robin handle, (M + dt K + pen E) u1 = M u0 with the
+    truncated mass M, against the oracle's Jacobi PCG on the same system; and the same system
+    solved by FP32 inner PCG inside FP64 refinement."""
+    n, N, pen, dt = 1, (22, 19, 25), 30.0, 0.01
+    hs = tuple(1.0 / (k + 1) for k in N)
+    P = oracle.Problem(*N, n, *hs, dt=dt)
+    P0 = oracle.Problem(*N, n, *hs, dt=0.0)
+    shape = oracle.robin_shape(P)
+    u0 = inputs.random_field(shape, 12).numpy()
+    b = oracle.op_robin(P0, 0.0, u0)                          # M u0
+    ref, _, rel, st = oracle.pcg(P, b, tol=1e-12, pen=pen, robin=True, max_iter=20000)
+    assert st == 0
+    for prec, tol in (("f64", 1e-10), ("f32_ir", 1e-9)):
+        H = api.Handle(shape[2], shape[1], shape[0], n, hs, dt, precision=prec)
+        H.set_boundary("robin", pen)
+        H.set_preconditioner("jacobi")
+        u = torch.from_numpy(u0).cuda()
+        rep = H.heat_step(u, nsteps=1, tol=tol, max_iter=20000)
+        assert rep["status"] == 0, rep
+        got = u.cpu().numpy()
+        # error <= condition number x residual; the linear Robin system here is moderately conditioned
+        assert np.linalg.norm(got - ref) <= 1e4 * tol * np.linalg.norm(ref), (prec, rep)
+
+
+def test_prolongation_fp32(api):
+    n = 3
+    Nc, Nf = (9, 7, 11), (19, 15, 23)
+    hc = tuple(1.0 / (k + 1) for k in Nc)
+    hf = tuple(1.0 / (k + 1) for k in Nf)
+    C = oracle.Problem(*Nc, n, *hc, dt=0.0)
+    F = oracle.Problem(*Nf, n, *hf, dt=0.0)
+    sc, sf = oracle.robin_shape(C), oracle.robin_shape(F)
+    Hc = api.Handle(sc[2], sc[1], sc[0], n, hc, 0.0, precision="f32")
+    Hf = api.Handle(sf[2], sf[1], sf[0], n, hf, 0.0, precision="f32")
+    Hc.set_boundary("robin", 1.0)
+    Hf.set_boundary("robin", 1.0)
+    xc = np.random.default_rng(4).standard_normal(sc).astype(np.float32)
+    xf = api.prolong(Hf, Hc, torch.from_numpy(xc).cuda()).double().cpu().numpy()
+    ref = oracle.prolong_robin(F, C, xc.astype(np.float64))
+    # computed in FP64 inside and rounded once to FP32
+    assert np.max(np.abs(xf - ref)) <= 1e-6 * np.max(np.abs(ref))

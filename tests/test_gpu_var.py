@@ -225,3 +225,21 @@ def test_jacobi_pcg_with_coefficients(api, prec, tol):
         H.set_preconditioner("none")
         rep2 = H.cg_solve(torch.from_numpy(b).cuda(), x2, tol=tol, max_iter=5000)
         assert rep2["status"] == 0 and rep["iterations"] < rep2["iterations"], (rep, rep2)
+
+
+def test_heat_step_with_coefficients(api):
+    """One implicit Euler step A(d, m) u1 = M u0 (constant mass on the right-hand side) against
+    the oracle's Jacobi PCG on the variable-coefficient system."""
+    n, dims = 3, (26, 22, 18)
+    P, hs, d, m, _ = case(n, dims, 95, masked=True)
+    u0 = inputs.random_field(P.shape, 96, mask=torch.from_numpy(P.mask)).numpy()
+    b = oracle.mass(P, u0)
+    ref, _, _, st = oracle.pcg_var(P, d, m, b, tol=1e-12)
+    assert st == 0
+    H = make_handle(api, P, hs, "f64")
+    set_fields(H, d, m)
+    u = torch.from_numpy(u0).cuda()
+    rep = H.heat_step(u, nsteps=1, tol=1e-11)
+    assert rep["status"] == 0
+    got = u.cpu().numpy()
+    assert np.linalg.norm(got - ref) <= 1e-8 * np.linalg.norm(ref)
