@@ -227,7 +227,7 @@ void fill_launch(const bsk_handle* h, bsk::OpLaunch& L, int mode)
     for (int d = 0; d < 3; d++) L.h[d] = h->h[d];
     L.dt = h->dt;
     for (int i = 0; i < 2; i++) {
-        L.rb[i] = h->rb[i];
+        L.rb[i] = h->bc == BSK_BC_ROBIN ? h->rb[i] : nullptr;
         L.jac[i] = h->pc && !h->jvec ? h->jac[i] : nullptr;
         L.jvec[i] = h->pc && (cg_es(h) == sizeof(double)) == (i == 1) ? h->jvec : nullptr;
     }
@@ -1010,6 +1010,12 @@ extern "C" int bsk_set_boundary(bsk_handle* h, int kind, double penalty)
     }
     h->bc = kind;
     h->pen = kind == BSK_BC_ROBIN ? penalty : 0.0;
+    if (kind != BSK_BC_ROBIN)
+        for (int i = 0; i < 2; i++)
+            if (h->rb[i]) {
+                cudaFree(h->rb[i]);
+                h->rb[i] = nullptr;
+            }
     refresh_paths(h);
     return refresh_tables(h);
 }

@@ -178,12 +178,16 @@ def test_argument_errors(api):
         H2.set_boundary("robin", 1.0)
     H2.set_preconditioner("jacobi")            # variable coefficients: probed diagonal
     H3 = api.Handle(20, 20, 20, 3, 1 / 17, 1e-3)
+    x = inputs.random_field((20, 20, 20), 13).cuda()
+    y_dir = H3.op_apply(x).clone()
     H3.set_boundary("robin", 1.0)
     with pytest.raises(Exception):
         H3.to_samples(torch.zeros((20, 20, 20), dtype=torch.float64, device="cuda"))
     with pytest.raises(Exception):
         H3.set_boundary("robin", -1.0)
-    H3.set_boundary("dirichlet")
+    assert not torch.equal(H3.op_apply(x), y_dir)
+    H3.set_boundary("dirichlet")              # back to the reflected basis: same operator again
+    assert torch.equal(H3.op_apply(x), y_dir)
     H3.to_samples(torch.zeros((20, 20, 20), dtype=torch.float64, device="cuda"))
 
 
