@@ -92,6 +92,9 @@ def lib():
                                           ctypes.c_int, ctypes.c_double, _D]
             L.orc_prolong_robin.argtypes = [P, P, _D, _D]
             L.orc_diag_var.argtypes = [P, _D, _D, _D]
+            L.orc_op_robin_points.argtypes = [P, ctypes.c_double, ctypes.c_void_p, ctypes.c_int,
+                                              ctypes.c_int, ctypes.c_longlong,
+                                              ctypes.POINTER(ctypes.c_longlong), _D]
             L.orc_pcg_var.argtypes = [P, _D, _D, _D, _D, ctypes.c_double, ctypes.c_int, _I, _D]
             for name in ("orc_op_var", "orc_abs_op_var", "orc_bruteforce_apply_var"):
                 getattr(L, name).argtypes = [P, _D, _D, _D, _D]
@@ -518,3 +521,16 @@ def pcg_var(prob: Problem, d, m, b, x0=None, tol=1e-10, max_iter=10000):
     st = _check(lib().orc_pcg_var(ctypes.byref(prob._c()), _dp(d), _dp(m), _dp(b), _dp(x), float(tol),
                                   int(max_iter), ctypes.byref(it), ctypes.byref(rel)))
     return x, it.value, rel.value, st
+
+
+def op_robin_points(prob: Problem, pen, x, points, absolute=False):
+    """(A_R x) at the given flat indices of the Robin grid only; x float32 or float64;
+    absolute=True gives the (|A_R| |x|) scale there."""
+    x = np.ascontiguousarray(x)
+    assert x.dtype in (np.float32, np.float64) and x.size == int(np.prod(robin_shape(prob)))
+    pts = np.ascontiguousarray(points, dtype=np.int64)
+    out = np.zeros(pts.size)
+    _check(lib().orc_op_robin_points(ctypes.byref(prob._c()), float(pen), x.ctypes.data,
+                                     int(x.dtype == np.float32), int(bool(absolute)), pts.size,
+                                     pts.ctypes.data_as(ctypes.POINTER(ctypes.c_longlong)), _dp(out)))
+    return out

@@ -1628,3 +1628,41 @@ int orc_pcg_var(const orc_problem* p, const double* d, const double* m, const do
     free(dg); free(r); free(z); free(pv); free(q); free(bm);
     return status;
 }
+
+/* A_R x at selected flat indices only (the band-sum definition of orc_op_robin), x read as float
+ * or double; with absmode the |A_R| |x| scale there. For parity checks at sizes where a full
+ * oracle pass is too slow. */
+int orc_op_robin_points(const orc_problem* p, double pen, const void* x, int x_is_f32, int absmode,
+                        long long npts, const long long* pts, double* out)
+{
+    if (!problem_ok(p) || p->mask) return -1;
+    robin_tabs t;
+    memset(&t, 0, sizeof t);
+    if (robin_init(p, &t, absmode)) { robin_free(&t); return -1; }
+    const double dtw = absmode ? fabs(p->dt) : p->dt, penw = absmode ? fabs(pen) : pen;
+    int n = p->n, *Nt = t.Nt;
+    const float* xf = (const float*)x;
+    const double* xd = (const double*)x;
+#pragma omp parallel for schedule(dynamic, 4)
+    for (long long q = 0; q < npts; q++) {
+        long long I = pts[q];
+        int l[3] = {(int)(I % Nt[0]), (int)((I / Nt[0]) % Nt[1]), (int)(I / ((long long)Nt[0] * Nt[1]))};
+        double s = 0.0;
+        for (int kz = l[2] - n; kz <= l[2] + n; kz++) {
+            if (kz < 0 || kz >= Nt[2]) continue;
+            for (int ky = l[1] - n; ky <= l[1] + n; ky++) {
+                if (ky < 0 || ky >= Nt[1]) continue;
+                for (int kx = l[0] - n; kx <= l[0] + n; kx++) {
+                    if (kx < 0 || kx >= Nt[0]) continue;
+                    int k[3] = {kx, ky, kz};
+                    size_t src = ((size_t)kz * Nt[1] + ky) * Nt[0] + kx;
+                    double xv = x_is_f32 ? (double)xf[src] : xd[src];
+                    s += robin_weight(&t, dtw, penw, l, k) * (absmode ? fabs(xv) : xv);
+                }
+            }
+        }
+        out[q] = s;
+    }
+    robin_free(&t);
+    return 0;
+}

@@ -233,3 +233,27 @@ def test_prolongation_fp32(api):
     ref = oracle.prolong_robin(F, C, xc.astype(np.float64))
     # computed in FP64 inside and rounded once to FP32
     assert np.max(np.abs(xf - ref)) <= 1e-6 * np.max(np.abs(ref))
+
+
+def test_robin_sampled_parity_at_scale(api):
+    """FP64 linear Robin operator on 200 x 200 x 800 unknowns (0.2 G-node box of the large-run
+    analogue's shape at a third of its size): 300 sampled outputs, the faces and corners
+    included, against the oracle's band sum at those points."""
+    n, pen, dt = 1, 1.0e3, 1.0
+    nt = (200, 200, 800)
+    N = tuple(k - 2 for k in nt)
+    h = 1.0 / (nt[2] - 1)
+    P = oracle.Problem(*N, n, h, dt=dt)
+    H = api.Handle(*nt, n, h, dt, precision="f64")
+    H.set_boundary("robin", pen)
+    x = inputs.random_field((nt[2], nt[1], nt[0]), 14, device="cuda")
+    y = H.op_apply(x).cpu().numpy().reshape(-1)
+    rng = np.random.default_rng(15)
+    corners = [((z * nt[1] + yy) * nt[0] + xx) for z in (0, nt[2] - 1) for yy in (0, nt[1] - 1) for xx in (0, nt[0] - 1)]
+    faces = [((rng.integers(nt[2]) * nt[1] + rng.integers(nt[1])) * nt[0] + f) for f in (0, 1, nt[0] - 2, nt[0] - 1)
+             for _ in range(8)]
+    pts = np.unique(np.concatenate([rng.choice(x.numel(), 260, replace=False), corners, faces]))
+    xh = x.cpu().numpy()
+    ref = oracle.op_robin_points(P, pen, xh, pts)
+    scale = np.max(oracle.op_robin_points(P, pen, xh, pts, absolute=True))
+    assert np.max(np.abs(y[pts] - ref)) <= 1e-12 * scale

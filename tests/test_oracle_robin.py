@@ -176,3 +176,13 @@ def test_prolongation_exact_on_nested_grids(n):
     # constants map to constants on any pair of grids (partition of unity)
     one = oracle.prolong_robin(F, C, np.ones(oracle.robin_shape(C)))
     assert np.max(np.abs(one - 1.0)) <= 1e-10
+
+
+def test_points_match_full():
+    P = oracle.Problem(6, 5, 7, 2, 1 / 7, 1 / 6, 1 / 8, dt=0.02)
+    x = np.random.default_rng(11).standard_normal(oracle.robin_shape(P))
+    y = oracle.op_robin(P, 4.5, x)
+    pts = np.random.default_rng(12).choice(x.size, 50, replace=False)
+    assert np.array_equal(oracle.op_robin_points(P, 4.5, x, pts), y.reshape(-1)[pts])
+    assert np.array_equal(oracle.op_robin_points(P, 4.5, x, pts, absolute=True),
+                          oracle.abs_op_robin(P, 4.5, x).reshape(-1)[pts])
