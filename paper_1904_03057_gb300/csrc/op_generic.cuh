@@ -11,7 +11,11 @@
 // which is M M M x + dt (K M M + M K M + M M K) x with 7 band convolutions per point (the
 // mass-only variant runs 3). Depending on the mode the kernel also fuses the CG vector work of
 // section 2.5 around the operator: the search-direction update p = r + beta p_old on the fly
-// while staging, the deferred x update, the residual b - A x, and the p.Ap / r.r reductions.
+// while staging (p = r / diag A + beta p_old with the Jacobi preconditioner of the large run of
+// section 3), the deferred x update, the residual b - A x, and the p.Ap / r.r reductions.
+// The RB instantiation takes Robin (boundary penalty) problems: the untruncated basis with zero
+// ghosts, and the band rows of the n + 1 positions nearest each face read from a table (the
+// integrals there are truncated to the box and carry the penalty term).
 #pragma once
 
 #include <cuda_bf16.h>

@@ -1,5 +1,6 @@
 // vec_kernels.cuh -- streaming CG vector kernels (section 2.5 of arXiv:1904.03057) with fused
-// reductions (FP64 across threads and blocks).
+// reductions (FP64 across threads and blocks), including the Jacobi-preconditioned variants
+// (the solver of the large run of section 3).
 #pragma once
 
 #include "bsk_device.cuh"
