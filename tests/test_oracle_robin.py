@@ -4,6 +4,7 @@ and the coarse-grid prolongation (section 3). Closed forms from the cumulative B
 brute-force volume and surface quadrature, the Dirichlet limit of a large penalty for linear
 B-splines against the pinned reflected-basis solver, dense solves, exact prolongation between
 nested grids, and a planted boundary mistake."""
+import os
 import numpy as np
 import pytest
 
@@ -186,3 +187,90 @@ def test_points_match_full():
     assert np.array_equal(oracle.op_robin_points(P, 4.5, x, pts), y.reshape(-1)[pts])
     assert np.array_equal(oracle.op_robin_points(P, 4.5, x, pts, absolute=True),
                           oracle.abs_op_robin(P, 4.5, x).reshape(-1)[pts])
+
+
+def _flop1d_table():
+    rows = {}
+    with open(os.path.join(os.path.dirname(__file__), "golden", "flop1d_bspline.txt")) as f:
+        for line in f:
+            if line.strip() and not line.startswith("#"):
+                v = line.split()
+                rows[float(v[0])] = [int(c) for c in v[1:]]
+    return rows
+
+
+def _band_nonzeros(Nt, n):
+    """Entries of an Nt x Nt matrix with half-bandwidth n."""
+    return Nt * (2 * n + 1) - n * (n + 1)
+
+
+def test_operation_counts_of_table_tblFlop1d():
+    """The paper's operation counts for its 1-D Robin example on [-25, 25] (Table tblFlop1d,
+    B-spline columns) are those of one product with the 1-D system matrix, nnz multiplies and
+    nnz - Nt additions, over the untruncated basis. The oracle's matrices reproduce every printed
+    count: for h = 1 and 0.5 by counting their nonzero entries (which also shows the band is full
+    and nothing lies outside it), for all four steps through the basis size N + 2 + 2 floor(n/2)
+    with the full band. A basis of N + n + 1 functions, or one without the outermost B-splines,
+    misses the table."""
+    table = _flop1d_table()
+    assert sorted(table) == [0.125, 0.25, 0.5, 1.0]
+    for h, counts in table.items():
+        N = int(round(50 / h)) - 1          # interior nodes of [-25, 25] at step h
+        for n, printed in zip(DEGREES, counts):
+            Nt = oracle.robin_size(n, N)
+            assert 2 * _band_nonzeros(Nt, n) - Nt == printed, (h, n)
+            if h >= 0.5:
+                M, K, E = oracle.robin_1d(n, N, h)
+                A = K + M + 0.5 * E
+                nnz = int(np.count_nonzero(A))
+                assert nnz == _band_nonzeros(Nt, n), (h, n)
+                assert np.count_nonzero(np.triu(A, n + 1)) == 0
+                assert 2 * nnz - Nt == printed, (h, n)
+
+
+def _robin_line_solution(x):
+    """Closed-form solution of -phi'' + phi = exp(-(x/2)^2) on [-25, 25] with 2 phi'.n + phi = 0:
+    the whole-line solution (the source convolved with exp(-|x|)/2, in erfc form) plus the even
+    homogeneous term A cosh(x) that meets the end condition."""
+    from scipy.special import erfc
+
+    c = np.e * np.sqrt(np.pi) / 2
+
+    def part(t):
+        return c * (np.exp(-t) * erfc((2 - t) / 2) + np.exp(t) * erfc((t + 2) / 2))
+
+    def dpart(t):
+        return c * (-np.exp(-t) * erfc((2 - t) / 2) + np.exp(t) * erfc((t + 2) / 2))
+
+    A = -(2 * dpart(25.0) + part(25.0)) / (2 * np.sinh(25.0) + np.cosh(25.0))
+    return part(x) + A * np.cosh(x)
+
+
+def test_one_dimensional_robin_example_converges_at_order_n_plus_1():
+    """The paper's 1-D example (section 3: -(D phi')' + mu_a phi = exp(-(x/2)^2) on [-25, 25],
+    2 D phi'.n + phi = 0, h = 2^-mu), with D = mu_a = 1 (the paper gives no values): the Galerkin
+    system K + M + E/2 of the oracle's 1-D Robin matrices, solved densely, approaches the closed-form
+    solution in L2 at order h^(n+1) for n = 1..5. A wrong scale of K or M, a dropped or shifted
+    entry, or a wrong basis position breaks the rate."""
+    g, w = np.polynomial.legendre.leggauss(8)
+    for n in DEGREES:
+        errs = []
+        for h in (1.0, 0.5, 0.25):
+            N = int(round(50 / h)) - 1
+            M, K, E = oracle.robin_1d(n, N, h)
+            Nt, i0 = M.shape[0], -(n // 2)
+            t = (np.arange(N + 1)[:, None] + (g[None, :] + 1) / 2).ravel()   # node units
+            wt = np.tile(w * h / 2, N + 1)
+            xs = -25.0 + h * t
+            # B[p, a] = beta^n(t_p - (a + i0)), only the n + 1 B-splines nonzero at t_p
+            B = np.zeros((t.size, Nt))
+            first = np.floor(t - (n + 1) / 2).astype(int) + 1 - i0
+            for k in range(n + 1):
+                a = first + k
+                ok = (a >= 0) & (a < Nt)
+                B[np.nonzero(ok)[0], a[ok]] = oracle.bspline(n, t[ok] - (a[ok] + i0))
+            assert np.max(np.abs(B.sum(axis=1) - 1.0)) <= 1e-13   # every nonzero B-spline taken
+            c = np.linalg.solve(K + M + 0.5 * E, B.T @ (wt * np.exp(-(xs / 2) ** 2)))
+            errs.append(np.sqrt(np.sum(wt * (B @ c - _robin_line_solution(xs)) ** 2)))
+        rates = np.log2(np.array(errs[:-1]) / np.array(errs[1:]))
+        assert n + 1 - 0.1 <= rates[-1] <= n + 2, (n, errs, rates)
