@@ -167,10 +167,11 @@ def run_reference(args, rank, world):
         total += secs
     value = len(vals) / sum(1.0 / v for v in vals)
     line = {
-        "impl": "reference", "metric": METRIC, "value": value, "unit": "GDoF/s", "n_gpus": 0,
+        "impl": "reference", "metric": METRIC, "value": value, "unit": "GDoF/s", "n_gpus": world,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * total / args.steps,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
-        "data": "synthetic", "config": {"workload": WORKLOAD, "sample": desc},
+        "data": "synthetic", "config": {"workload": WORKLOAD, "sample": desc,
+                                        "runs_on": "host CPU cores (FP64 oracle); rank 0 only"},
         "cpu_baseline": {"value": value, "unit": "GDoF/s", "cores": cores, "kind": "oracle",
                          "sample": desc},
         "e2e": {"value": value, "unit": "GDoF/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
