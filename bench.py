@@ -512,10 +512,29 @@ def robin_large_run(iters: int = 200):
 
 def profile_case(name: str):
     """Small cases for the profiler: `var240` runs the variable-coefficient operator (cubic, FP32,
-    240 x 240 x 960, the inclusion fields of `variable_coefficients`) three times."""
+    240 x 240 x 960, the inclusion fields of `variable_coefficients`) three times; `robin200` runs
+    10 iterations of the FP64 Jacobi-preconditioned Robin CG of `robin_large_run` on 200 x 200 x
+    800 unknowns (256 MB per vector), then times its fused CG pass alone."""
     import torch
 
     from paper_1904_03057_gb300 import api, inputs
+    if name == "robin200":
+        import numpy as np
+        nt = (200, 200, 800)
+        h = 1.0 / (nt[2] - 1)
+        H = api.Handle(*nt, 1, h, 1.0, precision="f64")
+        H.set_boundary("robin", 1.0e3)
+        H.set_preconditioner("jacobi")
+        rng = np.random.default_rng(6)
+        cs = [tuple(rng.uniform(0.2, 0.8, size=3) * np.array([(c - 1) * h for c in nt]) + h) for _ in range(8)]
+        q = inputs.gaussian_source(*nt, cs, sigma=0.03, h=(h, h, h), device="cuda")
+        b = H.mass_apply(q)
+        x = torch.zeros_like(b)
+        ms, rep = _timed_ms(lambda: H.cg_solve(b, x, tol=1e-14, max_iter=10))
+        ms_cgp = H.time_kernel(api.KERNEL_CG_FUSED, reps=3)
+        print(json.dumps({"profile_case": name, "solve_ms": ms, "iterations": rep["iterations"],
+                          "cg_fused_ms": ms_cgp}), flush=True)
+        return
     if name != "var240":
         raise ValueError(name)
     nx, ny, nz = 240, 240, 960
@@ -728,7 +747,7 @@ def main():
     ap.add_argument("--grid", type=int, default=N_GRID,
                     help="grid edge (default: the benchmark workload; smaller grids are the "
                          "profiler's small case)")
-    ap.add_argument("--profile-case", choices=["var240"], default=None,
+    ap.add_argument("--profile-case", choices=["var240", "robin200"], default=None,
                     help="run one small case for the profiler instead of the benchmark")
     args = ap.parse_args()
     if args.profile_case:
