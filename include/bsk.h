@@ -238,13 +238,13 @@ int bsk_set_boundary(bsk_handle* h, int kind, double penalty);
  * BSK_F32_IR refinement):
  *   BSK_PC_NONE    plain CG (default);
  *   BSK_PC_JACOBI  Jacobi-preconditioned CG, z = r / diag(A) (the solver of the paper's large run,
- *                  section 3). With constant coefficients the diagonal of the separable operator
- *                  is formed on the fly from per-axis diagonals (with the reflection terms of the
- *                  Dirichlet basis, or the Robin rows); with variable coefficients 1 / diag(A) is
- *                  kept per node, computed by probing: (n + 1)^3 operator applications to the
- *                  indicator vectors of the node classes congruent modulo n + 1 per axis
- *                  (repeated when the coefficients or dt change). The CG iteration then takes the
- *                  two-pass general kernels.
+ *                  section 3). The handle keeps 1 / diag(A) per node, one vector in the CG
+ *                  precision. With constant coefficients it is formed from the per-axis diagonals
+ *                  of the separable operator (with the reflection terms of the Dirichlet basis, or
+ *                  the Robin rows). With variable coefficients it is computed by probing:
+ *                  (n + 1)^3 operator applications to the indicator vectors of the node classes
+ *                  congruent modulo n + 1 per axis. Either is redone when the coefficients, dt or
+ *                  the boundary change. The CG iteration then takes the two-pass general kernels.
  * Synchronises the stream; BSK_ENOMEM if the per-node diagonal cannot be allocated. */
 #define BSK_PC_NONE 0
 #define BSK_PC_JACOBI 1

@@ -157,7 +157,7 @@ struct bsk_handle {
     int pc;               // BSK_PC_NONE or BSK_PC_JACOBI
     void* jac[2];         // Jacobi: per-axis diagonals [3][2][jn], float [0] / double [1]
     int jn;
-    void* jvec;           // Jacobi with variable coefficients: 1 / diag A per node, CG precision
+    void* jvec;           // Jacobi: 1 / diag A per node, CG precision
     float* fcg_ws;        // FCG work vectors z, rn, zn (allocated by the first fcg_solve)
     double* fcg_partials;
     void* fcg_state;
@@ -944,7 +944,23 @@ int probe_diagonal_t(bsk_handle* h)
     return BSK_OK;
 }
 
-int probe_diagonal(bsk_handle* h)
+// 1 / diag A per node of the constant-coefficient operator (Dirichlet or Robin) from the
+// per-axis diagonals just uploaded to jac, in the CG precision.
+int fill_diagonal(bsk_handle* h)
+{
+    if (cg_es(h) == sizeof(double))
+        BSK_CUDA(bsk::launch_jacobi_fill<double>(static_cast<double*>(h->jvec), h->len, h->nx, h->ny,
+                                                 static_cast<const double*>(h->jac[1]), h->jn, h->stream));
+    else
+        BSK_CUDA(bsk::launch_jacobi_fill<float>(static_cast<float*>(h->jvec), h->len, h->nx, h->ny,
+                                                static_cast<const float*>(h->jac[0]), h->jn, h->stream));
+    BSK_CUDA(cudaStreamSynchronize(h->stream));
+    return BSK_OK;
+}
+
+// The per-node inverse diagonal of a Jacobi handle: probed for variable coefficients, formed
+// from the separable per-axis diagonals otherwise.
+int node_diagonal(bsk_handle* h)
 {
     const size_t es = cg_es(h);
     cudaError_t e = cudaMalloc(&h->jvec, h->len * es);
@@ -953,7 +969,8 @@ int probe_diagonal(bsk_handle* h)
         h->jvec = nullptr;
         return fail(BSK_ENOMEM, "Jacobi diagonal: cudaMalloc(%zu) failed", h->len * es);
     }
-    return es == sizeof(double) ? probe_diagonal_t<double>(h) : probe_diagonal_t<float>(h);
+    if (h->cd[0] || h->cd[1]) return es == sizeof(double) ? probe_diagonal_t<double>(h) : probe_diagonal_t<float>(h);
+    return fill_diagonal(h);
 }
 
 // Rebuilds the Robin rows and Jacobi diagonals after a change of boundary, dt, coefficients or
@@ -975,7 +992,7 @@ int refresh_tables(bsk_handle* h)
         cudaFree(h->jvec);
         h->jvec = nullptr;
     }
-    if (h->pc == BSK_PC_JACOBI && (h->cd[0] || h->cd[1])) return probe_diagonal(h);
+    if (h->pc == BSK_PC_JACOBI) return node_diagonal(h);
     return BSK_OK;
 }
 

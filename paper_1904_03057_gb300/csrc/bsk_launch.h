@@ -50,8 +50,8 @@ struct OpLaunch {
     // null = no preconditioner
     const void* jac[2];
     int jn;                      // row length of the jac tables
-    // MODE_CGP of the variable-coefficient kernel: 1 / diag A per node (Jacobi), float [0] /
-    // double [1]; null = no preconditioner
+    // MODE_CGP: 1 / diag A per node (Jacobi), float [0] / double [1]; the kernels read it instead
+    // of the jac tables; null = no preconditioner
     const void* jvec[2];
 };
 
@@ -95,6 +95,10 @@ cudaError_t launch_cg_update_pc(T* r, const T* q, size_t len, int nx, int ny, co
 template <typename T>
 cudaError_t launch_pc_dot(const T* r, size_t len, int nx, int ny, const T* jac, int jn, const T* jvec,
                           Scalars* sc, double* partials, cudaStream_t s);
+// jinv[i] = 1 / diag A of the separable operator at flat index i, from the per-axis tables jac
+// (vec_kernels.cuh, k_jacobi_fill).
+template <typename T>
+cudaError_t launch_jacobi_fill(T* jinv, size_t len, int nx, int ny, const T* jac, int jn, cudaStream_t s);
 // Diagonal probing (var_impl.cuh): take = 0 fills v with the indicator of colour (cx, cy, cz)
 // modulo stride; take = 1 stores 1 / y at that colour's nodes into jinv.
 template <typename T>

@@ -70,6 +70,7 @@ static cudaError_t launch_generic(const OpLaunch& L, cudaStream_t s)
     a.rb = static_cast<const T*>(L.rb[sizeof(T) == 8]);
     a.jac = MODE == MODE_CGP ? static_cast<const T*>(L.jac[sizeof(T) == 8]) : nullptr;
     a.jn = L.jn;
+    a.jvec = MODE == MODE_CGP ? static_cast<const T*>(L.jvec[sizeof(T) == 8]) : nullptr;
     if (a.rb) k_op_generic<T, N, MODE, true><<<grid, kGenNT, smem, s>>>(a);
     else k_op_generic<T, N, MODE, false><<<grid, kGenNT, smem, s>>>(a);
     return cudaGetLastError();
@@ -136,6 +137,14 @@ cudaError_t launch_pc_dot<BSK_T>(const BSK_T* r, size_t len, int nx, int ny, con
                                  const BSK_T* jvec, Scalars* sc, double* partials, cudaStream_t s)
 {
     k_pc_dot<BSK_T><<<vec_grid(len), kVecNT, 0, s>>>(r, len, nx, ny, jac, jn, jvec, sc, partials);
+    return cudaGetLastError();
+}
+
+template <>
+cudaError_t launch_jacobi_fill<BSK_T>(BSK_T* jinv, size_t len, int nx, int ny, const BSK_T* jac, int jn,
+                                      cudaStream_t s)
+{
+    k_jacobi_fill<BSK_T><<<vec_grid(len), kVecNT, 0, s>>>(jinv, len, nx, ny, jac, jn);
     return cudaGetLastError();
 }
 

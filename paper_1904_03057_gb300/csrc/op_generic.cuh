@@ -44,6 +44,7 @@ struct OpArgs {
     const T* rb;      // Robin problems: band rows near the faces (robin_row), null otherwise
     const T* jac;     // CGP: Jacobi diagonal factors (jacobi_inv), null = no preconditioner
     int jn;           // row length of jac
+    const T* jvec;    // CGP: 1 / diag A per node (Jacobi), read instead of forming it from jac
 };
 
 // Robin (boundary penalty) problems use the untruncated basis with integrals truncated to the
@@ -166,8 +167,13 @@ __global__ void __launch_bounds__(kGenNT) k_op_generic(const __grid_constant__ O
                 const size_t o = ((size_t)sz * ny + sy) * nx + sx;
                 if (!mask || mask[o]) {
                     T u;
-                    if (MODE == MODE_CGP)
-                        u = (a.jac ? a.in0[o] * jacobi_inv(a.jac, a.jn, sx, sy, sz) : a.in0[o]) + beta * a.in1[o];
+                    if (MODE == MODE_CGP) {
+                        const T r = a.in0[o];
+                        const T zr = a.jvec  ? r * a.jvec[o]
+                                     : a.jac ? r * jacobi_inv(a.jac, a.jn, sx, sy, sz)
+                                             : r;
+                        u = zr + beta * a.in1[o];
+                    }
                     else if (MODE == MODE_MASS)
                         u = ld_io(a.in0, o, a.bf16io) + (a.in1 ? (T)a.s * ld_io(a.in1, o, a.bf16io) : T(0));
                     else if (MODE == MODE_OP) u = ld_io(a.in0, o, a.bf16io);

@@ -121,6 +121,18 @@ __global__ void __launch_bounds__(kVecNT) k_pc_dot(const T* __restrict__ r, size
     grid_reduce2<kVecNT>(rz.value(), 0.0, partials, sc, FIN_PC_INIT, 0);
 }
 
+// jinv[i] = 1 / diag A at flat index i: the per-node vector the preconditioned passes read, so
+// that the diagonal is formed once per solve setting rather than at every use (in FP64 on GB300
+// the formation costs more than the 8 bytes per node of the read).
+template <typename T>
+__global__ void __launch_bounds__(kVecNT) k_jacobi_fill(T* __restrict__ jinv, size_t len, int nx, int ny,
+                                                        const T* __restrict__ jac, int jn)
+{
+    for (size_t i = blockIdx.x * (size_t)kVecNT + threadIdx.x; i < len;
+         i += (size_t)gridDim.x * kVecNT)
+        jinv[i] = jacobi_inv_flat(jac, jn, i, nx, ny);
+}
+
 // x += alpha_prev p[p_cur]: applies the last deferred update once the iteration has stopped.
 template <typename T>
 __global__ void __launch_bounds__(kVecNT) k_cg_flush(T* __restrict__ x, const T* __restrict__ p0,
