@@ -1,6 +1,7 @@
 """ctypes binding of libbsk.so (include/bsk.h). Argument marshalling only: every step of the
-path runs in the library's CUDA kernels. Importing this module loads the library and raises if
-it is missing or fails to load: there is no fallback."""
+path runs in the library's CUDA kernels. The library is loaded on first use (built first if it
+is missing or older than its sources) and any failure to build or load raises: there is no
+fallback."""
 from __future__ import annotations
 
 import ctypes
