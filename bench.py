@@ -111,17 +111,24 @@ class ClockSampler:
             self.proc.wait(timeout=5)
         except Exception:
             self.proc.kill()
+        return self.summarise(self.lines)
+
+    @staticmethod
+    def summarise(lines):
+        """Median SM clock, maximum SM clock and the throttle reasons seen in `FIELDS` lines
+        (csv, no header, no units); lines that do not parse are skipped."""
         sm, mx, reasons = [], [], set()
         names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
-        for ln in self.lines:
+        for ln in lines:
             parts = [p.strip() for p in ln.split(",")]
             if len(parts) < 6:
                 continue
             try:
-                sm.append(float(parts[0]))
-                mx.append(float(parts[1]))
+                clk, clk_max = float(parts[0]), float(parts[1])
             except ValueError:
                 continue
+            sm.append(clk)
+            mx.append(clk_max)
             for nm, v in zip(names, parts[2:6]):
                 if v.lower().startswith("active"):
                     reasons.add(nm)
