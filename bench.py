@@ -483,13 +483,16 @@ def robin_large_run(iters: int = 200):
     ms_cgp = Hf.time_kernel(api.KERNEL_CG_FUSED, reps=3)
     ms_upd = Hf.time_kernel(api.KERNEL_CG_UPDATE, reps=3)
     flops = 14.0 * (2 * n + 1) * nodes
-    fp64_peak = 1.25   # TFLOP/s, nominal GB300 FP64 (no measured FP64 peak is recorded)
+    # TFLOP/s, nominal GB300 FP64: 152 SMs x 2 DFMA per clock x 2 flop x 2.07 GHz (ncu reports a
+    # DFMA peak of 304 per cycle for the whole GPU); no measured FP64 peak is recorded
+    fp64_peak = 1.25
     out["kernel_ms"] = {"cg_fused_f64": ms_cgp, "cg_update_f64": ms_upd}
     out["roofline"] = {"kernel": "k_op_generic<double,1,CGP,RB> (Robin, Jacobi)", "bound": "fp64",
                        "achieved": flops / (ms_cgp * 1e-3) / 1e12, "peak": fp64_peak, "unit": "TFLOP/s",
                        "frac": flops / (ms_cgp * 1e-3) / 1e12 / fp64_peak, "traffic": None,
                        "hbm_gbs": 48.0 * nodes / (ms_cgp * 1e-3) / 1e9,
-                       "note": "algorithmic 14 (2n + 1) flop per unknown; peak = nominal FP64 rate; "
+                       "note": "algorithmic 14 (2n + 1) flop per unknown; peak = nominal FP64 rate "
+                               "(152 SMs x 2 DFMA/clock x 2 flop x 2.07 GHz); "
                                "hbm_gbs = 48 B/unknown (r, p read, p, q written, x read and written)"}
     Hf.close()
     torch.cuda.empty_cache()
