@@ -490,10 +490,10 @@ def robin_large_run(iters: int = 200):
     out["roofline"] = {"kernel": "k_op_generic<double,1,CGP,RB> (Robin, Jacobi)", "bound": "fp64",
                        "achieved": flops / (ms_cgp * 1e-3) / 1e12, "peak": fp64_peak, "unit": "TFLOP/s",
                        "frac": flops / (ms_cgp * 1e-3) / 1e12 / fp64_peak, "traffic": None,
-                       "hbm_gbs": 48.0 * nodes / (ms_cgp * 1e-3) / 1e9,
+                       "hbm_gbs": 56.0 * nodes / (ms_cgp * 1e-3) / 1e9,
                        "note": "algorithmic 14 (2n + 1) flop per unknown; peak = nominal FP64 rate "
                                "(152 SMs x 2 DFMA/clock x 2 flop x 2.07 GHz); "
-                               "hbm_gbs = 48 B/unknown (r, p read, p, q written, x read and written)"}
+                               "hbm_gbs = 56 B/unknown (r, p, 1/diag A read; p, q written; x read and written)"}
     Hf.close()
     torch.cuda.empty_cache()
     # the same problem and start with FP32 inner PCG inside FP64 refinement (the library's
