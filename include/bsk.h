@@ -89,7 +89,10 @@ typedef struct bsk_problem {
 
 typedef struct bsk_handle bsk_handle;
 
-/* Creates a solver handle: validates the problem, uploads the kernels and the mask, allocates
+/* Creates a solver handle for the implicit-Euler system of one box (Eq. tensForm, section 2.4:
+ * A = Mz (x) My (x) Mx + dt (Kz (x) My (x) Mx + Mz (x) Ky (x) Mx + Mz (x) My (x) Kx) with the
+ * kernels of Table tblBsplines; with a mask, its principal submatrix on the active nodes).
+ * It validates the problem, uploads the kernels and the mask, allocates
  * every work vector the handle needs for op_apply, mass_apply, cg_solve and heat_step (the hot
  * loop never allocates), and binds the handle to `stream` (a cudaStream_t; NULL = the legacy
  * default stream). precision is BSK_F64, BSK_F32, BSK_F32_IR or BSK_BF16S (operator only, no
@@ -100,7 +103,9 @@ int bsk_create(const bsk_problem* prob, int precision, void* stream, bsk_handle*
 /* Releases the handle and its device memory (after synchronising its stream). NULL is a no-op. */
 void bsk_destroy(bsk_handle* h);
 
-/* Changes dt (the stiffness weight) of an existing handle. */
+/* Changes dt, the weight of the stiffness term in the implicit-Euler operator (Eq. tensForm),
+ * of an existing handle. The Robin rows and the Jacobi diagonal of the handle, which carry dt,
+ * are rebuilt. */
 int bsk_set_dt(bsk_handle* h, double dt);
 
 /* y = A x: the full operator, three axis sweeps fused in one pass (Fig. FiltAlg). x and y are
@@ -286,13 +291,15 @@ typedef struct bsk_batch bsk_batch;
 int bsk_batch_create(const bsk_problem* probs, int count, int precision, void* stream, bsk_batch** out);
 void bsk_batch_destroy(bsk_batch* b);
 
-/* b, x: HOST arrays of `count` DEVICE pointers to dense double vectors (x in: start, out:
+/* CG (section 2.5) on every problem's system A x = b (Eq. tensForm), inside iterative
+ * refinement. b, x: HOST arrays of `count` DEVICE pointers to dense double vectors (x in: start, out:
  * solution). reports (may be NULL): HOST array of `count` reports. The returned status is the
  * worst of the problems' statuses. opts as for cg_solve (applied to every problem). */
 int bsk_batch_cg_solve(bsk_batch* b, const void* const* bvec, void* const* x, const bsk_cg_opts* opts,
                        bsk_cg_report* reports);
 
-/* nsteps implicit Euler steps of every problem (as heat_step); q may be NULL or hold NULLs. */
+/* nsteps implicit Euler steps of every problem, as heat_step (right-hand side M (u + dt q), the
+ * source term of Eq. RitzGalerkin in the solution's basis); q may be NULL or hold NULLs. */
 int bsk_batch_heat_step(bsk_batch* b, void* const* u, const void* const* q, int nsteps,
                         const bsk_cg_opts* opts, bsk_cg_report* reports);
 
@@ -348,7 +355,8 @@ int bsk_net_adam(bsk_net* net, float lr, float grad_scale);
 /* Accumulated loss (host float) and, if grads is not NULL, the gradients (host floats). */
 int bsk_net_read_loss(bsk_net* net, float* loss, float* grads);
 
-/* Flexible CG (FCG(1), one previous direction kept A-orthogonal) preconditioned by the network,
+/* Not in the paper: the learned preconditioner of this library. Flexible CG (FCG(1), Notay's
+ * truncated flexible CG, one previous direction kept A-orthogonal) preconditioned by the network,
  * z = ||r|| N(r / ||r||) / (hx hy hz), as the inner FP32 solver of iterative refinement (handle
  * precision BSK_F32_IR; b, x double). The network must have been created for the handle's grid.
  * An iteration whose network direction is no descent direction (z.r <= 0) uses z = r for that
@@ -378,8 +386,8 @@ int fcg_solve(bsk_handle* h, bsk_net* net, const void* b, void* x, const bsk_cg_
 #define BSK_KERNEL_RES_DF 4
 int bsk_time_kernel(bsk_handle* h, int kernel, int reps, double* ms);
 
-/* Allocation-free residual: r = b - A x, with *rr = r.r and *bb = b.b reduced in FP64 (the
- * paper has no counterpart; this is an interface for callers that cannot allocate device
+/* Allocation-free residual: r = b - A x (A as for op_apply, Eq. tensForm), with *rr = r.r and
+ * *bb = b.b reduced in FP64 (the paper has no counterpart for this interface; this is an interface for callers that cannot allocate device
  * memory -- for example a solver plugin inside a host application that owns the device memory
  * budget and hands in pre-allocated buffers -- and therefore cannot create a handle).
  * It needs no handle and allocates nothing: its scratch (an FP64 scalar block and the partial
