@@ -521,13 +521,39 @@ def robin_large_run(iters: int = 200):
 
 
 def profile_case(name: str):
-    """Small cases for the profiler: `var240` runs the variable-coefficient operator (cubic, FP32,
+    """Small cases for the profiler: `cg512` runs 12 single-pass FP32 CG iterations of the
+    benchmark's operator at 512^3 (537 MB per vector, a 3.8 GB handle) and then times that pass
+    alone; `op384` applies the FP32 cubic operator of the benchmark
+    (unmasked box, dt = 5e-4) to the benchmark's kind of field at 384^3 (226 MB per vector, larger
+    than L2) four times; `var240` runs the variable-coefficient operator (cubic, FP32,
     240 x 240 x 960, the inclusion fields of `variable_coefficients`) three times; `robin200` runs
     10 iterations of the FP64 Jacobi-preconditioned Robin CG of `robin_large_run` on 200 x 200 x
     800 unknowns (256 MB per vector), then times its fused CG pass alone."""
     import torch
 
     from paper_1904_03057_gb300 import api, inputs
+    if name == "cg512":
+        N = 512
+        h = 1.0 / (N + 1)
+        H = api.Handle(N, N, N, DEGREE, h, DT, precision="f32")
+        modes = inputs.random_sine_modes(SEED, NMODES, KMAX)
+        b = inputs.sine_mode_field(N, N, N, modes, device="cuda", dtype=torch.float64).float()
+        x = torch.zeros_like(b)
+        ms, rep = _timed_ms(lambda: H.cg_solve(b, x, tol=1e-30, max_iter=12, check_every=4))
+        ms_cg = H.time_kernel(api.KERNEL_CG_FUSED, reps=5)
+        print(json.dumps({"profile_case": name, "solve_ms": ms, "iterations": rep["iterations"],
+                          "cg_fused_ms": ms_cg}), flush=True)
+        return
+    if name == "op384":
+        N = 384
+        h = 1.0 / (N + 1)
+        H = api.Handle(N, N, N, DEGREE, h, DT, precision="f32")
+        modes = inputs.random_sine_modes(SEED, NMODES, KMAX)
+        x = inputs.sine_mode_field(N, N, N, modes, device="cuda", dtype=torch.float64).float()
+        y = torch.empty_like(x)
+        ms = [_timed_ms(lambda: H.op_apply(x, y))[0] for _ in range(4)]
+        print(json.dumps({"profile_case": name, "ms": ms, "max_abs_y": float(y.abs().max())}), flush=True)
+        return
     if name == "robin200":
         import numpy as np
         nt = (200, 200, 800)
@@ -757,7 +783,7 @@ def main():
     ap.add_argument("--grid", type=int, default=N_GRID,
                     help="grid edge (default: the benchmark workload; smaller grids are the "
                          "profiler's small case)")
-    ap.add_argument("--profile-case", choices=["var240", "robin200"], default=None,
+    ap.add_argument("--profile-case", choices=["op384", "cg512", "var240", "robin200"], default=None,
                     help="run one small case for the profiler instead of the benchmark")
     args = ap.parse_args()
     if args.profile_case:

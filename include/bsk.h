@@ -386,23 +386,45 @@ int fcg_solve(bsk_handle* h, bsk_net* net, const void* b, void* x, const bsk_cg_
 #define BSK_KERNEL_RES_DF 4
 int bsk_time_kernel(bsk_handle* h, int kernel, int reps, double* ms);
 
-/* Allocation-free residual: r = b - A x (A as for op_apply, Eq. tensForm), with *rr = r.r and
- * *bb = b.b reduced in FP64 (the paper has no counterpart for this interface; this is an interface for callers that cannot allocate device
- * memory -- for example a solver plugin inside a host application that owns the device memory
- * budget and hands in pre-allocated buffers -- and therefore cannot create a handle).
+/* Choice of the kernel that runs the single-pass FP32 CG iteration (the CG stage of section 2.5
+ * with the operator of Eq. tensForm; bsk_cg_solve, heat_step and the FP32 inner iterations of
+ * BSK_F32_IR). Two kernels implement the same iteration on unmasked grids with 16-byte rows
+ * and degree <= 4: a warp-specialised pass (BSK_CG_KERNEL_WS: 64 x 32 tiles, one block per SM)
+ * and the two-block-per-SM pass used for every other grid (BSK_CG_KERNEL_CLASSIC); neither is
+ * the faster on every grid shape. bsk_create chooses with BSK_CG_KERNEL_AUTO, which times both
+ * on the handle's own work vectors (zeroing them; about four passes each) and keeps the faster.
+ * request: BSK_CG_KERNEL_AUTO, BSK_CG_KERNEL_WS or BSK_CG_KERNEL_CLASSIC; *chosen (nullable)
+ * receives the kernel now in use (WS or CLASSIC). Call it between solves only, never while the
+ * handle's stream is capturing. Returns BSK_EINVAL for an unknown request or for
+ * BSK_CG_KERNEL_WS on a handle that cannot use it (masked grid, BSK_F64, degree 5, rows that
+ * are not 16-byte multiples); AUTO on such a handle selects CLASSIC without timing. */
+#define BSK_CG_KERNEL_AUTO 0
+#define BSK_CG_KERNEL_WS 1
+#define BSK_CG_KERNEL_CLASSIC 2
+int bsk_select_cg_kernel(bsk_handle* h, int request, int* chosen);
+
+/* Allocation-free residual: r = b - A x (A as for op_apply), with *rr = r.r and *bb = b.b
+ * reduced in FP64. The paper has no counterpart for this interface: it serves callers that
+ * cannot allocate device memory -- for example a solver plugin inside a host application that
+ * owns the device memory budget and hands in pre-allocated buffers -- and therefore cannot
+ * create a handle.
  * It needs no handle and allocates nothing: its scratch (an FP64 scalar block and the partial
  * sums of the two reductions, about 256 KB) is a file-scope static device array that every GPU
  * loading this library holds until the process exits. prob describes the grid as for
  * bsk_create (prob->mask, if set, is read in place); precision is BSK_F64 (double vectors) or
  * BSK_F32 (float vectors; reductions still FP64); x, b, r are DEVICE vectors of nx*ny*nz
  * elements owned by the caller, r must not overlap x or b; stream is a cudaStream_t.
- * The first call on a device looks up the scratch's device address with that device current;
- * make that first call before any stream capture. Every call shares the one scratch array and
- * clears what must start at zero itself; calls that overlap on the GPU (other streams, other
- * threads) race on it and must be serialised by the caller. The call synchronises `stream`.
- * Returns BSK_EINVAL (with a message in bsk_last_error) for a grid whose general operator
- * kernel needs more than 16384 blocks (about 2048^3 unknowns), for bad arguments, or for
- * precision BSK_F32_IR. */
+ * The first call on a device looks up the scratch's device address with that device current
+ * (and the first call per precision and degree sets up that operator kernel); make that first
+ * call before any stream capture. Every call reads its two norms back to the host and
+ * synchronises `stream`; a call made while `stream` is capturing returns BSK_EINVAL without
+ * touching the capture.
+ * Every call shares the one scratch array and clears what must start at zero itself; calls
+ * that overlap on the GPU (other streams, other threads) race on it and must be serialised by
+ * the caller.
+ * Returns BSK_EINVAL (with a message in bsk_last_error) for a grid with
+ * ceil(nx/32) * ceil(ny/16) > 16384 (about 8.4 M nodes per x-y plane; nz is not limited), for
+ * bad arguments, or for precision BSK_F32_IR. */
 int residual_noalloc(const bsk_problem* prob, int precision, const void* x, const void* b, void* r,
                      double* rr, double* bb, void* stream);
 

@@ -151,6 +151,7 @@ struct bsk_handle {
     void* cd[2];
     void* cm[2];
     bool use_tma0, tma640, res_df0;   // TMA eligibility of the constant-coefficient operator
+    int cg_impl;          // single-pass FP32 CG iteration: 0 = warp-specialised, 1 = op_tma.cuh
     int bc;               // BSK_BC_DIRICHLET (odd reflection) or BSK_BC_ROBIN (untruncated basis)
     double pen;           // Robin: weight of the boundary term
     void* rb[2];          // Robin: band rows near the faces, float [0] / double [1]
@@ -176,6 +177,7 @@ void fill_tma(const bsk_handle* h, bsk::TmaLaunch& L, int mode)
     memset(&L, 0, sizeof L);
     L.work = h->work;
     L.mode = mode;
+    L.impl = h->cg_impl;
     L.degree = h->n;
     L.nx = h->nx;
     L.ny = h->ny;
@@ -199,6 +201,12 @@ bool tma_ok(const bsk_handle* h, size_t es, std::initializer_list<const void*> p
     for (const void* p : ptrs)
         if (!aligned16(p)) return false;
     return true;
+}
+
+// Can the single-pass FP32 CG iteration of this handle run as the warp-specialised pass?
+bool cg_ws_eligible(const bsk_handle* h)
+{
+    return h->use_tma0 && (h->prec == BSK_F32 || h->prec == BSK_F32_IR) && !h->mask && bsk::ws_supported(h->n);
 }
 
 cudaError_t tma_launch_es(size_t es, const bsk::TmaLaunch& L, cudaStream_t s)
@@ -766,6 +774,12 @@ extern "C" int bsk_create(const bsk_problem* prob, int precision, void* stream, 
     e = cudaStreamSynchronize(h->stream);
     if (e != cudaSuccess) return cleanup(cuda_fail(e, "bsk_create"));
 #undef BSK_ALLOC
+    h->cg_impl = 1;
+    if (cg_ws_eligible(h)) {
+        // two single-pass CG kernels implement the same iteration; neither is the faster one on
+        // every grid shape, so time both on this handle's vectors and keep the faster
+        if (int rc = bsk_select_cg_kernel(h, BSK_CG_KERNEL_AUTO, nullptr)) return cleanup(rc);
+    }
     *out = h;
     return BSK_OK;
 }
@@ -1462,6 +1476,47 @@ extern "C" int bsk_time_kernel(bsk_handle* h, int kernel, int reps, double* ms)
     if (e1) cudaEventDestroy(e1);
     if (err != cudaSuccess) return cuda_fail(err, "bsk_time_kernel");
     *ms = (double)total / reps;
+    return BSK_OK;
+}
+
+extern "C" int bsk_select_cg_kernel(bsk_handle* h, int request, int* chosen)
+{
+    if (int rc = check_handle(h)) return rc;
+    if (request != BSK_CG_KERNEL_AUTO && request != BSK_CG_KERNEL_WS && request != BSK_CG_KERNEL_CLASSIC)
+        return fail(BSK_EINVAL, "unknown CG kernel request %d", request);
+    const bool ws_ok = cg_ws_eligible(h);
+    if (request == BSK_CG_KERNEL_WS && !ws_ok)
+        return fail(BSK_EINVAL, "the warp-specialised CG pass needs an unmasked FP32 TMA grid of degree <= 4");
+    int impl = request == BSK_CG_KERNEL_WS ? 0 : 1;
+    if (request == BSK_CG_KERNEL_AUTO && ws_ok) {
+        // time both passes on the handle's own vectors (bsk_time_kernel zeroes them first and
+        // launches once untimed); the first measurement of each warms it up
+        const bool tma_now = h->use_tma;
+        h->use_tma = h->use_tma0;
+        double best = 0.0;
+        for (int cand = 0; cand < 2; cand++) {
+            h->cg_impl = cand;
+            double ms = 0.0;
+            int rc = bsk_time_kernel(h, BSK_KERNEL_CG_FUSED, 1, &ms);
+            if (rc == BSK_OK) rc = bsk_time_kernel(h, BSK_KERNEL_CG_FUSED, 2, &ms);
+            if (rc != BSK_OK) {
+                h->use_tma = tma_now;
+                return rc;
+            }
+            if (cand == 0 || ms < best) {
+                best = ms;
+                impl = cand;
+            }
+        }
+        h->use_tma = tma_now;
+    }
+    h->cg_impl = impl;
+    if (h->graph) {   // the captured CG chunk holds the previous kernel
+        cudaStreamSynchronize(h->stream);
+        cudaGraphExecDestroy(h->graph);
+        h->graph = nullptr;
+    }
+    if (chosen) *chosen = impl == 0 ? BSK_CG_KERNEL_WS : BSK_CG_KERNEL_CLASSIC;
     return BSK_OK;
 }
 

@@ -144,6 +144,8 @@ struct TmaLaunch {
     double* partials;            // 3 doubles per block of the resident grid
     unsigned int* work;          // 2 counters, zero between launches (dynamic item queue)
     int fin;
+    int impl;                    // TMODE_CG, FP32, unmasked, degree <= 4: 0 = the warp-specialised
+                                 // pass (op_ws.cuh), 1 = the single-pass kernel of op_tma.cuh
 };
 // In-place banded triangular solves along one axis (0 = x, 1 = y, 2 = z) of an nx*ny*nz grid,
 // one thread per line: L holds a banded Cholesky factor of half-width p <= 5 (transform.cu).
@@ -162,6 +164,13 @@ template <typename T>
 int tma_grid(int degree, int mode);   // resident blocks (after prepare_tma), 0 if unsupported
 template <typename T>
 cudaError_t launch_tma(const TmaLaunch& L, cudaStream_t s);
+
+// Warp-specialised FP32 passes (op_ws.cuh): unmasked y = A x and the single-pass CG iteration,
+// degrees 1..4; launch_tma<float> takes them for TMODE_OP and TMODE_CG without a mask.
+// prepare_ws is called by prepare_tma<float>.
+bool ws_supported(int degree);
+cudaError_t prepare_ws(int degree);
+cudaError_t launch_ws(const TmaLaunch& L, cudaStream_t s);
 
 // Batched single-pass CG iteration (FP32): one persistent launch over the items of all the
 // problems of one degree; desc points to BatchProblem<float>[nprobs] in device memory.

@@ -18,6 +18,9 @@
 namespace {
 
 // Largest operator grid (blocks of the general operator kernel) the static scratch can reduce.
+// The general kernel's grid has ceil(nx/32) * ceil(ny/16) blocks per z-slab and a single slab
+// once that product reaches 1216, so the bound is ceil(nx/32) * ceil(ny/16) <= 16384 (about
+// 8.4 M nodes per x-y plane), whatever nz is.
 constexpr size_t kNoAllocMaxBlocks = 16384;
 
 struct NoAllocScratch {
@@ -30,12 +33,14 @@ __device__ __align__(256) unsigned char g_noalloc_scratch[sizeof(NoAllocScratch)
 std::mutex g_noalloc_mu;
 constexpr int kMaxDevices = 64;
 void* g_noalloc_addr[kMaxDevices] = {};   // device address of g_noalloc_scratch, per device
+bool g_noalloc_prepared[kMaxDevices][2][6] = {};   // kernel set-up done: device, FP64?, degree
 
 int noalloc_fail(int code, const char* msg) { return bsk::set_error(code, msg); }
 
 // Host code cannot use g_noalloc_scratch as a device address (on the host that name is only a
-// stand-in), so each device's address is fetched once, with that device current.
-int scratch_address(void** out)
+// stand-in), so each device's address is fetched once, with that device current. The operator
+// kernels' shared-memory limits are set once per device, precision and degree at the same time.
+int scratch_address(void** out, bool fp64, int degree)
 {
     int dev = 0;
     if (cudaGetDevice(&dev) != cudaSuccess) return noalloc_fail(BSK_ECUDA, "cudaGetDevice failed");
@@ -49,6 +54,14 @@ int scratch_address(void** out)
             return noalloc_fail(BSK_ECUDA, "cudaGetSymbolAddress of the static scratch failed");
         }
         g_noalloc_addr[dev] = p;
+    }
+    if (!g_noalloc_prepared[dev][fp64][degree]) {
+        const cudaError_t e = fp64 ? bsk::prepare_op<double>(degree) : bsk::prepare_op<float>(degree);
+        if (e != cudaSuccess) {
+            cudaGetLastError();
+            return noalloc_fail(BSK_ECUDA, "kernel set-up failed");
+        }
+        g_noalloc_prepared[dev][fp64][degree] = true;
     }
     *out = g_noalloc_addr[dev];
     return BSK_OK;
@@ -73,7 +86,8 @@ extern "C" int residual_noalloc(const bsk_problem* prob, int precision, const vo
         char msg[200];
         snprintf(msg, sizeof msg,
                  "grid too large for the static scratch: %zu operator blocks, at most %zu "
-                 "(about 2048^3 unknowns)", blocks, kNoAllocMaxBlocks);
+                 "(ceil(nx/32) * ceil(ny/16) <= 16384, about 8.4 M nodes per x-y plane, any nz)",
+                 blocks, kNoAllocMaxBlocks);
         return noalloc_fail(BSK_EINVAL, msg);
     }
     const size_t es = precision == BSK_F64 ? sizeof(double) : sizeof(float);
@@ -82,14 +96,21 @@ extern "C" int residual_noalloc(const bsk_problem* prob, int precision, const vo
     if ((pr < px + len * es && px < pr + len * es) || (pr < pb + len * es && pb < pr + len * es))
         return noalloc_fail(BSK_EINVAL, "r overlaps x or b");
 
-    void* base = nullptr;
-    if (int rc = scratch_address(&base)) return rc;
-    NoAllocScratch* s = static_cast<NoAllocScratch*>(base);
     cudaStream_t st = (cudaStream_t)stream;
-    cudaError_t e = es == sizeof(double) ? bsk::prepare_op<double>(n) : bsk::prepare_op<float>(n);
-    if (e != cudaSuccess) return noalloc_fail(BSK_ECUDA, "kernel set-up failed");
+    // every call reads its result back and synchronises the stream, which a capture cannot hold
+    cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
+    if (cudaStreamIsCapturing(st, &cap) != cudaSuccess) {
+        cudaGetLastError();
+        return noalloc_fail(BSK_ECUDA, "cudaStreamIsCapturing failed");
+    }
+    if (cap != cudaStreamCaptureStatusNone)
+        return noalloc_fail(BSK_EINVAL, "residual_noalloc cannot run while its stream is capturing");
+
+    void* base = nullptr;
+    if (int rc = scratch_address(&base, es == sizeof(double), n)) return rc;
+    NoAllocScratch* s = static_cast<NoAllocScratch*>(base);
     // the scratch keeps the previous call's contents: the reduction counter must start at zero
-    e = cudaMemsetAsync(&s->sc, 0, sizeof(bsk::Scalars), st);
+    cudaError_t e = cudaMemsetAsync(&s->sc, 0, sizeof(bsk::Scalars), st);
     if (e != cudaSuccess) return noalloc_fail(BSK_ECUDA, "cudaMemsetAsync failed");
 
     bsk::OpLaunch L;

@@ -92,6 +92,9 @@ template <int N>
 cudaError_t prepare_degree_tma()
 {
     cudaError_t e = prepare_one<N, TMODE_OP>();
+    if constexpr (std::is_same<BSK_T, float>::value && N <= 4) {
+        if (e == cudaSuccess) e = prepare_ws(N);
+    }
     if (e == cudaSuccess) e = prepare_one<N, TMODE_RES>();
 #if !BSK_TMA_NO_CG
     if (e == cudaSuccess) e = prepare_one<N, TMODE_CG>();
@@ -131,6 +134,10 @@ void plan(int nx, int ny, int nz, int n, int grid, int& tiles_x, int& tiles_y, i
 template <int N, int MODE>
 cudaError_t launch_one(const TmaLaunch& L, cudaStream_t s)
 {
+    if constexpr (std::is_same<BSK_T, float>::value && (MODE == TMODE_OP || MODE == TMODE_CG) && N <= 4) {
+        // the warp-specialised operator pass; for CG the one the handle's tuning chose
+        if (!L.mask && (MODE == TMODE_OP || L.impl == 0)) return launch_ws(L, s);
+    }
     TmaInfo& info = tma_info<N, MODE>();
     if (!info.ready) return cudaErrorNotReady;   // prepare_tma was not called
     using G = TGeo<BSK_T, N>;

@@ -73,7 +73,11 @@ OP_CASES = [
     (3, 3, 4, 3, 0.1, True),
     (4, 5, 4, 4, 0.1, False),
     (5, 5, 6, 5, 0.1, False),
-    # unmasked grids with 16-byte rows take the TMA kernels: 64 x 24 tiles, ragged x / y / z
+    # unmasked grids with 16-byte rows take the TMA kernels: 64 x 32 tiles for the FP32 operator
+    # (64 x 24 for the other passes), ragged x / y / z
+    (68, 5120, 8, 3, 1e-3, False),   # 160 tiles: blocks take two items; loads run across items
+    (196, 70, 45, 3, 2e-3, False),
+    (64, 32, 300, 2, 5e-3, False),   # several z-chunks per tile
     (68, 50, 30, 1, 0.02, False),
     (68, 50, 30, 2, 0.01, False),
     (68, 50, 31, 3, 1e-3, False),
@@ -150,6 +154,62 @@ def test_cg_solve_matches_oracle(api, orc, precision, tol, masked, nx):
         assert abs(rep["iterations"] - it_o) <= 3
     if p.mask is not None:
         assert np.all(x[p.mask == 0] == 0)
+
+
+TMA_CG_CASES = [
+    # nx, ny, nz, n, isotropic -- unmasked 16-byte rows: the single-pass iteration on 64 x 32 tiles
+    (132, 70, 40, 3, True),     # ragged tiles in x and y
+    (132, 70, 40, 3, False),    # anisotropic steps: four z tap sets
+    (68, 2600, 6, 2, True),     # 164 tiles: blocks take two items
+    (68, 40, 30, 4, False),
+    (64, 32, 150, 1, True),     # several z-chunks per tile
+]
+
+
+@pytest.mark.parametrize("nx,ny,nz,n,iso", TMA_CG_CASES)
+@pytest.mark.parametrize("precision,tol", [("f32", 1e-5), ("f32_ir", 1e-10)])
+@pytest.mark.parametrize("kernel", ["ws", "classic"])
+def test_cg_solve_tma_tiles_matches_oracle(api, orc, nx, ny, nz, n, iso, precision, tol, kernel):
+    """The single-pass CG iteration, with each of its two kernels, on grids spanning several tiles,
+    items and z-chunks, judged by the oracle's FP64 true residual of the returned solution and its
+    distance to the oracle's solution (kappa times the residual)."""
+    dt = 2e-3
+    h = 1 / (max(nx, ny, nz) + 1)
+    hs = (h, h, h) if iso else (1 / (nx + 1), 1 / (ny + 1), 1 / (nz + 1))
+    p = orc.Problem(nx, ny, nz, n, *hs, dt=dt)
+    b = np.random.default_rng(nx + ny + n).standard_normal(p.shape)
+    H = handle(api, p, hs, precision)
+    assert H.select_cg_kernel(kernel) == kernel
+    tdt = torch.float32 if precision == "f32" else torch.float64
+    bt = torch.from_numpy(b).to("cuda", tdt)
+    xt = torch.zeros_like(bt)
+    rep = H.cg_solve(bt, xt, tol=tol, max_iter=5000)
+    assert rep["status"] == 0, rep
+    x = xt.double().cpu().numpy()
+    bin_ = bt.double().cpu().numpy()
+    r = bin_ - orc.op_separable(p, x)
+    true_rel = np.linalg.norm(r) / np.linalg.norm(bin_)
+    assert true_rel <= (10 * tol if precision == "f32" else 1.5 * tol), true_rel
+    xr, _, _, _ = orc.cg(p, bin_, tol=1e-13, max_iter=5000)
+    kappa = box_kappa(nx, ny, nz, n, hs, dt)
+    err = np.linalg.norm(x - xr) / np.linalg.norm(xr)
+    assert err <= kappa * true_rel * 1.01 + 1e-12
+
+
+def test_cg_kernel_selection(api):
+    """bsk_select_cg_kernel: AUTO picks one of the two kernels; the warp-specialised pass is
+    refused where it does not apply (masked grid, FP64, degree 5); a forced choice sticks."""
+    H = api.Handle(68, 40, 20, 3, 1 / 69, 1e-3, precision="f32_ir")
+    assert H.select_cg_kernel("auto") in ("ws", "classic")
+    assert H.select_cg_kernel("classic") == "classic"
+    assert H.select_cg_kernel("ws") == "ws"
+    for kw in (dict(precision="f64"), dict(precision="f32", degree=5),
+               dict(precision="f32", mask=torch.ones((20, 40, 68), dtype=torch.uint8, device="cuda"))):
+        deg = kw.pop("degree", 3)
+        Hx = api.Handle(68, 40, 20, deg, 1 / 69, 1e-3, **kw)
+        with pytest.raises(RuntimeError, match="-1"):
+            Hx.select_cg_kernel("ws")
+        assert Hx.select_cg_kernel("auto") == "classic"
 
 
 def test_heat_step_32cube_closed_form(api, orc):

@@ -45,20 +45,35 @@ def test_residual_noalloc_matches_handle_entry_points(orc, precision, masked):
         prob.mask = keep.data_ptr()
     prec = api.F64 if precision == "f64" else api.F32
     stream = torch.cuda.current_stream()
+    # the oracle's residual of the same inputs (FP64, the definition of b - A x)
+    xin = x.double().cpu().numpy()
+    r_orc = b.double().cpu().numpy() - orc.op_separable(p, xin)
+    if mask is not None:
+        r_orc = r_orc * mask.numpy()
+    rs = [torch.full_like(x, float("nan")) for _ in range(2)]   # allocated before the calls
+    torch.cuda.synchronize()
+    free = []
     for call in range(2):
-        r = torch.full_like(x, float("nan"))
+        r = rs[call]
         rr = ctypes.c_double(-1.0)
         bb = ctypes.c_double(-1.0)
         rc = L.residual_noalloc(ctypes.byref(prob), prec, x.data_ptr(), b.data_ptr(),
                                 r.data_ptr(), ctypes.byref(rr), ctypes.byref(bb),
                                 ctypes.c_void_p(stream.cuda_stream))
         assert rc == 0, L.bsk_last_error()
+        torch.cuda.synchronize()
+        free.append(torch.cuda.mem_get_info()[0])
         err = torch.max(torch.abs(r.double() - r_ref.double())).item()
         assert err <= tol * scale, (call, err, scale)
+        err_orc = float(np.max(np.abs(r.double().cpu().numpy() - r_orc)))
+        assert err_orc <= tol * scale, (call, err_orc, scale)
         assert abs(rr.value - rr_ref) <= 1e-9 * rr_ref + tol
+        assert abs(rr.value - float(np.sum(r_orc * r_orc))) <= 1e-9 * rr.value + tol * scale * np.sqrt(r_orc.size)
         assert abs(bb.value - bb_ref) <= 1e-9 * bb_ref
         if mask is not None:
             assert torch.count_nonzero(r[mask.cuda() == 0]).item() == 0
+    # the second call (module loaded, scratch address known) took no device memory
+    assert free[1] == free[0], free
 
 
 def test_residual_noalloc_rejects_oversize_and_bad_arguments():
@@ -67,12 +82,38 @@ def test_residual_noalloc_rejects_oversize_and_bad_arguments():
     from paper_1904_03057_gb300 import _native, api
     L = _native.load()
     rr, bb = ctypes.c_double(), ctypes.c_double()
-    big = _native.Problem(4096, 4096, 4096, 3, 1e-3, 1e-3, 1e-3, 0.0, None)
     dummy = torch.zeros(16, device="cuda")
     p = dummy.data_ptr()
-    rc = L.residual_noalloc(ctypes.byref(big), api.F32, p, p + 64, p + 128, ctypes.byref(rr),
-                            ctypes.byref(bb), None)
-    assert rc == -1 and b"too large" in L.bsk_last_error()
+    # the bound is ceil(nx/32) * ceil(ny/16) <= 16384 blocks of the general kernel, any nz:
+    # 4096 x 2049 x 3 is just over it, 4096 x 2048 x 3 at it
+    for big in (_native.Problem(4096, 4096, 4096, 3, 1e-3, 1e-3, 1e-3, 0.0, None),
+                _native.Problem(4096, 2049, 3, 3, 1e-3, 1e-3, 1e-3, 0.0, None)):
+        rc = L.residual_noalloc(ctypes.byref(big), api.F32, p, p + 64, p + 128, ctypes.byref(rr),
+                                ctypes.byref(bb), None)
+        assert rc == -1 and b"too large" in L.bsk_last_error()
+    edge = _native.Problem(4096, 2048, 3, 3, 1e-3, 1e-3, 1e-3, 1e-4, None)
+    x = torch.ones((3, 2048, 4096), device="cuda")
+    b = torch.ones_like(x)
+    r = torch.empty_like(x)
+    rc = L.residual_noalloc(ctypes.byref(edge), api.F32, x.data_ptr(), b.data_ptr(), r.data_ptr(),
+                            ctypes.byref(rr), ctypes.byref(bb), None)
+    assert rc == 0, L.bsk_last_error()
+    assert bb.value == float(x.numel()) and rr.value >= 0.0
+    del x, b, r
+    # a call on a stream that is capturing a graph is refused and leaves the capture intact
+    small = _native.Problem(8, 8, 8, 3, 0.1, 0.1, 0.1, 0.0, None)
+    xs = torch.ones((8, 8, 8), device="cuda")
+    bs = torch.ones_like(xs)
+    rs_ = torch.empty_like(xs)
+    side = torch.cuda.Stream()
+    g = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(g, stream=side):
+        xs.add_(0.0)
+        rc = L.residual_noalloc(ctypes.byref(small), api.F32, xs.data_ptr(), bs.data_ptr(), rs_.data_ptr(),
+                                ctypes.byref(rr), ctypes.byref(bb), ctypes.c_void_p(side.cuda_stream))
+    assert rc == -1 and b"capturing" in L.bsk_last_error()
+    g.replay()
+    torch.cuda.synchronize()
     small = _native.Problem(8, 8, 8, 3, 0.1, 0.1, 0.1, 0.0, None)
     assert L.residual_noalloc(ctypes.byref(small), api.F32_IR, p, p, p, ctypes.byref(rr),
                               ctypes.byref(bb), None) == -1
