@@ -35,13 +35,14 @@ N_GRID, DEGREE, DT, TOL, SEED, NMODES, KMAX = 928, 3, 5e-4, 1e-8, 3, 64, 16
 WORKLOAD = "heat3d_928cube_cubic_f32sweeps_f64refinement"
 
 
-# DRAM bytes per unknown of one fused CG-iteration launch (dram__bytes_read.sum +
-# dram__bytes_write.sum over the unknowns of the launch), from the ncu capture summarised in
-# profiles/k_op_tma_cg_f32_928cube_dram.md; valid only while the kernel's sources hash to
-# CG_TRAFFIC_SOURCES_SHA256.
-CG_TRAFFIC_BYTES_PER_UNKNOWN = 38.03   # 928^3, three launches: 17.63 GB read + 12.76 GB written
-CG_TRAFFIC_SOURCES_SHA256 = "bba51d31b6ab9701861aedcaf7dd3aed5ad91567ed43c4f534c0eec6a6b364fd"
-CG_KERNEL_SOURCES = ("op_tma.cuh", "tma_impl.cuh", "tma_util.cuh", "bsk_device.cuh", "tma_f32.cu", "dfloat.cuh")
+# DRAM bytes per unknown of one launch of each single-pass CG kernel (dram__bytes_read.sum +
+# dram__bytes_write.sum over the unknowns of the launch), measured on the 512^3 profiling case
+# (`--profile-case cg512`) and scaled to the benchmark grid by its unknowns; valid only while the
+# kernels' sources hash to CG_TRAFFIC_SOURCES_SHA256 (None: no capture of the current sources).
+CG_TRAFFIC_BYTES_PER_UNKNOWN = {"classic": None, "ws": None}
+CG_TRAFFIC_SOURCES_SHA256 = None
+CG_KERNEL_SOURCES = ("op_tma.cuh", "op_ws.cuh", "tma_impl.cuh", "tma_util.cuh", "bsk_device.cuh",
+                     "tma_f32.cu", "ws_f32.cu")
 
 
 def cg_kernel_sources_sha256() -> str:
@@ -520,7 +521,7 @@ def robin_large_run(iters: int = 200):
     return out
 
 
-def profile_case(name: str):
+def profile_case(name: str, cg_kernel: str = "auto"):
     """Small cases for the profiler: `cg512` runs 12 single-pass FP32 CG iterations of the
     benchmark's operator at 512^3 (537 MB per vector, a 3.8 GB handle) and then times that pass
     alone; `op384` applies the FP32 cubic operator of the benchmark
@@ -536,13 +537,14 @@ def profile_case(name: str):
         N = 512
         h = 1.0 / (N + 1)
         H = api.Handle(N, N, N, DEGREE, h, DT, precision="f32")
+        kern = H.select_cg_kernel(cg_kernel)
         modes = inputs.random_sine_modes(SEED, NMODES, KMAX)
         b = inputs.sine_mode_field(N, N, N, modes, device="cuda", dtype=torch.float64).float()
         x = torch.zeros_like(b)
         ms, rep = _timed_ms(lambda: H.cg_solve(b, x, tol=1e-30, max_iter=12, check_every=4))
         ms_cg = H.time_kernel(api.KERNEL_CG_FUSED, reps=5)
-        print(json.dumps({"profile_case": name, "solve_ms": ms, "iterations": rep["iterations"],
-                          "cg_fused_ms": ms_cg}), flush=True)
+        print(json.dumps({"profile_case": name, "cg_kernel": kern, "solve_ms": ms,
+                          "iterations": rep["iterations"], "cg_fused_ms": ms_cg}), flush=True)
         return
     if name == "op384":
         N = 384
@@ -598,6 +600,7 @@ def run_ours(args, rank, world, dist):
     u = inputs.sine_mode_field(N, N, N, modes, device="cuda", dtype=torch.float64)
     stream = torch.cuda.current_stream()
     H = api.Handle(N, N, N, DEGREE, h, DT, precision="f32_ir", stream=stream)
+    cg_kernel = H.select_cg_kernel(args.cg_kernel if args.cg_kernel != "auto" else "current")
     opts = dict(tol=TOL, check_every=16)
 
     def barrier():
@@ -705,8 +708,9 @@ def run_ours(args, rank, world, dist):
     Hb.close()
     ach = bytes_fused / (ms_fused_live * 1e-3) / 1e9
     traffic = None
-    if CG_TRAFFIC_BYTES_PER_UNKNOWN is not None and cg_kernel_sources_sha256() == CG_TRAFFIC_SOURCES_SHA256:
-        traffic = CG_TRAFFIC_BYTES_PER_UNKNOWN * dofs
+    per_unknown = CG_TRAFFIC_BYTES_PER_UNKNOWN.get(cg_kernel)
+    if per_unknown is not None and cg_kernel_sources_sha256() == CG_TRAFFIC_SOURCES_SHA256:
+        traffic = per_unknown * dofs
 
     line = {
         "metric": METRIC, "value": value, "unit": "GDoF/s", "n_gpus": world,
@@ -719,6 +723,8 @@ def run_ours(args, rank, world, dist):
             "tol": TOL, "precision": "FP32 operator sweeps; true residual in double-float "
                                      "(FP64-accurate) on FP64 vectors; FP64 update and CG scalars",
             "l2": f"inputs larger than L2 ({4 * dofs / 1e9:.2f} GB FP32 / {8 * dofs / 1e9:.2f} GB FP64 vectors)",
+            "cg_kernel": cg_kernel + " (chosen per handle by timing both single-pass CG kernels)"
+                         if args.cg_kernel == "auto" else cg_kernel + " (forced)",
             "op_applications_per_step": op_apps / len(reps),
             "cg_iterations_per_step": inner / len(reps),
             "refinement_steps_per_step": outer / len(reps),
@@ -738,8 +744,8 @@ def run_ours(args, rank, world, dist):
                                       "kernel": "general kernel, FP32 arithmetic, BF16 in/out"},
             "parallelism": f"{world} independent problems (one per GPU)",
         },
-        "roofline": {"kernel": "k_op_tma<float,3,CG>: one CG iteration (p, r, x updates + A p + "
-                               "r.r, p.Ap, Ap.Ap)",
+        "roofline": {"kernel": ("k_ws<3,WS_CG>" if cg_kernel == "ws" else "k_op_tma<float,3,CG>")
+                               + ": one CG iteration (p, r, x updates + A p + r.r, p.Ap, Ap.Ap)",
                      "bound": "hbm", "achieved": ach, "peak": hbm, "unit": "GB/s",
                      "frac": ach / hbm, "traffic": traffic,
                      "note": f"peak = {peak_kind} HBM copy bandwidth; algorithmic 32 B/unknown "
@@ -783,11 +789,13 @@ def main():
     ap.add_argument("--grid", type=int, default=N_GRID,
                     help="grid edge (default: the benchmark workload; smaller grids are the "
                          "profiler's small case)")
+    ap.add_argument("--cg-kernel", choices=["auto", "ws", "classic"], default="auto",
+                    help="single-pass CG kernel: chosen per handle by timing (default) or forced")
     ap.add_argument("--profile-case", choices=["op384", "cg512", "var240", "robin200"], default=None,
                     help="run one small case for the profiler instead of the benchmark")
     args = ap.parse_args()
     if args.profile_case:
-        profile_case(args.profile_case)
+        profile_case(args.profile_case, args.cg_kernel)
         return
     if args.grid < 16 or args.grid % 4:
         ap.error("--grid must be a multiple of 4 (16-byte FP32 rows for the TMA kernels), >= 16")

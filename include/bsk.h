@@ -393,14 +393,15 @@ int bsk_time_kernel(bsk_handle* h, int kernel, int reps, double* ms);
  * and the two-block-per-SM pass used for every other grid (BSK_CG_KERNEL_CLASSIC); neither is
  * the faster on every grid shape. bsk_create chooses with BSK_CG_KERNEL_AUTO, which times both
  * on the handle's own work vectors (zeroing them; about four passes each) and keeps the faster.
- * request: BSK_CG_KERNEL_AUTO, BSK_CG_KERNEL_WS or BSK_CG_KERNEL_CLASSIC; *chosen (nullable)
- * receives the kernel now in use (WS or CLASSIC). Call it between solves only, never while the
+ * request: BSK_CG_KERNEL_AUTO, BSK_CG_KERNEL_WS, BSK_CG_KERNEL_CLASSIC, or BSK_CG_KERNEL_CURRENT
+ * (no change, no timing); *chosen (nullable) receives the kernel now in use (WS or CLASSIC). Call it between solves only, never while the
  * handle's stream is capturing. Returns BSK_EINVAL for an unknown request or for
  * BSK_CG_KERNEL_WS on a handle that cannot use it (masked grid, BSK_F64, degree 5, rows that
  * are not 16-byte multiples); AUTO on such a handle selects CLASSIC without timing. */
 #define BSK_CG_KERNEL_AUTO 0
 #define BSK_CG_KERNEL_WS 1
 #define BSK_CG_KERNEL_CLASSIC 2
+#define BSK_CG_KERNEL_CURRENT 3
 int bsk_select_cg_kernel(bsk_handle* h, int request, int* chosen);
 
 /* Allocation-free residual: r = b - A x (A as for op_apply), with *rr = r.r and *bb = b.b

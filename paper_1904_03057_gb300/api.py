@@ -19,7 +19,7 @@ _PREC = {"f64": F64, "f32": F32, "f32_ir": F32_IR, "bf16s": BF16S,
 
 OK, NOT_CONVERGED, STALLED = 0, 1, 2
 KERNEL_OP, KERNEL_CG_FUSED, KERNEL_CG_UPDATE, KERNEL_RES64, KERNEL_RES_DF = 0, 1, 2, 3, 4
-CG_KERNEL_AUTO, CG_KERNEL_WS, CG_KERNEL_CLASSIC = 0, 1, 2
+CG_KERNEL_AUTO, CG_KERNEL_WS, CG_KERNEL_CLASSIC, CG_KERNEL_CURRENT = 0, 1, 2, 3
 EINVAL, ECUDA, ENOMEM, ETIMEOUT, EBREAKDOWN = -1, -2, -3, -4, -5
 
 
@@ -154,8 +154,10 @@ class Handle:
 
     def select_cg_kernel(self, request: str = "auto") -> str:
         """Kernel of the single-pass FP32 CG iteration (bsk_select_cg_kernel): "auto" times both
-        and keeps the faster, "ws" / "classic" force one. Returns the kernel now in use."""
-        req = {"auto": CG_KERNEL_AUTO, "ws": CG_KERNEL_WS, "classic": CG_KERNEL_CLASSIC}[request]
+        and keeps the faster, "ws" / "classic" force one, "current" only reports. Returns the
+        kernel now in use."""
+        req = {"auto": CG_KERNEL_AUTO, "ws": CG_KERNEL_WS, "classic": CG_KERNEL_CLASSIC,
+               "current": CG_KERNEL_CURRENT}[request]
         out = ctypes.c_int(0)
         _native.check(self._lib.bsk_select_cg_kernel(self._ptr, req, ctypes.byref(out)))
         return "ws" if out.value == CG_KERNEL_WS else "classic"

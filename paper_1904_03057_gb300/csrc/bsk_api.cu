@@ -1482,8 +1482,13 @@ extern "C" int bsk_time_kernel(bsk_handle* h, int kernel, int reps, double* ms)
 extern "C" int bsk_select_cg_kernel(bsk_handle* h, int request, int* chosen)
 {
     if (int rc = check_handle(h)) return rc;
-    if (request != BSK_CG_KERNEL_AUTO && request != BSK_CG_KERNEL_WS && request != BSK_CG_KERNEL_CLASSIC)
+    if (request != BSK_CG_KERNEL_AUTO && request != BSK_CG_KERNEL_WS && request != BSK_CG_KERNEL_CLASSIC &&
+        request != BSK_CG_KERNEL_CURRENT)
         return fail(BSK_EINVAL, "unknown CG kernel request %d", request);
+    if (request == BSK_CG_KERNEL_CURRENT) {
+        if (chosen) *chosen = h->cg_impl == 0 ? BSK_CG_KERNEL_WS : BSK_CG_KERNEL_CLASSIC;
+        return BSK_OK;
+    }
     const bool ws_ok = cg_ws_eligible(h);
     if (request == BSK_CG_KERNEL_WS && !ws_ok)
         return fail(BSK_EINVAL, "the warp-specialised CG pass needs an unmasked FP32 TMA grid of degree <= 4");

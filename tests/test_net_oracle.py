@@ -2,6 +2,7 @@
 differences of its own loss (FP64, no BF16 rounding), and adjoint identities of the gather /
 scatter convolution pair, on tiny grids. A planted mistake (dropped skip gradient) must fail."""
 import numpy as np
+import pytest
 
 from oracle import net_ref as nr
 
@@ -124,3 +125,53 @@ def test_linear_backward_matches_finite_differences():
         fd = (nr.loss_and_grad(p1, r, e, mask, False, "linear")[0]
               - nr.loss_and_grad(p2, r, e, mask, False, "linear")[0]) / (2 * eps)
         assert abs(fd - g[i]) <= 1e-6 * max(1.0, abs(g[i])) + 1e-8, (i, fd, g[i])
+
+
+def _conv_f32(x, W, mode, dout):
+    """The reference's gather convolution with FP32 accumulation: the kind of rounding the GPU's
+    sums have, used to check that the element-wise comparison tolerates it."""
+    out = np.zeros(tuple(dout) + (W.shape[1],), dtype=np.float32)
+    x = x.astype(np.float32)
+    W = W.astype(np.float32)
+    for k, kz, ky, kx in nr._taps():
+        iz, oz = nr._src(mode, dout[0], kz, x.shape[0])
+        iy, oy = nr._src(mode, dout[1], ky, x.shape[1])
+        ix, ox = nr._src(mode, dout[2], kx, x.shape[2])
+        g = x[np.ix_(iz, iy, ix)] * (oz[:, None, None] & oy[None, :, None] & ox[None, None, :])[..., None]
+        out += (g @ W[k].T).astype(np.float32)
+    return out.astype(np.float64)
+
+
+@pytest.mark.parametrize("act", ["relu", "linear"])
+def test_elementwise_comparison_tolerates_fp32_sums_and_catches_a_wrong_tap(act, monkeypatch):
+    """The GPU-vs-reference comparison of tests/netcheck.py passes the reference evaluated with
+    FP32 sums, and fails when a 16->16 convolution reads one tap from the wrong weight block (a
+    planted mistake in the reference: tap 13 of W2 replaced by tap 14), or when the weight
+    gradient of one tap comes from the wrong tap."""
+    import netcheck
+    rng = np.random.default_rng(0)
+    shape = (16, 16, 16)
+    p = nr.init_params(3, out_scale=1.0) + rng.standard_normal(nr.NPARAM) * 0.02
+    mask = (rng.random(shape) < 0.85).astype(np.float64)
+    r = rng.standard_normal(shape) * mask * 0.05
+    zr, _ = nr.forward(p, r, mask, act=act)
+    S, _ = netcheck.abs_forward(p, r, mask, act)
+    with monkeypatch.context() as m:
+        m.setattr(nr, "conv", _conv_f32)
+        z32, _ = nr.forward(p, r, mask, act=act)
+    assert netcheck.forward_ok(z32, zr, S, mask)
+    q = nr.unpack(p)
+    q = {k: v.copy() for k, v in q.items()}
+    q["W2"][13] = q["W2"][14]
+    zp, _ = nr.forward(nr.pack(q), r, mask, act=act)
+    assert not netcheck.forward_ok(zp, zr, S, mask)
+    # gradients: one tap of dL/dW3 taken from the neighbouring tap
+    e = rng.standard_normal(shape) * 0.05
+    _, gr, _ = nr.loss_and_grad(p, r, e, mask, act=act)
+    Gs = netcheck.abs_gradient_scale(p, r, e, mask, act)
+    assert max(netcheck.gradient_errors(gr, gr, Gs).values()) == 0.0
+    gp = nr.unpack(gr)
+    gp = {k: v.copy() for k, v in gp.items()}
+    gp["W3"][13] = gp["W3"][14]
+    errs = netcheck.gradient_errors(nr.pack(gp), gr, Gs)
+    assert not netcheck.gradient_ok(errs), errs
