@@ -163,6 +163,107 @@ def cpu_oracle_sample(reps: int = 3, planes: int = 16):
     return dofs / dt_s / 1e9, cores, dt_s, desc
 
 
+def cpu_model() -> str:
+    """The host CPU's name as /proc/cpuinfo gives it (x86 "model name", Arm implementer/part)."""
+    try:
+        info = open("/proc/cpuinfo").read()
+    except OSError:
+        return "unknown"
+    for key in ("model name", "Model", "CPU part"):
+        for ln in info.splitlines():
+            if ln.startswith(key):
+                val = ln.split(":", 1)[1].strip()
+                if key == "CPU part":
+                    impl = next((x.split(":", 1)[1].strip() for x in info.splitlines()
+                                 if x.startswith("CPU implementer")), "?")
+                    return f"Arm CPU implementer {impl}, part {val}"
+                return val
+    return "unknown"
+
+
+def cpu_baseline_by_config(line) -> dict:
+    """The FP64 oracle timed on the host cores for every workload the line reports, next to the
+    GPU figure. Config 1 is solved whole; the others take the oracle's measured time per
+    operator application (a separable FP64 sweep over the whole grid, every core) times the
+    operator applications the GPU run needed, and are labelled extrapolated. About 10 s of CPU
+    work in all."""
+    import numpy as np
+    import torch
+
+    import oracle
+    from paper_1904_03057_gb300 import inputs
+
+    def t_op(p, x):
+        oracle.op_separable(p, x)                 # warm-up (pages, threads)
+        t0 = time.perf_counter()
+        oracle.op_separable(p, x)
+        return time.perf_counter() - t0
+
+    out = {"cores": int(os.environ.get("OMP_NUM_THREADS", os.cpu_count() or 1)), "cpu": cpu_model()}
+    # config 1: 32^3, cubic, sin sin sin, dt = 1e-3, 10 steps, tol 1e-10, FP64 -- whole solve
+    c1 = line.get("c1_32cube_fp64")
+    if c1:
+        N = 32
+        h = 1.0 / (N + 1)
+        p = oracle.Problem(N, N, N, DEGREE, h, dt=1e-3)
+        u0 = inputs.sine_mode_field(N, N, N, [((1, 1, 1), 1.0)]).numpy()
+        t0 = time.perf_counter()
+        oracle.heat(p, u0, None, 10, tol=1e-10)
+        out["c1_32cube_10_steps"] = {"oracle_ms": 1e3 * (time.perf_counter() - t0), "gpu_ms": c1["ms"],
+                                     "kind": "measured"}
+    # config 2: 256^3 sphere, FP64 CG, 50 steps
+    c2 = line.get("mixed_precision_sphere256")
+    if c2:
+        N = 256
+        h = 1.0 / (N + 1)
+        mask = inputs.sphere_mask(N, N, N, (0.5, 0.5, 0.5), 0.45, h=h).numpy()
+        p = oracle.Problem(N, N, N, DEGREE, h, dt=1e-3, mask=mask)
+        t = t_op(p, np.random.default_rng(0).standard_normal(p.shape) * mask)
+        apps = c2["f64"]["iterations_per_step"] + 2   # CG iterations + right-hand side + residual
+        out["c2_256_sphere_50_steps"] = {
+            "oracle_ms": 1e3 * t * apps * 50, "gpu_ms_fp64": c2["f64"]["ms_per_step"] * 50,
+            "gpu_ms_f32_ir": c2["f32_ir"]["ms_per_step"] * 50, "oracle_ms_per_operator": 1e3 * t,
+            "kind": "extrapolated (oracle operator time x the FP64 run's applications)"}
+    # config 3: 928^3 heat step (the line's headline), from the slab sample of the same field
+    v, cores, secs, desc = cpu_oracle_sample(reps=1)
+    apps = line["config"]["op_applications_per_step"]
+    out["c3_928_heat_step"] = {"oracle_ms": 1e3 * N_GRID ** 3 * apps / (v * 1e9), "gpu_ms": line["ms_per_step"],
+                               "oracle_gdofs": v, "kind": "extrapolated (" + desc + ")"}
+    # config 4: the 64 boxes, from one box solved whole
+    c4 = line.get("batch_64_boxes")
+    if c4:
+        specs = inputs.batch_problems(seed=4)
+        s = sorted(specs, key=lambda q: q.nx * q.ny * q.nz)[len(specs) // 2]   # the median box
+        p = oracle.Problem(s.nx, s.ny, s.nz, s.degree, s.h, dt=1e-3)
+        qf = inputs.gaussian_source(s.nx, s.ny, s.nz, s.centers, 0.03, h=s.h).numpy()
+        t0 = time.perf_counter()
+        _, its, _, _ = oracle.heat(p, np.zeros(p.shape), qf, 1, tol=1e-8)
+        dt_s = time.perf_counter() - t0
+        rate = s.nx * s.ny * s.nz * (int(np.sum(its)) + 2) / dt_s          # unknowns x applications / s
+        apps_b = c4["batched_gdofs"] * 1e9 * c4["batched_ms"] * 1e-3
+        out["c4_64_boxes"] = {"oracle_ms": 1e3 * apps_b / rate, "gpu_ms_batched": c4["batched_ms"],
+                              "gpu_ms_sequential": c4["sequential_ms"],
+                              "kind": f"extrapolated (box {s.nx}x{s.ny}x{s.nz} n={s.degree} solved whole: "
+                                      f"{rate / 1e9:.3f} GDoF/s)"}
+    # config 5: 512^3 union of spheres, plain FP64 CG to 1e-8
+    c5 = line.get("fcg_race")
+    if c5:
+        N = 512
+        h = 1.0 / (N + 1)
+        centers, radii = inputs.random_spheres(5, 40, 0.05, 0.2)
+        mask = inputs.union_of_spheres_mask(N, N, N, centers, radii, h=h).numpy()
+        p = oracle.Problem(N, N, N, DEGREE, h, dt=1e-3, mask=mask)
+        t = t_op(p, np.random.default_rng(0).standard_normal(p.shape) * mask)
+        apps = c5["fp64_cg"]["iterations"] + 2
+        out["c5_512_spheres_to_1e-8"] = {
+            "oracle_ms": 1e3 * t * apps, "gpu_ms_fp64_cg": c5["fp64_cg"]["ms"],
+            "gpu_ms_f32_ir_cg": c5["f32_ir_cg"]["ms"], "gpu_ms_fcg_net_ir": c5["fcg_net_ir"]["ms"],
+            "oracle_ms_per_operator": 1e3 * t,
+            "kind": "extrapolated (oracle operator time x the FP64 CG run's applications)"}
+    del torch
+    return out
+
+
 def run_reference(args, rank, world):
     if rank != 0:
         return
@@ -758,6 +859,17 @@ def run_ours(args, rank, world, dist):
         line["e2e"] = e2e
     H.close()
     del u
+    torch.cuda.empty_cache()
+    if rank == 0:
+        # config 1 (32^3, sin sin sin, dt = 1e-3, 10 steps, tol 1e-10, FP64), for the CPU baseline
+        hc = 1.0 / 33
+        Hc = api.Handle(32, 32, 32, DEGREE, hc, 1e-3, precision="f64", stream=stream)
+        u1 = inputs.sine_mode_field(32, 32, 32, [((1, 1, 1), 1.0)], device="cuda")
+        Hc.heat_step(u1.clone(), None, 10, tol=1e-10)        # warm-up
+        ms_c1, rep_c1 = _timed_ms(lambda: Hc.heat_step(u1, None, 10, tol=1e-10))
+        line["c1_32cube_fp64"] = {"ms": ms_c1, "iterations": rep_c1["iterations"],
+                                  "rel_residual": rep_c1["rel_residual"]}
+        Hc.close()
     if rank == 0 and not args.no_fcg_race and args.grid == N_GRID:
         line["fcg_race"] = fcg_race()
     if rank == 0 and not args.no_extra_configs and args.grid == N_GRID:
@@ -768,7 +880,8 @@ def run_ours(args, rank, world, dist):
     if rank == 0 and not args.no_cpu_baseline:
         v, cores, secs, desc = cpu_oracle_sample()
         line["cpu_baseline"] = {"value": v, "unit": "GDoF/s", "cores": cores, "kind": "oracle",
-                                "sample": desc}
+                                "sample": desc, "cpu": cpu_model(),
+                                "by_config": cpu_baseline_by_config(line)}
     if rank == 0:
         print(json.dumps(line), flush=True)
 
