@@ -429,6 +429,71 @@ int bsk_select_cg_kernel(bsk_handle* h, int request, int* chosen);
 int residual_noalloc(const bsk_problem* prob, int precision, const void* x, const void* b, void* r,
                      double* rr, double* bb, void* stream);
 
+/* ---- z-slab split of one grid across devices (section 3 distributes the unknowns of one
+ * problem over several GPUs; here each device holds a contiguous range of z-planes) ----
+ *
+ * A slab handle is an ordinary handle created (bsk_create) for the LOCAL grid nx x ny x nz of
+ * one slab (precision BSK_F64 or BSK_F32, no mask, odd reflection at the faces, constant
+ * coefficients), then told where the slab sits with bsk_set_slab. The slab calls below then
+ * treat its nz planes as planes z_off .. z_off + nz - 1 of a grid of nz_glob planes: the
+ * operator of Eq. tensForm couples a plane to the n planes on each side, so inputs of the
+ * operator carry n HALO planes on each side (nz + 2n planes, plane i of the array being global
+ * plane z_off - n + i), and odd reflection applies at the global faces z = 0 and z = nz_glob - 1
+ * only (halo planes beyond a global face are never read). Halo planes are the caller's to fill
+ * from the neighbouring slabs (NCCL send/recv, peer copies, host copies).
+ * The other calls (op_apply, bsk_cg_solve, ...) keep treating the handle as a whole grid of nz
+ * planes. Vectors are DEVICE arrays of the handle's element type owned by the caller. */
+
+/* Places the handle's grid as planes z_off .. z_off + nz - 1 of a grid of nz_glob planes.
+ * Returns BSK_EINVAL for z_off < 0, z_off + nz > nz_glob, or a handle that is not of the kind
+ * described above. */
+int bsk_set_slab(bsk_handle* h, int z_off, int nz_glob);
+
+/* y = A x on the slab's planes (A of Eq. tensForm, as for op_apply), x_halo holding nz + 2n
+ * planes (n halo planes below and above the local ones), y the nz local planes. x_halo and y
+ * must not overlap. Asynchronous on the handle's stream. */
+int bsk_slab_apply(bsk_handle* h, const void* x_halo, void* y);
+
+/* Scalars of a slab CG solve: a DEVICE array of BSK_SLAB_SCALARS doubles owned by the caller,
+ * on which the all-reduces act in place. Between the passes below the caller sums, over all
+ * slabs of the grid, the entries the previous pass left as local partial sums:
+ *   after bsk_slab_cg_begin:  RR_NEW and BB (2 doubles from BSK_SLAB_RR_NEW)
+ *   after bsk_slab_cg_matvec: PQ (1 double at BSK_SLAB_PQ)
+ *   after bsk_slab_cg_update: RR_NEW (1 double at BSK_SLAB_RR_NEW)
+ * DONE becomes 1 when the solve has ended (on every slab alike, the scalars being global), with
+ * STATUS 0 (converged: r.r <= tol^2 b.b), 1 (max_iter iterations) or -5 (breakdown: p.Ap <= 0 or
+ * a non-finite norm); ITER counts the iterations and RR holds the last global r.r. Passes
+ * launched after DONE change neither x nor r, so a caller may queue several iterations between
+ * reads of DONE. */
+#define BSK_SLAB_PQ 0
+#define BSK_SLAB_RR_NEW 1
+#define BSK_SLAB_BB 2
+#define BSK_SLAB_RR 3
+#define BSK_SLAB_TOL2 4
+#define BSK_SLAB_MAX_ITER 5
+#define BSK_SLAB_ITER 6
+#define BSK_SLAB_DONE 7
+#define BSK_SLAB_STATUS 8
+#define BSK_SLAB_SCALARS 16
+
+/* Starts CG (section 2.5) on a slab: r = b - ax, p = r (local planes of p_halo, which holds
+ * nz + 2n planes), with ax = A x0 computed by the caller (bsk_slab_apply on the halo-extended
+ * x0, or zeros for x0 = 0); resets s for tolerance tol (relative, ||r|| <= tol ||b||) and
+ * max_iter; leaves local r.r and b.b in s. After the all-reduce, call
+ * bsk_slab_cg_direction(first = 1). r, b, ax are nz-plane vectors. */
+int bsk_slab_cg_begin(bsk_handle* h, const void* b, const void* ax, void* r, void* p_halo, double* s,
+                      double tol, int max_iter);
+
+/* q = A p (p_halo with filled halo planes) and local p.q into s. */
+int bsk_slab_cg_matvec(bsk_handle* h, const void* p_halo, void* q, double* s);
+
+/* alpha = RR / PQ; x += alpha p, r -= alpha q on the local planes; local r.r into s. */
+int bsk_slab_cg_update(bsk_handle* h, void* x, void* r, const void* p_halo, const void* q, double* s);
+
+/* p = r + beta p on the local planes of p_halo, beta = RR_NEW / RR (0 when first is non-zero),
+ * then the convergence test; the halo planes of p are to be exchanged before the next matvec. */
+int bsk_slab_cg_direction(bsk_handle* h, const void* r, void* p_halo, double* s, int first);
+
 /* Text of the last error raised on the calling thread ("" if none). */
 const char* bsk_last_error(void);
 

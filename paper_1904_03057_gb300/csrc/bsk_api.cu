@@ -162,6 +162,11 @@ struct bsk_handle {
     float* fcg_ws;        // FCG work vectors z, rn, zn (allocated by the first fcg_solve)
     double* fcg_partials;
     void* fcg_state;
+    // z-slab placement (bsk_set_slab): global offset and plane count (0 = not a slab), and the
+    // reduction scratch of the slab CG passes
+    int z_off, nz_glob;
+    double* slab_partials;
+    unsigned* slab_ctr;
 };
 
 namespace {
@@ -798,6 +803,8 @@ extern "C" void bsk_destroy(bsk_handle* h)
     if (h->fcg_ws) cudaFree(h->fcg_ws);
     if (h->fcg_partials) cudaFree(h->fcg_partials);
     if (h->fcg_state) cudaFree(h->fcg_state);
+    if (h->slab_partials) cudaFree(h->slab_partials);
+    if (h->slab_ctr) cudaFree(h->slab_ctr);
     for (int d = 0; d < 3; d++)
         if (h->tr_L[d]) cudaFree(h->tr_L[d]);
     if (h->cap_stream) cudaStreamDestroy(h->cap_stream);
@@ -1895,6 +1902,130 @@ extern "C" int bsk_norm2(bsk_handle* h, const void* x, double* out)
     if (int rc = sync_scalars(h, h->sc_aux)) return rc;
     *out = h->h_sc->rr_true;
     return BSK_OK;
+}
+
+// ---- z-slab split (section 3: one problem distributed over several GPUs, here by z-planes) ----
+
+namespace {
+
+int check_slab(const bsk_handle* h)
+{
+    if (int rc = check_handle(h)) return rc;
+    if (h->nz_glob <= 0) return fail(BSK_EINVAL, "the handle has no slab placement (bsk_set_slab)");
+    return BSK_OK;
+}
+
+size_t plane_len(const bsk_handle* h) { return (size_t)h->nx * h->ny; }
+
+// Local planes of a halo-extended slab vector (n halo planes first).
+const void* slab_local(const bsk_handle* h, const void* v_halo)
+{
+    return static_cast<const char*>(v_halo) + (size_t)h->n * plane_len(h) * user_es(h);
+}
+
+int slab_pass_es(bsk_handle* h, int pass, const bsk::SlabVectors& v, double* s)
+{
+    if (!s) return fail(BSK_EINVAL, "null scalar array");
+    const cudaError_t e = user_es(h) == sizeof(double)
+                              ? bsk::slab_pass<double>(pass, v, h->len, s, h->slab_partials, h->slab_ctr, h->stream)
+                              : bsk::slab_pass<float>(pass, v, h->len, s, h->slab_partials, h->slab_ctr, h->stream);
+    if (e != cudaSuccess) return cuda_fail(e, "slab CG pass");
+    h->launches += 1;
+    return BSK_OK;
+}
+
+}  // namespace
+
+extern "C" int bsk_set_slab(bsk_handle* h, int z_off, int nz_glob)
+{
+    if (int rc = check_handle(h)) return rc;
+    if (h->prec != BSK_F64 && h->prec != BSK_F32)
+        return fail(BSK_EINVAL, "slab handles take precision BSK_F64 or BSK_F32");
+    if (h->mask || h->bc != BSK_BC_DIRICHLET || h->cd[0] || h->cd[1])
+        return fail(BSK_EINVAL, "slab handles take unmasked, constant-coefficient grids with odd reflection");
+    if (z_off < 0 || nz_glob < 1 || (long long)z_off + h->nz > nz_glob)
+        return fail(BSK_EINVAL, "slab planes %d..%d do not lie in a grid of %d planes", z_off, z_off + h->nz - 1,
+                    nz_glob);
+    if (!h->slab_partials) {
+        BSK_CUDA(cudaMalloc((void**)&h->slab_partials, bsk::slab_partials_doubles() * sizeof(double)));
+        BSK_CUDA(cudaMalloc((void**)&h->slab_ctr, sizeof(unsigned)));
+        BSK_CUDA(cudaMemsetAsync(h->slab_ctr, 0, sizeof(unsigned), h->stream));
+    }
+    h->z_off = z_off;
+    h->nz_glob = nz_glob;
+    return BSK_OK;
+}
+
+extern "C" int bsk_slab_apply(bsk_handle* h, const void* x_halo, void* y)
+{
+    if (int rc = check_slab(h)) return rc;
+    if (!x_halo || !y) return fail(BSK_EINVAL, "null vector");
+    const size_t es = user_es(h);
+    const size_t in_bytes = (size_t)(h->nz + 2 * h->n) * plane_len(h) * es;
+    const char *a = (const char*)x_halo, *b = (const char*)y;
+    if (a < b + h->len * es && b < a + in_bytes) return fail(BSK_EINVAL, "x_halo and y overlap");
+    bsk::OpLaunch L;
+    fill_launch(h, L, bsk::MODE_OP);
+    L.in0 = x_halo;
+    L.out0 = y;
+    L.fin = bsk::FIN_NONE;
+    L.z_off = h->z_off;
+    L.nz_glob = h->nz_glob;
+    L.zpad = h->n;
+    const cudaError_t e = op_launch_es(es, L, h->stream);
+    if (e != cudaSuccess) return cuda_fail(e, "slab operator launch");
+    h->launches += 1;
+    return BSK_OK;
+}
+
+extern "C" int bsk_slab_cg_begin(bsk_handle* h, const void* b, const void* ax, void* r, void* p_halo, double* s,
+                                 double tol, int max_iter)
+{
+    if (int rc = check_slab(h)) return rc;
+    if (!b || !ax || !r || !p_halo || !s) return fail(BSK_EINVAL, "null argument");
+    if (!(tol >= 0.0) || max_iter < 0) return fail(BSK_EINVAL, "tol must be >= 0 and max_iter >= 0");
+    double init[BSK_SLAB_SCALARS] = {};
+    init[BSK_SLAB_TOL2] = tol * tol;
+    init[BSK_SLAB_MAX_ITER] = (double)max_iter;
+    // pageable source: the copy has left `init` when cudaMemcpyAsync returns
+    BSK_CUDA(cudaMemcpyAsync(s, init, sizeof init, cudaMemcpyHostToDevice, h->stream));
+    bsk::SlabVectors v = {};
+    v.b = b;
+    v.ax = ax;
+    v.r = r;
+    v.p = const_cast<void*>(slab_local(h, p_halo));
+    return slab_pass_es(h, bsk::SLAB_BEGIN, v, s);
+}
+
+extern "C" int bsk_slab_cg_matvec(bsk_handle* h, const void* p_halo, void* q, double* s)
+{
+    if (int rc = bsk_slab_apply(h, p_halo, q)) return rc;
+    bsk::SlabVectors v = {};
+    v.p = const_cast<void*>(slab_local(h, p_halo));
+    v.q = q;
+    return slab_pass_es(h, bsk::SLAB_DOT, v, s);
+}
+
+extern "C" int bsk_slab_cg_update(bsk_handle* h, void* x, void* r, const void* p_halo, const void* q, double* s)
+{
+    if (int rc = check_slab(h)) return rc;
+    if (!x || !r || !p_halo || !q) return fail(BSK_EINVAL, "null vector");
+    bsk::SlabVectors v = {};
+    v.x = x;
+    v.r = r;
+    v.p = const_cast<void*>(slab_local(h, p_halo));
+    v.q = q;
+    return slab_pass_es(h, bsk::SLAB_UPDATE, v, s);
+}
+
+extern "C" int bsk_slab_cg_direction(bsk_handle* h, const void* r, void* p_halo, double* s, int first)
+{
+    if (int rc = check_slab(h)) return rc;
+    if (!r || !p_halo) return fail(BSK_EINVAL, "null vector");
+    bsk::SlabVectors v = {};
+    v.r = const_cast<void*>(r);
+    v.p = const_cast<void*>(slab_local(h, p_halo));
+    return slab_pass_es(h, first ? bsk::SLAB_FIRST : bsk::SLAB_DIRECTION, v, s);
 }
 
 extern "C" const char* bsk_last_error(void) { return g_err.c_str(); }

@@ -78,7 +78,13 @@ struct Geom {
     int nx, ny, nz;
     int tz;                 // output planes per block along z
     const uint8_t* mask;    // node mask (nullptr = whole box)
+    // z-slab of a larger grid (MODE_OP only): the nz local planes are global planes
+    // z_off .. z_off + nz - 1 of nz_glob, and the input carries zpad extra planes on each side
+    // (input plane i is global plane z_off - zpad + i). Odd reflection applies at the global
+    // faces only. A whole grid has z_off = 0, nz_glob = nz, zpad = 0.
+    int z_off, nz_glob, zpad;
 };
+
 
 // Index of array position a (0-based) after odd reflection about the faces at -1 and N.
 // Returns +1 (interior, src = a), -1 (ghost, src = mirror image), 0 (face or beyond: zero).
@@ -89,6 +95,16 @@ __device__ __forceinline__ int reflect_index(int a, int N, int& src)
     if ((unsigned)r >= (unsigned)N) return 0;
     src = r;
     return -1;
+}
+
+// Input plane (counted in the input array) that holds global plane g of a z-slab after odd
+// reflection about the global faces; returns the sign (+1, -1, 0 = face or beyond).
+__device__ __forceinline__ int slab_plane(int g, const Geom& geo, int& src)
+{
+    int sg = 0;
+    const int s = reflect_index(g, geo.nz_glob, sg);
+    src = sg - geo.z_off + geo.zpad;
+    return s;
 }
 
 __device__ __forceinline__ double warp_sum(double v)

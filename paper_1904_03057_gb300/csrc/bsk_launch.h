@@ -53,6 +53,9 @@ struct OpLaunch {
     // MODE_CGP: 1 / diag A per node (Jacobi), float [0] / double [1]; the kernels read it instead
     // of the jac tables; null = no preconditioner
     const void* jvec[2];
+    // MODE_OP on a z-slab (Geom): global offset, global plane count (0 = nz: a whole grid) and
+    // the halo planes in0 carries on each side
+    int z_off, nz_glob, zpad;
 };
 
 // Grid of the operator kernel for a problem; partial-sum buffers hold 2 doubles per block.
@@ -208,6 +211,17 @@ int fcg_inner(const FcgVectors& V, size_t n, const uint8_t* mask, double tol, in
               const std::function<int(bsk_net*, const float*, const uint8_t*, float*)>& net_forward,
               cudaStream_t s, int* iters, int* fallback_iter, int* rejected, double time_limit,
               std::chrono::steady_clock::time_point t0);
+
+// ---- CG vector passes of a z-slab (slab.cu); s is the BSK_SLAB_* scalar array ----
+enum SlabPass { SLAB_BEGIN, SLAB_DOT, SLAB_UPDATE, SLAB_FIRST, SLAB_DIRECTION };
+struct SlabVectors {
+    const void *b, *ax, *q;   // local planes
+    void *x, *r, *p;          // local planes (p: the first local plane of the halo array)
+};
+template <typename T>
+cudaError_t slab_pass(int pass, const SlabVectors& v, size_t len, double* s, double* partials, unsigned* ctr,
+                      cudaStream_t st);
+size_t slab_partials_doubles();
 
 cudaError_t launch_ir_scale_down(const double* r64, float* r32, size_t len, const Scalars* outer,
                                  cudaStream_t s);

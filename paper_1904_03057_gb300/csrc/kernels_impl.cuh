@@ -54,6 +54,9 @@ static cudaError_t launch_generic(const OpLaunch& L, cudaStream_t s)
     a.g.nz = L.nz;
     a.g.tz = tz;
     a.g.mask = L.mask;
+    a.g.z_off = L.z_off;
+    a.g.nz_glob = L.nz_glob > 0 ? L.nz_glob : L.nz;
+    a.g.zpad = L.zpad;
     a.c = make_coef<T>(L);
     a.in0 = static_cast<const T*>(L.in0);
     a.in1 = static_cast<const T*>(L.in1);

@@ -147,7 +147,8 @@ __global__ void __launch_bounds__(kGenNT) k_op_generic(const __grid_constant__ O
             sz = gz;
             sgz = (unsigned)gz < (unsigned)nz;
         } else {
-            sgz = reflect_index(gz, nz, sz);
+            // local plane gz is global plane z_off + gz (a whole grid: z_off = 0, no padding)
+            sgz = slab_plane(a.g.z_off + gz, a.g, sz);
         }
         for (int i = tid; i < HY * HX; i += NT) {
             const int hy = i / HX, hx = i - hy * HX;
