@@ -315,6 +315,16 @@ def batch_64_boxes():
     B = api.BatchHandle(specs, dt)
     tune = B.autotune(3)
     dofs = [s.nx * s.ny * s.nz for s in specs]
+    # each degree group's tuned pass against HBM: 32 algorithmic bytes per unknown per
+    # single-pass CG iteration (read r, q, p, x; write r, q, p, x in FP32)
+    peak, peak_kind = peaks()
+    tune["hbm_peak"] = {"gbs": peak, "kind": peak_kind}
+    for g in tune["groups"]:
+        unknowns = sum(d for d, s in zip(dofs, specs) if s.degree == g["degree"])
+        gbs = 32.0 * unknowns / (g["ms"] * 1e-3) / 1e9 if g["ms"] > 0 else None
+        g["unknowns"] = unknowns
+        g["hbm_gbs"] = gbs
+        g["hbm_frac"] = gbs / peak if (gbs and peak) else None
 
     def fresh():
         return [torch.zeros((s.nz, s.ny, s.nx), dtype=torch.float64, device="cuda") for s in specs]
@@ -630,10 +640,14 @@ def profile_case(name: str, cg_kernel: str = "auto"):
     than L2) four times; `var240` runs the variable-coefficient operator (cubic, FP32,
     240 x 240 x 960, the inclusion fields of `variable_coefficients`) three times; `robin200` runs
     10 iterations of the FP64 Jacobi-preconditioned Robin CG of `robin_large_run` on 200 x 200 x
-    800 unknowns (256 MB per vector), then times its fused CG pass alone."""
+    800 unknowns (256 MB per vector), then times its fused CG pass alone; `batch64` runs the 64-box
+batched measurement (autotuned tiles and z-chunks) and prints it."""
     import torch
 
     from paper_1904_03057_gb300 import api, inputs
+    if name == "batch64":
+        print(json.dumps({"profile_case": name, **batch_64_boxes()}), flush=True)
+        return
     if name == "cg512":
         N = 512
         h = 1.0 / (N + 1)
@@ -904,7 +918,7 @@ def main():
                          "profiler's small case)")
     ap.add_argument("--cg-kernel", choices=["auto", "ws", "classic"], default="auto",
                     help="single-pass CG kernel: chosen per handle by timing (default) or forced")
-    ap.add_argument("--profile-case", choices=["op384", "cg512", "var240", "robin200"], default=None,
+    ap.add_argument("--profile-case", choices=["op384", "cg512", "var240", "robin200", "batch64"], default=None,
                     help="run one small case for the profiler instead of the benchmark")
     args = ap.parse_args()
     if args.profile_case:

@@ -303,14 +303,25 @@ int bsk_batch_cg_solve(bsk_batch* b, const void* const* bvec, void* const* x, co
 int bsk_batch_heat_step(bsk_batch* b, void* const* u, const void* const* q, int nsteps,
                         const bsk_cg_opts* opts, bsk_cg_report* reports);
 
-/* Autotuner: times whole-batch CG iterations (`reps` each, CUDA events) for several work
- * decompositions (z-chunks per problem 1, 2, 3, 4, 6, 8), keeps the fastest and derives the
- * graph length from its iteration time. Overwrites the batch's work vectors. Outputs (may be
- * NULL): chosen z-chunks, graph length, mean ms per batched iteration. */
-int bsk_batch_autotune(bsk_batch* b, int reps, int* nzc, int* check_every, double* ms);
+/* Autotuner. The problems of one B-spline degree form a group, whose CG iteration is one
+ * persistent launch over (problem, tile, z-chunk) items. For every group it times that launch
+ * (`reps` each, CUDA events, finalisers off) for each tile shape -- 64 columns x 16, 24 or 32
+ * rows (32 for degrees <= 4 only) -- and each z-chunking (1, 2, 3, 4, 6, 8 chunks per problem),
+ * keeps the fastest per group and derives the graph length from the summed iteration time.
+ * Overwrites the batch's work vectors. Outputs (may be NULL): graph length, mean ms of one
+ * batched iteration (all groups). bsk_batch_groups reports the choices. */
+int bsk_batch_autotune(bsk_batch* b, int reps, int* check_every, double* ms);
 
-/* Sets the decomposition and graph length directly (e.g. from a cached autotuning result). */
-int bsk_batch_configure(bsk_batch* b, int nzc, int check_every);
+/* The degree groups of a batch: for group g < min(cap, count) writes its degree, tile rows (16,
+ * 24 or 32; tiles are 64 columns wide), z-chunks per problem and autotuned ms per pass (0 if
+ * not tuned). Any output array may be NULL. Returns the number of groups (or a negative
+ * status). */
+int bsk_batch_groups(bsk_batch* b, int cap, int* degree, int* tile_rows, int* nzc, double* ms);
+
+/* Sets the decomposition of the group of `degree` (0: every group) and the graph length directly
+ * (e.g. from a cached autotuning result). Returns BSK_EINVAL for a tile shape the degree lacks
+ * (tile_rows not 16, 24 or 32; 32 with degree 5) or a degree no problem has. */
+int bsk_batch_configure(bsk_batch* b, int degree, int tile_rows, int nzc, int check_every);
 
 /* ---- the learned preconditioner and flexible CG ---------------------------------------------
  * A 3-level convolutional network N maps a normalised residual to an error estimate

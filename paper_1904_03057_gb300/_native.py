@@ -90,11 +90,12 @@ SIGNATURES = {
     "bsk_batch_heat_step": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p,
                                            ctypes.c_int, ctypes.POINTER(CgOpts),
                                            ctypes.POINTER(CgReport)]),
-    "bsk_batch_autotune": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int,
-                                          ctypes.POINTER(ctypes.c_int),
-                                          ctypes.POINTER(ctypes.c_int),
+    "bsk_batch_autotune": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int, ctypes.POINTER(ctypes.c_int),
                                           ctypes.POINTER(ctypes.c_double)]),
-    "bsk_batch_configure": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int, ctypes.c_int]),
+    "bsk_batch_groups": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int, ctypes.c_void_p, ctypes.c_void_p,
+                                        ctypes.c_void_p, ctypes.c_void_p]),
+    "bsk_batch_configure": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int, ctypes.c_int, ctypes.c_int,
+                                           ctypes.c_int]),
     "bsk_net_param_count": (ctypes.c_int, []),
     "bsk_net_create": (ctypes.c_int, [ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_void_p,
                                       ctypes.POINTER(ctypes.c_void_p)]),

@@ -297,13 +297,28 @@ class BatchHandle:
         return self._reports(reps)
 
     def autotune(self, reps: int = 3) -> dict:
-        nzc, ce, ms = ctypes.c_int(0), ctypes.c_int(0), ctypes.c_double(0.0)
-        _native.check(self._lib.bsk_batch_autotune(self._ptr, int(reps), ctypes.byref(nzc),
-                                                   ctypes.byref(ce), ctypes.byref(ms)))
-        return {"nzc": nzc.value, "check_every": ce.value, "ms_per_iteration": ms.value}
+        """Times every tile shape x z-chunking per degree group and keeps the fastest
+        (bsk_batch_autotune). Returns the graph length, the ms of one batched iteration and,
+        per group, the degree, tile [64, rows], z-chunks and ms."""
+        ce, ms = ctypes.c_int(0), ctypes.c_double(0.0)
+        _native.check(self._lib.bsk_batch_autotune(self._ptr, int(reps), ctypes.byref(ce), ctypes.byref(ms)))
+        return {"check_every": ce.value, "ms_per_iteration": ms.value, "groups": self.groups()}
 
-    def configure(self, nzc: int, check_every: int):
-        _native.check(self._lib.bsk_batch_configure(self._ptr, int(nzc), int(check_every)))
+    def groups(self) -> list:
+        """Per degree group: degree, tile [columns, rows], z-chunks per problem, tuned ms per pass."""
+        n = _native.check(self._lib.bsk_batch_groups(self._ptr, 0, None, None, None, None))
+        deg, rows, nzc = (np.zeros(n, dtype=np.int32) for _ in range(3))
+        ms = np.zeros(n)
+        _native.check(self._lib.bsk_batch_groups(self._ptr, n, deg.ctypes.data, rows.ctypes.data,
+                                                 nzc.ctypes.data, ms.ctypes.data))
+        return [{"degree": int(d), "tile": [64, int(r)], "nzc": int(c), "ms": float(t)}
+                for d, r, c, t in zip(deg, rows, nzc, ms)]
+
+    def configure(self, groups, check_every: int):
+        """Sets each group's tile and z-chunks (a list as returned by groups()) and the graph length."""
+        for g in groups:
+            _native.check(self._lib.bsk_batch_configure(self._ptr, int(g["degree"]), int(g["tile"][1]),
+                                                        int(g["nzc"]), int(check_every)))
 
     def close(self):
         if self._ptr:
@@ -402,14 +417,19 @@ class Net:
             pass
 
 
+# Version of the autotuner's search space; results tuned over another space are not reused.
+AUTOTUNE_SPACE = "tiles64x16,24,32;nzc1,2,3,4,6,8"
+
+
 def autotune_cached(batch: BatchHandle, key_problems, cache_path: str, reps: int = 3) -> dict:
-    """Autotunes a batch once per (GPU, problem list) and keeps the result in a JSON cache file."""
+    """Autotunes a batch once per (GPU, search space, problem list) and keeps the result -- the
+    tile shape and z-chunks of each degree group, and the graph length -- in a JSON cache file."""
     import hashlib
     import json
     import os
     gpu = torch.cuda.get_device_name()
     desc = ";".join(f"{p.nx}x{p.ny}x{p.nz}n{p.degree}" for p in key_problems)
-    key = f"{gpu}|f32|{hashlib.sha1(desc.encode()).hexdigest()}"
+    key = f"{gpu}|f32|{AUTOTUNE_SPACE}|{hashlib.sha1(desc.encode()).hexdigest()}"
     cache = {}
     if os.path.exists(cache_path):
         try:
@@ -418,7 +438,7 @@ def autotune_cached(batch: BatchHandle, key_problems, cache_path: str, reps: int
         except (OSError, ValueError):
             cache = {}
     if key in cache:
-        batch.configure(cache[key]["nzc"], cache[key]["check_every"])
+        batch.configure(cache[key]["groups"], cache[key]["check_every"])
         return dict(cache[key], cached=True)
     res = batch.autotune(reps)
     cache[key] = res

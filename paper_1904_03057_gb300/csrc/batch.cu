@@ -8,7 +8,8 @@
 // scalars; converged problems drop out of the queue. A CUDA graph holds `check_every`
 // iterations; the host polls one status array per graph launch. Around the FP32 iteration the
 // FP64 true residual and update of iterative refinement run per problem, in lockstep. An
-// autotuner times the work decomposition (z-chunks per problem) and the graph length.
+// autotuner times, per degree, the tile shape (64 x 16, 24 or 32) and z-chunks per problem, and
+// derives the graph length.
 #include <algorithm>
 #include <chrono>
 #include <cmath>
@@ -70,6 +71,9 @@ struct Prob {
 
 struct Group {
     int degree = 0;
+    int rows = 3;                  // output rows per warp of the group's tiles (tile 64 x 8 rows)
+    int nzc = 1;                   // z-chunks asked for per problem (at most nz per problem)
+    double tuned_ms = 0.0;         // autotuned time of the group's pass (0: not tuned)
     std::vector<int> members;
     void* desc = nullptr;          // BatchProblem<float>[members] in device memory
     double* partials = nullptr;    // 3 doubles per item
@@ -119,7 +123,7 @@ int build_groups(bsk_batch* B, int timing)
             for (int d = 0; d < 3; d++)
                 for (int j = 0; j < bsk::kMaxTaps; j++) Kdt[d][j] = B->dt * p.K[d][j];
             int nit = 0;
-            BCUDA(bsk::fill_batch_problem(descs.data() + i * bsk::batch_problem_bytes(), g.degree, p.nx, p.ny,
+            BCUDA(bsk::fill_batch_problem(descs.data() + i * bsk::batch_problem_bytes(), g.degree, g.rows, p.nx, p.ny,
                                           p.nz, p.pitch, p.nzc, item, p.M, Kdt, p.r, p.q, p.p, p.x,
                                           B->sc + g.members[i], nullptr, g.items_done + i, timing, &nit));
             item += nit;
@@ -141,7 +145,7 @@ int build_groups(bsk_batch* B, int timing)
             double Kdt[3][bsk::kMaxTaps];
             for (int dd = 0; dd < 3; dd++)
                 for (int j = 0; j < bsk::kMaxTaps; j++) Kdt[dd][j] = B->dt * p.K[dd][j];
-            BCUDA(bsk::fill_batch_problem(d, g.degree, p.nx, p.ny, p.nz, p.pitch, p.nzc, item, p.M, Kdt, p.r,
+            BCUDA(bsk::fill_batch_problem(d, g.degree, g.rows, p.nx, p.ny, p.nz, p.pitch, p.nzc, item, p.M, Kdt, p.r,
                                           p.q, p.p, p.x, B->sc + g.members[i], g.partials + 3 * (size_t)item,
                                           g.items_done + i, timing, &nit));
             item += nit;
@@ -156,19 +160,25 @@ int build_groups(bsk_batch* B, int timing)
     return BSK_OK;
 }
 
+int enqueue_group(bsk_batch* B, const Group& g, int parity, cudaStream_t s)
+{
+    bsk::TmaBatchLaunch L;
+    L.degree = g.degree;
+    L.rows = g.rows;
+    L.desc = g.desc;
+    L.nprobs = (int)g.members.size();
+    L.nitems = g.nitems;
+    L.parity = parity;
+    L.work = g.work;
+    L.status = B->gstatus;
+    BCUDA(bsk::launch_tma_batch(L, s));
+    return BSK_OK;
+}
+
 int enqueue_pass(bsk_batch* B, int parity, cudaStream_t s)
 {
-    for (Group& g : B->groups) {
-        bsk::TmaBatchLaunch L;
-        L.degree = g.degree;
-        L.desc = g.desc;
-        L.nprobs = (int)g.members.size();
-        L.nitems = g.nitems;
-        L.parity = parity;
-        L.work = g.work;
-        L.status = B->gstatus;
-        BCUDA(bsk::launch_tma_batch(L, s));
-    }
+    for (Group& g : B->groups)
+        if (int rc = enqueue_group(B, g, parity, s)) return rc;
     return BSK_OK;
 }
 
@@ -414,7 +424,7 @@ extern "C" int bsk_batch_create(const bsk_problem* probs, int count, int precisi
     }
     for (int d = 1; d <= 5; d++) {
         if (!degrees_present[d]) continue;
-        if (bsk::batch_grid(d) < 1) return cleanup(bfail(BSK_ECUDA, "batched kernel set-up failed"));
+        if (bsk::batch_grid(d, 3) < 1) return cleanup(bfail(BSK_ECUDA, "batched kernel set-up failed"));
         Group g;
         g.degree = d;
         for (int i = 0; i < count; i++)
@@ -524,52 +534,102 @@ extern "C" int bsk_batch_heat_step(bsk_batch* B, void* const* u, const void* con
     return st;
 }
 
-extern "C" int bsk_batch_autotune(bsk_batch* B, int reps, int* nzc_out, int* check_every_out,
-                                  double* ms_out)
+extern "C" int bsk_batch_autotune(bsk_batch* B, int reps, int* check_every_out, double* ms_out)
 {
     if (!B || reps < 1) return bfail(BSK_EINVAL, "bad argument");
-    // time whole-batch CG passes (finalisers off, no problem stops) for each z-chunking
+    // time each degree group's CG pass (finalisers off, no problem stops) for every tile shape and
+    // z-chunking, and keep the fastest per group
     memset(B->h_sc, 0, sizeof(Scalars) * B->count);
     int rc = write_scalars(B, B->sc);
     if (rc) return rc;
-    static const int cands[] = {1, 2, 3, 4, 6, 8};
-    int best = 1;
-    double best_ms = -1.0;
+    static const int rows_cands[] = {2, 3, 4};
+    static const int nzc_cands[] = {1, 2, 3, 4, 6, 8};
+    const size_t ng = B->groups.size();
+    std::vector<double> best_ms(ng, -1.0);
+    std::vector<int> best_rows(ng, 3), best_nzc(ng, 1);
     cudaEvent_t e0, e1;
     BCUDA(cudaEventCreate(&e0));
     BCUDA(cudaEventCreate(&e1));
-    for (int c : cands) {
-        for (Prob& p : B->P) p.nzc = std::min(c, p.nz);
-        if ((rc = build_groups(B, 1))) break;
-        for (Group& g : B->groups) BCUDA(cudaMemsetAsync(g.work, 0, 2 * sizeof(unsigned int), B->stream));
-        if ((rc = enqueue_pass(B, 0, B->stream))) break;   // warm-up
-        BCUDA(cudaEventRecord(e0, B->stream));
-        for (int r = 0; r < reps && rc == BSK_OK; r++) rc = enqueue_pass(B, r & 1, B->stream);
-        BCUDA(cudaEventRecord(e1, B->stream));
-        BCUDA(cudaEventSynchronize(e1));
-        float ms = 0.f;
-        BCUDA(cudaEventElapsedTime(&ms, e0, e1));
-        const double per = ms / reps;
-        if (best_ms < 0 || per < best_ms) { best_ms = per; best = c; }
+    for (int rows : rows_cands) {
+        for (int c : nzc_cands) {
+            for (Group& g : B->groups) {
+                g.rows = bsk::batch_rows_supported(g.degree, rows) ? rows : 3;
+                for (int m : g.members) B->P[m].nzc = std::min(c, B->P[m].nz);
+            }
+            if ((rc = build_groups(B, 1))) break;
+            for (size_t gi = 0; gi < ng && rc == BSK_OK; gi++) {
+                Group& g = B->groups[gi];
+                if (g.rows != rows) continue;   // this tile shape does not exist for the degree
+                BCUDA(cudaMemsetAsync(g.work, 0, 2 * sizeof(unsigned int), B->stream));
+                if ((rc = enqueue_group(B, g, 0, B->stream))) break;   // warm-up
+                BCUDA(cudaEventRecord(e0, B->stream));
+                for (int r = 0; r < reps && rc == BSK_OK; r++) rc = enqueue_group(B, g, r & 1, B->stream);
+                BCUDA(cudaEventRecord(e1, B->stream));
+                BCUDA(cudaEventSynchronize(e1));
+                float ms = 0.f;
+                BCUDA(cudaEventElapsedTime(&ms, e0, e1));
+                const double per = ms / reps;
+                if (best_ms[gi] < 0 || per < best_ms[gi]) {
+                    best_ms[gi] = per;
+                    best_rows[gi] = rows;
+                    best_nzc[gi] = c;
+                }
+            }
+            if (rc) break;
+        }
+        if (rc) break;
     }
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
-    for (Prob& p : B->P) p.nzc = std::min(best, p.nz);
+    double total = 0.0;
+    for (size_t gi = 0; gi < ng; gi++) {
+        Group& g = B->groups[gi];
+        g.rows = best_rows[gi];
+        g.nzc = best_nzc[gi];
+        g.tuned_ms = best_ms[gi];
+        for (int m : g.members) B->P[m].nzc = std::min(best_nzc[gi], B->P[m].nz);
+        total += best_ms[gi];
+    }
     int rc2 = build_groups(B, 0);
     if (rc) return rc;
     if (rc2) return rc2;
     // graph length: longer graphs poll less, shorter ones stop sooner after convergence
-    B->check_every = best_ms > 0.5 ? 8 : (best_ms > 0.1 ? 16 : 32);
-    if (nzc_out) *nzc_out = best;
+    B->check_every = total > 0.5 ? 8 : (total > 0.1 ? 16 : 32);
     if (check_every_out) *check_every_out = B->check_every;
-    if (ms_out) *ms_out = best_ms;
+    if (ms_out) *ms_out = total;
     return BSK_OK;
 }
 
-extern "C" int bsk_batch_configure(bsk_batch* B, int nzc, int check_every)
+extern "C" int bsk_batch_groups(bsk_batch* B, int cap, int* degree, int* tile_rows, int* nzc, double* ms)
 {
-    if (!B || nzc < 1 || check_every < 1) return bfail(BSK_EINVAL, "bad argument");
-    for (Prob& p : B->P) p.nzc = std::min(nzc, p.nz);
+    if (!B || cap < 0) return bfail(BSK_EINVAL, "bad argument");
+    const int ng = (int)B->groups.size();
+    for (int gi = 0; gi < ng && gi < cap; gi++) {
+        const Group& g = B->groups[gi];
+        if (degree) degree[gi] = g.degree;
+        if (tile_rows) tile_rows[gi] = 8 * g.rows;
+        if (nzc) nzc[gi] = g.nzc;
+        if (ms) ms[gi] = g.tuned_ms;
+    }
+    return ng;
+}
+
+extern "C" int bsk_batch_configure(bsk_batch* B, int degree, int tile_rows, int nzc, int check_every)
+{
+    if (!B || nzc < 1 || check_every < 1 || tile_rows % 8 != 0) return bfail(BSK_EINVAL, "bad argument");
+    const int rows = tile_rows / 8;
+    bool any = false;
+    for (Group& g : B->groups) {
+        if (degree != 0 && g.degree != degree) continue;
+        if (!bsk::batch_rows_supported(g.degree, rows)) return bfail(BSK_EINVAL, "tile shape not available for this degree");
+        if (bsk::batch_grid(g.degree, rows) < 1) return bfail(BSK_ECUDA, "batched kernel set-up failed");
+        g.rows = rows;
+        g.nzc = nzc;
+        g.tuned_ms = 0.0;
+        for (int m : g.members) B->P[m].nzc = std::min(nzc, B->P[m].nz);
+        any = true;
+    }
+    if (!any) return bfail(BSK_EINVAL, "no group of that degree");
     B->check_every = check_every + (check_every & 1);
     return build_groups(B, 0);
 }

@@ -1964,15 +1964,28 @@ extern "C" int bsk_slab_apply(bsk_handle* h, const void* x_halo, void* y)
     const size_t in_bytes = (size_t)(h->nz + 2 * h->n) * plane_len(h) * es;
     const char *a = (const char*)x_halo, *b = (const char*)y;
     if (a < b + h->len * es && b < a + in_bytes) return fail(BSK_EINVAL, "x_halo and y overlap");
-    bsk::OpLaunch L;
-    fill_launch(h, L, bsk::MODE_OP);
-    L.in0 = x_halo;
-    L.out0 = y;
-    L.fin = bsk::FIN_NONE;
-    L.z_off = h->z_off;
-    L.nz_glob = h->nz_glob;
-    L.zpad = h->n;
-    const cudaError_t e = op_launch_es(es, L, h->stream);
+    cudaError_t e;
+    if (tma_ok(h, es, {x_halo, y})) {   // 16-byte rows: the TMA operator kernel
+        bsk::TmaLaunch T;
+        fill_tma(h, T, bsk::TMODE_OP);
+        T.in[0] = x_halo;
+        T.out0 = y;
+        T.fin = bsk::FIN_NONE;
+        T.z_off = h->z_off;
+        T.nz_glob = h->nz_glob;
+        T.zpad = h->n;
+        e = tma_launch_es(es, T, h->stream);
+    } else {
+        bsk::OpLaunch L;
+        fill_launch(h, L, bsk::MODE_OP);
+        L.in0 = x_halo;
+        L.out0 = y;
+        L.fin = bsk::FIN_NONE;
+        L.z_off = h->z_off;
+        L.nz_glob = h->nz_glob;
+        L.zpad = h->n;
+        e = op_launch_es(es, L, h->stream);
+    }
     if (e != cudaSuccess) return cuda_fail(e, "slab operator launch");
     h->launches += 1;
     return BSK_OK;

@@ -149,6 +149,9 @@ struct TmaLaunch {
     int fin;
     int impl;                    // TMODE_CG, FP32, unmasked, degree <= 4: 0 = the warp-specialised
                                  // pass (op_ws.cuh), 1 = the single-pass kernel of op_tma.cuh
+    // TMODE_OP on a z-slab: global offset, global plane count (0 = nz) and the halo planes in[0]
+    // carries on each side (0 = a whole grid)
+    int z_off, nz_glob, zpad;
 };
 // In-place banded triangular solves along one axis (0 = x, 1 = y, 2 = z) of an nx*ny*nz grid,
 // one thread per line: L holds a banded Cholesky factor of half-width p <= 5 (transform.cu).
@@ -179,6 +182,7 @@ cudaError_t launch_ws(const TmaLaunch& L, cudaStream_t s);
 // problems of one degree; desc points to BatchProblem<float>[nprobs] in device memory.
 struct TmaBatchLaunch {
     int degree;
+    int rows;                    // output rows per warp of the tile (tile = 64 x 8 rows): 2, 3 or 4
     const void* desc;
     int nprobs;
     int nitems;
@@ -186,10 +190,14 @@ struct TmaBatchLaunch {
     unsigned int* work;          // 2 counters, zero between launches
     Scalars* status;             // receives a wait time-out
 };
+// Highest degree with a 64 x 32 batched tile (its accumulators would spill above it).
+constexpr int kBatchMaxDegreeR4 = 4;
 size_t batch_problem_bytes();
-int batch_grid(int degree);     // resident blocks (after prepare_tma<float>(degree))
-// Fills one BatchProblem<float> (host memory, batch_problem_bytes() bytes) for a padded problem.
-cudaError_t fill_batch_problem(void* host_desc, int degree, int nx, int ny, int nz, int pitch,
+bool batch_rows_supported(int degree, int rows);
+int batch_grid(int degree, int rows);   // resident blocks of the batched kernel (0 if unsupported)
+// Fills one BatchProblem<float> (host memory, batch_problem_bytes() bytes) for a padded problem
+// cut into tiles of 64 x 8 rows and nzc z-chunks.
+cudaError_t fill_batch_problem(void* host_desc, int degree, int rows, int nx, int ny, int nz, int pitch,
                                int nzc, int item0, const double (*M)[kMaxTaps],
                                const double (*Kdt)[kMaxTaps], float* const r[2], float* const q[2],
                                float* const p[2], float* x, Scalars* sc, double* partials,

@@ -33,7 +33,8 @@
 namespace bsk {
 
 constexpr int kTX = 64;     // output columns per tile
-constexpr int kTY = 24;     // output rows per tile (8 warps x 3 rows)
+constexpr int kTR = 3;      // output rows per warp of the single-problem kernels
+constexpr int kTY = 8 * kTR;   // their output rows per tile (8 warps x 3 rows)
 constexpr int kTNT = 256;   // threads per block
 
 template <typename T>
@@ -49,6 +50,10 @@ struct TmaArgs {
     const uint8_t* occ;   // with a mask: occ[z * tiles + tile] != 0 iff tile has an active node in
                           // plane z; items with none are skipped (their outputs stay zero)
     int nx, ny, nz;
+    // OP on a z-slab: the nz local planes are planes z_off .. of a grid of nz_glob planes, and
+    // tin[0] holds nz + 2 zpad planes (plane i = global plane z_off - zpad + i); odd reflection
+    // at the global faces only. A whole grid: z_off = 0, nz_glob = nz, zpad = 0.
+    int z_off, nz_glob, zpad;
     int pitch;            // elements per row in memory (>= nx; rows of 16-byte multiples)
     int tiles_x, tiles_y, tz, nitems;
     T M[3][kMaxTaps];     // per-axis mass kernels, index j + n
@@ -84,12 +89,15 @@ struct BatchProblem {
     int pad[5];
 };
 
-template <typename T, int N>
+// Tile geometry: 64 columns x 8 R rows (R output rows per warp; the batched kernels come in
+// R = 2, 3, 4, the single-problem kernels use R = 3).
+template <typename T, int N, int R = kTR>
 struct TGeo {
     static constexpr int L = 2 * N + 1;
+    static constexpr int TY = 8 * R;                    // output rows per tile
     static constexpr int HL = N <= 4 ? 4 : 8;          // halo columns staged on each side
     static constexpr int BX = kTX + 2 * HL + 4;         // box width; +4 columns spread smem banks
-    static constexpr int HY = kTY + 2 * N;              // box height (tile rows + y halo)
+    static constexpr int HY = TY + 2 * N;               // box height (tile rows + y halo)
     static constexpr int MXP = kTX + 4;                 // row pitch of the x-sweep results
     // interior box (b or x) width = row pitch of it and of the ring: 16 bytes over the tile,
     // so that threads on consecutive rows hit distinct shared-memory banks
@@ -97,14 +105,14 @@ struct TGeo {
     static constexpr int WIN = 8 + 2 * HL;              // x-window loaded per 8 outputs
 };
 
-template <typename T, int N, int MODE>
+template <typename T, int N, int MODE, int R = kTR>
 struct TLayout {
-    using G = TGeo<T, N>;
+    using G = TGeo<T, N, R>;
     static constexpr int NIN = MODE == TMODE_CG ? 3 : 1;
     static constexpr int NINT = MODE == TMODE_OP ? 0 : 1;
     static constexpr size_t rnd(size_t b) { return (b + 127) / 128 * 128; }
     static constexpr size_t in_bytes = rnd(sizeof(T) * G::HY * G::BX);
-    static constexpr size_t int_bytes = rnd(sizeof(T) * kTY * G::IP);
+    static constexpr size_t int_bytes = rnd(sizeof(T) * G::TY * G::IP);
     static constexpr size_t stage_bytes = NIN * in_bytes + NINT * int_bytes;
     static constexpr int S = MODE == TMODE_OP ? 4 : 2;   // pipeline stages
     static constexpr size_t off_mx = S * stage_bytes;
@@ -114,7 +122,7 @@ struct TLayout {
     static constexpr size_t off_bar = off_ring + ring_bytes;
     static constexpr size_t total = off_bar + 64;
     static constexpr uint32_t tx_bytes =
-        (uint32_t)(NIN * sizeof(T) * G::HY * G::BX + NINT * sizeof(T) * kTY * G::IP);
+        (uint32_t)(NIN * sizeof(T) * G::HY * G::BX + NINT * sizeof(T) * G::TY * G::IP);
 };
 
 // Packed pair arithmetic: f32x2 instructions for FP32, two scalar operations for FP64.
@@ -185,10 +193,10 @@ __device__ __forceinline__ void load_window(T (&v)[W], const T* src)
 
 // Odd reflection of the ghost rows / columns of one staged box that the sweeps read (at most n
 // on each side); ghosts further out stay as loaded (zero) and feed no output that is stored.
-template <typename T, int N>
+template <typename T, int N, int R = kTR>
 __device__ __forceinline__ void patch_rows(T* box, int y0, int ny)
 {
-    using G = TGeo<T, N>;
+    using G = TGeo<T, N, R>;
     // box row br <-> grid row y0 - N + br; ghosts read: [0, N) when y0 == 0, and
     // [ny - y0 + N, ny - y0 + 2N) at the far face
     const int lo_n = (y0 == 0) ? N : 0;
@@ -206,10 +214,10 @@ __device__ __forceinline__ void patch_rows(T* box, int y0, int ny)
     }
 }
 
-template <typename T, int N>
+template <typename T, int N, int R = kTR>
 __device__ __forceinline__ void patch_cols(T* box, int x0, int nx)
 {
-    using G = TGeo<T, N>;
+    using G = TGeo<T, N, R>;
     // box column bc <-> grid column x0 - HL + bc; ghosts read: [HL - N, HL) when x0 == 0, and
     // [nx - x0 + HL, nx - x0 + HL + N) at the far face
     const int lo_n = (x0 == 0) ? N : 0;
@@ -229,13 +237,13 @@ __device__ __forceinline__ void patch_cols(T* box, int x0, int nx)
 
 // z push of one plane into the accumulator ring (slot of output plane z + d is (J + d) mod L),
 // then hand back the completed output plane z - n (slot (J - n) mod L) and clear its slot.
-template <typename T2, typename PP, int N, int J>
-__device__ __forceinline__ void push_plane(T2 (&acc)[3][2 * N + 1], const T2 (&U)[3], const T2 (&V)[3],
-                                           const T2 (&w1z)[N + 1], const T2 (&mz)[N + 1], T2 (&q)[3])
+template <typename T2, typename PP, int N, int R, int J>
+__device__ __forceinline__ void push_plane(T2 (&acc)[R][2 * N + 1], const T2 (&U)[R], const T2 (&V)[R],
+                                           const T2 (&w1z)[N + 1], const T2 (&mz)[N + 1], T2 (&q)[R])
 {
     constexpr int L = 2 * N + 1;
 #pragma unroll
-    for (int t = 0; t < 3; t++) {
+    for (int t = 0; t < R; t++) {
 #pragma unroll
         for (int dd = -N; dd <= N; dd++) {
             const int sl = ((J + dd) % L + L) % L;
@@ -249,34 +257,34 @@ __device__ __forceinline__ void push_plane(T2 (&acc)[3][2 * N + 1], const T2 (&U
     }
 }
 
-template <typename T2, typename PP, int N>
-__device__ __forceinline__ void push_dispatch(int j, T2 (&acc)[3][2 * N + 1], const T2 (&U)[3],
-                                              const T2 (&V)[3], const T2 (&w1z)[N + 1],
-                                              const T2 (&mz)[N + 1], T2 (&q)[3])
+template <typename T2, typename PP, int N, int R>
+__device__ __forceinline__ void push_dispatch(int j, T2 (&acc)[R][2 * N + 1], const T2 (&U)[R],
+                                              const T2 (&V)[R], const T2 (&w1z)[N + 1],
+                                              const T2 (&mz)[N + 1], T2 (&q)[R])
 {
     switch (j) {
-    case 0: push_plane<T2, PP, N, 0>(acc, U, V, w1z, mz, q); break;
-    case 1: push_plane<T2, PP, N, 1>(acc, U, V, w1z, mz, q); break;
-    case 2: push_plane<T2, PP, N, 2>(acc, U, V, w1z, mz, q); break;
+    case 0: push_plane<T2, PP, N, R, 0>(acc, U, V, w1z, mz, q); break;
+    case 1: push_plane<T2, PP, N, R, 1>(acc, U, V, w1z, mz, q); break;
+    case 2: push_plane<T2, PP, N, R, 2>(acc, U, V, w1z, mz, q); break;
     default:
         if constexpr (N >= 2) {
             switch (j) {
-            case 3: push_plane<T2, PP, N, 3>(acc, U, V, w1z, mz, q); break;
-            case 4: push_plane<T2, PP, N, 4>(acc, U, V, w1z, mz, q); break;
+            case 3: push_plane<T2, PP, N, R, 3>(acc, U, V, w1z, mz, q); break;
+            case 4: push_plane<T2, PP, N, R, 4>(acc, U, V, w1z, mz, q); break;
             default:
                 if constexpr (N >= 3) {
                     switch (j) {
-                    case 5: push_plane<T2, PP, N, 5>(acc, U, V, w1z, mz, q); break;
-                    case 6: push_plane<T2, PP, N, 6>(acc, U, V, w1z, mz, q); break;
+                    case 5: push_plane<T2, PP, N, R, 5>(acc, U, V, w1z, mz, q); break;
+                    case 6: push_plane<T2, PP, N, R, 6>(acc, U, V, w1z, mz, q); break;
                     default:
                         if constexpr (N >= 4) {
                             switch (j) {
-                            case 7: push_plane<T2, PP, N, 7>(acc, U, V, w1z, mz, q); break;
-                            case 8: push_plane<T2, PP, N, 8>(acc, U, V, w1z, mz, q); break;
+                            case 7: push_plane<T2, PP, N, R, 7>(acc, U, V, w1z, mz, q); break;
+                            case 8: push_plane<T2, PP, N, R, 8>(acc, U, V, w1z, mz, q); break;
                             default:
                                 if constexpr (N >= 5) {
-                                    if (j == 9) push_plane<T2, PP, N, 9>(acc, U, V, w1z, mz, q);
-                                    else push_plane<T2, PP, N, 10>(acc, U, V, w1z, mz, q);
+                                    if (j == 9) push_plane<T2, PP, N, R, 9>(acc, U, V, w1z, mz, q);
+                                    else push_plane<T2, PP, N, R, 10>(acc, U, V, w1z, mz, q);
                                 }
                             }
                         }
@@ -287,12 +295,14 @@ __device__ __forceinline__ void push_dispatch(int j, T2 (&acc)[3][2 * N + 1], co
     }
 }
 
-template <typename T, int N, int MODE, bool BATCH>
+template <typename T, int N, int MODE, bool BATCH, int R = kTR>
 __global__ void __launch_bounds__(kTNT, (sizeof(T) == 4 && N <= 4 && !BATCH) ? 2 : 1)
     k_op_tma(const __grid_constant__ TmaArgs<T> a)
 {
-    using G = TGeo<T, N>;
-    using LY = TLayout<T, N, MODE>;
+    using G = TGeo<T, N, R>;
+    using LY = TLayout<T, N, MODE, R>;
+    constexpr int TY = G::TY;
+    static_assert(BATCH || R == kTR, "single-problem kernels use 64 x 24 tiles");
     using PP = P2<T>;
     using T2 = typename PP::t;
     constexpr int L = G::L, HY = G::HY, BX = G::BX, MXP = G::MXP, HL = G::HL, WIN = G::WIN, IP = G::IP;
@@ -380,8 +390,8 @@ __global__ void __launch_bounds__(kTNT, (sizeof(T) == 4 && N <= 4 && !BATCH) ? 2
     constexpr bool ONE_TASK = NTASK <= kTNT;
     const int xrow = tid % HY, xg = tid / HY;
     // y-sweep / z push: this thread's column pair and first row in the x-sweep results
-    const T* mxb = MXs + 3 * warp * MXP + 2 * lane;
-    const T* kxb = KXs + 3 * warp * MXP + 2 * lane;
+    const T* mxb = MXs + R * warp * MXP + 2 * lane;
+    const T* kxb = KXs + R * warp * MXP + 2 * lane;
 
     using Acc = std::conditional_t<DF, float, T>;
     KSum<Acc> d0, d1, d2;
@@ -423,12 +433,14 @@ __global__ void __launch_bounds__(kTNT, (sizeof(T) == 4 && N <= 4 && !BATCH) ? 2
         const int item = item_g - item0;
         const int ntiles = tiles_x * tiles_y;
         const int tile = item % ntiles, zc = item / ntiles;
-        const int x0 = (tile % tiles_x) * kTX, y0 = (tile / tiles_x) * kTY;
+        const int x0 = (tile % tiles_x) * kTX, y0 = (tile / tiles_x) * TY;
         const int z0 = zc * tz, z1 = min(z0 + tz, nz);
         const int zs = z0 - N;
         const int np = (z1 - z0) + 2 * N;
         const bool patch_x = (x0 == 0) || (x0 + kTX + N > nx);
-        const bool patch_y = (y0 == 0) || (y0 + kTY + N > ny);
+        const bool patch_y = (y0 == 0) || (y0 + TY + N > ny);
+        // z-slab geometry (single-problem OP passes; a batch problem is always a whole grid)
+        const int z_off = BATCH ? 0 : a.z_off, nz_glob = BATCH ? nz : a.nz_glob, zpad = BATCH ? 0 : a.zpad;
         if (!BATCH && a.occ) {
             // brick occupancy: an item whose output box holds no active node is left out. Its
             // outputs are zero and already zero in the solvers' vectors (which are zero off the
@@ -447,7 +459,10 @@ __global__ void __launch_bounds__(kTNT, (sizeof(T) == 4 && N <= 4 && !BATCH) ? 2
             unsigned char* st = smem + (c % S) * LY::stage_bytes;
             int zsrc = 0;
             const int zz = zs + k;
-            if (!reflect_index(zz, nz, zsrc)) zsrc = 0;   // a face plane: any plane, scaled by 0
+            // global plane z_off + zz, reflected about the global faces, as a plane of the input
+            // array (a face plane: any plane, scaled by 0)
+            if (!reflect_index(z_off + zz, nz_glob, zsrc)) zsrc = z_off;
+            zsrc += zpad - z_off;
             uint64_t* bar = &bars[c % S];
             mbar_arrive_expect_tx(bar, LY::tx_bytes);
             const CUtensorMap* maps[3] = {tin0, tin1, tin2};
@@ -463,9 +478,9 @@ __global__ void __launch_bounds__(kTNT, (sizeof(T) == 4 && N <= 4 && !BATCH) ? 2
             for (int k = 0; k < S && k < np; k++) issue(k);
         }
 
-        T2 acc[3][L];
+        T2 acc[R][L];
 #pragma unroll
-        for (int t = 0; t < 3; t++)
+        for (int t = 0; t < R; t++)
 #pragma unroll
             for (int s = 0; s < L; s++) acc[t][s] = PP::zero();
 
@@ -491,11 +506,11 @@ __global__ void __launch_bounds__(kTNT, (sizeof(T) == 4 && N <= 4 && !BATCH) ? 2
                 // the box holds FP64 as loaded: reflect in FP64, then split in place
                 double* bd = reinterpret_cast<double*>(in0);
                 if (patch_y) {
-                    patch_rows<double, N>(bd, y0, ny);
+                    patch_rows<double, N, R>(bd, y0, ny);
                     __syncthreads();
                 }
                 if (patch_x) {
-                    patch_cols<double, N>(bd, x0, nx);
+                    patch_cols<double, N, R>(bd, x0, nx);
                     __syncthreads();
                 }
                 for (int i = tid; i < HY * BX; i += kTNT) {
@@ -505,20 +520,20 @@ __global__ void __launch_bounds__(kTNT, (sizeof(T) == 4 && N <= 4 && !BATCH) ? 2
                 __syncthreads();
             } else {
                 if (patch_y) {
-                    patch_rows<T, N>(in0, y0, ny);
-                    if (NIN > 1) { patch_rows<T, N>(in1, y0, ny); patch_rows<T, N>(in2, y0, ny); }
+                    patch_rows<T, N, R>(in0, y0, ny);
+                    if (NIN > 1) { patch_rows<T, N, R>(in1, y0, ny); patch_rows<T, N, R>(in2, y0, ny); }
                     __syncthreads();
                 }
                 if (patch_x) {
-                    patch_cols<T, N>(in0, x0, nx);
-                    if (NIN > 1) { patch_cols<T, N>(in1, x0, nx); patch_cols<T, N>(in2, x0, nx); }
+                    patch_cols<T, N, R>(in0, x0, nx);
+                    if (NIN > 1) { patch_cols<T, N, R>(in1, x0, nx); patch_cols<T, N, R>(in2, x0, nx); }
                     __syncthreads();
                 }
             }
 
             {
                 int zsrc = 0;
-                const int zsi = reflect_index(z, nz, zsrc);   // 1, -1 (mirror plane) or 0 (face)
+                const int zsi = reflect_index(z_off + z, nz_glob, zsrc);   // 1, -1 (mirror plane) or 0 (face)
                 const T zsgn = (T)zsi;
                 const bool zint = (z >= z0 && z < z1);
                 const int rslot = zint ? (z - z0) % (N + 1) : 0;
@@ -530,7 +545,7 @@ __global__ void __launch_bounds__(kTNT, (sizeof(T) == 4 && N <= 4 && !BATCH) ? 2
                     else { row = t % HY; g = t / HY; }
                     T v[WIN];
                     load_window<T, WIN>(v, in0 + row * BX + 8 * g);
-                    const bool interior = zint && row >= N && row < N + kTY;
+                    const bool interior = zint && row >= N && row < N + TY;
                     if constexpr (MODE == TMODE_CG) {
                         // p_m = (r - alpha q) + beta p of the previous iteration's vectors
                         T qv[WIN], pv[WIN];
@@ -546,7 +561,7 @@ __global__ void __launch_bounds__(kTNT, (sizeof(T) == 4 && N <= 4 && !BATCH) ? 2
                         if (interior) {
                             const int gy = y0 + row - N;
                             const T* xin = inint + (row - N) * IP + 8 * g;
-                            T* rg = ring + rslot * (kTY * IP) + (row - N) * IP + 8 * g;
+                            T* rg = ring + rslot * (TY * IP) + (row - N) * IP + 8 * g;
                             T xi8[8];
                             load_window<T, 8>(xi8, xin);
 #pragma unroll
@@ -595,7 +610,7 @@ __global__ void __launch_bounds__(kTNT, (sizeof(T) == 4 && N <= 4 && !BATCH) ? 2
                         // keep b of this plane for the residual of output plane z
                         T b8[8];
                         load_window<T, 8>(b8, inint + (row - N) * IP + 8 * g);
-                        T* rg = ring + rslot * (kTY * IP) + (row - N) * IP + 8 * g;
+                        T* rg = ring + rslot * (TY * IP) + (row - N) * IP + 8 * g;
                         if constexpr (sizeof(T) == 4) {
                             reinterpret_cast<float4*>(rg)[0] = make_float4(b8[0], b8[1], b8[2], b8[3]);
                             reinterpret_cast<float4*>(rg)[1] = make_float4(b8[4], b8[5], b8[6], b8[7]);
@@ -666,16 +681,16 @@ __global__ void __launch_bounds__(kTNT, (sizeof(T) == 4 && N <= 4 && !BATCH) ? 2
             // ---- y-sweep in registers, then the z push ----
             {
                 const int c2 = 2 * lane;
-                constexpr int NR = 3 + 2 * N;
+                constexpr int NR = R + 2 * N;
                 T2 mv[NR], kv[NR];
 #pragma unroll
                 for (int r = 0; r < NR; r++) {
                     mv[r] = *reinterpret_cast<const T2*>(mxb + r * MXP);
                     kv[r] = *reinterpret_cast<const T2*>(kxb + r * MXP);
                 }
-                T2 U[3], V[3], q[3];
+                T2 U[R], V[R], q[R];
 #pragma unroll
-                for (int t = 0; t < 3; t++) {
+                for (int t = 0; t < R; t++) {
                     const int cc = t + N;   // centre row in mv/kv
                     T2 u = PP::fma(my[0], mv[cc], PP::zero());
                     T2 w = PP::fma(ky[0], mv[cc], PP::zero());
@@ -691,14 +706,14 @@ __global__ void __launch_bounds__(kTNT, (sizeof(T) == 4 && N <= 4 && !BATCH) ? 2
                     U[t] = u;
                     V[t] = w;
                 }
-                push_dispatch<T2, PP, N>(jslot, acc, U, V, w1z, mz, q);
+                push_dispatch<T2, PP, N, R>(jslot, acc, U, V, w1z, mz, q);
                 // output plane z - N is complete
                 const int zo = z - N;
                 if (zo >= z0 && zo < z1) {
                     const int oslot = (zo - z0) % (N + 1);
 #pragma unroll
-                    for (int t = 0; t < 3; t++) {
-                        const int gy = y0 + 3 * warp + t, gx = x0 + c2;
+                    for (int t = 0; t < R; t++) {
+                        const int gy = y0 + R * warp + t, gx = x0 + c2;
                         if (gy < ny && gx < nx) {
                             const size_t o = ((size_t)zo * ny + gy) * pitch + gx;
                             unsigned mm = 0x0101u;
@@ -712,7 +727,7 @@ __global__ void __launch_bounds__(kTNT, (sizeof(T) == 4 && N <= 4 && !BATCH) ? 2
                             } else if constexpr (DF) {
                                 // r = b - A x in FP64 from the double-float A x; b is still FP64
                                 const double2 bq = *reinterpret_cast<const double2*>(
-                                    ring + oslot * (kTY * IP) + (3 * warp + t) * IP + c2);
+                                    ring + oslot * (TY * IP) + (R * warp + t) * IP + c2);
                                 const double bx = (mm & 0xffu) ? bq.x : 0.0, by = (mm >> 8) ? bq.y : 0.0;
                                 const double qx = (mm & 0xffu) ? df_to_double(q[t].x) : 0.0;
                                 const double qy = (mm >> 8) ? df_to_double(q[t].y) : 0.0;
@@ -734,7 +749,7 @@ __global__ void __launch_bounds__(kTNT, (sizeof(T) == 4 && N <= 4 && !BATCH) ? 2
                                 __stcs(reinterpret_cast<T2*>(out0 + o), q[t]);
                             } else {
                                 T2 rg = *reinterpret_cast<const T2*>(
-                                    ring + oslot * (kTY * IP) + (3 * warp + t) * IP + c2);
+                                    ring + oslot * (TY * IP) + (R * warp + t) * IP + c2);
                                 if constexpr (MODE == TMODE_RES) {
                                     T2 r;
                                     rg.x *= mk2.x;   // b off the mask is ignored

@@ -136,8 +136,10 @@ cudaError_t launch_one(const TmaLaunch& L, cudaStream_t s)
 {
     if constexpr (std::is_same<BSK_T, float>::value && (MODE == TMODE_OP || MODE == TMODE_CG) && N <= 4) {
         // the warp-specialised operator pass; for CG the one the handle's tuning chose
-        if (!L.mask && (MODE == TMODE_OP || L.impl == 0)) return launch_ws(L, s);
+        if (!L.mask && !L.zpad && (MODE == TMODE_OP || L.impl == 0)) return launch_ws(L, s);
     }
+    if (L.zpad && MODE != TMODE_OP) return cudaErrorInvalidValue;   // slabs: operator passes only
+    const int nz_in = L.nz + 2 * L.zpad;                              // planes of the input array
     TmaInfo& info = tma_info<N, MODE>();
     if (!info.ready) return cudaErrorNotReady;   // prepare_tma was not called
     using G = TGeo<BSK_T, N>;
@@ -147,7 +149,7 @@ cudaError_t launch_one(const TmaLaunch& L, cudaStream_t s)
     cudaError_t e;
     const int nin = MODE == TMODE_CG ? 3 : 1;
     for (int i = 0; i < nin; i++)
-        if ((e = encode_box(&a.tin[i], L.in[i], L.nx, L.ny, L.nz, G::BX, G::HY)) != cudaSuccess) return e;
+        if ((e = encode_box(&a.tin[i], L.in[i], L.nx, L.ny, nz_in, G::BX, G::HY)) != cudaSuccess) return e;
     if (MODE != TMODE_OP)
         if ((e = encode_box(&a.tint, L.inint, L.nx, L.ny, L.nz, G::IP, kTY)) != cudaSuccess) return e;
     a.out0 = static_cast<BSK_T*>(L.out0);
@@ -159,6 +161,9 @@ cudaError_t launch_one(const TmaLaunch& L, cudaStream_t s)
     a.nx = L.nx;
     a.ny = L.ny;
     a.nz = L.nz;
+    a.z_off = L.z_off;
+    a.nz_glob = L.nz_glob > 0 ? L.nz_glob : L.nz;
+    a.zpad = L.zpad;
     a.pitch = L.nx;
     plan(L.nx, L.ny, L.nz, N, info.grid, a.tiles_x, a.tiles_y, a.tz, a.nitems);
     for (int d = 0; d < 3; d++)

@@ -3,7 +3,9 @@ copies, against the oracle on the whole grid (FP64 parity at 1e-12).
 
 - bsk_slab_apply: each slab's A x from its halo-extended planes equals the oracle's A x on the
   whole grid, planes z_off .. z_off + nz - 1. Halo planes beyond the global faces hold NaN, so
-  a kernel that read them (instead of reflecting about the global face) would fail.
+  a kernel that read them (instead of reflecting about the global face) would fail. Rows of
+  16-byte multiples take the TMA kernel (FP32 up to degree 5, FP64 up to degree 3), the others
+  the general kernel; the cases cover both.
 - the slab CG driver: x after k iterations equals the oracle's CG iterate x_k element by
   element, and the converged solution solves the whole-grid system.
 """
@@ -33,6 +35,8 @@ def _halo_of(x, z, nz, n):
     (4, (35, 26, 30), [(0, 13), (13, 17)], "f64"),
     (5, (24, 22, 25), [(0, 5), (5, 12), (17, 8)], "f64"),
     (3, (64, 40, 26), [(0, 13), (13, 13)], "f32"),
+    (5, (72, 30, 23), [(0, 5), (5, 9), (14, 9)], "f32"),
+    (3, (32, 20, 9), [(0, 3), (3, 3), (6, 3)], "f64"),
 ], ids=lambda v: str(v).replace(" ", ""))
 def test_slab_apply_matches_oracle(orc, n, shape, parts, prec):
     from paper_1904_03057_gb300 import slab as sl
@@ -84,10 +88,12 @@ def _split_cg(orc, shape, n, parts, iters=None, tol=1e-13):
     return orc.Problem(nx, ny, nzg, n, h, dt=dt), b, x, rep
 
 
-@pytest.mark.parametrize("parts", [[(0, 12), (12, 11)], [(0, 9), (9, 3), (12, 11)]],
-                         ids=["two-slabs", "three-slabs-thin-middle"])
-def test_slab_cg_iterates_match_oracle(orc, parts):
-    shape, n, k = (41, 30, 23), 3, 8
+@pytest.mark.parametrize("shape,parts", [((41, 30, 23), [(0, 12), (12, 11)]),
+                                         ((41, 30, 23), [(0, 9), (9, 3), (12, 11)]),
+                                         ((40, 30, 23), [(0, 12), (12, 11)])],
+                         ids=["two-slabs", "three-slabs-thin-middle", "two-slabs-tma-rows"])
+def test_slab_cg_iterates_match_oracle(orc, shape, parts):
+    n, k = 3, 8
     prob, b, x, rep = _split_cg(orc, shape, n, parts, iters=k)
     assert rep["status"] == 1 and rep["iterations"] == k
     xr, it, _, st = orc.cg(prob, b, tol=0.0, max_iter=k)
