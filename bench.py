@@ -39,8 +39,12 @@ WORKLOAD = "heat3d_928cube_cubic_f32sweeps_f64refinement"
 # dram__bytes_write.sum over the unknowns of the launch), measured on the 512^3 profiling case
 # (`--profile-case cg512`) and scaled to the benchmark grid by its unknowns; valid only while the
 # kernels' sources hash to CG_TRAFFIC_SOURCES_SHA256 (None: no capture of the current sources).
-CG_TRAFFIC_BYTES_PER_UNKNOWN = {"classic": None, "ws": None}
-CG_TRAFFIC_SOURCES_SHA256 = None
+# 512^3 capture (--metrics dram__bytes_read.sum,dram__bytes_write.sum,gpu__time_duration.sum):
+# k_op_tma<float,3,CG> 2.879 + 1.568 GB, k_ws<3,WS_CG> 2.192 + 1.559 GB per launch.
+CG_TRAFFIC_BYTES_PER_UNKNOWN = {"classic": 33.13, "ws": 27.95}
+# Algorithmic bytes per unknown of one single-pass FP32 CG iteration.
+CG_BYTES_PER_UNKNOWN = 28.0
+CG_TRAFFIC_SOURCES_SHA256 = "24e2db71dfd98f9b709e0583064e64cbca798475f0eecbf2c13faa24304c08b3"
 CG_KERNEL_SOURCES = ("op_tma.cuh", "op_ws.cuh", "tma_impl.cuh", "tma_util.cuh", "bsk_device.cuh",
                      "tma_f32.cu", "ws_f32.cu")
 
@@ -790,7 +794,9 @@ def run_ours(args, rank, world, dist):
     iter_ms = sum(r["iter_ms"] for r in reps)
     ms_fused_live = iter_ms / max(inner, 1)
     ms_fused = H.time_kernel(api.KERNEL_CG_FUSED, reps=10)
-    bytes_fused = 32.0 * dofs   # read r, q, p, x; write r, q, p, x (FP32 single-pass iteration)
+    # FP32 single-pass iteration: read p_{m-1}, q_{m-1}, p_{m-2}, x; write p_m, q_m, x (r is
+    # rebuilt from the two p and never stored)
+    bytes_fused = CG_BYTES_PER_UNKNOWN * dofs
     ms_op = H.time_kernel(api.KERNEL_OP, reps=10)
     bytes_op = 8.0 * dofs       # read x, write y (FP32)
     ms_res64 = H.time_kernel(api.KERNEL_RES64, reps=3)
@@ -860,12 +866,16 @@ def run_ours(args, rank, world, dist):
             "parallelism": f"{world} independent problems (one per GPU)",
         },
         "roofline": {"kernel": ("k_ws<3,WS_CG>" if cg_kernel == "ws" else "k_op_tma<float,3,CG>")
-                               + ": one CG iteration (p, r, x updates + A p + r.r, p.Ap, Ap.Ap)",
+                               + ": one CG iteration (r rebuilt, p and x updates + A p + r.r, p.Ap, Ap.Ap)",
                      "bound": "hbm", "achieved": ach, "peak": hbm, "unit": "GB/s",
                      "frac": ach / hbm, "traffic": traffic,
-                     "note": f"peak = {peak_kind} HBM copy bandwidth; algorithmic 32 B/unknown "
-                             "(read r, q, p, x; write r, q, p, x); duration = mean per iteration "
-                             "over the timed region (CUDA events on the launching stream)"},
+                     "note": f"peak = {peak_kind} HBM copy bandwidth; algorithmic "
+                             f"{CG_BYTES_PER_UNKNOWN:.0f} B/unknown (read p_m-1, q_m-1, p_m-2, x; write "
+                             "p_m, q_m, x); duration = mean per iteration over the timed region (CUDA "
+                             "events on the launching stream); traffic = DRAM bytes per unknown of the "
+                             "same kernel captured at 512^3 (--profile-case cg512), times the unknowns",
+                     "traffic_source": "profile case cg512 (512^3), scaled by unknowns"
+                                       if traffic is not None else None},
         "clocks": clocks,
         "gpu_launches": launches,
     }

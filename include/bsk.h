@@ -120,7 +120,8 @@ int mass_apply(bsk_handle* h, const void* x, void* y);
 typedef struct bsk_cg_opts {
     double tol;            /* stop when ||r|| <= tol ||b|| [1e-8]                                */
     int max_iter;          /* CG iterations (inner iterations summed, in BSK_F32_IR) [10000]     */
-    int check_every;       /* iterations per device-side chunk between host polls [16]          */
+    int check_every;       /* iterations per device-side chunk between host polls, rounded up
+                              to a multiple of 6 [16 -> 18]                                      */
     int stall_window;      /* stop with BSK_STALLED when ||r|| has not reached a new minimum for
                               this many iterations [0 = off]                                     */
     double inner_tol;      /* BSK_F32_IR: relative tolerance of each inner FP32 solve [1e-5]    */
@@ -504,6 +505,14 @@ int bsk_slab_cg_update(bsk_handle* h, void* x, void* r, const void* p_halo, cons
 /* p = r + beta p on the local planes of p_halo, beta = RR_NEW / RR (0 when first is non-zero),
  * then the convergence test; the halo planes of p are to be exchanged before the next matvec. */
 int bsk_slab_cg_direction(bsk_handle* h, const void* r, void* p_halo, double* s, int first);
+
+/* out = 1 / diag A per node (the Jacobi scaling of bsk_set_preconditioner: for constant
+ * coefficients the diagonal of the separable operator of Eq. tensForm including the mirror images
+ * near the faces, with the boundary term for Robin handles; probed for variable coefficients;
+ * zero on inactive nodes of a mask). out is a DEVICE vector of nx*ny*nz elements of the handle's
+ * element type (BSK_F64 or BSK_F32 handles). Returns BSK_EINVAL when the handle has no Jacobi
+ * preconditioner set. Asynchronous on the handle's stream. */
+int bsk_inverse_diagonal(bsk_handle* h, void* out);
 
 /* Text of the last error raised on the calling thread ("" if none). */
 const char* bsk_last_error(void);

@@ -216,6 +216,12 @@ class Handle:
         k = {"dirichlet": 0, "robin": 1}[kind]
         _native.check(self._lib.bsk_set_boundary(self._ptr, k, float(penalty)))
 
+    def inverse_diagonal(self, out: Optional[torch.Tensor] = None) -> torch.Tensor:
+        """1 / diag A per node (bsk_inverse_diagonal; needs set_preconditioner("jacobi"))."""
+        out = self.empty() if out is None else out
+        _native.check(self._lib.bsk_inverse_diagonal(self._ptr, self._vec(out, "out")))
+        return out
+
     def set_preconditioner(self, kind: str = "none"):
         """'none' or 'jacobi' (Jacobi-preconditioned CG)."""
         k = {"none": 0, "jacobi": 1}[kind]

@@ -124,6 +124,7 @@ struct bsk_handle {
     cudaStream_t cap_stream;   // private stream used only to capture the CG graph (the legacy
                                // default stream cannot be captured; the graph runs on `stream`)
     uint8_t* mask;
+    uint32_t* mbits;              // the mask bit-packed for the TMA kernels (TMA grids), or null
     uint8_t* occ;                 // tile occupancy per plane of the mask (TMA grids), or null
     double M[3][bsk::kMaxTaps];   // per-axis mass kernels
     double K[3][bsk::kMaxTaps];   // per-axis stiffness kernels (not yet multiplied by dt)
@@ -188,12 +189,32 @@ void fill_tma(const bsk_handle* h, bsk::TmaLaunch& L, int mode)
     L.ny = h->ny;
     L.nz = h->nz;
     L.mask = h->mask;
+    L.mbits = h->mbits;
     L.occ = h->occ;
     for (int d = 0; d < 3; d++)
         for (int j = 0; j < bsk::kMaxTaps; j++) {
             L.M[d][j] = h->M[d][j];
             L.Kdt[d][j] = h->dt * h->K[d][j];
         }
+}
+
+// Vectors of single-pass CG pass `it` (op_tma.cuh / op_ws.cuh). The pass keeps no r: it reads
+// p_{m-1}, q_{m-1} and p_{m-2} and writes p_m and q_m, so p and q each rotate through three
+// buffers (period 3; pass 0 reads r_0 from h->r as "p_{-1}", with p_{-2} = h->p0 and q = h->q
+// zero). Graph chunks are multiples of 3 so that every launch starts from the same buffers.
+void cg1_vectors(const bsk_handle* h, int it, bsk::TmaLaunch& L)
+{
+    void* P[3] = {h->r, h->p1, h->p0};
+    void* Q[3] = {h->q, h->q2, h->r2};
+    const int i = it % 3, o = (it + 1) % 3, older = (it + 2) % 3;
+    L.in[0] = P[i];
+    L.in[1] = Q[i];
+    L.in[2] = P[older];
+    L.inint = h->x;
+    L.out0 = Q[o];
+    L.out1 = nullptr;
+    L.out2 = P[o];
+    L.xvec = h->x;
 }
 
 bool aligned16(const void* p) { return ((uintptr_t)p & 15u) == 0; }
@@ -301,7 +322,10 @@ Opts resolve(const bsk_cg_opts* o)
     r.tol = (o && o->tol > 0) ? o->tol : 1e-8;
     r.max_iter = (o && o->max_iter > 0) ? o->max_iter : 10000;
     r.check_every = (o && o->check_every > 0) ? o->check_every : 16;
-    r.check_every += r.check_every & 1;   // even: ping-pong parity repeats across graph launches
+    // a multiple of 6: the two-pass iteration's p alternates between two buffers and the
+    // single-pass iteration's p and q rotate through three, and each graph launch must start
+    // from the same buffers
+    r.check_every = (r.check_every + 5) / 6 * 6;
     r.stall_window = (o && o->stall_window > 0) ? o->stall_window : 0;
     r.inner_tol = (o && o->inner_tol > 0) ? o->inner_tol : 1e-5;
     r.max_outer = (o && o->max_outer > 0) ? o->max_outer : 30;
@@ -347,21 +371,11 @@ int enqueue_chunk(bsk_handle* h, int chunk)
     cudaStream_t s = h->cap_stream;
     T* p[2] = {static_cast<T*>(h->p0), static_cast<T*>(h->p1)};
     if (h->use_tma) {
-        // one kernel per iteration: pass m reads the (r, q, p) of m-1 and writes those of m
-        void* rr[2] = {h->r, h->r2};
-        void* qq[2] = {h->q, h->q2};
+        // one kernel per iteration: pass m reads p_{m-1}, q_{m-1}, p_{m-2} and writes p_m, q_m
         for (int it = 0; it < chunk; it++) {
             bsk::TmaLaunch L;
             fill_tma(h, L, bsk::TMODE_CG);
-            const int i = it & 1, o = (it + 1) & 1;
-            L.in[0] = rr[i];
-            L.in[1] = qq[i];
-            L.in[2] = p[i];
-            L.inint = h->x;
-            L.out0 = qq[o];
-            L.out1 = rr[o];
-            L.out2 = p[o];
-            L.xvec = h->x;
+            cg1_vectors(h, it, L);
             L.sc = h->sc;
             L.partials = h->partials;
             L.fin = bsk::FIN_CG1;
@@ -721,6 +735,10 @@ extern "C" int bsk_create(const bsk_problem* prob, int precision, void* stream, 
             BSK_ALLOC(h->occ, (size_t)bsk::tma_tiles(prob->nx, prob->ny) * prob->nz);
             e = bsk::launch_tile_occupancy(h->mask, prob->nx, prob->ny, prob->nz, h->occ, h->stream);
             if (e != cudaSuccess) return cleanup(cuda_fail(e, "occupancy launch"));
+            // and the mask itself as bits, which the TMA kernels read (1/8 byte per unknown)
+            BSK_ALLOC(h->mbits, (size_t)bsk::mask_words(prob->nx) * prob->ny * prob->nz * sizeof(uint32_t));
+            e = bsk::launch_pack_mask(h->mask, prob->nx, prob->ny, prob->nz, h->mbits, h->stream);
+            if (e != cudaSuccess) return cleanup(cuda_fail(e, "mask packing launch"));
         }
     }
     const size_t ces = cg_es(h);
@@ -794,7 +812,7 @@ extern "C" void bsk_destroy(bsk_handle* h)
     if (!h) return;
     cudaStreamSynchronize(h->stream);
     if (h->graph) cudaGraphExecDestroy(h->graph);
-    void* ptrs[] = {h->mask, h->occ, h->x, h->r, h->p0, h->p1, h->q, h->bvec, h->r2, h->q2, h->r64, h->b64,
+    void* ptrs[] = {h->mask, h->mbits, h->occ, h->x, h->r, h->p0, h->p1, h->q, h->bvec, h->r2, h->q2, h->r64, h->b64,
                     h->sc, h->sc64, h->sc_aux, h->partials, h->work, h->cd[0], h->cd[1], h->cm[0], h->cm[1],
                     h->rb[0], h->rb[1], h->jac[0], h->jac[1], h->jvec};
     for (void* p : ptrs)
@@ -1378,6 +1396,24 @@ extern "C" int fcg_solve(bsk_handle* h, bsk_net* net, const void* bv, void* xv, 
     return st;
 }
 
+extern "C" int bsk_inverse_diagonal(bsk_handle* h, void* out)
+{
+    if (int rc = check_handle(h)) return rc;
+    if (!out) return fail(BSK_EINVAL, "null vector");
+    if (h->prec != BSK_F64 && h->prec != BSK_F32)
+        return fail(BSK_EINVAL, "bsk_inverse_diagonal takes BSK_F64 or BSK_F32 handles");
+    if (!h->pc || !h->jvec) return fail(BSK_EINVAL, "the handle has no Jacobi preconditioner (bsk_set_preconditioner)");
+    if (overlaps(out, h->jvec, h->len * cg_es(h))) return fail(BSK_EINVAL, "out overlaps the handle's diagonal");
+    // the handle's vector is not masked (the solvers' residuals are zero off the mask anyway)
+    if (cg_es(h) == sizeof(double))
+        BSK_CUDA(bsk::launch_copy_masked<double>(static_cast<const double*>(h->jvec), static_cast<double*>(out),
+                                                 h->len, h->mask, h->stream));
+    else
+        BSK_CUDA(bsk::launch_copy_masked<float>(static_cast<const float*>(h->jvec), static_cast<float*>(out),
+                                                h->len, h->mask, h->stream));
+    return BSK_OK;
+}
+
 extern "C" int bsk_time_kernel(bsk_handle* h, int kernel, int reps, double* ms)
 {
     if (int rc = check_handle(h)) return rc;
@@ -1413,18 +1449,8 @@ extern "C" int bsk_time_kernel(bsk_handle* h, int kernel, int reps, double* ms)
             return op_launch_es(ces, L, h->stream);
         case BSK_KERNEL_CG_FUSED:
             if (h->use_tma) {
-                void* rr[2] = {h->r, h->r2};
-                void* qq[2] = {h->q, h->q2};
-                void* pp[2] = {h->p0, h->p1};
                 fill_tma(h, T, bsk::TMODE_CG);
-                T.in[0] = rr[i & 1];
-                T.in[1] = qq[i & 1];
-                T.in[2] = pp[i & 1];
-                T.inint = h->x;
-                T.out0 = qq[(i + 1) & 1];
-                T.out1 = rr[(i + 1) & 1];
-                T.out2 = pp[(i + 1) & 1];
-                T.xvec = h->x;
+                cg1_vectors(h, i, T);
                 T.sc = h->sc_aux;
                 T.partials = h->partials;
                 T.fin = bsk::FIN_NORM;   // reduces without touching the CG state of sc

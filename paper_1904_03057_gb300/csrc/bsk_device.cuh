@@ -64,6 +64,7 @@ struct Scalars {
     int pass;           // single-pass CG: passes completed (pass m produces x_m, r_m)
     double rz;          // preconditioned CG: r.z of the current residual (z = r / diag A)
     int pc;             // non-zero: Jacobi-preconditioned CG (alpha and beta from rz)
+    double beta_prev;   // single-pass CG: the coefficient before `beta` (rebuilds r from two p)
 };
 
 // Per-axis kernels in compute precision: M[d][j + n], K[d][j + n] with K already scaled by dt.
@@ -145,6 +146,7 @@ __device__ __forceinline__ void finalize(Scalars* sc, int fin, double s0, double
         sc->alpha = 0.0;
         sc->alpha_prev = 0.0;
         sc->beta = 0.0;
+        sc->beta_prev = 0.0;
         sc->p_cur = 0;
         sc->zero_b = 0;
         sc->done = 0;
@@ -229,6 +231,7 @@ __device__ __forceinline__ void finalize_cg1(Scalars* sc, double rr, double pq, 
     double rr_next = alpha * alpha * qq - rr;
     if (rr_next < 0.0) rr_next = 0.0;
     sc->alpha = alpha;
+    sc->beta_prev = sc->beta;
     sc->beta = rr_next / rr;
 }
 

@@ -135,13 +135,14 @@ struct TmaLaunch {
     int nx, ny, nz;
     double M[3][kMaxTaps];
     double Kdt[3][kMaxTaps];
-    const void* in[3];           // OP/RES: {x}; CG: {r, q, p} of the previous iteration
+    const void* in[3];           // OP/RES: {x}; CG: {p_{m-1}, q_{m-1}, p_{m-2}} (no r is kept)
     const void* inint;           // RES: b; CG: x
-    void* out0;                  // OP y; RES r; CG q
-    void* out1;                  // CG r
-    void* out2;                  // CG p
+    void* out0;                  // OP y; RES r; CG q_m
+    void* out1;                  // unused
+    void* out2;                  // CG p_m
     void* xvec;                  // CG x (in place)
     const uint8_t* mask;         // node mask or null (outputs zeroed where 0; inputs must be)
+    const uint32_t* mbits;       // the same mask bit-packed (launch_pack_mask); required with mask
     const uint8_t* occ;          // tile occupancy per plane (tile_occupancy), null without a mask
     Scalars* sc;
     double* partials;            // 3 doubles per block of the resident grid
@@ -160,6 +161,10 @@ cudaError_t launch_band_solve(T* d, int nx, int ny, int nz, int axis, int p, con
 
 // occ[z * tiles + tile] = 1 iff the 64 x 24 tile (x fastest) has an active node in plane z.
 cudaError_t launch_tile_occupancy(const uint8_t* mask, int nx, int ny, int nz, uint8_t* occ, cudaStream_t s);
+// Bit-packed copy of a node mask for the TMA kernels: mask_words(nx) 32-bit words per
+// (z, y) row, bit i of word w = node x = 32 w + i (tma_f32.cu).
+int mask_words(int nx);
+cudaError_t launch_pack_mask(const uint8_t* mask, int nx, int ny, int nz, uint32_t* bits, cudaStream_t s);
 int tma_tiles(int nx, int ny);
 struct dfl;   // double-float element (dfloat.cuh): the FP64-accurate residual on the FP32 pipes
 template <typename T>

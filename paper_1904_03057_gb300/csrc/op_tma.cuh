@@ -17,7 +17,8 @@
 //      leaves the kernel straight from registers.
 // A node mask (principal submatrix of the box operator) needs no staging: every input the
 // kernel reads is zero on inactive nodes already (the solvers keep their vectors masked), so
-// only the operator outputs are multiplied by the mask, read straight from global memory.
+// only the operator outputs are multiplied by the mask, read as two bits per output pair from a
+// bit-packed copy (1/8 byte per unknown).
 // Blocks are persistent and walk a static list of (tile, z-chunk) items. In CG mode the staged
 // value is the new search direction p_m = (r - alpha q) + beta p of the previous iteration's
 // vectors, and the pass also writes r_m, p_m, x_m = x + alpha p and reduces r.r, p.Ap, Ap.Ap
@@ -39,14 +40,18 @@ constexpr int kTNT = 256;   // threads per block
 
 template <typename T>
 struct TmaArgs {
-    CUtensorMap tin[3];   // halo boxes: OP/RES {x}; CG {r, q, p} of the previous iteration
+    CUtensorMap tin[3];   // halo boxes: OP/RES {x}; CG {p_{m-1}, q_{m-1}, p_{m-2}} (batched CG:
+                          // {r, q, p} of the previous iteration)
     CUtensorMap tint;     // interior box: RES {b}; CG {x}
     T* out0;              // OP y; RES r; CG q_m = A p_m
-    T* out1;              // CG r_m
+    T* out1;              // batched CG r_m (single-problem CG keeps no r)
     T* out2;              // CG p_m
     T* xvec;              // CG x, updated in place
-    const uint8_t* mask;  // node mask [nz][ny][nx] or null: outputs (q, r) are zeroed where it is 0;
-                          // the inputs must already be zero there (principal submatrix)
+    const uint32_t* mbits;   // bit-packed node mask or null: row (z, y) holds mwords 32-bit words,
+                             // bit i of word w = node x = 32 w + i; outputs (q, r) are zeroed
+                             // where it is 0 and the inputs must already be zero there
+                             // (principal submatrix)
+    int mwords;
     const uint8_t* occ;   // with a mask: occ[z * tiles + tile] != 0 iff tile has an active node in
                           // plane z; items with none are skipped (their outputs stay zero)
     int nx, ny, nz;
@@ -363,10 +368,15 @@ __global__ void __launch_bounds__(kTNT, (sizeof(T) == 4 && N <= 4 && !BATCH) ? 2
     Scalars* sc = a.sc;
     constexpr bool DF = std::is_same<T, dfl>::value;   // double-float passes (FP64 vectors)
     static_assert(!DF || (MODE != TMODE_CG && !BATCH), "double-float: operator and residual passes only");
-    T alpha = T(0), beta = T(0);
+    // Single-problem CG passes keep no r: pass m reads p_{m-1}, p_{m-2} and q_{m-1} and rebuilds
+    // r_{m-1} = p_{m-1} - beta_{m-2} p_{m-2} (the p recurrence solved for r), which saves the r
+    // write and its re-read (28 instead of 32 bytes per unknown). Batched passes keep r.
+    constexpr bool RFOLD = (MODE == TMODE_CG && !BATCH);
+    T alpha = T(0), beta = T(0), beta_prev = T(0);
     if constexpr (!BATCH && MODE == TMODE_CG) {
         alpha = (T)a.sc->alpha;
         beta = (T)a.sc->beta;
+        beta_prev = (T)a.sc->beta_prev;
     }
     // packed taps: W1 = Mz + dt Kz and Mz for the z push; My and dt Ky for the y-sweep;
     // Mx and dt Kx for the x-sweep
@@ -547,16 +557,24 @@ __global__ void __launch_bounds__(kTNT, (sizeof(T) == 4 && N <= 4 && !BATCH) ? 2
                     load_window<T, WIN>(v, in0 + row * BX + 8 * g);
                     const bool interior = zint && row >= N && row < N + TY;
                     if constexpr (MODE == TMODE_CG) {
-                        // p_m = (r - alpha q) + beta p of the previous iteration's vectors
+                        // p_m = (r - alpha q) + beta p of the previous iteration's vectors; with
+                        // RFOLD the boxes are (p_{m-1}, q_{m-1}, p_{m-2}) and r is rebuilt first
                         T qv[WIN], pv[WIN];
                         load_window<T, WIN>(qv, in1 + row * BX + 8 * g);
                         load_window<T, WIN>(pv, in2 + row * BX + 8 * g);
                         T rc[8], pold[8];
 #pragma unroll
                         for (int i = 0; i < WIN; i++) {
-                            const T rn = fma(-alpha, qv[i], v[i]);
-                            if (i >= HL && i < HL + 8) { rc[i - HL] = rn; pold[i - HL] = pv[i]; }
-                            v[i] = fma(beta, pv[i], rn);
+                            if constexpr (RFOLD) {
+                                const T pc = v[i];                              // p_{m-1}
+                                const T rn = fma(-alpha, qv[i], fma(-beta_prev, pv[i], pc));
+                                if (i >= HL && i < HL + 8) { rc[i - HL] = rn; pold[i - HL] = pc; }
+                                v[i] = fma(beta, pc, rn);
+                            } else {
+                                const T rn = fma(-alpha, qv[i], v[i]);
+                                if (i >= HL && i < HL + 8) { rc[i - HL] = rn; pold[i - HL] = pv[i]; }
+                                v[i] = fma(beta, pv[i], rn);
+                            }
                         }
                         if (interior) {
                             const int gy = y0 + row - N;
@@ -590,14 +608,16 @@ __global__ void __launch_bounds__(kTNT, (sizeof(T) == 4 && N <= 4 && !BATCH) ? 2
                                     const size_t o = ((size_t)z * ny + gy) * pitch + gx;
                                     d0.add(part);
                                     if constexpr (sizeof(T) == 4) {
-                                        __stcs(reinterpret_cast<float4*>(out1 + o), make_float4(rn4[0], rn4[1], rn4[2], rn4[3]));
+                                        if constexpr (!RFOLD)
+                                            __stcs(reinterpret_cast<float4*>(out1 + o), make_float4(rn4[0], rn4[1], rn4[2], rn4[3]));
                                         __stcs(reinterpret_cast<float4*>(out2 + o), make_float4(pn4[0], pn4[1], pn4[2], pn4[3]));
                                         __stcs(reinterpret_cast<float4*>(xvec + o), make_float4(xn4[0], xn4[1], xn4[2], xn4[3]));
                                     } else {
 #pragma unroll
                                         for (int e = 0; e < 4; e += 2) {
                                             if (gx + e < nx) {   // FP64 rows are only 2-element aligned
-                                                *reinterpret_cast<T2*>(out1 + o + e) = T2{rn4[e], rn4[e + 1]};
+                                                if constexpr (!RFOLD)
+                                                    *reinterpret_cast<T2*>(out1 + o + e) = T2{rn4[e], rn4[e + 1]};
                                                 *reinterpret_cast<T2*>(out2 + o + e) = T2{pn4[e], pn4[e + 1]};
                                                 *reinterpret_cast<T2*>(xvec + o + e) = T2{xn4[e], xn4[e + 1]};
                                             }
@@ -717,8 +737,11 @@ __global__ void __launch_bounds__(kTNT, (sizeof(T) == 4 && N <= 4 && !BATCH) ? 2
                         if (gy < ny && gx < nx) {
                             const size_t o = ((size_t)zo * ny + gy) * pitch + gx;
                             unsigned mm = 0x0101u;
-                            if (!BATCH && a.mask)   // masked grids have even nx: whole pairs
-                                mm = *reinterpret_cast<const uint16_t*>(a.mask + ((size_t)zo * ny + gy) * nx + gx);
+                            if (!BATCH && a.mbits) {   // gx is even: both bits lie in one word
+                                const uint32_t w = a.mbits[((size_t)zo * ny + gy) * a.mwords + (gx >> 5)];
+                                const uint32_t pr = (w >> (gx & 31)) & 3u;
+                                mm = (pr & 1u) | ((pr & 2u) << 7);   // bytes (x, x + 1) as before
+                            }
                             if constexpr (DF && MODE == TMODE_OP) {
                                 // y = A x rounded once to FP64
                                 const double yx = (mm & 0xffu) ? df_to_double(q[t].x) : 0.0;

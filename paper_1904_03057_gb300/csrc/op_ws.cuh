@@ -17,9 +17,11 @@
 //                     (tile plus n rows and 4 columns of halo), complete the face ghosts by odd
 //                     reflection in registers (a ghost row reads its mirror row, ghost columns
 //                     are rebuilt in the loaded window) and run the x-sweep, writing MX and KX
-//                     into one of two shared-memory buffers. In CG mode the window first becomes
-//                     the new search direction p = (r - alpha q) + beta p, and the lane writes
-//                     r, p and x = x + alpha p_old of its interior row to HBM and reduces r.r.
+//                     into one of two shared-memory buffers. In CG mode the boxes hold p_{m-1},
+//                     q_{m-1} and p_{m-2}; the window first becomes r_{m-1} = p_{m-1} -
+//                     beta_{m-2} p_{m-2} (no r is stored), then r_m = r_{m-1} - alpha q_{m-1}
+//                     and the new search direction p_m = r_m + beta p_{m-1}, and the lane writes
+//                     p and x = x + alpha p_{m-1} of its interior row to HBM and reduces r.r.
 //   halo warps (4-7) -- the same x-sweep for the 2n halo rows of the box, 8 columns per lane;
 //                     lane 0 of warp 4 also issues the TMA loads into a stage ring, refilling a
 //                     stage once every x thread has released it.
@@ -82,10 +84,10 @@ struct WsGeo {
 };
 
 struct WsArgs {
-    CUtensorMap tin[3];   // halo boxes (BX, HY, 1): OP {x}; CG {r, q, p} of the previous iteration
+    CUtensorMap tin[3];   // halo boxes (BX, HY, 1): OP {x}; CG {p_{m-1}, q_{m-1}, p_{m-2}}
     CUtensorMap tint;     // CG: interior box (68, 32, 1) of x (64 columns used)
     float* out0;          // OP y; CG q = A p
-    float* out1;          // CG r
+    float* out1;          // unused (CG keeps no r)
     float* out2;          // CG p
     float* xvec;          // CG x, updated in place
     Scalars* sc;          // CG scalars; OP: receives status -4 on a wait time-out (may be null)
@@ -153,12 +155,11 @@ __device__ __forceinline__ void ws_fix_hi(float (&v)[W], int p)
 }
 
 // Interior bookkeeping of one x task in CG mode (z inside the item, row and columns inside the
-// grid): write r, p and x of the 16 outputs and add r.r. p is stored with the default cache
+// grid): write p and x of the 16 outputs and add r.r. p is stored with the default cache
 // policy: the y/z threads of the block read it back from L2 n planes later for p.q. On the
 // large grids measured this beat keeping a ring of p planes in shared memory, whose space now
 // holds one more TMA stage.
 struct WsCgOut {
-    float* r;
     float* p;
     float* x;
     const float4* xin;      // x of the 16 outputs (interior box in shared memory)
@@ -166,13 +167,14 @@ struct WsCgOut {
 };
 
 // x-sweep of G outputs of one box row from a 16-byte aligned window of G + 8 floats of each input
-// box. OP: the window is x. CG: the window is p_new = (r - alpha q) + beta p of the previous
-// iteration's r, q, p, and (G = 16 with `co` set) the lane also stores r, p, x of its interior
-// outputs. MX, KX of the G outputs are scaled by sgn (row sign x plane sign) when it is not 1.
+// box. OP: the window is x. CG: the window is p_new = (r - alpha q) + beta p_old with
+// r = p_old - beta_prev p_older rebuilt from the boxes (p_old, q, p_older), and (G = 16 with `co`
+// set) the lane also stores p, x of its interior outputs. MX, KX of the G outputs are scaled by sgn (row sign x plane sign) when it is not 1.
 template <int N, int G, int MODE>
 __device__ __forceinline__ void ws_x(const float* src0, const float* src1, const float* src2, float* mdst,
                                      float* kdst, const float2 (&mxp)[N + 1], const float2 (&kxp)[N + 1],
-                                     float sgn, bool lo, int hip, float alpha, float beta, const WsCgOut* co,
+                                     float sgn, bool lo, int hip, float alpha, float beta, float beta_prev,
+                                     const WsCgOut* co,
                                      float& rr_part, uint64_t* release)
 {
     constexpr int W = G + 8;
@@ -183,9 +185,11 @@ __device__ __forceinline__ void ws_x(const float* src0, const float* src1, const
         if constexpr (MODE == WS_CG) {
             const float4 fq = reinterpret_cast<const float4*>(src1)[qd];
             const float4 fp = reinterpret_cast<const float4*>(src2)[qd];
-            const float rn[4] = {fmaf(-alpha, fq.x, f.x), fmaf(-alpha, fq.y, f.y), fmaf(-alpha, fq.z, f.z),
-                                 fmaf(-alpha, fq.w, f.w)};
-            const float po[4] = {fp.x, fp.y, fp.z, fp.w};
+            const float po[4] = {f.x, f.y, f.z, f.w};   // p_{m-1}
+            const float rn[4] = {fmaf(-alpha, fq.x, fmaf(-beta_prev, fp.x, f.x)),
+                                 fmaf(-alpha, fq.y, fmaf(-beta_prev, fp.y, f.y)),
+                                 fmaf(-alpha, fq.z, fmaf(-beta_prev, fp.z, f.z)),
+                                 fmaf(-alpha, fq.w, fmaf(-beta_prev, fp.w, f.w))};
 #pragma unroll
             for (int e = 0; e < 4; e++) v[4 * qd + e] = fmaf(beta, po[e], rn[e]);
             // interior outputs occupy window positions 4 .. 4 + G - 1 (chunks 1 .. G/4)
@@ -193,7 +197,6 @@ __device__ __forceinline__ void ws_x(const float* src0, const float* src1, const
                 const int o = 4 * (qd - 1);
                 const float4 xi = co->xin[qd - 1];
                 const float4 pn = make_float4(v[4 * qd], v[4 * qd + 1], v[4 * qd + 2], v[4 * qd + 3]);
-                __stcs(reinterpret_cast<float4*>(co->r + o), make_float4(rn[0], rn[1], rn[2], rn[3]));
                 *reinterpret_cast<float4*>(co->p + o) = pn;
                 __stcs(reinterpret_cast<float4*>(co->x + o),
                        make_float4(fmaf(alpha, po[0], xi.x), fmaf(alpha, po[1], xi.y), fmaf(alpha, po[2], xi.z),
@@ -354,10 +357,11 @@ __global__ void __launch_bounds__(kWsNT, 1) k_ws(const __grid_constant__ WsArgs 
     };
     auto mx_buf = [&](int d) { return reinterpret_cast<float*>(smem + G::off_mx + 2 * d * G::mx_bytes); };
     auto kx_buf = [&](int d) { return reinterpret_cast<float*>(smem + G::off_mx + (2 * d + 1) * G::mx_bytes); };
-    float alpha = 0.f, beta = 0.f;
+    float alpha = 0.f, beta = 0.f, beta_prev = 0.f;
     if (CG) {
         alpha = (float)a.sc->alpha;
         beta = (float)a.sc->beta;
+        beta_prev = (float)a.sc->beta_prev;
     }
     WsKSum d0, d1, d2;   // CG: r.r (x warps), p.q and q.q (y/z warps)
     uint32_t c = 0;      // planes consumed by this thread's role
@@ -469,7 +473,6 @@ __global__ void __launch_bounds__(kWsNT, 1) k_ws(const __grid_constant__ WsArgs 
 
                         if (CG && interior_row && inz && ncols > 0) {
                             const size_t o = (size_t)z * planesz + rowoff;
-                            co.r = a.out1 + o;
                             co.p = a.out2 + o;
                             co.x = a.xvec + o;
                             co.xin = reinterpret_cast<const float4*>(
@@ -477,10 +480,10 @@ __global__ void __launch_bounds__(kWsNT, 1) k_ws(const __grid_constant__ WsArgs 
                             co.ncols = ncols;
                         }
                         ws_x<N, 16, MODE>(b0, b1, b2, md, kd, mxp, kxp, zsg * rsg, lo, hip, alpha, beta,
-                                          (CG && interior_row && inz && ncols > 0) ? &co : nullptr, rr_part,
+                                          beta_prev, (CG && interior_row && inz && ncols > 0) ? &co : nullptr, rr_part,
                                           &empty[st]);
                     } else {
-                        ws_x<N, 8, MODE>(b0, b1, b2, md, kd, mxp, kxp, zsg * rsg, lo, hip, alpha, beta, nullptr,
+                        ws_x<N, 8, MODE>(b0, b1, b2, md, kd, mxp, kxp, zsg * rsg, lo, hip, alpha, beta, beta_prev, nullptr,
                                          rr_part, &empty[st]);
                     }
                 } else {

@@ -30,7 +30,34 @@ __global__ void k_tile_occupancy(const uint8_t* __restrict__ mask, int nx, int n
     if (lane == 0) occ[(size_t)z * ntiles + tile] = any ? 1 : 0;
 }
 
+// One thread per 32-bit word of the bit-packed mask: bit i of word w of row (z, y) is node
+// x = 32 w + i of that row (rows padded to whole words with zero bits).
+__global__ void k_pack_mask(const uint8_t* __restrict__ mask, int nx, long long rows, int words,
+                            uint32_t* __restrict__ bits)
+{
+    const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= rows * words) return;
+    const long long row = t / words;
+    const int w = (int)(t - row * words);
+    const uint8_t* src = mask + row * nx + 32 * w;
+    const int n = min(32, nx - 32 * w);
+    uint32_t v = 0u;
+    for (int i = 0; i < n; i++) v |= (src[i] != 0 ? 1u : 0u) << i;
+    bits[t] = v;
+}
+
 }  // namespace
+
+int mask_words(int nx) { return (nx + 31) / 32; }
+
+cudaError_t launch_pack_mask(const uint8_t* mask, int nx, int ny, int nz, uint32_t* bits, cudaStream_t s)
+{
+    const long long rows = (long long)ny * nz;
+    const int words = mask_words(nx);
+    const long long n = rows * words;
+    k_pack_mask<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(mask, nx, rows, words, bits);
+    return cudaGetLastError();
+}
 
 int tma_tiles(int nx, int ny) { return ((nx + kTX - 1) / kTX) * ((ny + kTY - 1) / kTY); }
 

@@ -156,7 +156,9 @@ cudaError_t launch_one(const TmaLaunch& L, cudaStream_t s)
     a.out1 = static_cast<BSK_T*>(L.out1);
     a.out2 = static_cast<BSK_T*>(L.out2);
     a.xvec = static_cast<BSK_T*>(L.xvec);
-    a.mask = L.mask;
+    if (L.mask && !L.mbits) return cudaErrorInvalidValue;   // the kernels read the packed mask
+    a.mbits = L.mask ? L.mbits : nullptr;
+    a.mwords = mask_words(L.nx);
     a.occ = L.mask ? L.occ : nullptr;
     a.nx = L.nx;
     a.ny = L.ny;

@@ -210,11 +210,17 @@ def init_params(seed: int = 0, out_scale: float = 0.1, h: float = 1.0 / 513, dt:
     for _ in range(3):
         parts += [torch.randn(KT * C * C, generator=g) * math.sqrt(2.0 / (KT * C)), torch.zeros(C)]
     parts += [torch.randn(KT * C, generator=g) * math.sqrt(1.0 / (KT * C)) * out_scale, torch.zeros(1)]
-    M1, K1 = api.bspline_kernels(degree, h)
-    c = degree
-    aii = (M1[c] ** 3 + dt * 3 * K1[c] * M1[c] ** 2) / h ** 3   # stencil diagonal / (hx hy hz)
+    # 1 / A_ii at a node n + 1 away from every face (the library's Jacobi diagonal), in the
+    # network's output unit (the operator scaled by 1 / (hx hy hz))
+    m = 2 * degree + 3
+    H = api.Handle(m, m, m, degree, h, dt, precision="f64")
+    try:
+        H.set_preconditioner("jacobi")
+        inv_aii = float(H.inverse_diagonal()[m // 2, m // 2, m // 2]) * h ** 3
+    finally:
+        H.close()
     wf = torch.zeros(KT)
-    wf[13] = 1.0 / aii
+    wf[13] = inv_aii
     parts.append(wf)
     return torch.cat(parts).float()
 
