@@ -381,6 +381,17 @@ int bsk_net_read_loss(bsk_net* net, float* loss, float* grads);
 int fcg_solve(bsk_handle* h, bsk_net* net, const void* b, void* x, const bsk_cg_opts* opts,
               bsk_cg_report* report);
 
+/* The states flexible CG meets, for training the network on them (on-policy pairs). Runs one
+ * inner FCG solve of fcg_solve from x = 0 on A d = b / ||b|| (b a DEVICE double vector, handle
+ * precision BSK_F32_IR), for `steps` iterations unless it breaks down or stalls, and copies the
+ * inner residual r_k = b / ||b|| - A d_k and the iterate d_k (FP32) before each iteration k into
+ * r_rec + k n and x_rec + k n (DEVICE float arrays of steps * n elements, n = nx*ny*nz). The
+ * solution of A x = b after k iterations is ||b|| d_k, its residual ||b|| r_k. Writes ||b|| to
+ * *bnorm (host) and the number of states recorded to *recorded (host; states past a breakdown
+ * or stall repeat the last one and are not counted). Uses the handle's FP64 scratch vector. */
+int fcg_record(bsk_handle* h, bsk_net* net, const void* b, int steps, float* r_rec, float* x_rec,
+               double* bnorm, int* recorded);
+
 /* Kernel timing for roofline measurements. Launches one of the library's kernels `reps` times
  * back to back on the handle's stream, on the handle's own work vectors (which it first zeroes,
  * so any state of a previous solve is lost), and writes the mean device time of one launch in

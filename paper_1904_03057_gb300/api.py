@@ -145,6 +145,19 @@ class Handle:
                                           ctypes.byref(rep)))
         return _report(rep)
 
+    def fcg_record(self, b: torch.Tensor, steps: int, net: Optional["Net"] = None):
+        """The states of one inner flexible-CG solve from x = 0 (fcg_record): returns (r, d,
+        bnorm) with r[k], d[k] the inner residual and iterate of A d = b / ||b|| before
+        iteration k (float32, k < the number recorded) and bnorm = ||b||."""
+        n = self.shape
+        r = torch.empty((steps,) + n, dtype=torch.float32, device="cuda")
+        d = torch.empty_like(r)
+        bn, k = ctypes.c_double(0.0), ctypes.c_int(0)
+        _native.check(self._lib.fcg_record(self._ptr, net._ptr if net is not None else None, self._vec(b, "b"),
+                                           int(steps), r.data_ptr(), d.data_ptr(), ctypes.byref(bn),
+                                           ctypes.byref(k)))
+        return r[:k.value], d[:k.value], bn.value
+
     def time_kernel(self, kernel: int, reps: int = 10) -> float:
         """Mean device time (ms) of one launch of a library kernel (bsk_time_kernel)."""
         out = ctypes.c_double(0.0)

@@ -1290,15 +1290,11 @@ extern "C" int heat_step(bsk_handle* h, void* u, const void* q, int nsteps, cons
 extern "C" int bsk_net_forward(bsk_net* net, const float* r, const uint8_t* mask, float* z);
 
 // Iterative refinement around the preconditioned inner FCG solve (fcg.cu).
-extern "C" int fcg_solve(bsk_handle* h, bsk_net* net, const void* bv, void* xv, const bsk_cg_opts* opts,
-                         bsk_cg_report* rep)
+// Flexible CG inside FP64 refinement (fcg_solve); with rec_r set, the first inner solve also
+// records its residual and iterate before each of its first rec_steps iterations (fcg_record).
+static int fcg_impl(bsk_handle* h, bsk_net* net, const void* bv, void* xv, const Opts& o, bsk_cg_report* rep,
+                    std::chrono::steady_clock::time_point t0, float* rec_r, float* rec_x, int rec_steps)
 {
-    auto t0 = std::chrono::steady_clock::now();
-    if (int rc = check_handle(h)) return rc;
-    if (h->prec != BSK_F32_IR) return fail(BSK_EINVAL, "fcg_solve needs a BSK_F32_IR handle");
-    if (!bv || !xv) return fail(BSK_EINVAL, "null vector");
-    if (overlaps(bv, xv, h->len * sizeof(double))) return fail(BSK_EINVAL, "b and x overlap");
-    const Opts o = resolve(opts);
     if (rep) memset(rep, 0, sizeof *rep);
     h->launches = 0;
     const double* b = (const double*)bv;
@@ -1313,7 +1309,7 @@ extern "C" int fcg_solve(bsk_handle* h, bsk_net* net, const void* bv, void* xv, 
         }
         BSK_CUDA(cudaMemsetAsync(h->fcg_state, 0, bsk::fcg_state_bytes(), h->stream));
     }
-    bsk::FcgVectors V;
+    bsk::FcgVectors V = {};
     V.b = static_cast<const float*>(h->r);   // the scaled residual is written here, then copied to r
     V.x = static_cast<float*>(h->x);
     V.r = static_cast<float*>(h->r);
@@ -1324,6 +1320,9 @@ extern "C" int fcg_solve(bsk_handle* h, bsk_net* net, const void* bv, void* xv, 
     V.zn = h->fcg_ws + 2 * h->len;
     V.partials = h->fcg_partials;
     V.state = h->fcg_state;
+    V.rec_r = rec_r;
+    V.rec_x = rec_x;
+    V.rec_steps = rec_steps;
     auto op = [&](const float* p, float* q) -> int {
         cudaError_t e;
         if (tma_ok(h, sizeof(float), {p, q})) {
@@ -1375,6 +1374,7 @@ extern "C" int fcg_solve(bsk_handle* h, bsk_net* net, const void* bv, void* xv, 
         const double out_scale = 1.0 / (h->h[0] * h->h[1] * h->h[2]);
         int ist = bsk::fcg_inner(V, h->len, h->mask, inner, o.max_iter - total_iters, o.stall_window,
                                  out_scale, 0.0, op, net, netf, h->stream, &it, &fbi, &rej, o.time_limit, t0);
+        V.rec_r = V.rec_x = nullptr;   // only the first inner solve is recorded
         h->launches += 6LL * it;
         total_iters += it;
         total_rejected += rej;
@@ -1394,6 +1394,42 @@ extern "C" int fcg_solve(bsk_handle* h, bsk_net* net, const void* bv, void* xv, 
         rep->net_rejected = total_rejected;
     }
     return st;
+}
+
+extern "C" int fcg_solve(bsk_handle* h, bsk_net* net, const void* bv, void* xv, const bsk_cg_opts* opts,
+                         bsk_cg_report* rep)
+{
+    auto t0 = std::chrono::steady_clock::now();
+    if (int rc = check_handle(h)) return rc;
+    if (h->prec != BSK_F32_IR) return fail(BSK_EINVAL, "fcg_solve needs a BSK_F32_IR handle");
+    if (!bv || !xv) return fail(BSK_EINVAL, "null vector");
+    if (overlaps(bv, xv, h->len * sizeof(double))) return fail(BSK_EINVAL, "b and x overlap");
+    return fcg_impl(h, net, bv, xv, resolve(opts), rep, t0, nullptr, nullptr, 0);
+}
+
+extern "C" int fcg_record(bsk_handle* h, bsk_net* net, const void* bv, int steps, float* r_rec, float* x_rec,
+                          double* bnorm, int* recorded)
+{
+    auto t0 = std::chrono::steady_clock::now();
+    if (int rc = check_handle(h)) return rc;
+    if (h->prec != BSK_F32_IR) return fail(BSK_EINVAL, "fcg_record needs a BSK_F32_IR handle");
+    if (!bv || !r_rec || !x_rec || !bnorm || !recorded || steps < 1) return fail(BSK_EINVAL, "bad argument");
+    *recorded = 0;
+    // one inner solve of A d = b / ||b|| from d = 0, exactly `steps` iterations unless it breaks
+    // down or stalls; x (FP64) lives in the handle's b64 scratch
+    Opts o = resolve(nullptr);
+    o.tol = 0.0;
+    o.inner_tol = 0.0;
+    o.max_iter = steps;
+    o.max_outer = 1;
+    BSK_CUDA(cudaMemsetAsync(h->b64, 0, h->len * sizeof(double), h->stream));
+    bsk_cg_report rep;
+    const int st = fcg_impl(h, net, bv, h->b64, o, &rep, t0, r_rec, x_rec, steps);
+    if (st < 0) return st;
+    BSK_CUDA(cudaStreamSynchronize(h->stream));
+    *bnorm = std::sqrt(h->h_sc->bb_true);
+    *recorded = std::min(rep.iterations + 1, steps);
+    return BSK_OK;
 }
 
 extern "C" int bsk_inverse_diagonal(bsk_handle* h, void* out)

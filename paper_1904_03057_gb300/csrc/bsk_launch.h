@@ -215,6 +215,11 @@ struct FcgVectors {
     float *x, *r, *p, *q, *z, *rn, *zn;
     double* partials;    // 3 doubles per block of the vector kernels (1216 blocks at most)
     void* state;         // fcg_state_bytes()
+    // optional record of the iteration (fcg_record): before iteration k < rec_steps, r and x
+    // are copied to rec_r + k n and rec_x + k n; null = no record
+    float* rec_r;
+    float* rec_x;
+    int rec_steps;
 };
 size_t fcg_state_bytes();
 // The network maps r linearly (BSK_ACT_LINEAR): N(r / ||r||) ||r|| = N(r), no normalisation.

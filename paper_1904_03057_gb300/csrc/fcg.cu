@@ -317,6 +317,10 @@ int fcg_inner(const FcgVectors& V, size_t n, const uint8_t* mask, double tol, in
     for (;;) {
         // a few iterations between polls
         for (int j = 0; j < 4; j++, k++) {
+            if (V.rec_r && k < V.rec_steps) {   // the state this iteration starts from
+                FCUDA(cudaMemcpyAsync(V.rec_r + (size_t)k * n, V.r, n * sizeof(float), cudaMemcpyDeviceToDevice, s));
+                FCUDA(cudaMemcpyAsync(V.rec_x + (size_t)k * n, V.x, n * sizeof(float), cudaMemcpyDeviceToDevice, s));
+            }
             if (net) {
                 if (!lin) {
                     k_fcg_normalise<<<gb, NT, 0, s>>>(V.r, V.rn, n, st);

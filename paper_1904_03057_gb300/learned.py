@@ -141,43 +141,26 @@ def fcg_pairs(net: api.Net, problems: list, steps: int = 30, h: float = 1.0 / 51
     the given problems (the first `steps` iterations from x = 0), with their errors. A network
     trained only on the plain solver's residuals is good on those but poor on the residuals it
     leaves behind, which are exactly the ones flexible CG then hands it; adding these pairs and
-    training again (a few rounds) removes that mismatch. The iteration here is bookkeeping for
-    data generation (torch vector arithmetic, FP64); the operator and the network run in the
-    library's kernels."""
+    training again (a few rounds) removes that mismatch. The iteration is the library's own
+    (fcg_record: the inner FP32 solve of fcg_solve, with its fallbacks); this function only turns
+    each recorded state (r_k, d_k of A d = b / ||b||) into a pair (r_k / ||r_k||, the scaled
+    error of x_k = ||b|| d_k)."""
     n = problems[0].mask.shape[0]
     vol = h ** 3
-    H = api.Handle(n, n, n, degree, h, dt, precision="f64")   # masked operator: mask A (mask v)
     Rs, Es, Ms = [], [], []
-    try:
-        for P in problems:
-            m = P.mask.double()
-            A = lambda v: H.op_apply((v * m).contiguous()) * m  # noqa: E731
-            x = torch.zeros_like(P.b)
-            r = P.b.clone()
-            p = q = None
-            nb = torch.linalg.vector_norm(r).item()
-            for _ in range(steps):
-                nr = torch.linalg.vector_norm(r).item()
-                if not (nr > 1e-7 * nb) or not math.isfinite(nr):
-                    break
-                rn = (r / nr).float().contiguous()
-                Rs.append(rn)
-                Es.append(((P.xs - x) * (vol / nr)).float())
-                Ms.append(P.mask)
-                z = net.forward(rn, P.mask).double() * (nr / vol)
-                if not torch.dot(z.flatten(), r.flatten()).item() > 0:
-                    z = r.clone()
-                az = A(z)
-                if p is None:
-                    p, q = z, az
-                else:
-                    beta = -torch.dot(z.flatten(), q.flatten()).item() / torch.dot(p.flatten(), q.flatten()).item()
-                    p, q = z + beta * p, az + beta * q
-                alpha = torch.dot(r.flatten(), p.flatten()).item() / torch.dot(p.flatten(), q.flatten()).item()
-                x = x + alpha * p
-                r = r - alpha * q
-    finally:
-        H.close()
+    for P in problems:
+        H = api.Handle(n, n, n, degree, h, dt, mask=P.mask, precision="f32_ir")
+        try:
+            r, d, bnorm = H.fcg_record(P.b, steps, net)
+        finally:
+            H.close()
+        for k in range(r.shape[0]):
+            nr = torch.linalg.vector_norm(r[k]).item()
+            if not (nr > 1e-7) or not math.isfinite(nr):
+                break
+            Rs.append((r[k] / nr).contiguous())
+            Es.append(((P.xs - bnorm * d[k].double()) * (vol / (bnorm * nr))).float())
+            Ms.append(P.mask)
     return PairSet(torch.stack(Rs), torch.stack(Es), torch.stack(Ms), (n, n, n), h, dt, degree)
 
 

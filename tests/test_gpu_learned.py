@@ -271,3 +271,34 @@ def test_race_512_learned_solution_judged_by_oracle(mods, orc):
     assert np.max(np.abs(got - ref)) <= 1e-12 * scale
     net.close()
     H32.close()
+
+
+def test_fcg_record_states_match_the_oracle(mods):
+    """fcg_record (the states the on-policy training pairs are made of): with no network the
+    recorded iterates are plain CG's, so ||b|| d_k equals the oracle's CG iterate x_k, and every
+    recorded residual is b / ||b|| - A d_k of the oracle's operator (FP32 states: 1e-5 of the
+    scale)."""
+    import oracle
+    api, inputs, learned = mods
+    n, h, dt, steps = 24, 1.0 / 25, 1e-3, 12
+    mask, b = _masked_problem(inputs, n, 5, h)
+    H = api.Handle(n, n, n, 3, h, dt, mask=mask, precision="f32_ir")
+    r, d, bnorm = H.fcg_record(b, steps)
+    H.close()
+    assert r.shape[0] == steps
+    p = oracle.Problem(n, n, n, 3, h, dt=dt, mask=mask.cpu().numpy())
+    bn = b.cpu().numpy() * p.mask
+    assert abs(bnorm - np.linalg.norm(bn)) <= 1e-12 * np.linalg.norm(bn)
+    for k in range(steps):
+        dk = d[k].double().cpu().numpy()
+        rk = r[k].double().cpu().numpy()
+        want_r = (bn / bnorm - oracle.op_separable(p, dk)) * p.mask
+        assert np.abs(rk - want_r).max() <= 1e-5 * np.abs(bn / bnorm).max(), k
+        xk, it, _, _ = oracle.cg(p, bn, tol=0.0, max_iter=k) if k > 0 else (np.zeros_like(bn), 0, 0, 0)
+        assert np.abs(bnorm * dk - xk).max() <= 1e-4 * max(np.abs(xk).max(), 1e-300) + 1e-30, k
+    # with a network the first state is the scaled right-hand side, and the states are finite
+    net = api.Net(n, n, n)
+    net.set_params(learned.init_params(0, h=h, dt=dt))
+    r2, d2, _ = api.Handle(n, n, n, 3, h, dt, mask=mask, precision="f32_ir").fcg_record(b, steps, net)
+    assert torch.allclose(r2[0].double(), torch.from_numpy(bn / bnorm).to(r2.device), atol=1e-6)
+    assert torch.isfinite(r2).all() and torch.isfinite(d2).all() and torch.count_nonzero(d2[0]) == 0

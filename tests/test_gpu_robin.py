@@ -212,7 +212,10 @@ def test_robin_heat_step_and_mixed_precision(api):
         rep = H.heat_step(u, nsteps=1, tol=tol, max_iter=20000)
         assert rep["status"] == 0, rep
         got = u.cpu().numpy()
-        # error <= condition number x residual; the linear Robin system here is moderately conditioned
+        # the oracle's own true residual of the returned step, against the requested tolerance
+        res = b - oracle.op_robin(P, pen, got)
+        assert np.linalg.norm(res) <= 1.5 * tol * np.linalg.norm(b), (prec, rep)
+        # and the error, bounded by the condition number times that residual (moderate here)
         assert np.linalg.norm(got - ref) <= 1e4 * tol * np.linalg.norm(ref), (prec, rep)
 
 
