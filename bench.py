@@ -41,7 +41,7 @@ WORKLOAD = "heat3d_928cube_cubic_f32sweeps_f64refinement"
 # kernels' sources hash to CG_TRAFFIC_SOURCES_SHA256 (None: no capture of the current sources).
 # 512^3 capture (--metrics dram__bytes_read.sum,dram__bytes_write.sum,gpu__time_duration.sum):
 # k_op_tma<float,3,CG> 2.879 + 1.568 GB, k_ws<3,WS_CG> 2.192 + 1.559 GB per launch.
-CG_TRAFFIC_BYTES_PER_UNKNOWN = {"classic": 33.13, "ws": 27.95}
+CG_TRAFFIC_BYTES_PER_UNKNOWN = {"classic": 33.13, "ws": 27.95, "ws_columns": None}
 # Algorithmic bytes per unknown of one single-pass FP32 CG iteration.
 CG_BYTES_PER_UNKNOWN = 28.0
 CG_TRAFFIC_SOURCES_SHA256 = "24e2db71dfd98f9b709e0583064e64cbca798475f0eecbf2c13faa24304c08b3"
@@ -758,40 +758,30 @@ def run_ours(args, rank, world, dist):
     ms_step = elapsed_ms / args.steps
     worst_res = max(r["rel_residual"] for r in reps)
 
-    # end to end through the public API with host buffers: H2D of u, heat_step, D2H of u
+    # end to end through the public API with host buffers: heat_step_host copies u from the
+    # pinned host buffer to the device, steps it and copies it back, all inside the library
     e2e = None
     if not args.no_e2e:
         uh.copy_(u)
         barrier()
         e2e_steps = max(1, min(args.steps, 2))
-        # one untimed round trip through the pinned staging buffer first (its pages are mapped
-        # for the copy engines on first use), as the main loop has its warm-up steps
-        u.copy_(uh, non_blocking=True)
-        H.heat_step(u, None, 1, **opts)
-        uh.copy_(u, non_blocking=True)
+        H.heat_step_host(uh, None, 1, **opts)          # untimed round trip (first-call set-up)
         barrier()
-        ev = [[torch.cuda.Event(enable_timing=True) for _ in range(4)] for _ in range(e2e_steps)]
         t0 = time.perf_counter()
         e2e_apps = 0
+        h2d_ms = d2h_ms = solve_ms = 0.0
         for k in range(e2e_steps):
-            ev[k][0].record(stream)
-            u.copy_(uh, non_blocking=True)
-            ev[k][1].record(stream)
-            r = H.heat_step(u, None, 1, **opts)
-            ev[k][2].record(stream)
-            uh.copy_(u, non_blocking=True)
-            ev[k][3].record(stream)
-            torch.cuda.current_stream().synchronize()
+            r = H.heat_step_host(uh, None, 1, **opts)
             e2e_apps += r["iterations"] + r["outer_iterations"] + 1
+            h2d_ms += r["h2d_ms"] / e2e_steps
+            d2h_ms += r["d2h_ms"] / e2e_steps
+            solve_ms += (r["elapsed_ms"] - r["h2d_ms"] - r["d2h_ms"]) / e2e_steps
         t_e2e = max_over_ranks(time.perf_counter() - t0, dist)
-        h2d_ms = sum(e[0].elapsed_time(e[1]) for e in ev) / e2e_steps
-        solve_ms = sum(e[1].elapsed_time(e[2]) for e in ev) / e2e_steps
-        d2h_ms = sum(e[2].elapsed_time(e[3]) for e in ev) / e2e_steps
         e2e = {"value": whole_job_gdofs(world, dofs, e2e_apps, t_e2e), "unit": "GDoF/s",
                "h2d_bytes_per_step": dofs * 8, "d2h_bytes_per_step": dofs * 8,
                "ms_per_step": 1e3 * t_e2e / e2e_steps, "h2d_ms": h2d_ms, "solve_ms": solve_ms,
                "d2h_ms": d2h_ms, "h2d_gbs": dofs * 8 / (h2d_ms * 1e-3) / 1e9,
-               "d2h_gbs": dofs * 8 / (d2h_ms * 1e-3) / 1e9}
+               "d2h_gbs": dofs * 8 / (d2h_ms * 1e-3) / 1e9, "api": "heat_step_host (host buffers)"}
         del uh
 
     # dominant kernel: the fused CG iteration (one launch per inner iteration). Its average
@@ -837,7 +827,12 @@ def run_ours(args, rank, world, dist):
     Hb.close()
     ach = bytes_fused / (ms_fused_live * 1e-3) / 1e9
     traffic = None
-    per_unknown = CG_TRAFFIC_BYTES_PER_UNKNOWN.get(cg_kernel)
+    # the traffic figure of the plan actually in use: classic, or the warp-specialised pass with
+    # chunked or whole-column items
+    plan = H.cg_kernel_config()
+    plan_key = "classic" if plan["kernel"] == "classic" else (
+        "ws_columns" if plan["zchunk_planes"] >= N else "ws")
+    per_unknown = CG_TRAFFIC_BYTES_PER_UNKNOWN.get(plan_key)
     if per_unknown is not None and cg_kernel_sources_sha256() == CG_TRAFFIC_SOURCES_SHA256:
         traffic = per_unknown * dofs
 
@@ -854,6 +849,7 @@ def run_ours(args, rank, world, dist):
             "l2": f"inputs larger than L2 ({4 * dofs / 1e9:.2f} GB FP32 / {8 * dofs / 1e9:.2f} GB FP64 vectors)",
             "cg_kernel": cg_kernel + " (chosen per handle by timing both single-pass CG kernels)"
                          if args.cg_kernel == "auto" else cg_kernel + " (forced)",
+            "cg_kernel_config": H.cg_kernel_config(),
             "op_applications_per_step": op_apps / len(reps),
             "cg_iterations_per_step": inner / len(reps),
             "refinement_steps_per_step": outer / len(reps),
@@ -873,7 +869,8 @@ def run_ours(args, rank, world, dist):
                                       "kernel": "general kernel, FP32 arithmetic, BF16 in/out"},
             "parallelism": f"{world} independent problems (one per GPU)",
         },
-        "roofline": {"kernel": ("k_ws<3,WS_CG>" if cg_kernel == "ws" else "k_op_tma<float,3,CG>")
+        "roofline": {"kernel": ("k_ws<3,WS_CG>" + (" (whole-column items)" if plan_key == "ws_columns" else "")
+                                if cg_kernel == "ws" else "k_op_tma<float,3,CG>")
                                + ": one CG iteration (r rebuilt, p and x updates + A p + r.r, p.Ap, Ap.Ap)",
                      "bound": "hbm", "achieved": ach, "peak": hbm, "unit": "GB/s",
                      "frac": ach / hbm, "traffic": traffic,
@@ -934,8 +931,10 @@ def main():
     ap.add_argument("--grid", type=int, default=N_GRID,
                     help="grid edge (default: the benchmark workload; smaller grids are the "
                          "profiler's small case)")
-    ap.add_argument("--cg-kernel", choices=["auto", "ws", "classic"], default="auto",
-                    help="single-pass CG kernel: chosen per handle by timing (default) or forced")
+    ap.add_argument("--cg-kernel", choices=["auto", "ws", "classic", "ws_chunked", "ws_columns"], default="auto",
+                    help="single-pass CG kernel: chosen per handle by timing (default) or forced "
+                         "(ws_chunked / ws_columns: the warp-specialised pass with z-chunks of <= 128 "
+                         "planes or whole-column items)")
     ap.add_argument("--profile-case", choices=["op384", "cg512", "var240", "robin200", "batch64"], default=None,
                     help="run one small case for the profiler instead of the benchmark")
     args = ap.parse_args()

@@ -150,6 +150,8 @@ typedef struct bsk_cg_report {
                               the iterations bounds the time of one iteration's kernel from above
                               (the few launches that find the solve done add to it). 0 for
                               fcg_solve and the batch solvers.                                    */
+    double h2d_ms;         /* heat_step_host: device time of the host -> device copies; else 0   */
+    double d2h_ms;         /* heat_step_host: device time of the device -> host copy; else 0     */
 } bsk_cg_report;
 
 /* Solves A x = b by conjugate gradients (section 2.5), starting from the x passed in, which
@@ -414,18 +416,29 @@ int bsk_time_kernel(bsk_handle* h, int kernel, int reps, double* ms);
  * BSK_F32_IR). Two kernels implement the same iteration on unmasked grids with 16-byte rows
  * and degree <= 4: a warp-specialised pass (BSK_CG_KERNEL_WS: 64 x 32 tiles, one block per SM)
  * and the two-block-per-SM pass used for every other grid (BSK_CG_KERNEL_CLASSIC); neither is
- * the faster on every grid shape. bsk_create chooses with BSK_CG_KERNEL_AUTO, which times both
- * on the handle's own work vectors (zeroing them; about four passes each) and keeps the faster.
+ * the faster on every grid shape. bsk_create chooses with BSK_CG_KERNEL_AUTO, which times
+ * three candidates on the handle's own work vectors (zeroing them; about three passes each) and
+ * keeps the fastest: the warp-specialised pass with z-chunks of at most 128 planes, the same
+ * pass with whole-column items, and the two-block pass. BSK_CG_KERNEL_WS times the first two only.
  * request: BSK_CG_KERNEL_AUTO, BSK_CG_KERNEL_WS, BSK_CG_KERNEL_CLASSIC, or BSK_CG_KERNEL_CURRENT
- * (no change, no timing); *chosen (nullable) receives the kernel now in use (WS or CLASSIC). Call it between solves only, never while the
- * handle's stream is capturing. Returns BSK_EINVAL for an unknown request or for
- * BSK_CG_KERNEL_WS on a handle that cannot use it (masked grid, BSK_F64, degree 5, rows that
+ * (no change, no timing); *chosen (nullable) receives the kernel now in use (WS or CLASSIC).
+ * Call it between solves only, never while the handle's stream is capturing. Returns BSK_EINVAL for an unknown request or for
+ * BSK_CG_KERNEL_WS (or _WS_CHUNKED, _WS_COLUMNS) on a handle that cannot use it (masked grid, BSK_F64, degree 5, rows that
  * are not 16-byte multiples); AUTO on such a handle selects CLASSIC without timing. */
 #define BSK_CG_KERNEL_AUTO 0
 #define BSK_CG_KERNEL_WS 1
 #define BSK_CG_KERNEL_CLASSIC 2
 #define BSK_CG_KERNEL_CURRENT 3
+/* the warp-specialised pass with a fixed item plan, no timing: z-chunks of at most 128 planes, or
+ * whole columns */
+#define BSK_CG_KERNEL_WS_CHUNKED 4
+#define BSK_CG_KERNEL_WS_COLUMNS 5
 int bsk_select_cg_kernel(bsk_handle* h, int request, int* chosen);
+
+/* The CG kernel in use (BSK_CG_KERNEL_WS or _CLASSIC) and, for the warp-specialised pass, the
+ * most planes per z-chunk its items take (the whole column when that was faster). Either output
+ * may be NULL. */
+int bsk_cg_kernel_config(bsk_handle* h, int* kernel, int* zchunk_planes);
 
 /* Allocation-free residual: r = b - A x (A as for op_apply), with *rr = r.r and *bb = b.b
  * reduced in FP64. The paper has no counterpart for this interface: it serves callers that
@@ -524,6 +537,16 @@ int bsk_slab_cg_direction(bsk_handle* h, const void* r, void* p_halo, double* s,
  * element type (BSK_F64 or BSK_F32 handles). Returns BSK_EINVAL when the handle has no Jacobi
  * preconditioner set. Asynchronous on the handle's stream. */
 int bsk_inverse_diagonal(bsk_handle* h, void* out);
+
+/* heat_step on HOST buffers: copies u (and q, if not NULL) from the host to device vectors the
+ * handle keeps for this purpose (allocated by the first call), runs heat_step there, and copies
+ * the new u back into u_host, all on the handle's stream; returns after the copy back. u_host and
+ * q_host are HOST arrays of nx*ny*nz elements of the handle's element type; pinned memory
+ * (cudaHostAlloc, or torch's pin_memory) lets the copies run at the link's speed, pageable
+ * memory works but is staged by the driver. report (may be NULL) is heat_step's, with h2d_ms and
+ * d2h_ms the device times of the copies and elapsed_ms the whole call. */
+int heat_step_host(bsk_handle* h, void* u_host, const void* q_host, int nsteps, const bsk_cg_opts* opts,
+                   bsk_cg_report* report);
 
 /* Text of the last error raised on the calling thread ("" if none). */
 const char* bsk_last_error(void);

@@ -37,6 +37,7 @@ class CgReport(ctypes.Structure):
         ("outer_iterations", ctypes.c_int), ("rel_residual", ctypes.c_double),
         ("elapsed_ms", ctypes.c_double), ("kernel_launches", ctypes.c_longlong),
         ("fallback_iter", ctypes.c_int), ("net_rejected", ctypes.c_int), ("iter_ms", ctypes.c_double),
+        ("h2d_ms", ctypes.c_double), ("d2h_ms", ctypes.c_double),
     ]
 
 
@@ -69,8 +70,11 @@ SIGNATURES = {
     "bsk_time_kernel": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int, ctypes.c_int,
                                        ctypes.POINTER(ctypes.c_double)]),
     "bsk_select_cg_kernel": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int, ctypes.POINTER(ctypes.c_int)]),
+    "bsk_cg_kernel_config": (ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_int)]),
     "bsk_set_slab": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int, ctypes.c_int]),
     "bsk_inverse_diagonal": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p]),
+    "heat_step_host": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int,
+                                      ctypes.c_void_p, ctypes.c_void_p]),
     "fcg_record": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int,
                                   ctypes.c_void_p, ctypes.c_void_p, ctypes.POINTER(ctypes.c_double),
                                   ctypes.POINTER(ctypes.c_int)]),

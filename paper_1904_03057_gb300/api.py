@@ -20,6 +20,7 @@ _PREC = {"f64": F64, "f32": F32, "f32_ir": F32_IR, "bf16s": BF16S,
 OK, NOT_CONVERGED, STALLED = 0, 1, 2
 KERNEL_OP, KERNEL_CG_FUSED, KERNEL_CG_UPDATE, KERNEL_RES64, KERNEL_RES_DF = 0, 1, 2, 3, 4
 CG_KERNEL_AUTO, CG_KERNEL_WS, CG_KERNEL_CLASSIC, CG_KERNEL_CURRENT = 0, 1, 2, 3
+CG_KERNEL_WS_CHUNKED, CG_KERNEL_WS_COLUMNS = 4, 5
 EINVAL, ECUDA, ENOMEM, ETIMEOUT, EBREAKDOWN = -1, -2, -3, -4, -5
 
 
@@ -51,7 +52,7 @@ def _report(rep: _native.CgReport) -> dict:
             "outer_iterations": rep.outer_iterations, "rel_residual": rep.rel_residual,
             "elapsed_ms": rep.elapsed_ms, "kernel_launches": rep.kernel_launches,
             "fallback_iter": rep.fallback_iter, "net_rejected": rep.net_rejected,
-            "iter_ms": rep.iter_ms}
+            "iter_ms": rep.iter_ms, "h2d_ms": rep.h2d_ms, "d2h_ms": rep.d2h_ms}
 
 
 class Handle:
@@ -134,6 +135,22 @@ class Handle:
                                           ctypes.byref(o), ctypes.byref(rep)))
         return _report(rep)
 
+    def heat_step_host(self, u: torch.Tensor, q: Optional[torch.Tensor] = None, nsteps: int = 1,
+                       **opts) -> dict:
+        """heat_step on HOST tensors (heat_step_host): u (and q) are copied to the device, stepped
+        and u copied back, inside the library; pinned tensors copy at the link's speed."""
+        def host(t, name):
+            if not isinstance(t, torch.Tensor) or t.is_cuda or t.dtype != self.dtype or not t.is_contiguous() \
+                    or t.numel() != self.shape[0] * self.shape[1] * self.shape[2]:
+                raise ValueError(f"{name} must be a contiguous host tensor of dtype {self.dtype} with "
+                                 f"{self.shape} elements")
+            return t.data_ptr()
+        o = _opts(**opts)
+        rep = _native.CgReport()
+        _native.check(self._lib.heat_step_host(self._ptr, host(u, "u"), None if q is None else host(q, "q"),
+                                               int(nsteps), ctypes.byref(o), ctypes.byref(rep)))
+        return _report(rep)
+
     def fcg_solve(self, b: torch.Tensor, x: torch.Tensor, net: Optional["Net"] = None,
                   **opts) -> dict:
         """Flexible CG with the learned preconditioner (net=None: no preconditioner) inside
@@ -166,14 +183,22 @@ class Handle:
         return out.value
 
     def select_cg_kernel(self, request: str = "auto") -> str:
-        """Kernel of the single-pass FP32 CG iteration (bsk_select_cg_kernel): "auto" times both
-        and keeps the faster, "ws" / "classic" force one, "current" only reports. Returns the
-        kernel now in use."""
+        """Kernel of the single-pass FP32 CG iteration (bsk_select_cg_kernel): "auto" times the
+        candidates and keeps the fastest, "ws" (its z-chunking timed) / "classic" force a kernel,
+        "ws_chunked" / "ws_columns" the warp-specialised pass with a fixed item plan, "current"
+        only reports. Returns the kernel now in use."""
         req = {"auto": CG_KERNEL_AUTO, "ws": CG_KERNEL_WS, "classic": CG_KERNEL_CLASSIC,
-               "current": CG_KERNEL_CURRENT}[request]
+               "current": CG_KERNEL_CURRENT, "ws_chunked": CG_KERNEL_WS_CHUNKED,
+               "ws_columns": CG_KERNEL_WS_COLUMNS}[request]
         out = ctypes.c_int(0)
         _native.check(self._lib.bsk_select_cg_kernel(self._ptr, req, ctypes.byref(out)))
         return "ws" if out.value == CG_KERNEL_WS else "classic"
+
+    def cg_kernel_config(self) -> dict:
+        """The CG kernel in use and, for the warp-specialised pass, its z-chunk cap in planes."""
+        k, c = ctypes.c_int(0), ctypes.c_int(0)
+        _native.check(self._lib.bsk_cg_kernel_config(self._ptr, ctypes.byref(k), ctypes.byref(c)))
+        return {"kernel": "ws" if k.value == CG_KERNEL_WS else "classic", "zchunk_planes": c.value}
 
     def norm2(self, x: torch.Tensor) -> float:
         out = ctypes.c_double(0.0)

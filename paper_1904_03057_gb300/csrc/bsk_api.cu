@@ -153,6 +153,7 @@ struct bsk_handle {
     void* cm[2];
     bool use_tma0, tma640, res_df0;   // TMA eligibility of the constant-coefficient operator
     int cg_impl;          // single-pass FP32 CG iteration: 0 = warp-specialised, 1 = op_tma.cuh
+    int ws_chunk;         // warp-specialised CG pass: most planes per z-chunk (0 = its default)
     int bc;               // BSK_BC_DIRICHLET (odd reflection) or BSK_BC_ROBIN (untruncated basis)
     double pen;           // Robin: weight of the boundary term
     void* rb[2];          // Robin: band rows near the faces, float [0] / double [1]
@@ -168,6 +169,9 @@ struct bsk_handle {
     int z_off, nz_glob;
     double* slab_partials;
     unsigned* slab_ctr;
+    // heat_step_host: device copies of the caller's host u and q (allocated by the first call)
+    void *u_dev, *q_dev;
+    cudaEvent_t io_ev[4];
 };
 
 namespace {
@@ -184,6 +188,7 @@ void fill_tma(const bsk_handle* h, bsk::TmaLaunch& L, int mode)
     L.work = h->work;
     L.mode = mode;
     L.impl = h->cg_impl;
+    L.ws_chunk = h->ws_chunk;
     L.degree = h->n;
     L.nx = h->nx;
     L.ny = h->ny;
@@ -822,6 +827,10 @@ extern "C" void bsk_destroy(bsk_handle* h)
     if (h->fcg_partials) cudaFree(h->fcg_partials);
     if (h->fcg_state) cudaFree(h->fcg_state);
     if (h->slab_partials) cudaFree(h->slab_partials);
+    if (h->u_dev) cudaFree(h->u_dev);
+    if (h->q_dev) cudaFree(h->q_dev);
+    for (int i = 0; i < 4; i++)
+        if (h->io_ev[i]) cudaEventDestroy(h->io_ev[i]);
     if (h->slab_ctr) cudaFree(h->slab_ctr);
     for (int d = 0; d < 3; d++)
         if (h->tr_L[d]) cudaFree(h->tr_L[d]);
@@ -1287,6 +1296,40 @@ extern "C" int heat_step(bsk_handle* h, void* u, const void* q, int nsteps, cons
     return st;
 }
 
+extern "C" int heat_step_host(bsk_handle* h, void* u_host, const void* q_host, int nsteps, const bsk_cg_opts* opts,
+                              bsk_cg_report* report)
+{
+    auto t0 = std::chrono::steady_clock::now();
+    if (int rc = check_handle(h)) return rc;
+    if (!u_host) return fail(BSK_EINVAL, "null vector");
+    if (h->prec == BSK_BF16S) return fail(BSK_EINVAL, "BF16 storage is an operator-only variant");
+    const size_t bytes = h->len * user_es(h);
+    if (!h->u_dev) {
+        BSK_CUDA(cudaMalloc(&h->u_dev, bytes));
+        for (int i = 0; i < 4; i++) BSK_CUDA(cudaEventCreate(&h->io_ev[i]));
+    }
+    if (q_host && !h->q_dev) BSK_CUDA(cudaMalloc(&h->q_dev, bytes));
+    BSK_CUDA(cudaEventRecord(h->io_ev[0], h->stream));
+    BSK_CUDA(cudaMemcpyAsync(h->u_dev, u_host, bytes, cudaMemcpyHostToDevice, h->stream));
+    if (q_host) BSK_CUDA(cudaMemcpyAsync(h->q_dev, q_host, bytes, cudaMemcpyHostToDevice, h->stream));
+    BSK_CUDA(cudaEventRecord(h->io_ev[1], h->stream));
+    const int st = heat_step(h, h->u_dev, q_host ? h->q_dev : nullptr, nsteps, opts, report);
+    if (st < 0) return st;
+    BSK_CUDA(cudaEventRecord(h->io_ev[2], h->stream));
+    BSK_CUDA(cudaMemcpyAsync(u_host, h->u_dev, bytes, cudaMemcpyDeviceToHost, h->stream));
+    BSK_CUDA(cudaEventRecord(h->io_ev[3], h->stream));
+    BSK_CUDA(cudaEventSynchronize(h->io_ev[3]));
+    if (report) {
+        float a = 0.f, b = 0.f;
+        BSK_CUDA(cudaEventElapsedTime(&a, h->io_ev[0], h->io_ev[1]));
+        BSK_CUDA(cudaEventElapsedTime(&b, h->io_ev[2], h->io_ev[3]));
+        report->h2d_ms = a;
+        report->d2h_ms = b;
+        report->elapsed_ms = 1e3 * seconds_since(t0);
+    }
+    return st;
+}
+
 extern "C" int bsk_net_forward(bsk_net* net, const float* r, const uint8_t* mask, float* z);
 
 // Iterative refinement around the preconditioned inner FCG solve (fcg.cu).
@@ -1548,28 +1591,45 @@ extern "C" int bsk_time_kernel(bsk_handle* h, int kernel, int reps, double* ms)
     return BSK_OK;
 }
 
+extern "C" int bsk_cg_kernel_config(bsk_handle* h, int* kernel, int* zchunk_planes)
+{
+    if (int rc = check_handle(h)) return rc;
+    if (kernel) *kernel = h->cg_impl == 0 ? BSK_CG_KERNEL_WS : BSK_CG_KERNEL_CLASSIC;
+    if (zchunk_planes) *zchunk_planes = h->cg_impl == 0 ? (h->ws_chunk > 0 ? h->ws_chunk : 128) : 0;
+    return BSK_OK;
+}
+
 extern "C" int bsk_select_cg_kernel(bsk_handle* h, int request, int* chosen)
 {
     if (int rc = check_handle(h)) return rc;
     if (request != BSK_CG_KERNEL_AUTO && request != BSK_CG_KERNEL_WS && request != BSK_CG_KERNEL_CLASSIC &&
-        request != BSK_CG_KERNEL_CURRENT)
+        request != BSK_CG_KERNEL_CURRENT && request != BSK_CG_KERNEL_WS_CHUNKED &&
+        request != BSK_CG_KERNEL_WS_COLUMNS)
         return fail(BSK_EINVAL, "unknown CG kernel request %d", request);
     if (request == BSK_CG_KERNEL_CURRENT) {
         if (chosen) *chosen = h->cg_impl == 0 ? BSK_CG_KERNEL_WS : BSK_CG_KERNEL_CLASSIC;
         return BSK_OK;
     }
     const bool ws_ok = cg_ws_eligible(h);
-    if (request == BSK_CG_KERNEL_WS && !ws_ok)
+    const bool ws_req = request == BSK_CG_KERNEL_WS || request == BSK_CG_KERNEL_WS_CHUNKED ||
+                        request == BSK_CG_KERNEL_WS_COLUMNS;
+    if (ws_req && !ws_ok)
         return fail(BSK_EINVAL, "the warp-specialised CG pass needs an unmasked FP32 TMA grid of degree <= 4");
-    int impl = request == BSK_CG_KERNEL_WS ? 0 : 1;
-    if (request == BSK_CG_KERNEL_AUTO && ws_ok) {
-        // time both passes on the handle's own vectors (bsk_time_kernel zeroes them first and
-        // launches once untimed); the first measurement of each warms it up
+    int impl = ws_req ? 0 : 1, chunk = request == BSK_CG_KERNEL_WS_COLUMNS ? h->nz : 0;
+    if ((request == BSK_CG_KERNEL_AUTO || request == BSK_CG_KERNEL_WS) && ws_ok) {
+        // time the candidates on the handle's own vectors (bsk_time_kernel zeroes them first and
+        // launches once untimed); the first measurement of each warms it up. The warp-specialised
+        // pass runs with z-chunks of at most 128 planes and with whole columns (the chunk cap
+        // at nz): which is faster depends on how many rounds of items the grid makes.
+        struct Cand { int impl, chunk; };
+        const Cand cands[3] = {{0, 0}, {0, h->nz}, {1, 0}};
+        const int ncand = request == BSK_CG_KERNEL_AUTO ? 3 : 2;
         const bool tma_now = h->use_tma;
         h->use_tma = h->use_tma0;
         double best = 0.0;
-        for (int cand = 0; cand < 2; cand++) {
-            h->cg_impl = cand;
+        for (int c = 0; c < ncand; c++) {
+            h->cg_impl = cands[c].impl;
+            h->ws_chunk = cands[c].chunk;
             double ms = 0.0;
             int rc = bsk_time_kernel(h, BSK_KERNEL_CG_FUSED, 1, &ms);
             if (rc == BSK_OK) rc = bsk_time_kernel(h, BSK_KERNEL_CG_FUSED, 2, &ms);
@@ -1577,14 +1637,16 @@ extern "C" int bsk_select_cg_kernel(bsk_handle* h, int request, int* chosen)
                 h->use_tma = tma_now;
                 return rc;
             }
-            if (cand == 0 || ms < best) {
+            if (c == 0 || ms < best) {
                 best = ms;
-                impl = cand;
+                impl = cands[c].impl;
+                chunk = cands[c].chunk;
             }
         }
         h->use_tma = tma_now;
     }
     h->cg_impl = impl;
+    h->ws_chunk = chunk;
     if (h->graph) {   // the captured CG chunk holds the previous kernel
         cudaStreamSynchronize(h->stream);
         cudaGraphExecDestroy(h->graph);

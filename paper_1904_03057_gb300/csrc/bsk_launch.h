@@ -150,6 +150,7 @@ struct TmaLaunch {
     int fin;
     int impl;                    // TMODE_CG, FP32, unmasked, degree <= 4: 0 = the warp-specialised
                                  // pass (op_ws.cuh), 1 = the single-pass kernel of op_tma.cuh
+    int ws_chunk;                // warp-specialised CG pass: most planes per z-chunk (0 = 128)
     // TMODE_OP on a z-slab: global offset, global plane count (0 = nz) and the halo planes in[0]
     // carries on each side (0 = a whole grid)
     int z_off, nz_glob, zpad;

@@ -67,12 +67,17 @@ cudaError_t ws_prepare_n()
 }
 
 // Items = tiles x z-chunks, handed out round-robin to the resident blocks. The chunk count
-// minimises rounds x planes per item (2n halo planes included), with chunks of at most 128
-// planes so that the blocks working on neighbouring tiles stay close in z and their shared
-// halo rows meet in L2.
-void ws_plan(int nx, int ny, int nz, int n, int grid, int& tiles_x, int& tiles_y, int& tz, int& nitems)
+// minimises rounds x planes per item (2n halo planes included), with chunks of at most
+// max_chunk planes. The cap trades two effects that the cost model does not see: short chunks
+// keep the blocks working on neighbouring tiles close in z, so that their shared halo rows meet
+// in L2; but they make many rounds, over which the blocks drift apart all the same. The CG pass
+// takes the cap its handle's tuning chose (bsk_select_cg_kernel); the operator keeps 128.
+constexpr int kWsDefaultChunk = 128;
+
+void ws_plan(int nx, int ny, int nz, int n, int grid, int max_chunk, int& tiles_x, int& tiles_y, int& tz,
+             int& nitems)
 {
-    constexpr int kMaxChunk = 128;
+    const int kMaxChunk = max_chunk > 0 ? max_chunk : kWsDefaultChunk;
     tiles_x = (nx + kWsTX - 1) / kWsTX;
     tiles_y = (ny + kWsTY - 1) / kWsTY;
     const long long tiles = (long long)tiles_x * tiles_y;
@@ -141,7 +146,8 @@ cudaError_t ws_launch_k(const TmaLaunch& L, cudaStream_t s)
     a.nx = L.nx;
     a.ny = L.ny;
     a.nz = L.nz;
-    ws_plan(L.nx, L.ny, L.nz, N, info.grid, a.tiles_x, a.tiles_y, a.tz, a.nitems);
+    ws_plan(L.nx, L.ny, L.nz, N, info.grid, MODE == WS_CG ? L.ws_chunk : 0, a.tiles_x, a.tiles_y, a.tz,
+            a.nitems);
     for (int d = 0; d < 3; d++)
         for (int j = 0; j < kMaxTaps; j++) {
             a.M[d][j] = (float)L.M[d][j];

@@ -168,9 +168,10 @@ TMA_CG_CASES = [
 
 @pytest.mark.parametrize("nx,ny,nz,n,iso", TMA_CG_CASES)
 @pytest.mark.parametrize("precision,tol", [("f32", 1e-5), ("f32_ir", 1e-10)])
-@pytest.mark.parametrize("kernel", ["ws", "classic"])
+@pytest.mark.parametrize("kernel", ["ws_chunked", "ws_columns", "classic"])
 def test_cg_solve_tma_tiles_matches_oracle(api, orc, nx, ny, nz, n, iso, precision, tol, kernel):
-    """The single-pass CG iteration, with each of its two kernels, on grids spanning several tiles,
+    """The single-pass CG iteration, with each of its two kernels (the warp-specialised one with
+    chunked and with whole-column items), on grids spanning several tiles,
     items and z-chunks, judged by the oracle's FP64 true residual of the returned solution and its
     distance to the oracle's solution (kappa times the residual)."""
     dt = 2e-3
@@ -179,7 +180,7 @@ def test_cg_solve_tma_tiles_matches_oracle(api, orc, nx, ny, nz, n, iso, precisi
     p = orc.Problem(nx, ny, nz, n, *hs, dt=dt)
     b = np.random.default_rng(nx + ny + n).standard_normal(p.shape)
     H = handle(api, p, hs, precision)
-    assert H.select_cg_kernel(kernel) == kernel
+    assert H.select_cg_kernel(kernel) == ("classic" if kernel == "classic" else "ws")
     tdt = torch.float32 if precision == "f32" else torch.float64
     bt = torch.from_numpy(b).to("cuda", tdt)
     xt = torch.zeros_like(bt)
@@ -230,12 +231,17 @@ def test_cg_kernel_selection(api):
     assert H.select_cg_kernel("classic") == "classic"
     assert H.select_cg_kernel("ws") == "ws"
     assert H.select_cg_kernel("current") == "ws"
+    assert H.cg_kernel_config()["zchunk_planes"] in (128, 20)
+    assert H.select_cg_kernel("ws_columns") == "ws" and H.cg_kernel_config() == {"kernel": "ws", "zchunk_planes": 20}
+    assert H.select_cg_kernel("ws_chunked") == "ws" and H.cg_kernel_config() == {"kernel": "ws", "zchunk_planes": 128}
+    assert H.select_cg_kernel("classic") == "classic" and H.cg_kernel_config()["zchunk_planes"] == 0
     for kw in (dict(precision="f64"), dict(precision="f32", degree=5),
                dict(precision="f32", mask=torch.ones((20, 40, 68), dtype=torch.uint8, device="cuda"))):
         deg = kw.pop("degree", 3)
         Hx = api.Handle(68, 40, 20, deg, 1 / 69, 1e-3, **kw)
-        with pytest.raises(RuntimeError, match="-1"):
-            Hx.select_cg_kernel("ws")
+        for req in ("ws", "ws_chunked", "ws_columns"):
+            with pytest.raises(RuntimeError, match="-1"):
+                Hx.select_cg_kernel(req)
         assert Hx.select_cg_kernel("auto") == "classic"
 
 
@@ -388,3 +394,30 @@ def test_full_size_928_heat_step_ir_closed_form(api):
     err = (torch.linalg.vector_norm(u - want) / torch.linalg.vector_norm(want)).item()
     kappa = box_kappa(N, N, N, n, (h, h, h), dt)
     assert err <= K * kappa * tol, err
+
+
+@pytest.mark.parametrize("precision", ["f64", "f32_ir", "f32"])
+@pytest.mark.parametrize("pinned", [True, False])
+def test_heat_step_host_buffers(api, orc, precision, pinned):
+    """heat_step_host: the same step as heat_step on device vectors, from and back into host
+    buffers (pinned or pageable), with a source term; the copies' device times are reported."""
+    N, n, dt = (40, 28, 19), 3, 2e-3
+    hs = tuple(1 / (k + 1) for k in N)
+    H = api.Handle(*N, n, hs, dt, precision=precision)
+    dt_t = torch.float32 if precision == "f32" else torch.float64
+    u0 = inputs.random_field((N[2], N[1], N[0]), 21).to(dt_t)
+    q = inputs.random_field((N[2], N[1], N[0]), 22).to(dt_t)
+    ud = u0.cuda()
+    rep_d = H.heat_step(ud, q.cuda(), 2, tol=1e-10)
+    uh = u0.clone().pin_memory() if pinned else u0.clone()
+    qh = q.clone().pin_memory() if pinned else q.clone()
+    rep_h = H.heat_step_host(uh, qh, 2, tol=1e-10)
+    assert rep_h["status"] == rep_d["status"] == 0
+    # the same kernels on the same data; the dynamic item queue of the two-block CG kernel sums
+    # the dot products in a run-dependent order, so the two solves may differ in the last bits
+    assert abs(rep_h["iterations"] - rep_d["iterations"]) <= 2
+    rel = (torch.linalg.vector_norm((uh - ud.cpu()).double()) / torch.linalg.vector_norm(ud.cpu().double())).item()
+    assert rel <= (1e-4 if precision == "f32" else 1e-9), rel
+    assert rep_h["h2d_ms"] > 0 and rep_h["d2h_ms"] > 0 and rep_h["elapsed_ms"] >= rep_h["h2d_ms"]
+    with pytest.raises(ValueError):
+        H.heat_step_host(ud, None, 1)                     # device tensors are not host buffers
