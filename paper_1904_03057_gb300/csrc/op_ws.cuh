@@ -37,6 +37,8 @@
 // runs ahead across item boundaries.
 #pragma once
 
+#include <type_traits>
+
 #include "bsk_device.cuh"
 #include "tma_util.cuh"
 
@@ -64,7 +66,9 @@ struct WsGeo {
     static constexpr int NXT = 32 * (kWsWX + kWsWH);   // x and halo threads
     static constexpr int NYZ = 32 * kWsWY;
     static constexpr int NIN = MODE == WS_CG ? 3 : 1;   // halo boxes per stage: x, or r, q, p
-    static constexpr int S = MODE == WS_CG ? (N >= 4 ? 3 : 4) : 6;   // TMA stages
+    // TMA stages: as many as shared memory allows the CG pass; 8 (a power of two, so the stage
+    // index and parity are a mask and a shift) for the operator, which measured 2 % faster than 6
+    static constexpr int S = MODE == WS_CG ? (N >= 4 ? 3 : 4) : 8;
     static constexpr int D = 2;                         // MX / KX buffers
     static constexpr size_t rnd(size_t b) { return (b + 127) / 128 * 128; }
     static constexpr size_t box_bytes = rnd(sizeof(float) * HY * BX);
@@ -300,6 +304,20 @@ __device__ __forceinline__ void ws_push_dispatch(int j, float2 (&acc)[kWsR][2 * 
     }
 }
 
+// Planes k + J, J = 0 .. L - 1 (those below np) of a y/z thread's march, each with its
+// compile-time accumulator slot J; false as soon as one step reports a wait that gave up.
+template <int J, int L, typename F>
+__device__ __forceinline__ bool ws_unroll_planes(F& step, int k, int np)
+{
+    if constexpr (J < L) {
+        if (k + J >= np) return true;
+        if (!step(k + J, std::integral_constant<int, J>{})) return false;
+        return ws_unroll_planes<J + 1, L>(step, k, np);
+    } else {
+        return true;
+    }
+}
+
 // Compensated (Kahan) FP32 running sum, converted to FP64 once per thread.
 struct WsKSum {
     float s = 0.f, c = 0.f;
@@ -529,10 +547,13 @@ __global__ void __launch_bounds__(kWsNT, 1) k_ws(const __grid_constant__ WsArgs 
             for (int t = 0; t < kWsR; t++)
 #pragma unroll
                 for (int s = 0; s < L; s++) acc[t][s] = make_float2(0.f, 0.f);
-            int jslot = 0;
-            for (int k = 0; k < np; k++, c++) {
+            // one input plane; its accumulator slot (k mod L, as every item starts at slot 0) is
+            // either a compile-time constant (the operator's plane loop is unrolled by L) or a
+            // runtime index (the CG pass and degree 4, whose unrolled forms spilled); false: a
+            // wait gave up
+            auto plane_step = [&](int k, auto jc) -> bool {
                 const int d = (int)(c % D);
-                if (!ws_wait(&mxfull[d], (c / D) & 1u, abort_flag)) { stop = true; break; }
+                if (!ws_wait(&mxfull[d], (c / D) & 1u, abort_flag)) return false;
                 const float* mxb = mx_buf(d) + r0 * MXP + c2;
                 const float* kxb = kx_buf(d) + r0 * MXP + c2;
                 const int zo = z0 - 2 * N + k;   // output plane completed by this input plane
@@ -579,9 +600,14 @@ __global__ void __launch_bounds__(kWsNT, 1) k_ws(const __grid_constant__ WsArgs 
                 }
                 ws_arrive(&mxempty[d]);
                 float2 q[kWsR];
-                if constexpr (ISO) ws_push_dispatch<N>(jslot, acc, A, B, my, ky, q);
-                else ws_push_dispatch<N>(jslot, acc, A, B, c1, c2t, q);
-                jslot = (jslot + 1 == L) ? 0 : jslot + 1;
+                if constexpr (std::is_integral<decltype(jc)>::value) {
+                    if constexpr (ISO) ws_push_dispatch<N>(jc, acc, A, B, my, ky, q);
+                    else ws_push_dispatch<N>(jc, acc, A, B, c1, c2t, q);
+                } else {
+                    constexpr int J = decltype(jc)::value;
+                    if constexpr (ISO) ws_push<N, J>(acc, A, B, my, ky, q);
+                    else ws_push<N, J>(acc, A, B, c1, c2t, q);
+                }
                 if (zo >= z0 && colok) {
                     float* o = obase + (size_t)zo * plane;
 #pragma unroll
@@ -593,6 +619,24 @@ __global__ void __launch_bounds__(kWsNT, 1) k_ws(const __grid_constant__ WsArgs 
                                 d2.add(fmaf(q[t].x, q[t].x, q[t].y * q[t].y));
                             }
                         }
+                }
+                c++;
+                return true;
+            };
+            if constexpr (MODE == WS_OP && N <= 3) {   // degree 4 spilled when unrolled
+                for (int k = 0; k < np; k += L)
+                    if (!ws_unroll_planes<0, L>(plane_step, k, np)) {
+                        stop = true;
+                        break;
+                    }
+            } else {
+                int jslot = 0;
+                for (int k = 0; k < np; k++) {
+                    if (!plane_step(k, jslot)) {
+                        stop = true;
+                        break;
+                    }
+                    jslot = (jslot + 1 == L) ? 0 : jslot + 1;
                 }
             }
         }
