@@ -717,9 +717,8 @@ def run_ours(args, rank, world, dist):
     h = 1.0 / (N + 1)
     dofs = N ** 3
     # the pinned host buffer of the end-to-end steps is allocated first and touched once. The
-    # link moves 190-210 GB/s either way, but copies from a buffer pinned late in a busy process
-    # ran at 13-36 GB/s in some runs (cause not isolated; allocating early is the cheap
-    # precaution). The measured rates are reported with the e2e figure.
+    # host link moves up to 190-210 GB/s, but the rate varies from box to box (device-to-host
+    # ran at 12-19 GB/s on some); the measured rates are reported with the e2e figure.
     uh = None
     if not args.no_e2e:
         uh = torch.empty((N, N, N), dtype=torch.float64, pin_memory=True)
