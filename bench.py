@@ -646,7 +646,9 @@ def profile_case(name: str, cg_kernel: str = "auto"):
     240 x 240 x 960, the inclusion fields of `variable_coefficients`) three times; `robin200` runs
     10 iterations of the FP64 Jacobi-preconditioned Robin CG of `robin_large_run` on 200 x 200 x
     800 unknowns (256 MB per vector), then times its fused CG pass alone; `batch64` runs the 64-box
-batched measurement (autotuned tiles and z-chunks) and prints it."""
+    batched measurement (autotuned tiles and z-chunks) and prints it; `net512` applies the learned
+    preconditioner of `fcg_race` (linear network, Jacobi-scale start) to a masked residual at the
+    race's 512^3 four times (about 2.4 GB on the device: r, z, mask and four activations)."""
     import torch
 
     from paper_1904_03057_gb300 import api, inputs
@@ -675,6 +677,20 @@ batched measurement (autotuned tiles and z-chunks) and prints it."""
         y = torch.empty_like(x)
         ms = [_timed_ms(lambda: H.op_apply(x, y))[0] for _ in range(4)]
         print(json.dumps({"profile_case": name, "ms": ms, "max_abs_y": float(y.abs().max())}), flush=True)
+        return
+    if name == "net512":
+        from paper_1904_03057_gb300 import learned
+        N = 512
+        h = 1.0 / (N + 1)
+        centers, radii = inputs.random_spheres(5, 40, 0.05, 0.2)
+        mask = inputs.union_of_spheres_mask(N, N, N, centers, radii, h=h, device="cuda")
+        r = inputs.random_field((N, N, N), 9, device="cuda", dtype=torch.float32) * mask
+        net = api.Net(N, N, N, activation="linear")
+        net.set_params(learned.init_params(0, h=h, dt=1e-3))
+        z = torch.empty_like(r)
+        ms = [_timed_ms(lambda: net.forward(r, mask, z))[0] for _ in range(4)]
+        print(json.dumps({"profile_case": name, "ms": ms, "max_abs_z": float(z.abs().max())}), flush=True)
+        net.close()
         return
     if name == "robin200":
         import numpy as np
@@ -935,7 +951,7 @@ def main():
                     help="single-pass CG kernel: chosen per handle by timing (default) or forced "
                          "(ws_chunked / ws_columns: the warp-specialised pass with z-chunks of <= 128 "
                          "planes or whole-column items)")
-    ap.add_argument("--profile-case", choices=["op384", "cg512", "var240", "robin200", "batch64"], default=None,
+    ap.add_argument("--profile-case", choices=["op384", "cg512", "var240", "robin200", "batch64", "net512"], default=None,
                     help="run one small case for the profiler instead of the benchmark")
     args = ap.parse_args()
     if args.profile_case:

@@ -54,7 +54,8 @@ extern "C" {
 #define BSK_EINVAL (-1)       /* invalid argument (null pointer, size, degree, overlap, ...)  */
 #define BSK_ECUDA (-2)        /* a CUDA runtime call failed                                   */
 #define BSK_ENOMEM (-3)       /* device or host allocation failed                             */
-#define BSK_ETIMEOUT (-4)     /* the solve exceeded its wall-clock limit                      */
+#define BSK_ETIMEOUT (-4)     /* a wall-clock limit was exceeded: the solve's time limit, or a
+                                 bounded device wait of the network (bsk_net_read_loss)      */
 #define BSK_EBREAKDOWN (-5)   /* CG breakdown: p.Ap <= 0, or a NaN/Inf in a reduction         */
 
 /* ---- precision modes --------------------------------------------------------------------- */
@@ -329,7 +330,7 @@ int bsk_batch_configure(bsk_batch* b, int degree, int tile_rows, int nzc, int ch
 /* ---- the learned preconditioner and flexible CG ---------------------------------------------
  * A 3-level convolutional network N maps a normalised residual to an error estimate
  * (16 channels, 3^3 kernels, BF16 weights and activations, FP32 accumulation; the 16 -> 16
- * convolutions run on the tensor cores):
+ * convolutions run on the 5th-generation tensor cores, tcgen05 MMAs with TMEM accumulators):
  *   a1 = relu(conv_s2(r) + b1); a2 = relu(conv_s2(a1) + b2); a3 = relu(conv_s1(a2) + b3);
  *   a4 = relu(convT_s2(a3) + b4 + a1); z = mask * (convT_s2(a4) + b5 + conv_s1(r; Wf))
  * with stride-2 convolutions halving each axis (ceil) and their transposes restoring it. The
@@ -366,7 +367,11 @@ int bsk_net_backward(bsk_net* net, const float* r, const float* e, const uint8_t
 int bsk_net_backward_grad(bsk_net* net, const float* r, const float* dz, const uint8_t* mask, float scale);
 /* Adam step (beta1 0.9, beta2 0.999) with learning rate lr on the gradients times grad_scale. */
 int bsk_net_adam(bsk_net* net, float lr, float grad_scale);
-/* Accumulated loss (host float) and, if grads is not NULL, the gradients (host floats). */
+/* Accumulated loss (host float) and, if grads is not NULL, the gradients (host floats).
+ * bsk_net_read_loss and bsk_net_get_params synchronise the network's stream; they return
+ * BSK_ETIMEOUT if a convolution since the network's creation gave up a bounded wait for its
+ * loads or MMAs (its outputs were then set to NaN, which flexible CG treats as a failed network
+ * and falls back from). */
 int bsk_net_read_loss(bsk_net* net, float* loss, float* grads);
 
 /* Not in the paper: the learned preconditioner of this library. Flexible CG (FCG(1), Notay's

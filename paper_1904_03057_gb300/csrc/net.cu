@@ -11,8 +11,9 @@
 // With BSK_ACT_LINEAR relu is the identity and the biases are dropped: the network is then a
 // linear multilevel map of r (the form that works as a flexible-CG preconditioner).
 // Activations are BF16, channels-last (16 channels = 32 bytes per voxel). The 16 -> 16
-// convolutions run on the tensor cores (mma.sync m16n8k16 BF16 -> FP32, implicit GEMM over the
-// 27 taps); the 1-channel ends and the weight gradients run on the FP32 pipes. The paper has no
+// convolutions run on the 5th-generation tensor cores (tcgen05.mma, BF16 operands in shared
+// memory, FP32 accumulator in tensor memory; an implicit GEMM over the 27 taps); the 1-channel
+// ends and the weight gradients run on the FP32 pipes. The paper has no
 // learned component: this is the workload's addition to the CG stage of section 2.5.
 #include <algorithm>
 #include <cmath>
@@ -23,6 +24,8 @@
 
 #include "bsk.h"
 #include "bsk_launch.h"
+#include "tma_util.cuh"
+#include "umma_util.cuh"
 
 namespace {
 
@@ -61,136 +64,268 @@ __device__ __forceinline__ int src_index(int mode, int o, int k, int nin)
 
 struct D3 { int nx, ny, nz; };
 
-// ---- 16 -> 16 convolution on the tensor cores -------------------------------------------------
+// ---- 16 -> 16 convolution on the 5th-generation tensor cores ----------------------------------
 // out[o][co] = act( sum_{taps k, ci} W[k][co][ci] in[src(o,k)][ci] + bias[co] + skip[o][co] )
-// One warp computes 16 output voxels (consecutive x, or x of one parity for the transposed
-// convolution) x 16 channels with two m16n8k16 MMAs per tap.
-__device__ __forceinline__ void mma_bf16(float (&c)[4], const uint32_t (&a)[4], uint32_t b0, uint32_t b1)
-{
-    asm volatile(
-        "mma.sync.aligned.m16n8k16.row.col.f32.bf16.bf16.f32 {%0,%1,%2,%3}, {%4,%5,%6,%7}, {%8,%9}, "
-        "{%0,%1,%2,%3};"
-        : "+f"(c[0]), "+f"(c[1]), "+f"(c[2]), "+f"(c[3])
-        : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b0), "r"(b1));
-}
+// as an implicit GEMM on tcgen05. A tile is 128 outputs of one output row (z, y), at x indices
+// j0 .. j0 + 127 (for the transposed convolution, the outputs 2j and 2j + 1 for the same j, two
+// accumulators), and
+//   D[128][16] = sum over the tile's taps k of A_k[128][16] W_k^T,
+// with D in tensor memory (FP32), one M = 128, N = 16, K = 16 BF16 MMA per tap. A_k is never
+// gathered: along x the sources of consecutive outputs are consecutive voxels of one staged
+// "plane" (S1: the source row; S2: its even or its odd voxels; transposed: the source row), so
+// A_k is a plane seen from a start offset (the descriptor's start address). A plane holds 130
+// voxels as two 8-channel halves, [half][slot] with 16 bytes per slot: the K-major no-swizzle
+// operand layout (8 slots = one 128-byte core matrix, LBO = one half-plane, SBO = 128 bytes).
+// The weights sit in shared memory as [tap][half][co][8 ci] (LBO 256, SBO 128).
+// Per tile, one thread loads every half-plane the tile needs with a 4-D TMA box (the
+// activation seen as [row][x][half][8 channels], x-stride 32 bytes, or 64 bytes for the even and
+// odd voxels of S2; x neighbours outside the row arrive as zeros), all in flight at once on one
+// mbarrier; it then issues the tile's MMAs and commits them to a second mbarrier, and warp w
+// reads accumulator lanes 32w .. 32w + 31 (its outputs) for the epilogue. Several CTAs per SM
+// overlap one another's phases.
+constexpr int TC_M = 128;                  // outputs per tile (MMA M)
+constexpr int TC_SLOTS = TC_M + 2;         // voxels per plane: the tile and its x halo
+constexpr int TC_BOX = TC_SLOTS * 16;      // bytes one TMA box brings (one half-plane)
+constexpr int TC_HALF = 2176;              // half-plane stride: TC_BOX rounded up to 128 bytes
+constexpr int TC_PLANE = 2 * TC_HALF;
+constexpr int TC_WTAP = 2 * C * 16;        // bytes of one tap's weights
+constexpr uint32_t TC_COLS = 32;           // TMEM columns allocated (one or two 16-column accumulators)
+constexpr uint64_t TC_WAIT_NS = 2000000000ull;
 
 template <int MODE>
-__global__ void __launch_bounds__(128) k_conv16(const __nv_bfloat16* __restrict__ in, D3 din,
-                                                __nv_bfloat16* __restrict__ out, D3 dout,
-                                                const __nv_bfloat16* __restrict__ W,
-                                                const float* __restrict__ bias,
-                                                const __nv_bfloat16* __restrict__ skip, int relu)
+struct TcConv {
+    // planes: S1 one per source row (kz, ky); S2 an even and an odd one per row; the transposed
+    // convolution has at most 2 x 2 source rows, kept in (kz, ky) order
+    static constexpr int PLANES = MODE == CONV_S2 ? 18 : MODE == CONV_S1 ? 9 : 4;
+    static constexpr int IN_OFF = KT * TC_WTAP;
+    static constexpr int BAR_OFF = IN_OFF + PLANES * TC_PLANE;
+    static constexpr int SMEM = BAR_OFF + 32;   // two mbarriers and the TMEM address
+};
+
+struct ConvMaps {
+    CUtensorMap m[2];
+};
+
+struct ConvArgs {
+    CUtensorMap tin;        // the source activation (S2: its even voxels)
+    CUtensorMap tin_odd;    // S2: its odd voxels
+    D3 din, dout;
+    __nv_bfloat16* out;
+    const __nv_bfloat16* W;
+    const float* bias;
+    const __nv_bfloat16* skip;
+    int relu;
+    int* err;
+};
+
+template <int MODE>
+__global__ void __launch_bounds__(128) k_conv16(const __grid_constant__ ConvArgs a)
 {
-    __shared__ uint32_t sW[KT * C * C / 2];   // [tap][co][ci pairs]
-    const uint32_t* Wg = reinterpret_cast<const uint32_t*>(W);
-    for (int i = threadIdx.x; i < KT * C * C / 2; i += blockDim.x) sW[i] = Wg[i];
+    using L = TcConv<MODE>;
+    extern __shared__ __align__(1024) uint8_t tc_smem[];
+    uint8_t* sw = tc_smem;
+    uint8_t* sin = tc_smem + L::IN_OFF;
+    uint64_t* full = reinterpret_cast<uint64_t*>(tc_smem + L::BAR_OFF);
+    uint64_t* mma_done = full + 1;
+    uint32_t* tslot = reinterpret_cast<uint32_t*>(tc_smem + L::BAR_OFF + 16);
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    const D3 din = a.din, dout = a.dout;
+
+    // weights: global [k][co][16 ci] -> shared [k][half][co][8 ci], one 16-byte piece per step
+    const uint4* Wg = reinterpret_cast<const uint4*>(a.W);
+    for (int i = tid; i < KT * C * 2; i += blockDim.x) {
+        const int h = i & 1, co = (i >> 1) % C, k = i / (2 * C);
+        *reinterpret_cast<uint4*>(sw + k * TC_WTAP + h * (C * 16) + co * 16) = Wg[i];
+    }
+    if (warp == 0) bsk::tmem_alloc_warp(tslot, TC_COLS);
+    if (tid == 32) {
+        bsk::mbar_init(full, 1);
+        bsk::mbar_init(mma_done, 1);
+        bsk::fence_mbar_init();
+        bsk::prefetch_tensormap(&a.tin);
+        if (MODE == CONV_S2) bsk::prefetch_tensormap(&a.tin_odd);
+    }
+    bsk::fence_proxy_async_smem();
+    bsk::tc_fence_before_sync();
     __syncthreads();
+    bsk::tc_fence_after_sync();
+    const uint32_t tmem = *tslot;
 
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    const int g = lane >> 2, t = lane & 3;
-    // tiles: per output row (z, y): for the transposed conv two parity classes of x
-    const int xstep = MODE == CONVT_S2 ? 2 : 1;
     const int per_class = MODE == CONVT_S2 ? (dout.nx + 1) / 2 : dout.nx;
-    const int tiles_class = (per_class + 15) / 16;
-    const int tiles_row = tiles_class * xstep;
-    const long long ntiles = (long long)tiles_row * dout.ny * dout.nz;
-    const long long tile = (long long)blockIdx.x * 4 + warp;
-    if (tile >= ntiles) return;
-    const int tr = (int)(tile % tiles_row);
-    const long long row = tile / tiles_row;
-    const int oy = (int)(row % dout.ny), oz = (int)(row / dout.ny);
-    const int parity = MODE == CONVT_S2 ? tr / tiles_class : 0;
-    const int ox0 = (tr % tiles_class) * 16 * xstep + parity;
-    const int oxa = ox0 + xstep * g, oxb = ox0 + xstep * (g + 8);   // this lane's two rows
-
-    const uint32_t* inw = reinterpret_cast<const uint32_t*>(in);
-    float acc[2][4] = {{0, 0, 0, 0}, {0, 0, 0, 0}};
-    for (int kz = 0; kz < 3; kz++) {
-        const int iz = src_index(MODE, oz, kz, din.nz);
-        if (iz < 0) continue;
-        for (int ky = 0; ky < 3; ky++) {
-            const int iy = src_index(MODE, oy, ky, din.ny);
-            if (iy < 0) continue;
-            const long long rowbase = ((long long)iz * din.ny + iy) * din.nx;
+    const int segs = (per_class + TC_M - 1) / TC_M;
+    const long long ntiles = (long long)segs * dout.ny * dout.nz;
+    const uint32_t idesc = bsk::umma_idesc_bf16_f32(TC_M, C);
+    const uint32_t sin_a = bsk::smem_u32(sin), sw_a = bsk::smem_u32(sw);
+    uint32_t phase = 0;
+    int failed = 0;
+    for (long long tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
+        const int seg = (int)(tile % segs);
+        const long long row = tile / segs;
+        const int oy = (int)(row % dout.ny), oz = (int)(row / dout.ny);
+        const int j0 = seg * TC_M;
+        int rows = 0;   // bit kz * 3 + ky: source row (kz, ky) exists
+        for (int r = 0; r < 9; r++)
+            if (src_index(MODE, oz, r / 3, din.nz) >= 0 && src_index(MODE, oy, r % 3, din.ny) >= 0)
+                rows |= 1 << r;
+        if (tid == 0) {
+            const int per_row = MODE == CONV_S2 ? 4 : 2;
+            bsk::mbar_arrive_expect_tx(full, (uint32_t)(__popc(rows) * per_row * TC_BOX));
+            int q = 0;   // plane of the next source row (compacted for the transposed convolution)
+            for (int r = 0; r < 9; r++) {
+                if (!((rows >> r) & 1)) continue;
+                const int srow = src_index(MODE, oz, r / 3, din.nz) * din.ny + src_index(MODE, oy, r % 3, din.ny);
+                const int pl = MODE == CONV_S2 ? 2 * r : MODE == CONV_S1 ? r : q;
+                const int x0 = MODE == CONV_S1 ? j0 - 1 : j0;
+                for (int h = 0; h < 2; h++) {
+                    bsk::tma_load_4d(sin + pl * TC_PLANE + h * TC_HALF, &a.tin, full, 0, h, x0, srow);
+                    if (MODE == CONV_S2)   // odd voxels 2 (j0 + s) - 1 = 2 (j0 - 1 + s) + 1
+                        bsk::tma_load_4d(sin + (pl + 1) * TC_PLANE + h * TC_HALF, &a.tin_odd, full, 0, h, j0 - 1, srow);
+                }
+                q++;
+            }
+        }
+        // this thread's outputs: j; for the transposed convolution x = 2j and 2j + 1
+        const int j = j0 + 32 * warp + lane;
+        const int ox = MODE == CONVT_S2 ? 2 * j : j;
+        const bool mine0 = ox < dout.nx;
+        const bool mine1 = MODE == CONVT_S2 && ox + 1 < dout.nx;
+        const long long o = ((long long)oz * dout.ny + oy) * dout.nx + ox;
+        uint4 sk[4] = {};
+        if (a.skip) {   // fetched while the tile's loads and MMAs run
+            const uint4* sp = reinterpret_cast<const uint4*>(a.skip + o * C);
+            if (mine0) { sk[0] = sp[0]; sk[1] = sp[1]; }
+            if (mine1) { sk[2] = sp[2]; sk[3] = sp[3]; }
+        }
+        int bad = 0;
+        if (tid == 0) {
+            const bool landed = bsk::mbar_wait_bounded(full, phase, TC_WAIT_NS);
+            if (!landed) bad = 1;   // no MMAs on a tile whose loads did not land
+            bsk::tc_fence_after_sync();
+            uint32_t acc0 = 0, acc1 = 0;
+            int q = 0;
+            for (int r = 0; landed && r < 9; r++) {
+                if (!((rows >> r) & 1)) continue;
+                const uint32_t pbase = sin_a + (uint32_t)((MODE == CONV_S2 ? 2 * r : MODE == CONV_S1 ? r : q) * TC_PLANE);
+                for (int kx = 0; kx < 3; kx++) {
+                    // plane offset and start slot of tap kx (see the layout above)
+                    uint32_t off;
+                    if (MODE == CONV_S1) off = kx * 16;
+                    else if (MODE == CONV_S2) off = kx == 1 ? 0 : TC_PLANE + (kx == 2 ? 16 : 0);
+                    else off = kx == 0 ? 16 : 0;   // kx = 1 feeds x = 2j, kx = 0 and 2 feed 2j + 1
+                    const uint64_t ad = bsk::umma_desc_noswizzle(pbase + off, TC_HALF, 128);
+                    const uint64_t bd = bsk::umma_desc_noswizzle(sw_a + (uint32_t)((r * 3 + kx) * TC_WTAP), C * 16, 128);
+                    if (MODE == CONVT_S2 && kx != 1) {
+                        bsk::umma_bf16(tmem + 16, ad, bd, idesc, acc1);
+                        acc1 = 1;
+                    } else {
+                        bsk::umma_bf16(tmem, ad, bd, idesc, acc0);
+                        acc0 = 1;
+                    }
+                }
+                q++;
+            }
+            bsk::umma_commit(mma_done);   // arrives when the MMAs issued above are done
+        }
+        if (!bsk::mbar_wait_bounded(mma_done, phase, TC_WAIT_NS)) bad = 1;
+        phase ^= 1;
+        __nv_bfloat16* dst = a.out + o * C;
+        if (__syncthreads_or(bad)) {
+            // a load or the MMAs did not complete in time: mark this tile's outputs NaN, report, stop
+            const uint4 nan4 = make_uint4(0x7FC07FC0u, 0x7FC07FC0u, 0x7FC07FC0u, 0x7FC07FC0u);
+            uint4* d4 = reinterpret_cast<uint4*>(dst);
+            if (mine0) { d4[0] = nan4; d4[1] = nan4; }
+            if (mine1) { d4[2] = nan4; d4[3] = nan4; }
+            failed = 1;
+            break;
+        }
+        bsk::tc_fence_after_sync();
 #pragma unroll
-            for (int kx = 0; kx < 3; kx++) {
-                const int ixa = oxa < dout.nx ? src_index(MODE, oxa, kx, din.nx) : -1;
-                const int ixb = oxb < dout.nx ? src_index(MODE, oxb, kx, din.nx) : -1;
-                if (__all_sync(0xffffffffu, ixa < 0 && ixb < 0)) continue;
-                uint32_t a[4];
-                const long long va = (rowbase + ixa) * (C / 2), vb = (rowbase + ixb) * (C / 2);
-                a[0] = ixa >= 0 ? __ldg(inw + va + t) : 0u;
-                a[1] = ixb >= 0 ? __ldg(inw + vb + t) : 0u;
-                a[2] = ixa >= 0 ? __ldg(inw + va + t + 4) : 0u;
-                a[3] = ixb >= 0 ? __ldg(inw + vb + t + 4) : 0u;
-                const int k = (kz * 3 + ky) * 3 + kx;
+        for (int par = 0; par < (MODE == CONVT_S2 ? 2 : 1); par++) {
+            uint32_t v[16];
+            bsk::tmem_ld_32x32b_x16(tmem + ((uint32_t)(32 * warp) << 16) + 16 * par, v);
+            if (!(par ? mine1 : mine0)) continue;
+            float f[C];
 #pragma unroll
-                for (int nb = 0; nb < 2; nb++) {
-                    const uint32_t* wb = sW + (k * C + nb * 8 + g) * (C / 2);
-                    mma_bf16(acc[nb], a, wb[t], wb[t + 4]);
+            for (int c = 0; c < C; c++) f[c] = __uint_as_float(v[c]) + (a.bias ? a.bias[c] : 0.f);
+            if (a.skip) {
+                const uint32_t sv[8] = {sk[2 * par].x, sk[2 * par].y, sk[2 * par].z, sk[2 * par].w,
+                                        sk[2 * par + 1].x, sk[2 * par + 1].y, sk[2 * par + 1].z, sk[2 * par + 1].w};
+#pragma unroll
+                for (int c = 0; c < C / 2; c++) {
+                    const float2 t = __bfloat1622float2(*reinterpret_cast<const __nv_bfloat162*>(&sv[c]));
+                    f[2 * c] += t.x;
+                    f[2 * c + 1] += t.y;
                 }
             }
-        }
-    }
-    // epilogue: rows g and g+8, channels nb*8 + 2t, +1
+            uint32_t w[C / 2];
 #pragma unroll
-    for (int h = 0; h < 2; h++) {
-        const int ox = h ? oxb : oxa;
-        if (ox >= dout.nx) continue;
-        const long long o = ((long long)oz * dout.ny + oy) * dout.nx + ox;
-#pragma unroll
-        for (int nb = 0; nb < 2; nb++) {
-            const int co = nb * 8 + 2 * t;
-            float v0 = acc[nb][2 * h], v1 = acc[nb][2 * h + 1];
-            if (bias) { v0 += bias[co]; v1 += bias[co + 1]; }
-            if (skip) {
-                const __nv_bfloat162 s = reinterpret_cast<const __nv_bfloat162*>(skip + o * C)[co / 2];
-                v0 += __bfloat162float(s.x);
-                v1 += __bfloat162float(s.y);
+            for (int c = 0; c < C / 2; c++) {
+                float x0 = f[2 * c], x1 = f[2 * c + 1];
+                if (a.relu) { x0 = fmaxf(x0, 0.f); x1 = fmaxf(x1, 0.f); }
+                const __nv_bfloat162 hv = __floats2bfloat162_rn(x0, x1);
+                w[c] = *reinterpret_cast<const uint32_t*>(&hv);
             }
-            if (relu) { v0 = fmaxf(v0, 0.f); v1 = fmaxf(v1, 0.f); }
-            reinterpret_cast<__nv_bfloat162*>(out + o * C)[co / 2] = __floats2bfloat162_rn(v0, v1);
+            uint4* d4 = reinterpret_cast<uint4*>(dst) + 2 * par;
+            d4[0] = make_uint4(w[0], w[1], w[2], w[3]);
+            d4[1] = make_uint4(w[4], w[5], w[6], w[7]);
         }
+        bsk::tc_fence_before_sync();
+        __syncthreads();
+    }
+    if (failed) {
+        if (tid == 0) atomicExch(a.err, 1);
+        // let the loads and MMAs in flight finish (bounded) before the CTA's memory goes away
+        bsk::mbar_wait_bounded(full, phase ^ 1u, TC_WAIT_NS);
+        bsk::mbar_wait_bounded(mma_done, phase ^ 1u, TC_WAIT_NS);
+    }
+    bsk::tc_fence_before_sync();
+    __syncthreads();
+    if (warp == 0) {
+        bsk::tc_fence_after_sync();
+        bsk::tmem_dealloc_warp(tmem, TC_COLS);
     }
 }
 
 // ---- 1-channel ends (FP32 pipes) ----------------------------------------------------------
 // out[o][c] = act( sum_k W[k][c] x[2o + k - 1] + bias[c] ), x fine (FP32, 1 channel), out coarse.
-__global__ void k_down1(const float* __restrict__ x, D3 din, __nv_bfloat16* __restrict__ out, D3 dout,
+// One thread per coarse output; the grid is (x blocks, coarse y, coarse z), so no index is
+// decoded by division. Channel pairs accumulate in packed f32x2 FMAs (the same roundings as
+// scalar FMAs, in the same order).
+__global__ void __launch_bounds__(128) k_down1(const float* __restrict__ x, D3 din, __nv_bfloat16* __restrict__ out, D3 dout,
                         const float* __restrict__ W, const float* __restrict__ bias, int relu)
 {
-    __shared__ float sW[KT * C];
-    for (int i = threadIdx.x; i < KT * C; i += blockDim.x) sW[i] = W[i];
+    __shared__ float2 sW[KT * C / 2];
+    for (int i = threadIdx.x; i < KT * C / 2; i += blockDim.x) sW[i] = make_float2(W[2 * i], W[2 * i + 1]);
     __syncthreads();
-    const long long n = (long long)dout.nx * dout.ny * dout.nz;
-    const long long o = blockIdx.x * (long long)blockDim.x + threadIdx.x;
-    if (o >= n) return;
-    const int ox = (int)(o % dout.nx), oy = (int)((o / dout.nx) % dout.ny), oz = (int)(o / ((long long)dout.nx * dout.ny));
-    float acc[C];
+    const int ox = blockIdx.x * blockDim.x + threadIdx.x, oy = blockIdx.y, oz = blockIdx.z;
+    if (ox >= dout.nx) return;
+    float2 acc[C / 2];
 #pragma unroll
-    for (int c = 0; c < C; c++) acc[c] = bias ? bias[c] : 0.f;
+    for (int c = 0; c < C / 2; c++) acc[c] = bias ? make_float2(bias[2 * c], bias[2 * c + 1]) : make_float2(0.f, 0.f);
+    const int ix = 2 * ox;   // <= din.nx - 1: the coarse grid is the fine one halved, rounded up
     for (int kz = 0; kz < 3; kz++) {
-        const int iz = src_index(CONV_S2, oz, kz, din.nz);
-        if (iz < 0) continue;
+        const int iz = 2 * oz + kz - 1;
+        if (iz < 0 || iz >= din.nz) continue;
         for (int ky = 0; ky < 3; ky++) {
-            const int iy = src_index(CONV_S2, oy, ky, din.ny);
-            if (iy < 0) continue;
-            for (int kx = 0; kx < 3; kx++) {
-                const int ix = src_index(CONV_S2, ox, kx, din.nx);
-                if (ix < 0) continue;
-                const float v = x[((long long)iz * din.ny + iy) * din.nx + ix];
-                const float* w = sW + ((kz * 3 + ky) * 3 + kx) * C;
+            const int iy = 2 * oy + ky - 1;
+            if (iy < 0 || iy >= din.ny) continue;
+            const float* row = x + ((long long)iz * din.ny + iy) * din.nx;
+            const float v[3] = {ix >= 1 ? row[ix - 1] : 0.f, row[ix], ix + 1 < din.nx ? row[ix + 1] : 0.f};
 #pragma unroll
-                for (int c = 0; c < C; c++) acc[c] = fmaf(w[c], v, acc[c]);
+            for (int kx = 0; kx < 3; kx++) {
+                const float2 vv = make_float2(v[kx], v[kx]);
+                const float2* w = sW + ((kz * 3 + ky) * 3 + kx) * (C / 2);
+#pragma unroll
+                for (int c = 0; c < C / 2; c++) acc[c] = __ffma2_rn(w[c], vv, acc[c]);
             }
         }
     }
-    __nv_bfloat162* dst = reinterpret_cast<__nv_bfloat162*>(out + o * C);
+    __nv_bfloat162* dst = reinterpret_cast<__nv_bfloat162*>(out + (((long long)oz * dout.ny + oy) * dout.nx + ox) * C);
 #pragma unroll
-    for (int c = 0; c < C; c += 2) {
-        float v0 = acc[c], v1 = acc[c + 1];
+    for (int c = 0; c < C / 2; c++) {
+        float v0 = acc[c].x, v1 = acc[c].y;
         if (relu) { v0 = fmaxf(v0, 0.f); v1 = fmaxf(v1, 0.f); }
-        dst[c / 2] = __floats2bfloat162_rn(v0, v1);
+        dst[c] = __floats2bfloat162_rn(v0, v1);
     }
 }
 
@@ -198,9 +333,11 @@ __global__ void k_down1(const float* __restrict__ x, D3 din, __nv_bfloat16* __re
 //                                 + sum_k Wf[k] r[o + k - 1] ), a coarse (BF16), z and r fine.
 // One thread per 2 x 2 x 2 block of fine voxels (2m .. 2m+1 per axis), which gathers from the
 // 2 x 2 x 2 coarse voxels m .. m+1, so that each coarse voxel is loaded once for the eight
-// outputs it feeds. Along an axis, fine 2m + e
-// takes coarse m + d with tap k = e + 1 - 2d (the transposed stride-2 gather of src_index:
-// (e, d) = (0, 0) -> 1, (1, 0) -> 2, (1, 1) -> 0, (0, 1) none).
+// outputs it feeds. Along an axis, fine 2m + e takes coarse m + d with tap k = e + 1 - 2d (the
+// transposed stride-2 gather of src_index: (e, d) = (0, 0) -> 1, (1, 0) -> 2, (1, 1) -> 0,
+// (0, 1) none). The full-resolution filter of the eight outputs reads the 4 x 4 x 4 patch of r
+// around the block (fine 2m - 1 .. 2m + 2 per axis, zeros outside the grid) once. The grid is
+// (x blocks, coarse y, coarse z), so no index is decoded by division.
 __global__ void __launch_bounds__(128) k_up1b(const __nv_bfloat16* __restrict__ a, D3 din, float* __restrict__ z,
                                               D3 dout, const float* __restrict__ W,
                                               const float* __restrict__ bias, const uint8_t* __restrict__ mask,
@@ -211,10 +348,8 @@ __global__ void __launch_bounds__(128) k_up1b(const __nv_bfloat16* __restrict__ 
     for (int i = threadIdx.x; i < KT * C; i += blockDim.x) sW[i] = W[i];
     for (int i = threadIdx.x; i < KT; i += blockDim.x) sF[i] = Wf[i];
     __syncthreads();
-    const long long nb = (long long)din.nx * din.ny * din.nz;
-    const long long b = blockIdx.x * (long long)blockDim.x + threadIdx.x;
-    if (b >= nb) return;
-    const int mx = (int)(b % din.nx), my = (int)((b / din.nx) % din.ny), mz = (int)(b / ((long long)din.nx * din.ny));
+    const int mx = blockIdx.x * blockDim.x + threadIdx.x, my = blockIdx.y, mz = blockIdx.z;
+    if (mx >= din.nx) return;
     int act = 0;   // bit e: fine output e = (ez, ey, ex) exists and is active
 #pragma unroll
     for (int e = 0; e < 8; e++) {
@@ -260,26 +395,36 @@ __global__ void __launch_bounds__(128) k_up1b(const __nv_bfloat16* __restrict__ 
             acc[e] += s0 + s1;
         }
     }
+    float p[4][4][4];   // r at fine (2mz - 1 + i, 2my - 1 + j, 2mx - 1 + l)
+#pragma unroll
+    for (int i = 0; i < 4; i++) {
+        const int fz = 2 * mz - 1 + i;
+#pragma unroll
+        for (int j = 0; j < 4; j++) {
+            const int fy = 2 * my - 1 + j;
+            const bool rowok = fz >= 0 && fz < dout.nz && fy >= 0 && fy < dout.ny;
+            const float* rr = r + ((long long)(rowok ? fz : 0) * dout.ny + (rowok ? fy : 0)) * dout.nx;
+#pragma unroll
+            for (int l = 0; l < 4; l++) {
+                const int fx = 2 * mx - 1 + l;
+                p[i][j][l] = rowok && fx >= 0 && fx < dout.nx ? rr[fx] : 0.f;
+            }
+        }
+    }
     const float b5 = bias ? bias[0] : 0.f;
 #pragma unroll
     for (int e = 0; e < 8; e++) {
         if (!(act & (1 << e))) continue;
-        const int fz = 2 * mz + (e >> 2), fy = 2 * my + ((e >> 1) & 1), fx = 2 * mx + (e & 1);
-        float fine = 0.f;   // the full-resolution filter of r
-        for (int kz = 0; kz < 3; kz++) {
-            const int iz = fz + kz - 1;
-            if (iz < 0 || iz >= dout.nz) continue;
-            for (int ky = 0; ky < 3; ky++) {
-                const int iy = fy + ky - 1;
-                if (iy < 0 || iy >= dout.ny) continue;
-                const float* rr = r + ((long long)iz * dout.ny + iy) * dout.nx;
+        const int ez = e >> 2, ey = (e >> 1) & 1, ex = e & 1;
+        float fine = 0.f;   // the full-resolution filter of r, taps in (kz, ky, kx) order
 #pragma unroll
-                for (int kx = 0; kx < 3; kx++) {
-                    const int ix = fx + kx - 1;
-                    if (ix >= 0 && ix < dout.nx) fine = fmaf(sF[(kz * 3 + ky) * 3 + kx], rr[ix], fine);
-                }
-            }
-        }
+        for (int kz = 0; kz < 3; kz++)
+#pragma unroll
+            for (int ky = 0; ky < 3; ky++)
+#pragma unroll
+                for (int kx = 0; kx < 3; kx++)
+                    fine = fmaf(sF[(kz * 3 + ky) * 3 + kx], p[ez + kz][ey + ky][ex + kx], fine);
+        const int fz = 2 * mz + ez, fy = 2 * my + ey, fx = 2 * mx + ex;
         z[((long long)fz * dout.ny + fy) * dout.nx + fx] = acc[e] + b5 + fine;
     }
 }
@@ -499,6 +644,9 @@ __global__ void k_round_bf16(const float* __restrict__ src, float* __restrict__ 
 
 int blocks_for(long long n, int threads) { return (int)((n + threads - 1) / threads); }
 
+// Grid of the 1-channel end kernels: 128-thread blocks along x, one per coarse (y, z) row.
+dim3 grid_xyz(D3 d) { return dim3((unsigned)((d.nx + 127) / 128), (unsigned)d.ny, (unsigned)d.nz); }
+
 }  // namespace
 
 // ---- the network object ----------------------------------------------------------------------
@@ -511,6 +659,10 @@ struct bsk_net {
     __nv_bfloat16 *a1, *a2, *a3, *a4;            // activations
     __nv_bfloat16 *g1, *g2, *g3, *g4;            // activation gradients
     float *z, *dz, *loss;                        // output, output gradient, loss accumulator
+    int* tc_err;                                 // set by a convolution whose loads or MMAs timed out
+    void* tc_zero;                               // 64 zero bytes (conv_maps)
+    ConvMaps map_a1, map_a2, map_a3;             // sources of the forward convolutions
+    ConvMaps map_g4, map_g3, map_g2;             // sources of the backward (input-gradient) ones
     int adam_t;
     int linear;                                  // BSK_ACT_LINEAR: identity activations, no biases
 };
@@ -518,6 +670,16 @@ struct bsk_net {
 namespace {
 
 int nfail(int code, const char* msg) { return bsk::set_error(code, msg); }
+
+// After a synchronisation of the network's stream: BSK_ETIMEOUT if a convolution's MMAs did not
+// complete within its bounded wait (its outputs were then set to NaN), else BSK_OK.
+int tc_status(bsk_net* N)
+{
+    int flag = 0;
+    if (cudaMemcpy(&flag, N->tc_err, sizeof(int), cudaMemcpyDeviceToHost) != cudaSuccess)
+        return nfail(BSK_ECUDA, "reading the network's error word failed");
+    return flag ? nfail(BSK_ETIMEOUT, "a network convolution's tensor-core wait timed out") : BSK_OK;
+}
 
 #define NCUDA(call)                                                        \
     do {                                                                   \
@@ -528,15 +690,71 @@ int nfail(int code, const char* msg) { return bsk::set_error(code, msg); }
 D3 halfdims(D3 d) { return D3{(d.nx + 1) / 2, (d.ny + 1) / 2, (d.nz + 1) / 2}; }
 long long vox(D3 d) { return (long long)d.nx * d.ny * d.nz; }
 
+// Persistent launch: as many CTAs as fit on the SMs (shared memory decides: 4 per SM for S1, 2
+// for S2, 7 for the transposed convolution; their TMEM columns, 32 each, always fit in the 512),
+// each looping over tiles. `maps` holds the source activation's tensor maps (see conv_maps).
 template <int MODE>
-cudaError_t conv16(const __nv_bfloat16* in, D3 din, __nv_bfloat16* out, D3 dout, const __nv_bfloat16* W,
-                   const float* bias, const __nv_bfloat16* skip, int relu, cudaStream_t s)
+cudaError_t conv16(const ConvMaps& maps, D3 din, __nv_bfloat16* out, D3 dout, const __nv_bfloat16* W,
+                   const float* bias, const __nv_bfloat16* skip, int relu, int* err, cudaStream_t s)
 {
-    const int xstep = MODE == CONVT_S2 ? 2 : 1;
+    constexpr int smem = TcConv<MODE>::SMEM;
+    int dev = 0, sms = 0, smem_sm = 0, reserved = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&smem_sm, cudaDevAttrMaxSharedMemoryPerMultiprocessor, dev);
+    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&reserved, cudaDevAttrReservedSharedMemoryPerBlock, dev);
+    if (e == cudaSuccess) e = cudaFuncSetAttribute(k_conv16<MODE>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+    if (e == cudaSuccess)
+        e = cudaFuncSetAttribute(k_conv16<MODE>, cudaFuncAttributePreferredSharedMemoryCarveout,
+                                 cudaSharedmemCarveoutMaxShared);
+    if (e != cudaSuccess) return e;
+    // CTAs the SM's shared memory holds (at most 16 of 128 threads; 16 x 32 TMEM columns fit)
+    const int per_sm = std::max(1, std::min(16, smem_sm / (smem + reserved)));
+    ConvArgs a;
+    a.tin = maps.m[0];
+    a.tin_odd = maps.m[1];
+    a.din = din;
+    a.dout = dout;
+    a.out = out;
+    a.W = W;
+    a.bias = bias;
+    a.skip = skip;
+    a.relu = relu;
+    a.err = err;
     const int per_class = MODE == CONVT_S2 ? (dout.nx + 1) / 2 : dout.nx;
-    const long long tiles = (long long)((per_class + 15) / 16) * xstep * dout.ny * dout.nz;
-    k_conv16<MODE><<<(unsigned)((tiles + 3) / 4), 128, 0, s>>>(in, din, out, dout, W, bias, skip, relu);
+    const long long tiles = (long long)((per_class + TC_M - 1) / TC_M) * dout.ny * dout.nz;
+    const long long grid = std::min<long long>(tiles, (long long)sms * per_sm);
+    k_conv16<MODE><<<(unsigned)grid, 128, smem, s>>>(a);
     return cudaGetLastError();
+}
+
+// Tensor maps of a BF16 channels-last activation of grid d, seen as the 4-D array
+// [row = z * ny + y][x][half][8 channels]. A box is one half of 130 consecutive voxels of a row
+// (8 channels x 1 half x 130 x 1 = 2080 bytes), which lands in shared memory as a half-plane.
+// For a stride-2 source (S2) m[0] covers the even voxels and m[1] the odd ones (x-stride 64
+// bytes; the odd map starts at voxel 1); `zero` (64 zero bytes) stands in for the odd voxels of a
+// 1-voxel-wide grid.
+int conv_maps(ConvMaps& cm, const __nv_bfloat16* base, D3 d, bool stride2, const void* zero)
+{
+    auto fn = bsk::tensor_map_encoder();
+    if (!fn) return nfail(BSK_ECUDA, "cuTensorMapEncodeTiled is not available");
+    auto enc = [&](CUtensorMap* m, const void* ptr, long long nx, long long xstride, long long rows,
+                   long long rowstride) -> int {
+        const cuuint64_t dims[4] = {8u, 2u, (cuuint64_t)nx, (cuuint64_t)rows};
+        const cuuint64_t strides[3] = {16u, (cuuint64_t)xstride, (cuuint64_t)rowstride};
+        const cuuint32_t box[4] = {8u, 1u, (cuuint32_t)TC_SLOTS, 1u};
+        const cuuint32_t estr[4] = {1u, 1u, 1u, 1u};
+        CUresult r = fn(m, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 4, const_cast<void*>(ptr), dims, strides, box, estr,
+                        CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                        CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+        return r == CUDA_SUCCESS ? BSK_OK : nfail(BSK_ECUDA, "network tensor map encoding failed");
+    };
+    const long long rows = (long long)d.ny * d.nz, rs = (long long)d.nx * C * 2;
+    memset(&cm, 0, sizeof cm);
+    if (!stride2) return enc(&cm.m[0], base, d.nx, 32, rows, rs);
+    if (int rc = enc(&cm.m[0], base, (d.nx + 1) / 2, 64, rows, rs)) return rc;
+    if (d.nx >= 2) return enc(&cm.m[1], base + C, d.nx / 2, 64, rows, rs);
+    return enc(&cm.m[1], zero, 1, 64, 1, 64);
 }
 
 int prep_weights(bsk_net* N)
@@ -556,13 +774,14 @@ int forward(bsk_net* N, const float* r, const uint8_t* mask, float* z)
     const float* R = N->w_round;
     const int relu = !N->linear;
     auto bias = [&](int off) -> const float* { return N->linear ? nullptr : P + off; };
-    k_down1<<<blocks_for(vox(N->d1), 128), 128, 0, N->stream>>>(r, N->d0, N->a1, N->d1, R + OFF_W1, bias(OFF_B1),
+    k_down1<<<grid_xyz(N->d1), 128, 0, N->stream>>>(r, N->d0, N->a1, N->d1, R + OFF_W1, bias(OFF_B1),
                                                                 relu);
     NCUDA(cudaGetLastError());
-    NCUDA(conv16<CONV_S2>(N->a1, N->d1, N->a2, N->d2, N->w2, bias(OFF_B2), nullptr, relu, N->stream));
-    NCUDA(conv16<CONV_S1>(N->a2, N->d2, N->a3, N->d2, N->w3, bias(OFF_B3), nullptr, relu, N->stream));
-    NCUDA(conv16<CONVT_S2>(N->a3, N->d2, N->a4, N->d1, N->w4, bias(OFF_B4), N->a1, relu, N->stream));
-    k_up1b<<<blocks_for(vox(N->d1), 128), 128, 0, N->stream>>>(N->a4, N->d1, z, N->d0, R + OFF_W5, bias(OFF_B5),
+    NCUDA(conv16<CONV_S2>(N->map_a1, N->d1, N->a2, N->d2, N->w2, bias(OFF_B2), nullptr, relu, N->tc_err, N->stream));
+    NCUDA(conv16<CONV_S1>(N->map_a2, N->d2, N->a3, N->d2, N->w3, bias(OFF_B3), nullptr, relu, N->tc_err, N->stream));
+    NCUDA(conv16<CONVT_S2>(N->map_a3, N->d2, N->a4, N->d1, N->w4, bias(OFF_B4), N->a1, relu, N->tc_err,
+                           N->stream));
+    k_up1b<<<grid_xyz(N->d1), 128, 0, N->stream>>>(N->a4, N->d1, z, N->d0, R + OFF_W5, bias(OFF_B5),
                                                                mask, r, P + OFF_WF);
     NCUDA(cudaGetLastError());
     return BSK_OK;
@@ -584,6 +803,10 @@ extern "C" int bsk_net_create(int nx, int ny, int nz, void* stream, bsk_net** ou
     N->d0 = D3{nx, ny, nz};
     N->d1 = halfdims(N->d0);
     N->d2 = halfdims(N->d1);
+    if (N->d1.ny > 65535 || N->d1.nz > 65535) {   // grid_xyz: one block row per coarse (y, z)
+        delete N;
+        return nfail(BSK_EINVAL, "network grid too large in y or z");
+    }
     N->stream = (cudaStream_t)stream;
     const long long v0 = vox(N->d0), v1 = vox(N->d1), v2 = vox(N->d2);
     cudaError_t e = cudaSuccess;
@@ -606,10 +829,22 @@ extern "C" int bsk_net_create(int nx, int ny, int nz, void* stream, bsk_net** ou
     alloc((void**)&N->z, v0 * sizeof(float));
     alloc((void**)&N->dz, v0 * sizeof(float));
     alloc((void**)&N->loss, sizeof(float));
+    alloc((void**)&N->tc_err, sizeof(int));
+    alloc(&N->tc_zero, 64);
     if (e != cudaSuccess) {
         cudaGetLastError();
         bsk_net_destroy(N);
         return nfail(BSK_ENOMEM, "network allocation failed");
+    }
+    int rc = conv_maps(N->map_a1, N->a1, N->d1, true, N->tc_zero);
+    if (!rc) rc = conv_maps(N->map_a2, N->a2, N->d2, false, N->tc_zero);
+    if (!rc) rc = conv_maps(N->map_a3, N->a3, N->d2, false, N->tc_zero);
+    if (!rc) rc = conv_maps(N->map_g4, N->g4, N->d1, true, N->tc_zero);
+    if (!rc) rc = conv_maps(N->map_g3, N->g3, N->d2, false, N->tc_zero);
+    if (!rc) rc = conv_maps(N->map_g2, N->g2, N->d2, false, N->tc_zero);
+    if (rc) {
+        bsk_net_destroy(N);
+        return rc;
     }
     *out = N;
     return BSK_OK;
@@ -621,7 +856,7 @@ extern "C" void bsk_net_destroy(bsk_net* N)
     cudaStreamSynchronize(N->stream);
     void* ptrs[] = {N->params, N->grad, N->adam_m, N->adam_v, N->w_round, N->w2, N->w3, N->w4, N->w2t,
                     N->w3f, N->w4t, N->a1, N->a2, N->a3, N->a4, N->g1, N->g2, N->g3, N->g4, N->z, N->dz,
-                    N->loss};
+                    N->loss, N->tc_err, N->tc_zero};
     for (void* p : ptrs)
         if (p) cudaFree(p);
     delete N;
@@ -653,7 +888,7 @@ extern "C" int bsk_net_get_params(bsk_net* N, float* params)
     if (!N || !params) return nfail(BSK_EINVAL, "null argument");
     NCUDA(cudaMemcpyAsync(params, N->params, NPARAM * sizeof(float), cudaMemcpyDefault, N->stream));
     NCUDA(cudaStreamSynchronize(N->stream));
-    return BSK_OK;
+    return tc_status(N);
 }
 
 extern "C" int bsk_net_forward(bsk_net* N, const float* r, const uint8_t* mask, float* z)
@@ -694,24 +929,24 @@ int backward_from_dz(bsk_net* N, const float* r)
     // d a4 = down(dz; W5) (the adjoint of the transposed output convolution), then relu mask
     // (none for linear activations);
     // the skip connection passes the same gradient to a1
-    k_down1<<<blocks_for(v1, 128), 128, 0, s>>>(N->dz, N->d0, N->g4, N->d1, R + OFF_W5, nullptr, 0);
+    k_down1<<<grid_xyz(N->d1), 128, 0, s>>>(N->dz, N->d0, N->g4, N->d1, R + OFF_W5, nullptr, 0);
     NCUDA(cudaMemsetAsync(N->g1, 0, v1 * C * 2, s));
     relu_bwd(N->g4, N->a4, v1 * C, N->g1);
     bias_grad(N->g4, v1, OFF_B4);
     k_wgrad16<CONVT_S2><<<blocks_for(v1, 256), 256, 0, s>>>(N->a3, N->d2, N->g4, N->d1, G + OFF_W4, 256);
-    NCUDA(conv16<CONV_S2>(N->g4, N->d1, N->g3, N->d2, N->w4t, nullptr, nullptr, 0, s));
+    NCUDA(conv16<CONV_S2>(N->map_g4, N->d1, N->g3, N->d2, N->w4t, nullptr, nullptr, 0, N->tc_err, s));
     // middle layer
     relu_bwd(N->g3, N->a3, v2 * C, nullptr);
     bias_grad(N->g3, v2, OFF_B3);
     k_wgrad16<CONV_S1><<<blocks_for(v2, 256), 256, 0, s>>>(N->a2, N->d2, N->g3, N->d2, G + OFF_W3, 256);
-    NCUDA(conv16<CONV_S1>(N->g3, N->d2, N->g2, N->d2, N->w3f, nullptr, nullptr, 0, s));
+    NCUDA(conv16<CONV_S1>(N->map_g3, N->d2, N->g2, N->d2, N->w3f, nullptr, nullptr, 0, N->tc_err, s));
     // second layer
     relu_bwd(N->g2, N->a2, v2 * C, nullptr);
     bias_grad(N->g2, v2, OFF_B2);
     k_wgrad16<CONV_S2><<<blocks_for(v2, 256), 256, 0, s>>>(N->a1, N->d1, N->g2, N->d2, G + OFF_W2, 256);
     // first layer: its gradient is the skip gradient plus convT(g2; W2^T), masked by a1 > 0
     // (g4 is free again and serves as the L1-sized buffer)
-    NCUDA(conv16<CONVT_S2>(N->g2, N->d2, N->g4, N->d1, N->w2t, nullptr, N->g1, 0, s));
+    NCUDA(conv16<CONVT_S2>(N->map_g2, N->d2, N->g4, N->d1, N->w2t, nullptr, N->g1, 0, N->tc_err, s));
     relu_bwd(N->g4, N->a1, v1 * C, nullptr);
     bias_grad(N->g4, v1, OFF_B1);
     k_wgrad1<<<blocks_for(v1, 64), 448, 0, s>>>(N->g4, N->d1, r, N->d0, G + OFF_W1, 64);
@@ -764,5 +999,5 @@ extern "C" int bsk_net_read_loss(bsk_net* N, float* loss, float* grad_out)
     if (grad_out)
         NCUDA(cudaMemcpyAsync(grad_out, N->grad, NPARAM * sizeof(float), cudaMemcpyDeviceToHost, N->stream));
     NCUDA(cudaStreamSynchronize(N->stream));
-    return BSK_OK;
+    return tc_status(N);
 }

@@ -14,19 +14,7 @@ namespace bsk {
 
 namespace {
 
-PFN_cuTensorMapEncodeTiled_v12000 batch_encode_fn()
-{
-    static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
-    if (!fn) {
-        void* p = nullptr;
-        cudaDriverEntryPointQueryResult q;
-        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) ==
-                cudaSuccess &&
-            q == cudaDriverEntryPointSuccess)
-            fn = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(p);
-    }
-    return fn;
-}
+PFN_cuTensorMapEncodeTiled_v12000 batch_encode_fn() { return tensor_map_encoder(); }
 
 struct BatchInfo {
     bool ready = false;

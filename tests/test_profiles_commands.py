@@ -39,7 +39,9 @@ def test_profile_commands_are_reproducible():
                     assert opt in options, (os.path.basename(path), opt)
 
 
-SMALL_CASES = {"op384", "cg512", "var240", "robin200"}
+# bench.py --profile-case: each holds at most a few GB on the device (net512: the network at
+# 512^3, about 2.4 GB)
+SMALL_CASES = {"op384", "cg512", "var240", "robin200", "net512"}
 
 
 def _collects_more_than_durations(cmd):
