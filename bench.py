@@ -40,12 +40,12 @@ WORKLOAD = "heat3d_928cube_cubic_f32sweeps_f64refinement"
 # (`--profile-case cg512`) and scaled to the benchmark grid by its unknowns; valid only while the
 # kernels' sources hash to CG_TRAFFIC_SOURCES_SHA256 (None: no capture of the current sources).
 # 512^3 capture (--metrics dram__bytes_read.sum,dram__bytes_write.sum,gpu__time_duration.sum):
-# k_op_tma<float,3,CG> 2.899 + 1.568 GB, k_ws<3,WS_CG> with chunked items 2.191 + 1.559 GB and
-# with whole-column items 2.151 + 1.558 GB per launch.
-CG_TRAFFIC_BYTES_PER_UNKNOWN = {"classic": 33.28, "ws": 27.94, "ws_columns": 27.64}
+# k_op_tma<float,3,CG> 2.915 + 1.569 GB, k_ws<3,WS_CG> with chunked items 2.191 + 1.559 GB and
+# with whole-column items 2.151 + 1.559 GB per launch.
+CG_TRAFFIC_BYTES_PER_UNKNOWN = {"classic": 33.41, "ws": 27.94, "ws_columns": 27.64}
 # Algorithmic bytes per unknown of one single-pass FP32 CG iteration.
 CG_BYTES_PER_UNKNOWN = 28.0
-CG_TRAFFIC_SOURCES_SHA256 = "86b2aa65255e0d924ef4d5ac5092a93cf499721fccbce0be4f2a104108b698cb"
+CG_TRAFFIC_SOURCES_SHA256 = "fbb43515eb447f8e6870b37431ce25ee7b4f83b8ab0fc17502205d2a888f04fb"
 CG_KERNEL_SOURCES = ("op_tma.cuh", "op_ws.cuh", "tma_impl.cuh", "tma_util.cuh", "bsk_device.cuh",
                      "tma_f32.cu", "ws_f32.cu")
 
