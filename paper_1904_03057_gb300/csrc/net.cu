@@ -320,13 +320,17 @@ __global__ void __launch_bounds__(128) k_down1(const float* __restrict__ x, D3 d
             }
         }
     }
-    __nv_bfloat162* dst = reinterpret_cast<__nv_bfloat162*>(out + (((long long)oz * dout.ny + oy) * dout.nx + ox) * C);
+    uint32_t w[C / 2];   // the voxel's 16 channels, stored as two 16-byte vectors
 #pragma unroll
     for (int c = 0; c < C / 2; c++) {
         float v0 = acc[c].x, v1 = acc[c].y;
         if (relu) { v0 = fmaxf(v0, 0.f); v1 = fmaxf(v1, 0.f); }
-        dst[c] = __floats2bfloat162_rn(v0, v1);
+        const __nv_bfloat162 h = __floats2bfloat162_rn(v0, v1);
+        w[c] = *reinterpret_cast<const uint32_t*>(&h);
     }
+    uint4* dst = reinterpret_cast<uint4*>(out + (((long long)oz * dout.ny + oy) * dout.nx + ox) * C);
+    dst[0] = make_uint4(w[0], w[1], w[2], w[3]);
+    dst[1] = make_uint4(w[4], w[5], w[6], w[7]);
 }
 
 // Output layer, z[o] = mask * ( sum_{k valid} sum_c W[k][c] a[srcT(o,k)][c] + b
@@ -336,8 +340,8 @@ __global__ void __launch_bounds__(128) k_down1(const float* __restrict__ x, D3 d
 // outputs it feeds. Along an axis, fine 2m + e takes coarse m + d with tap k = e + 1 - 2d (the
 // transposed stride-2 gather of src_index: (e, d) = (0, 0) -> 1, (1, 0) -> 2, (1, 1) -> 0,
 // (0, 1) none). The full-resolution filter of the eight outputs reads the 4 x 4 x 4 patch of r
-// around the block (fine 2m - 1 .. 2m + 2 per axis, zeros outside the grid) once. The grid is
-// (x blocks, coarse y, coarse z), so no index is decoded by division.
+// around the block (fine 2m - 1 .. 2m + 2 per axis, zeros outside the grid) once, one z-plane at
+// a time. The grid is (x blocks, coarse y, coarse z), so no index is decoded by division.
 __global__ void __launch_bounds__(128) k_up1b(const __nv_bfloat16* __restrict__ a, D3 din, float* __restrict__ z,
                                               D3 dout, const float* __restrict__ W,
                                               const float* __restrict__ bias, const uint8_t* __restrict__ mask,
@@ -395,10 +399,16 @@ __global__ void __launch_bounds__(128) k_up1b(const __nv_bfloat16* __restrict__ 
             acc[e] += s0 + s1;
         }
     }
-    float p[4][4][4];   // r at fine (2mz - 1 + i, 2my - 1 + j, 2mx - 1 + l)
+    // the full-resolution filter of r: the 4 x 4 x 4 patch around the block (fine 2m - 1 .. 2m + 2
+    // per axis, zeros outside the grid), one z-plane of it at a time; plane i feeds the outputs
+    // with ez + kz = i, so each output still adds its taps in (kz, ky, kx) order
+    float fine[8];
+#pragma unroll
+    for (int e = 0; e < 8; e++) fine[e] = 0.f;
 #pragma unroll
     for (int i = 0; i < 4; i++) {
         const int fz = 2 * mz - 1 + i;
+        float p[4][4];   // r at fine (fz, 2my - 1 + j, 2mx - 1 + l)
 #pragma unroll
         for (int j = 0; j < 4; j++) {
             const int fy = 2 * my - 1 + j;
@@ -407,25 +417,27 @@ __global__ void __launch_bounds__(128) k_up1b(const __nv_bfloat16* __restrict__ 
 #pragma unroll
             for (int l = 0; l < 4; l++) {
                 const int fx = 2 * mx - 1 + l;
-                p[i][j][l] = rowok && fx >= 0 && fx < dout.nx ? rr[fx] : 0.f;
+                p[j][l] = rowok && fx >= 0 && fx < dout.nx ? rr[fx] : 0.f;
             }
+        }
+#pragma unroll
+        for (int e = 0; e < 8; e++) {
+            const int ez = e >> 2, ey = (e >> 1) & 1, ex = e & 1;
+            const int kz = i - ez;
+            if (kz < 0 || kz > 2 || !(act & (1 << e))) continue;
+#pragma unroll
+            for (int ky = 0; ky < 3; ky++)
+#pragma unroll
+                for (int kx = 0; kx < 3; kx++)
+                    fine[e] = fmaf(sF[(kz * 3 + ky) * 3 + kx], p[ey + ky][ex + kx], fine[e]);
         }
     }
     const float b5 = bias ? bias[0] : 0.f;
 #pragma unroll
     for (int e = 0; e < 8; e++) {
         if (!(act & (1 << e))) continue;
-        const int ez = e >> 2, ey = (e >> 1) & 1, ex = e & 1;
-        float fine = 0.f;   // the full-resolution filter of r, taps in (kz, ky, kx) order
-#pragma unroll
-        for (int kz = 0; kz < 3; kz++)
-#pragma unroll
-            for (int ky = 0; ky < 3; ky++)
-#pragma unroll
-                for (int kx = 0; kx < 3; kx++)
-                    fine = fmaf(sF[(kz * 3 + ky) * 3 + kx], p[ez + kz][ey + ky][ex + kx], fine);
-        const int fz = 2 * mz + ez, fy = 2 * my + ey, fx = 2 * mx + ex;
-        z[((long long)fz * dout.ny + fy) * dout.nx + fx] = acc[e] + b5 + fine;
+        const int fz = 2 * mz + (e >> 2), fy = 2 * my + ((e >> 1) & 1), fx = 2 * mx + (e & 1);
+        z[((long long)fz * dout.ny + fy) * dout.nx + fx] = acc[e] + b5 + fine[e];
     }
 }
 
